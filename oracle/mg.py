@@ -1,0 +1,126 @@
+"""Multigrid cycle and setup (oracle; test infrastructure).
+
+Sec. 2.1 describes the pieces but not the algorithmic parameters:
+  * the solver class calls itself recursively over the levels;
+  * the initial setup (from HDCR) iterates a smoother on random vectors to get
+    near-null vectors, then builds the intergrid and coarse operators;
+  * the iterative-refinement setup (from DDalphaAMG) then applies the whole MG
+    preconditioner to the near-null vectors and rebuilds the operators;
+  * MR is the smoother, GMRES the coarsest solver, FGMRES the outer solver.
+
+Readings used here (each listed with the other readings of the paper):
+  cycle  M_l(r):  e = P_l CoarseSolve_{l+1}(P_l^dag r);  e += MR_k(D_l; r - D_l e);
+         no pre-smoothing.  CoarseSolve is GMRES(m) with a relative tolerance at the
+         coarsest level and one application of M_{l+1} (V-cycle) in between.
+  initial setup on level l: for each sweep, for each i:
+         v_i <- MR_k(D_l; v_i) (zero initial guess), v_i <- v_i / ||v_i||;
+         then P_l (block orthonormalisation) and D_{l+1} = P_l^dag D_l P_l; recurse
+         with the level-(l+1) random vectors.
+  iterative refinement: for each sweep: v_i <- M_0(v_i), v_i <- v_i/||v_i|| for all i
+         (all using the current hierarchy), then rebuild P_0 and D_1; every coarser
+         non-coarsest level then runs one warm-started initial sweep on its current
+         vectors with its new operator and rebuilds its own P and D.
+The outcome of the setup depends on every step, so it has no closed form: the
+setup is "parity unpinned" beyond its per-operator pins.
+"""
+from dataclasses import dataclass, field
+from typing import List, Sequence
+
+from .aggregation import Aggregation
+from .coarse import coarsen
+from .solvers import fgmres, gmres, mr, norm
+
+
+@dataclass
+class MGParams:
+    blocks: Sequence[Sequence[int]]          # one block per coarsening, (bx, by, bz, bt)
+    nvecs: Sequence[int]                     # Nvec per coarsening
+    smoother_steps: int = 4
+    init_sweeps: int = 3
+    refine_sweeps: int = 0
+    coarse_restart: int = 20
+    coarse_tol: float = 0.05
+    coarse_maxiter: int = 100
+    outer_restart: int = 20
+    outer_tol: float = 1e-10
+    outer_maxiter: int = 1000
+
+
+@dataclass
+class Level:
+    op: object
+    dims: tuple
+    vecs: list = field(default_factory=list)   # raw (normalised) near-null vectors
+    agg: object = None
+
+
+class Multigrid:
+    def __init__(self, fine_op, params: MGParams, init_vecs: List[list], build=True):
+        """init_vecs[l] is the list of Nvec random fields of level l (generator data)."""
+        self.p = params
+        self.levels: List[Level] = [Level(fine_op, tuple(fine_op.dims))]
+        self.init_vecs = init_vecs
+        if build:
+            self.setup()
+
+    @property
+    def nlevels(self):
+        return len(self.p.blocks) + 1
+
+    # ---------------- setup ----------------
+    def _smooth_sweep(self, l):
+        lev = self.levels[l]
+        out = []
+        for v in lev.vecs:
+            x = mr(lev.op, v, self.p.smoother_steps)
+            out.append(x / norm(x))
+        lev.vecs = out
+
+    def _build(self, l):
+        lev = self.levels[l]
+        lev.agg = Aggregation(lev.dims, self.p.blocks[l], lev.vecs)
+        Dc = coarsen(lev.op, lev.agg)
+        if len(self.levels) > l + 1:
+            self.levels[l + 1].op = Dc
+        else:
+            self.levels.append(Level(Dc, tuple(lev.agg.cdims)))
+
+    def setup(self):
+        for l in range(self.nlevels - 1):
+            self.levels[l].vecs = [v.copy() for v in self.init_vecs[l]]
+            for _ in range(self.p.init_sweeps):
+                self._smooth_sweep(l)
+            self._build(l)
+        for _ in range(self.p.refine_sweeps):
+            self.refine_sweep()
+
+    def refine_sweep(self):
+        lev = self.levels[0]
+        new = []
+        for v in lev.vecs:
+            x = self.cycle(0, v)
+            new.append(x / norm(x))
+        lev.vecs = new
+        self._build(0)
+        for l in range(1, self.nlevels - 1):
+            self._smooth_sweep(l)
+            self._build(l)
+
+    # ---------------- solve ----------------
+    def coarse_solve(self, l, r):
+        """Solve on level l (l >= 1): GMRES at the coarsest level, else one cycle."""
+        if l == self.nlevels - 1:
+            x, _ = gmres(self.levels[l].op, r, restart=self.p.coarse_restart,
+                         tol=self.p.coarse_tol, maxiter=self.p.coarse_maxiter)
+            return x
+        return self.cycle(l, r)
+
+    def cycle(self, l, r):
+        lev = self.levels[l]
+        e = lev.agg.prolong(self.coarse_solve(l + 1, lev.agg.restrict(r)))
+        return e + mr(lev.op, r - lev.op(e), self.p.smoother_steps)
+
+    def solve(self, b, x0=None):
+        return fgmres(self.levels[0].op, b, lambda v: self.cycle(0, v),
+                      restart=self.p.outer_restart, tol=self.p.outer_tol,
+                      maxiter=self.p.outer_maxiter, x0=x0, verify=True)

@@ -1,0 +1,76 @@
+"""Pins of the multigrid cycle and solve (Sec. 2.1 recursive solver class,
+FGMRES outer solver right-preconditioned by the MG cycle)."""
+import numpy as np
+import pytest
+
+from oracle.lattice import to_grid
+from oracle.mg import MGParams, Multigrid
+from oracle.solvers import gmres
+from oracle.wilson import WilsonClover
+from paper_1904_08678_gb300 import inputs
+from tests.helpers import rel
+
+
+def config1(eps=0.3, m0=-0.1):
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, eps, 1001)
+    D = WilsonClover(U, dims, m0, 1.0)
+    V = int(np.prod(dims))
+    b = to_grid(inputs.source(dims, 0)[0].reshape(V, 12), dims)
+    return dims, D, b
+
+
+def test_block_1_nvec_6_is_exact_preconditioner():
+    """Block 1^4 with Nvec = 6: P is unitary per site, D_c is unitarily similar to D,
+    and with an exact coarse solve the cycle is D^-1: FGMRES needs one iteration."""
+    dims, D, b = config1()
+    V = int(np.prod(dims))
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 6, 0, 1001)]]
+    p = MGParams(blocks=[(1, 1, 1, 1)], nvecs=[6], init_sweeps=1, coarse_restart=400,
+                 coarse_tol=1e-13, coarse_maxiter=4000, outer_tol=1e-10)
+    mg = Multigrid(D, p, iv)
+    x, info = mg.solve(b)
+    assert info.converged and info.iterations == 1
+
+
+def test_config1_solve_matches_dense_solution():
+    dims, D, b = config1()
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 8, 0, 1001)]]
+    mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[8]), iv)
+    x, info = mg.solve(b)
+    assert info.converged and info.true_residual <= 1e-10
+    x_ref, ir = gmres(D, b, restart=60, tol=1e-13, maxiter=5000, verify=True)
+    assert ir.converged
+    assert rel(x, x_ref) < 1e-8
+    # the preconditioner helps: far fewer outer iterations than unpreconditioned GMRES(20)
+    _, plain = gmres(D, b, restart=20, tol=1e-10, maxiter=5000, verify=True)
+    assert info.iterations * 3 < plain.iterations
+
+
+@pytest.mark.slow
+def test_three_level_solve_converges():
+    dims = (8, 8, 8, 8)
+    U = inputs.random_gauge(dims, 0.3, 1003)
+    D = WilsonClover(U, dims, -0.1, 1.0)
+    V = int(np.prod(dims))
+    b = to_grid(inputs.source(dims, 0)[0].reshape(V, 12), dims)
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 6, 0, 1003)],
+          [to_grid(v, (4, 4, 4, 4)) for v in inputs.setup_vectors((4, 4, 4, 4), 12, 4, 1, 1003)]]
+    p = MGParams(blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvecs=[6, 4], refine_sweeps=1)
+    mg = Multigrid(D, p, iv)
+    x, info = mg.solve(b)
+    assert info.converged and info.true_residual <= 1e-10
+    assert rel(D(x), b) <= 1e-10
+
+
+def test_refinement_reduces_iterations():
+    """Sec. 2.1 / Table 2 trend: iterative-refinement sweeps improve the near-null space."""
+    dims, D, b = config1(eps=0.45, m0=-0.3)
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 4, 0, 1001)]]
+    its = []
+    for nref in (0, 2):
+        mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[4], init_sweeps=1, refine_sweeps=nref), iv)
+        x, info = mg.solve(b)
+        assert info.converged
+        its.append(info.iterations)
+    assert its[1] < its[0]
