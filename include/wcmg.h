@@ -1,0 +1,185 @@
+/*
+ * wcmg.h -- C-ABI of the GB300 Wilson-clover multigrid library (libwcmg.so).
+ *
+ * Method: Richtmann, Boyle, Wettig, "Multigrid for Wilson Clover Fermions in
+ * Grid" (LATTICE2018, arXiv:1904.08678).  The calls follow the paper's statement
+ * of the problem: set the gauge field and clover term (Sec. 1, Sec. 2.1); build
+ * near-null vectors by the initial and the iterative-refinement setup (Sec. 2.1);
+ * apply D, restrict, prolong and the coarse D (Sec. 2.1 Aggregation /
+ * CoarsenedMatrix Mdiag + Mdir); solve D x = b with FGMRES preconditioned by the
+ * multigrid cycle (Sec. 2.1).  Everything runs on one CUDA device.
+ *
+ * Conventions
+ *  - Every call returns WCMG_OK (0) or a negative wcmg_status.  No exception
+ *    crosses the ABI.  wcmg_last_error() gives a message for the last failure.
+ *  - External buffers are complex128 (interleaved re, im doubles) in these
+ *    layouts, site index s = x + Lx*(y + Ly*(z + Lz*t)) on the level's lattice:
+ *      gauge        [4][V][3][3]           U_mu(x), link x -> x + mu, mu = x,y,z,t
+ *      fine field   [nrhs][V][4][3]        spin-major, colour-minor, chiral gamma basis
+ *      coarse field [nrhs][Vc][nbasis]     first Nvec components chirality +, then -
+ *      coarse links [9][Vc][nbasis][nbasis] block d = 0 self, 1+2mu reads
+ *                                           phi(x+mu), 2+2mu reads phi(x-mu)
+ *      clover       [V][12][12]            C(x) including (4 + m0)
+ *  - `where` says whether a buffer pointer is host (WCMG_HOST) or device
+ *    (WCMG_DEVICE) memory.  Host buffers are copied through library-owned device
+ *    staging; device buffers are read/written in place.  The caller keeps
+ *    ownership of its buffers; they must stay valid until the call returns
+ *    (host) or until `stream` has completed the call's work (device).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are stream
+ *    ordered; a call that needs a host decision (a solver's stopping test)
+ *    synchronises `stream` itself.
+ *  - `prec` selects the arithmetic of a single operator application:
+ *    WCMG_F64 or WCMG_F32 (external data stays complex128).
+ *  - A context is not thread safe: use one per host thread.  The library owns
+ *    all internal buffers, allocated on the device current at wcmg_create.
+ */
+#ifndef WCMG_H
+#define WCMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WCMG_MAX_LEVELS 4
+
+typedef enum {
+  WCMG_OK = 0,
+  WCMG_ERR_ARG = -1,            /* invalid argument or size */
+  WCMG_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  WCMG_ERR_STATE = -3,          /* call out of order (e.g. solve before setup) */
+  WCMG_ERR_NOT_CONVERGED = -4,  /* iteration limit hit; outputs and stats are valid */
+  WCMG_ERR_NAN = -5,            /* non-finite norm or rank-deficient aggregate */
+  WCMG_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+  WCMG_ERR_OOM = -7             /* device allocation failed */
+} wcmg_status;
+
+typedef enum { WCMG_F64 = 0, WCMG_F32 = 1, WCMG_BF16 = 2, WCMG_F16 = 3 } wcmg_prec;
+typedef enum { WCMG_HOST = 0, WCMG_DEVICE = 1 } wcmg_where;
+
+typedef struct wcmg_params {
+  int dims[4];                          /* fine Lx, Ly, Lz, Lt (periodic) */
+  int n_levels;                         /* 2 .. WCMG_MAX_LEVELS */
+  int block[WCMG_MAX_LEVELS - 1][4];    /* aggregate extents per coarsening */
+  int nvec[WCMG_MAX_LEVELS - 1];        /* near-null vectors per coarsening (nbasis = 2 nvec) */
+  double m0;                            /* bare mass: D has (4 + m0) on the diagonal */
+  double csw;                           /* clover coefficient */
+  int smoother_steps;                   /* MR steps of the post-smoother and setup smoother */
+  int setup_init_sweeps;                /* initial-setup sweeps per level */
+  int setup_refine_sweeps;              /* iterative-refinement sweeps */
+  int coarse_restart;                   /* GMRES(m) on the coarsest level */
+  int coarse_maxiter;
+  double coarse_tol;                    /* relative residual of the coarsest solve */
+  int outer_restart;                    /* FGMRES(m) outer solver */
+  int outer_maxiter;                    /* total outer iterations */
+  double outer_tol;                     /* true relative residual ||b - D x|| / ||b|| */
+  int inner_prec;                       /* WCMG_F64: all FP64; WCMG_F32: preconditioner,
+                                           setup and coarse operators FP32 with FP64
+                                           outer residual / orthonormalisation / Hessenberg */
+  int coarse_link_prec;                 /* storage of coarse links when inner_prec = F32:
+                                           WCMG_F32, WCMG_BF16 or WCMG_F16 (FP32 accumulate) */
+  int max_rhs;                          /* largest nrhs of any call */
+  int profile;                          /* nonzero: time every kernel launch with CUDA events */
+} wcmg_params;
+
+/* Per-kernel-class counters, filled when params.profile != 0. */
+#define WCMG_NKCLASS 12
+typedef struct wcmg_kstat {
+  long long launches;
+  double ms;                            /* summed CUDA-event time of the launches */
+  double bytes;                         /* algorithmic bytes moved (per the kernel's model) */
+  double flops;                         /* algorithmic flops */
+} wcmg_kstat;
+
+typedef struct wcmg_stats {
+  int outer_iterations;                 /* FGMRES iterations summed over restarts (max over rhs) */
+  int restarts;
+  int converged;                        /* 1 if every rhs met outer_tol */
+  double true_residual;                 /* max over rhs of ||b - D x|| / ||b|| (FP64) */
+  long long coarse_iterations;          /* coarsest-level GMRES iterations, summed */
+  double ms_setup_init;                 /* wall time of the phases (host clock around synced work) */
+  double ms_setup_refine;
+  double ms_solve;
+  wcmg_kstat k[WCMG_NKCLASS];           /* index: wcmg_kclass */
+} wcmg_stats;
+
+typedef enum {
+  WCMG_K_DSLASH = 0, WCMG_K_COARSE = 1, WCMG_K_RESTRICT = 2, WCMG_K_PROLONG = 3,
+  WCMG_K_BLAS = 4, WCMG_K_ORTHO = 5, WCMG_K_COARSEN = 6, WCMG_K_CLOVER = 7,
+  WCMG_K_PACK = 8, WCMG_K_KRYLOV = 9, WCMG_K_DSLASH64 = 10, WCMG_K_OTHER = 11
+} wcmg_kclass;
+
+typedef struct wcmg_ctx wcmg_ctx;
+
+/* Fill *p with the defaults of the 4^4 two-level case (blocks 2^4, Nvec 8, MR(4),
+ * 3 initial sweeps, GMRES(20) to 0.05 / 100 its, FGMRES(20) to 1e-10, FP64). */
+int wcmg_default_params(wcmg_params* p);
+
+/* Validate *p (every extent divisible by its block, nvec <= 32, nbasis even) and
+ * allocate the context on the current device.  ERR_ARG, ERR_OOM, ERR_CUDA. */
+int wcmg_create(const wcmg_params* p, wcmg_ctx** out);
+void wcmg_destroy(wcmg_ctx* ctx);
+const char* wcmg_last_error(const wcmg_ctx* ctx);
+
+/* Sec. 2.1 (fine operator D): set U_mu(x).  Builds the FP64 and FP32 internal
+ * copies and the clover term C(x) of Sec. 1 "clover" (Sheikholeslami-Wohlert,
+ * four-leaf field strength) with params.m0 / params.csw. */
+int wcmg_set_gauge(wcmg_ctx* ctx, const void* U, int where, void* stream);
+
+/* Read back C(x) (FP64), external clover layout. */
+int wcmg_get_clover(wcmg_ctx* ctx, void* C, int where, void* stream);
+
+/* out = D in on the fine lattice (Sec. 2.1: MG runs on D itself), nrhs fields. */
+int wcmg_apply_D(wcmg_ctx* ctx, const void* in, void* out, int nrhs, int prec, int where, void* stream);
+
+/* Sec. 2.1 / 2.2: give the Nvec raw near-null vectors of level `level`
+ * ([nvec][V_level][ncomp] complex128); they are block-orthonormalised per
+ * aggregate and chirality (FP64) to form P_level.  Does not coarsen. */
+int wcmg_set_nullvecs(wcmg_ctx* ctx, int level, const void* vecs, int where, void* stream);
+/* The block-orthonormalised vectors of P_level, same layout. */
+int wcmg_get_nullvecs(wcmg_ctx* ctx, int level, void* vecs, int where, void* stream);
+
+/* Sec. 2.1 CoarsenOperator: D_{level+1} = P_level^dag D_level P_level as the
+ * nine-block stencil (Sec. 4: 9 stencil points).  Needs P_level and D_level. */
+int wcmg_coarsen(wcmg_ctx* ctx, int level, void* stream);
+int wcmg_get_coarse_links(wcmg_ctx* ctx, int level, void* A, int where, void* stream);
+int wcmg_set_coarse_links(wcmg_ctx* ctx, int level, const void* A, int where, void* stream);
+
+/* Sec. 3 blockProject: coarse = P_level^dag fine (level -> level+1). */
+int wcmg_restrict(wcmg_ctx* ctx, int level, const void* fine, void* coarse, int nrhs, int prec, int where, void* stream);
+/* fine = P_level coarse (level+1 -> level). */
+int wcmg_prolong(wcmg_ctx* ctx, int level, const void* coarse, void* fine, int nrhs, int prec, int where, void* stream);
+/* Sec. 2.1 Mdiag + 8 x Mdir: out = D_level in, level >= 1. */
+int wcmg_apply_coarse(wcmg_ctx* ctx, int level, const void* in, void* out, int nrhs, int prec, int where, void* stream);
+
+/* Sec. 2.1 setup: initial setup on every level from the given random vectors
+ * (init_vecs[l] = [nvec_l][V_l][ncomp_l] complex128, concatenated over
+ * l = 0 .. n_levels-2), then params.setup_refine_sweeps iterative-refinement
+ * sweeps.  Fills every P_l and D_{l+1}. */
+int wcmg_setup(wcmg_ctx* ctx, const void* init_vecs, int where, void* stream, wcmg_stats* st);
+
+/* One application of the multigrid preconditioner M_0 to nrhs fine fields. */
+int wcmg_mg_cycle(wcmg_ctx* ctx, const void* r, void* e, int nrhs, int where, void* stream);
+
+/* Krylov solve of D_level x = b at the inner precision: kind 0 = MR(steps,
+ * zero guess), kind 1 = GMRES(restart) to tol (relative to ||b||) / maxiter.
+ * iters_out (nullable) receives the iterations of the slowest rhs. */
+int wcmg_krylov(wcmg_ctx* ctx, int level, int kind, const void* b, void* x, int nrhs,
+                int steps_or_restart, double tol, int maxiter, int where, void* stream, int* iters_out);
+
+/* Sec. 2.1 outer solver: FGMRES(outer_restart) right-preconditioned by M_0 on D,
+ * from a zero initial guess, until ||b - D x|| / ||b|| <= outer_tol (FP64 true
+ * residual) for every rhs.  With inner_prec = F32 each restart cycle runs in FP32
+ * and the FP64 residual is recomputed at every restart (defect correction).
+ * Returns ERR_NOT_CONVERGED (x and *st valid) at outer_maxiter. */
+int wcmg_solve(wcmg_ctx* ctx, const void* b, void* x, int nrhs, int where, void* stream, wcmg_stats* st);
+
+/* Checkpoint of the setup (near-null vectors and coarse links of every level). */
+int wcmg_save_setup(wcmg_ctx* ctx, const char* path);
+int wcmg_load_setup(wcmg_ctx* ctx, const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WCMG_H */

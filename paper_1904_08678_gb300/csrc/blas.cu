@@ -1,0 +1,362 @@
+// BLAS-1 kernels and the device-side Arnoldi/Givens bookkeeping of the Krylov
+// solvers (Sec. 2.1: MR, GMRES, FGMRES).  Fields are batches [nrhs][n] of
+// complex numbers; every per-rhs scalar stays in device memory so the solver
+// loops issue no host round trip except their stopping tests.
+// Reductions are two-stage with fixed block counts and fixed summation trees:
+// results are bitwise reproducible run to run.
+#include "kernels.h"
+
+namespace wcmg {
+
+constexpr int RED_T = 256;
+static inline int red_blocks(long long n) {
+  long long b = (n + 8 * RED_T - 1) / (8 * RED_T);
+  return (int)(b < 1 ? 1 : (b > 608 ? 608 : b));
+}
+
+template <typename A, typename B>
+__global__ void k_convert(cplx<B>* __restrict__ out, const cplx<A>* __restrict__ in, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = from_c64<B>(to_c64(in[i]));
+}
+template <typename A, typename B>
+void launch_convert(cplx<B>* out, const cplx<A>* in, long long n, cudaStream_t st) {
+  k_convert<A, B><<<nblk(n, 256), 256, 0, st>>>(out, in, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---- dot / norm ----
+template <typename R>
+__global__ void __launch_bounds__(RED_T) k_dot_partial(double2* __restrict__ partial, const cplx<R>* __restrict__ a,
+                                                       const cplx<R>* __restrict__ b, long long n) {
+  __shared__ double2 scratch[RED_T / 32];
+  __shared__ double2 red[1];
+  const int r = blockIdx.y;
+  a += (long long)r * n;
+  b += (long long)r * n;
+  cplx<R> acc = czero<R>();
+  for (long long i = blockIdx.x * (long long)RED_T + threadIdx.x; i < n; i += (long long)gridDim.x * RED_T)
+    cjmac(acc, a[i], b[i]);
+  double2 v = to_c64(acc);
+  block_sum_many<double2>(&v, 1, scratch, red);
+  if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = red[0];
+}
+template <typename R>
+__global__ void __launch_bounds__(RED_T) k_norm_partial(double* __restrict__ partial, const cplx<R>* __restrict__ a,
+                                                        long long n) {
+  __shared__ double scratch[RED_T / 32];
+  __shared__ double red[1];
+  const int r = blockIdx.y;
+  a += (long long)r * n;
+  R acc = 0;
+  for (long long i = blockIdx.x * (long long)RED_T + threadIdx.x; i < n; i += (long long)gridDim.x * RED_T)
+    acc += cnorm2(a[i]);
+  double v = acc;
+  block_sum_many<double>(&v, 1, scratch, red);
+  if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = red[0];
+}
+// out[r * ldo + i] = sum_{b < count} partial[r * pr + i * pi + b]  (grid: r = x, i = y)
+template <typename T>
+__global__ void __launch_bounds__(RED_T) k_final(T* __restrict__ out, const T* __restrict__ partial, int count,
+                                                 long long pr, long long pi, int ldo) {
+  __shared__ T scratch[RED_T / 32];
+  __shared__ T red[1];
+  const int r = blockIdx.x, i = blockIdx.y;
+  const T* p = partial + r * pr + i * pi;
+  T acc;
+  memset(&acc, 0, sizeof(T));
+  for (int b = threadIdx.x; b < count; b += RED_T) acc += p[b];
+  block_sum_many<T>(&acc, 1, scratch, red);
+  if (threadIdx.x == 0) out[(long long)r * ldo + i] = red[0];
+}
+
+template <typename R>
+void launch_dot(double2* out, const cplx<R>* a, const cplx<R>* b, long long n, int nrhs, double2* partial,
+                cudaStream_t st) {
+  const int nb = red_blocks(n);
+  k_dot_partial<R><<<dim3(nb, nrhs), RED_T, 0, st>>>(partial, a, b, n);
+  k_final<double2><<<dim3(nrhs, 1), RED_T, 0, st>>>(out, partial, nb, nb, 0, 1);
+  WCMG_LAUNCH_CHECK();
+}
+template <typename R>
+void launch_norm2(double* out, const cplx<R>* a, long long n, int nrhs, double* partial, cudaStream_t st) {
+  const int nb = red_blocks(n);
+  k_norm_partial<R><<<dim3(nb, nrhs), RED_T, 0, st>>>(partial, a, n);
+  k_final<double><<<dim3(nrhs, 1), RED_T, 0, st>>>(out, partial, nb, nb, 0, 1);
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---- multi-dot against a Krylov basis (chunks of 8 basis vectors) ----
+constexpr int MD_K = 8;
+template <typename R>
+__global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict__ partial,
+                                                            const cplx<R>* __restrict__ basis, long long bstride,
+                                                            int k, const cplx<R>* __restrict__ w, long long n,
+                                                            int kpad) {
+  __shared__ double2 scratch[(RED_T / 32) * MD_K];
+  __shared__ double2 red[MD_K];
+  const int r = blockIdx.y, i0 = blockIdx.z * MD_K;
+  const long long off = (long long)r * n;
+  cplx<R> acc[MD_K];
+#pragma unroll
+  for (int q = 0; q < MD_K; ++q) acc[q] = czero<R>();
+  for (long long e = blockIdx.x * (long long)RED_T + threadIdx.x; e < n; e += (long long)gridDim.x * RED_T) {
+    const cplx<R> x = w[off + e];
+#pragma unroll
+    for (int q = 0; q < MD_K; ++q)
+      if (i0 + q < k) cjmac(acc[q], basis[(i0 + q) * bstride + off + e], x);
+  }
+  double2 v[MD_K];
+#pragma unroll
+  for (int q = 0; q < MD_K; ++q) v[q] = to_c64(acc[q]);
+  block_sum_many<double2>(v, MD_K, scratch, red);
+  if (threadIdx.x < MD_K && i0 + threadIdx.x < k)
+    partial[((long long)r * kpad + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x];
+}
+template <typename R>
+void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int k, int ldo, const cplx<R>* w,
+                     long long n, int nrhs, double2* partial, cudaStream_t st) {
+  const int nb = red_blocks(n);
+  const int nchunk = (k + MD_K - 1) / MD_K, kpad = nchunk * MD_K;
+  k_multidot_partial<R><<<dim3(nb, nrhs, nchunk), RED_T, 0, st>>>(partial, basis, bstride, k, w, n, kpad);
+  k_final<double2><<<dim3(nrhs, k), RED_T, 0, st>>>(out, partial, nb, (long long)kpad * nb, nb, ldo);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_multiaxpy(cplx<R>* __restrict__ w, const cplx<R>* __restrict__ basis, long long bstride, int k,
+                           const double2* __restrict__ coef, int ldc, R sign, long long n) {
+  const int r = blockIdx.y;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const long long off = (long long)r * n + e;
+  cplx<R> acc = w[off];
+  for (int i = 0; i < k; ++i) {
+    const double2 c = coef[(long long)r * ldc + i];
+    cmac(acc, cmk(R(sign * c.x), R(sign * c.y)), basis[i * bstride + off]);
+  }
+  w[off] = acc;
+}
+template <typename R>
+void launch_multiaxpy(cplx<R>* w, const cplx<R>* basis, long long bstride, int k, const double2* coef, int ldc,
+                      double sign, long long n, int nrhs, cudaStream_t st) {
+  if (k <= 0) return;
+  k_multiaxpy<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(w, basis, bstride, k, coef, ldc, (R)sign, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_axpby(cplx<R>* __restrict__ y, R a, const cplx<R>* __restrict__ x, R b, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+template <typename R>
+void launch_axpby(cplx<R>* y, double a, const cplx<R>* x, double b, long long n, int nrhs, cudaStream_t st) {
+  const long long N = n * nrhs;
+  k_axpby<R><<<nblk(N, 256), 256, 0, st>>>(y, (R)a, x, (R)b, N);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_scale_dev(cplx<R>* __restrict__ y, const cplx<R>* __restrict__ x, const double* __restrict__ s,
+                            int inv_sqrt, long long n) {
+  const int r = blockIdx.y;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double f = s[r];
+  if (inv_sqrt) f = f > 0.0 ? 1.0 / sqrt(f) : 0.0;
+  y[(long long)r * n + e] = (R)f * x[(long long)r * n + e];
+}
+template <typename R>
+void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqrt, long long n, int nrhs,
+                      cudaStream_t st) {
+  k_scale_dev<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(y, x, s, inv_sqrt, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_mr_update(cplx<R>* __restrict__ x, cplx<R>* __restrict__ r, const cplx<R>* __restrict__ p,
+                            const double2* __restrict__ pr, const double* __restrict__ pp, long long n) {
+  const int q = blockIdx.y;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double d = pp[q];
+  const double2 al = d != 0.0 ? make_double2(pr[q].x / d, pr[q].y / d) : make_double2(0, 0);
+  const cplx<R> a = cmk((R)al.x, (R)al.y);
+  const long long o = (long long)q * n + e;
+  const cplx<R> rv = r[o];
+  cmac(x[o], a, rv);
+  r[o] = rv - cmul(a, p[o]);
+}
+template <typename R>
+void launch_mr_update(cplx<R>* x, cplx<R>* r, const cplx<R>* p, const double2* pr, const double* pp, long long n,
+                      int nrhs, cudaStream_t st) {
+  k_mr_update<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(x, r, p, pr, pp, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_mask_rhs(cplx<R>* __restrict__ x, const int* __restrict__ mask, long long n) {
+  const int r = blockIdx.y;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < n && mask[r]) x[(long long)r * n + e] = czero<R>();
+}
+template <typename R>
+void launch_mask_rhs(cplx<R>* x, const int* mask, long long n, int nrhs, cudaStream_t st) {
+  k_mask_rhs<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(x, mask, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_fill_zero(cplx<R>* x, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = czero<R>();
+}
+template <typename R>
+void launch_fill_zero(cplx<R>* x, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_fill_zero<R><<<nblk(n, 256), 256, 0, st>>>(x, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---- (F)GMRES bookkeeping (K8), one thread per rhs, FP64 ----
+// Complex Givens rotation G = [[c, s], [-conj(s), c]], c real, with
+// G [a, b]^T = [rho, 0]^T.
+__device__ void givens(double2 a, double2 b, double& c, double2& s, double2& rho) {
+  const double aa = sqrt(cnorm2(a));
+  if (aa == 0.0) { c = 0.0; s = make_double2(1, 0); rho = b; return; }
+  const double r = sqrt(cnorm2(a) + cnorm2(b));
+  const double2 ph = make_double2(a.x / aa, a.y / aa);
+  c = aa / r;
+  s = (1.0 / r) * cmul(ph, conjg(b));
+  rho = r * ph;
+}
+
+__global__ void k_gmres_start(GmresState S, const double* __restrict__ nrm2, double tol, int nrhs,
+                              double* __restrict__ inv_beta) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const double beta = sqrt(nrm2[r]);
+  const int m = S.m;
+  for (int i = 0; i <= m; ++i) S.g[(long long)r * (m + 1) + i] = make_double2(0, 0);
+  S.g[(long long)r * (m + 1)] = make_double2(beta, 0);
+  S.resid[r] = beta;
+  S.jdone[r] = 0;
+  const bool go = !S.done[r] && beta > tol * S.bnorm[r] && beta > 0.0;
+  S.active[r] = go ? 1 : 0;
+  inv_beta[r] = go ? 1.0 / beta : 0.0;
+}
+
+__global__ void k_gmres_step(GmresState S, int j, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                             const double* __restrict__ hnorm2, double tol, int final_done, int nrhs,
+                             double* __restrict__ inv_h) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int m = S.m;
+  if (!S.active[r]) { inv_h[r] = 0.0; return; }
+  double2* H = S.H + (long long)r * (m + 1) * m;
+  double* cs = S.cs + (long long)r * m;
+  double2* sn = S.sn + (long long)r * m;
+  double2* g = S.g + (long long)r * (m + 1);
+  for (int i = 0; i <= j; ++i) H[i * m + j] = h1[(long long)r * (m + 1) + i] + h2[(long long)r * (m + 1) + i];
+  const double h = sqrt(hnorm2[r]);
+  H[(j + 1) * m + j] = make_double2(h, 0);
+  inv_h[r] = h > 0.0 ? 1.0 / h : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double2 a = H[i * m + j], b = H[(i + 1) * m + j];
+    H[i * m + j] = cs[i] * a + cmul(sn[i], b);
+    H[(i + 1) * m + j] = cs[i] * b - cmul(conjg(sn[i]), a);
+  }
+  double c; double2 s, rho;
+  givens(H[j * m + j], H[(j + 1) * m + j], c, s, rho);
+  cs[j] = c; sn[j] = s;
+  H[j * m + j] = rho;
+  H[(j + 1) * m + j] = make_double2(0, 0);
+  const double2 gj = g[j];
+  g[j + 1] = -cmul(conjg(s), gj);
+  g[j] = c * gj;
+  const double res = sqrt(cnorm2(g[j + 1]));
+  S.resid[r] = res;
+  S.jdone[r] = j + 1;
+  if (res <= tol * S.bnorm[r]) {
+    S.active[r] = 0;
+    if (final_done) S.done[r] = 1;
+  }
+}
+
+__global__ void k_gmres_solve_y(GmresState S, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int m = S.m, jd = S.jdone[r];
+  const double2* H = S.H + (long long)r * (m + 1) * m;
+  const double2* g = S.g + (long long)r * (m + 1);
+  double2* y = S.y + (long long)r * m;
+  for (int i = m - 1; i >= jd; --i) y[i] = make_double2(0, 0);
+  for (int i = jd - 1; i >= 0; --i) {
+    double2 t = g[i];
+    for (int k = i + 1; k < jd; ++k) t -= cmul(H[i * m + k], y[k]);
+    const double2 d = H[i * m + i];
+    const double dd = cnorm2(d);
+    y[i] = dd > 0.0 ? (1.0 / dd) * cjmul(d, t) : make_double2(0, 0);
+  }
+}
+
+__global__ void k_gmres_mark_done(GmresState S, const double* __restrict__ nrm2, double tol, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const double lim = tol * S.bnorm[r];
+  if (sqrt(nrm2[r]) <= lim) S.done[r] = 1;
+}
+
+void launch_gmres_start(const GmresState& s, const double* nrm2, double tol, int nrhs, double* inv_beta,
+                        cudaStream_t st) {
+  k_gmres_start<<<nblk(nrhs, 64), 64, 0, st>>>(s, nrm2, tol, nrhs, inv_beta);
+  WCMG_LAUNCH_CHECK();
+}
+void launch_gmres_step(const GmresState& s, int j, const double2* h1, const double2* h2, const double* hnorm2,
+                       double tol, int final_done, int nrhs, double* inv_h, cudaStream_t st) {
+  k_gmres_step<<<nblk(nrhs, 64), 64, 0, st>>>(s, j, h1, h2, hnorm2, tol, final_done, nrhs, inv_h);
+  WCMG_LAUNCH_CHECK();
+}
+void launch_gmres_solve_y(const GmresState& s, int nrhs, cudaStream_t st) {
+  k_gmres_solve_y<<<nblk(nrhs, 64), 64, 0, st>>>(s, nrhs);
+  WCMG_LAUNCH_CHECK();
+}
+void launch_gmres_mark_done(const GmresState& s, const double* nrm2, double tol, int nrhs, cudaStream_t st) {
+  k_gmres_mark_done<<<nblk(nrhs, 64), 64, 0, st>>>(s, nrm2, tol, nrhs);
+  WCMG_LAUNCH_CHECK();
+}
+
+#define WCMG_INST(R)                                                                                             \
+  template void launch_dot<R>(double2*, const cplx<R>*, const cplx<R>*, long long, int, double2*, cudaStream_t); \
+  template void launch_norm2<R>(double*, const cplx<R>*, long long, int, double*, cudaStream_t);                 \
+  template void launch_multidot<R>(double2*, const cplx<R>*, long long, int, int, const cplx<R>*, long long, int, \
+                                   double2*, cudaStream_t);                                                      \
+  template void launch_multiaxpy<R>(cplx<R>*, const cplx<R>*, long long, int, const double2*, int, double,       \
+                                    long long, int, cudaStream_t);                                               \
+  template void launch_axpby<R>(cplx<R>*, double, const cplx<R>*, double, long long, int, cudaStream_t);         \
+  template void launch_scale_dev<R>(cplx<R>*, const cplx<R>*, const double*, int, long long, int, cudaStream_t); \
+  template void launch_mr_update<R>(cplx<R>*, cplx<R>*, const cplx<R>*, const double2*, const double*, long long, \
+                                    int, cudaStream_t);                                                          \
+  template void launch_mask_rhs<R>(cplx<R>*, const int*, long long, int, cudaStream_t);                          \
+  template void launch_fill_zero<R>(cplx<R>*, long long, cudaStream_t);
+WCMG_INST(double)
+WCMG_INST(float)
+#undef WCMG_INST
+template void launch_convert<double, float>(float2*, const double2*, long long, cudaStream_t);
+template void launch_convert<float, double>(double2*, const float2*, long long, cudaStream_t);
+template void launch_convert<double, double>(double2*, const double2*, long long, cudaStream_t);
+template void launch_convert<float, float>(float2*, const float2*, long long, cudaStream_t);
+
+}  // namespace wcmg
+
+namespace wcmg {
+__global__ void k_sqrt_inplace(double* x, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = sqrt(x[i]);
+}
+void launch_sqrt_inplace(double* x, int n, cudaStream_t st) {
+  k_sqrt_inplace<<<nblk(n, 64), 64, 0, st>>>(x, n);
+  WCMG_LAUNCH_CHECK();
+}
+}  // namespace wcmg

@@ -1,0 +1,239 @@
+// Coarse-level kernels: the coarse Dirac operator as a nine-point stencil
+// (Sec. 2.1 CoarsenedMatrix: Mdiag = self block, Mdir = hop block of one
+// direction; Sec. 4: 9 stencil points), fused over all nine blocks:
+//   y(x) = A_0(x) phi(x) + sum_mu [ A_{+mu}(x) phi(x + mu) + A_{-mu}(x) phi(x - mu) ]
+// Per site the nine nb x nb blocks are stored as one row-major nb x ld matrix
+// M(x) = [A_0 | A_{+x} | A_{-x} | ... | A_{-t}] (ld = 9 nb rounded up to 4), so
+// y(x) = M(x) Phi(x) with Phi(x) the nine gathered neighbour vectors (staged in
+// shared memory).  One CTA per coarse site streams M(x) with 16-byte loads; one
+// warp per row, lanes split the row, warp-shuffle reduction.  The same kernel,
+// with masked gathers, gives the block-interior and single-face parts that the
+// Galerkin construction (CoarsenOperator) of the next level needs.
+#include "kernels.h"
+
+namespace wcmg {
+
+struct BlockInfoC { int b[4]; int bvol; };
+
+__device__ __forceinline__ bool c_on_face(const BlockInfoC& bi, int s, int d) {
+  int loc = s % bi.bvol;
+  int l[4];
+  l[0] = loc % bi.b[0]; loc /= bi.b[0];
+  l[1] = loc % bi.b[1]; loc /= bi.b[1];
+  l[2] = loc % bi.b[2];
+  l[3] = loc / bi.b[2];
+  const int mu = d >> 1;
+  return (d & 1) ? (l[mu] == 0) : (l[mu] == bi.b[mu] - 1);
+}
+
+template <typename L, int VEC> struct alignas(16) LinkVec { L v[VEC]; };
+
+template <typename R, typename L, int RR, int VEC>
+__global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                      const L* __restrict__ links, const int* __restrict__ nbr,
+                                                      int Vc, int nb, int ld, int nrhs, int mode, int hopdir,
+                                                      BlockInfoC bi) {
+  using T = cplx<R>;
+  extern __shared__ unsigned char smem_raw[];
+  T* phi = reinterpret_cast<T*>(smem_raw);  // [RR][ld]
+  const int site = blockIdx.x, r0 = blockIdx.y * RR;
+  const int K = 9 * nb;
+  for (int idx = threadIdx.x; idx < RR * ld; idx += blockDim.x) {
+    const int r = idx / ld, k = idx % ld;
+    T v = czero<R>();
+    if (k < K && r0 + r < nrhs) {
+      const int d = k / nb, c = k % nb;
+      bool inc = true;
+      if (mode == ST_BLOCK_INTERIOR) inc = (d == 0) || !c_on_face(bi, site, d - 1);
+      else if (mode == ST_FACE_HOP) inc = (d >= 1) && (d - 1 == hopdir) && c_on_face(bi, site, d - 1);
+      if (inc) {
+        const int n = d == 0 ? site : nbr[(d - 1) * Vc + site];
+        v = in[((long long)(r0 + r) * Vc + n) * nb + c];
+      }
+    }
+    phi[idx] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int row = warp; row < nb; row += nw) {
+    const L* lr = links + ((long long)site * nb + row) * ld;
+    T acc[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) acc[r] = czero<R>();
+    for (int k0 = lane * VEC; k0 < ld; k0 += 32 * VEC) {
+      const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + k0);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const T a = link_load<L, R>(lv.v[v]);
+#pragma unroll
+        for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + k0 + v]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const T s = warp_sum(acc[r]);
+      if (lane == 0 && r0 + r < nrhs) out[((long long)(r0 + r) * Vc + site) * nb + row] = s;
+    }
+  }
+}
+
+template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
+
+template <typename R, typename L, int RR>
+static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
+                            int mode, int hopdir, cudaStream_t st) {
+  constexpr int VEC = VecOf<L>::v;
+  const int ld = links_ld(nb);
+  BlockInfoC bi;
+  for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
+  bi.bvol = g.bvol;
+  const size_t smem = (size_t)RR * ld * sizeof(cplx<R>);
+  auto kern = k_coarse_apply<R, L, RR, VEC>;
+  if (smem > 48 * 1024) WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int threads = nb >= 32 ? 512 : 256;
+  kern<<<dim3(g.V, (nrhs + RR - 1) / RR), threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, nrhs, mode,
+                                                               hopdir, bi);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R, typename L>
+void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
+                         int mode, int hopdir, cudaStream_t st) {
+  if (nrhs == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, st);
+  else if (nrhs <= 4 || sizeof(R) == 8) coarse_apply_rr<R, L, 4>(out, in, links, g, nb, nrhs, mode, hopdir, st);
+  else coarse_apply_rr<R, L, 8>(out, in, links, g, nb, nrhs, mode, hopdir, st);
+}
+
+// ---------------- link packing / assembly ----------------
+template <typename L>
+__global__ void k_pack_links(L* __restrict__ links, const double2* __restrict__ ext, const int* __restrict__ perm,
+                             int Vc, int nb, int ld) {
+  const int s = blockIdx.x;
+  const int lex = perm[s];
+  for (int idx = threadIdx.x; idx < nb * ld; idx += blockDim.x) {
+    const int a = idx / ld, k = idx % ld;
+    double2 v = make_double2(0, 0);
+    if (k < 9 * nb) {
+      const int d = k / nb, b = k % nb;
+      v = ext[(((long long)d * Vc + lex) * nb + a) * nb + b];
+    }
+    links[(long long)s * nb * ld + idx] = link_store<L>(v);
+  }
+}
+
+template <typename L> __device__ __forceinline__ double2 link_to_c64(const L& l);
+template <> __device__ __forceinline__ double2 link_to_c64<double2>(const double2& l) { return l; }
+template <> __device__ __forceinline__ double2 link_to_c64<float2>(const float2& l) { return make_double2(l.x, l.y); }
+template <> __device__ __forceinline__ double2 link_to_c64<bf16c>(const bf16c& l) {
+  float2 f = __bfloat1622float2(l.v); return make_double2(f.x, f.y);
+}
+template <> __device__ __forceinline__ double2 link_to_c64<f16c>(const f16c& l) {
+  float2 f = __half22float2(l.v); return make_double2(f.x, f.y);
+}
+
+template <typename L>
+__global__ void k_unpack_links(double2* __restrict__ ext, const L* __restrict__ links, const int* __restrict__ perm,
+                               int Vc, int nb, int ld) {
+  const int s = blockIdx.x;
+  const int lex = perm[s];
+  for (int idx = threadIdx.x; idx < 9 * nb * nb; idx += blockDim.x) {
+    const int d = idx / (nb * nb), a = (idx / nb) % nb, b = idx % nb;
+    ext[(((long long)d * Vc + lex) * nb + a) * nb + b] = link_to_c64<L>(links[((long long)s * nb + a) * ld + d * nb + b]);
+  }
+}
+
+template <typename R, typename L>
+__global__ void k_scatter_links(L* __restrict__ links, const cplx<R>* __restrict__ res, int Vc, int nb, int ld, int d,
+                                int b0, int ncols) {
+  const int x = blockIdx.x;
+  for (int idx = threadIdx.x; idx < ncols * nb; idx += blockDim.x) {
+    const int j = idx / nb, a = idx % nb;
+    links[((long long)x * nb + a) * ld + d * nb + b0 + j] = link_store<L>(to_c64(res[((long long)j * Vc + x) * nb + a]));
+  }
+}
+
+template <typename Lin, typename Lout>
+__global__ void k_convert_links(Lout* __restrict__ out, const Lin* __restrict__ in, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = link_store<Lout>(link_to_c64<Lin>(in[i]));
+}
+
+template <typename R>
+__global__ void k_pack_coarse(cplx<R>* __restrict__ out, const double2* __restrict__ ext, const int* __restrict__ perm,
+                              int V, int nc) {
+  const int s = blockIdx.x, r = blockIdx.y;
+  const int lex = perm[s];
+  for (int c = threadIdx.x; c < nc; c += blockDim.x)
+    out[((long long)r * V + s) * nc + c] = from_c64<R>(ext[((long long)r * V + lex) * nc + c]);
+}
+template <typename R>
+__global__ void k_unpack_coarse(double2* __restrict__ ext, const cplx<R>* __restrict__ in, const int* __restrict__ perm,
+                                int V, int nc) {
+  const int s = blockIdx.x, r = blockIdx.y;
+  const int lex = perm[s];
+  for (int c = threadIdx.x; c < nc; c += blockDim.x)
+    ext[((long long)r * V + lex) * nc + c] = to_c64(in[((long long)r * V + s) * nc + c]);
+}
+
+template <typename L>
+void launch_pack_links(L* links, const double2* ext, const int* perm, int Vc, int nb, cudaStream_t st) {
+  k_pack_links<L><<<Vc, 256, 0, st>>>(links, ext, perm, Vc, nb, links_ld(nb));
+  WCMG_LAUNCH_CHECK();
+}
+template <typename L>
+void launch_unpack_links(double2* ext, const L* links, const int* perm, int Vc, int nb, cudaStream_t st) {
+  k_unpack_links<L><<<Vc, 256, 0, st>>>(ext, links, perm, Vc, nb, links_ld(nb));
+  WCMG_LAUNCH_CHECK();
+}
+template <typename R, typename L>
+void launch_scatter_links(L* links, const cplx<R>* res, int Vc, int nb, int d, int b0, int ncols, cudaStream_t st) {
+  k_scatter_links<R, L><<<Vc, 256, 0, st>>>(links, res, Vc, nb, links_ld(nb), d, b0, ncols);
+  WCMG_LAUNCH_CHECK();
+}
+template <typename Lin, typename Lout>
+void launch_convert_links(Lout* out, const Lin* in, long long n, cudaStream_t st) {
+  k_convert_links<Lin, Lout><<<nblk(n, 256), 256, 0, st>>>(out, in, n);
+  WCMG_LAUNCH_CHECK();
+}
+template <typename R>
+void launch_pack_coarse(cplx<R>* out, const double2* ext, const int* perm, int V, int nc, int nrhs, cudaStream_t st) {
+  k_pack_coarse<R><<<dim3(V, nrhs), 64, 0, st>>>(out, ext, perm, V, nc);
+  WCMG_LAUNCH_CHECK();
+}
+template <typename R>
+void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int V, int nc, int nrhs, cudaStream_t st) {
+  k_unpack_coarse<R><<<dim3(V, nrhs), 64, 0, st>>>(ext, in, perm, V, nc);
+  WCMG_LAUNCH_CHECK();
+}
+
+template void launch_coarse_apply<double, double2>(double2*, const double2*, const double2*, const LevelGeom&, int,
+                                                   int, int, int, cudaStream_t);
+template void launch_coarse_apply<float, float2>(float2*, const float2*, const float2*, const LevelGeom&, int, int,
+                                                 int, int, cudaStream_t);
+template void launch_coarse_apply<float, bf16c>(float2*, const float2*, const bf16c*, const LevelGeom&, int, int, int,
+                                                int, cudaStream_t);
+template void launch_coarse_apply<float, f16c>(float2*, const float2*, const f16c*, const LevelGeom&, int, int, int,
+                                               int, cudaStream_t);
+#define WCMG_INST_L(L)                                                                                   \
+  template void launch_pack_links<L>(L*, const double2*, const int*, int, int, cudaStream_t);           \
+  template void launch_unpack_links<L>(double2*, const L*, const int*, int, int, cudaStream_t);
+WCMG_INST_L(double2)
+WCMG_INST_L(float2)
+WCMG_INST_L(bf16c)
+WCMG_INST_L(f16c)
+#undef WCMG_INST_L
+template void launch_scatter_links<double, double2>(double2*, const double2*, int, int, int, int, int, cudaStream_t);
+template void launch_scatter_links<float, float2>(float2*, const float2*, int, int, int, int, int, cudaStream_t);
+template void launch_convert_links<float2, bf16c>(bf16c*, const float2*, long long, cudaStream_t);
+template void launch_convert_links<float2, f16c>(f16c*, const float2*, long long, cudaStream_t);
+template void launch_convert_links<double2, float2>(float2*, const double2*, long long, cudaStream_t);
+template void launch_convert_links<double2, bf16c>(bf16c*, const double2*, long long, cudaStream_t);
+template void launch_convert_links<double2, f16c>(f16c*, const double2*, long long, cudaStream_t);
+#define WCMG_INST(R)                                                                                     \
+  template void launch_pack_coarse<R>(cplx<R>*, const double2*, const int*, int, int, int, cudaStream_t); \
+  template void launch_unpack_coarse<R>(double2*, const cplx<R>*, const int*, int, int, int, cudaStream_t);
+WCMG_INST(double)
+WCMG_INST(float)
+#undef WCMG_INST
+
+}  // namespace wcmg

@@ -1,0 +1,133 @@
+// Shared device helpers of the wcmg kernels: complex arithmetic on double2 /
+// float2, link storage conversions, warp/block reductions, error plumbing.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+
+namespace wcmg {
+
+template <typename R> struct cplx_of;
+template <> struct cplx_of<double> { using type = double2; };
+template <> struct cplx_of<float> { using type = float2; };
+template <typename R> using cplx = typename cplx_of<R>::type;
+
+__host__ __device__ __forceinline__ double2 cmk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
+template <typename R> __host__ __device__ __forceinline__ cplx<R> czero() { return cmk(R(0), R(0)); }
+
+#define WCMG_CPLX_OPS(T, R)                                                                         \
+  __host__ __device__ __forceinline__ T operator+(T a, T b) { return cmk(a.x + b.x, a.y + b.y); }   \
+  __host__ __device__ __forceinline__ T operator-(T a, T b) { return cmk(a.x - b.x, a.y - b.y); }   \
+  __host__ __device__ __forceinline__ T operator-(T a) { return cmk(-a.x, -a.y); }                  \
+  __host__ __device__ __forceinline__ T operator*(R s, T a) { return cmk(s * a.x, s * a.y); }       \
+  __host__ __device__ __forceinline__ T& operator+=(T& a, T b) { a.x += b.x; a.y += b.y; return a; } \
+  __host__ __device__ __forceinline__ T& operator-=(T& a, T b) { a.x -= b.x; a.y -= b.y; return a; } \
+  /* a * b */                                                                                       \
+  __host__ __device__ __forceinline__ T cmul(T a, T b) {                                            \
+    return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);                                       \
+  }                                                                                                 \
+  /* conj(a) * b */                                                                                 \
+  __host__ __device__ __forceinline__ T cjmul(T a, T b) {                                           \
+    return cmk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);                                       \
+  }                                                                                                 \
+  /* acc += a * b */                                                                                \
+  __host__ __device__ __forceinline__ void cmac(T& acc, T a, T b) {                                 \
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);                                    \
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);                                     \
+  }                                                                                                 \
+  /* acc += conj(a) * b */                                                                          \
+  __host__ __device__ __forceinline__ void cjmac(T& acc, T a, T b) {                                \
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);                                     \
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);                                    \
+  }                                                                                                 \
+  __host__ __device__ __forceinline__ T conjg(T a) { return cmk(a.x, -a.y); }                       \
+  /* i * a, -i * a */                                                                               \
+  __host__ __device__ __forceinline__ T mul_i(T a) { return cmk(-a.y, a.x); }                       \
+  __host__ __device__ __forceinline__ T mul_mi(T a) { return cmk(a.y, -a.x); }                      \
+  __host__ __device__ __forceinline__ R cnorm2(T a) { return a.x * a.x + a.y * a.y; }
+
+WCMG_CPLX_OPS(double2, double)
+WCMG_CPLX_OPS(float2, float)
+#undef WCMG_CPLX_OPS
+
+__host__ __device__ __forceinline__ double2 to_c64(double2 a) { return a; }
+__host__ __device__ __forceinline__ double2 to_c64(float2 a) { return make_double2(a.x, a.y); }
+template <typename R> __host__ __device__ __forceinline__ cplx<R> from_c64(double2 a);
+template <> __host__ __device__ __forceinline__ double2 from_c64<double>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2 from_c64<float>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// ---- coarse-link storage types: complex numbers stored as (re, im) pairs ----
+struct bf16c { __nv_bfloat162 v; };
+struct f16c { __half2 v; };
+
+template <typename L, typename R> __device__ __forceinline__ cplx<R> link_load(const L& l);
+template <> __device__ __forceinline__ double2 link_load<double2, double>(const double2& l) { return l; }
+template <> __device__ __forceinline__ float2 link_load<float2, float>(const float2& l) { return l; }
+template <> __device__ __forceinline__ float2 link_load<bf16c, float>(const bf16c& l) { return __bfloat1622float2(l.v); }
+template <> __device__ __forceinline__ float2 link_load<f16c, float>(const f16c& l) { return __half22float2(l.v); }
+
+template <typename L> __device__ __forceinline__ L link_store(double2 a);
+template <> __device__ __forceinline__ double2 link_store<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 link_store<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ bf16c link_store<bf16c>(double2 a) {
+  bf16c r; r.v = __floats2bfloat162_rn((float)a.x, (float)a.y); return r;
+}
+template <> __device__ __forceinline__ f16c link_store<f16c>(double2 a) {
+  f16c r; r.v = __floats2half2_rn((float)a.x, (float)a.y); return r;
+}
+
+// ---- reductions (fixed order: deterministic for fixed launch shapes) ----
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double2 warp_sum(double2 v) { return make_double2(warp_sum(v.x), warp_sum(v.y)); }
+__device__ __forceinline__ float2 warp_sum(float2 v) { return make_float2(warp_sum(v.x), warp_sum(v.y)); }
+
+// Sum `n` complex values held per thread across the whole block; result for value k
+// is left in red[k] (shared, size >= n).  scratch must hold (blockDim/32) * n values.
+template <typename T>
+__device__ __forceinline__ void block_sum_many(T* vals, int n, T* scratch, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < n; ++k) {
+    T s = warp_sum(vals[k]);
+    if (lane == 0) scratch[warp * n + k] = s;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    T s = scratch[k];
+    for (int w = 1; w < nw; ++w) s += scratch[w * n + k];
+    red[k] = s;
+  }
+  __syncthreads();
+}
+
+// ---- host-side error plumbing ----
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define WCMG_CUDA(call)                                                                          \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      throw ::wcmg::Error(e_ == cudaErrorMemoryAllocation ? -7 : -2,                             \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+#define WCMG_LAUNCH_CHECK() WCMG_CUDA(cudaGetLastError())
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace wcmg

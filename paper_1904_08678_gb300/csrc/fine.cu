@@ -1,0 +1,419 @@
+// Fine-level kernels: layout packing, gauge field, clover term (K0) and the
+// Wilson-clover Dslash (K1).
+//
+// Operator (Sec. 2.1: multigrid runs on the Wilson-clover D itself; Sec. 2.2:
+// chiral gamma basis so that gamma5 = diag(1, 1, -1, -1)):
+//   D psi(x) = C(x) psi(x) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                      + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
+// with gamma_mu = [[0, B_mu], [B_mu^dag, 0]], B_k = -i sigma_k (k = x, y, z),
+// B_t = 1.  The (1 -+ gamma_mu) projectors are applied as 2-spin half spinors:
+//   forward : h = psi_u - B psi_l,  upper += U h,      lower += -B^dag (U h)
+//   backward: h = psi_u + B psi_l,  upper += U^dag h,  lower += +B^dag (U^dag h)
+// C(x) = (4 + m0) + (c_sw/2) sum_{mu<nu} sigma_{mu nu} (x) i Fhat_{mu nu}(x) is
+// block diagonal in chirality (two Hermitian 6x6 blocks), stored compactly:
+// per chirality 3 pairs of real diagonal entries and 15 complex upper entries.
+//
+// Internal layouts (storage order of sites, see LevelGeom):
+//   spinor : [12][V] complex   (component c = 3 * spin + colour)
+//   gauge  : [4][9][V] complex (entry (mu, 3 a + b) = U_mu(x)[a][b])
+//   clover : [36][V] complex   (chirality s uses entries 18 s .. 18 s + 17)
+#include "kernels.h"
+
+namespace wcmg {
+
+// ---------------- packing ----------------
+template <typename R>
+__global__ void k_pack_fine(cplx<R>* __restrict__ out, const double2* __restrict__ ext, const int* __restrict__ perm,
+                            int V, int nrhs) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (s >= V) return;
+  const double2* e = ext + ((long long)r * V + perm[s]) * 12;
+  cplx<R>* o = out + (long long)r * 12 * V;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) o[(long long)c * V + s] = from_c64<R>(e[c]);
+}
+
+template <typename R>
+__global__ void k_unpack_fine(double2* __restrict__ ext, const cplx<R>* __restrict__ in, const int* __restrict__ perm,
+                              int V, int nrhs) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (s >= V) return;
+  double2* e = ext + ((long long)r * V + perm[s]) * 12;
+  const cplx<R>* i = in + (long long)r * 12 * V;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) e[c] = to_c64(i[(long long)c * V + s]);
+}
+
+template <typename R>
+__global__ void k_pack_gauge(cplx<R>* __restrict__ out, const double2* __restrict__ ext, const int* __restrict__ perm,
+                             int V) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int mu = blockIdx.y;
+  if (s >= V) return;
+  const double2* e = ext + ((long long)mu * V + perm[s]) * 9;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out[((long long)mu * 9 + k) * V + s] = from_c64<R>(e[k]);
+}
+
+template <typename R>
+void launch_pack_fine(cplx<R>* out, const double2* ext, const int* perm, int V, int nrhs, cudaStream_t st) {
+  k_pack_fine<R><<<dim3(nblk(V, 128), nrhs), 128, 0, st>>>(out, ext, perm, V, nrhs);
+  WCMG_LAUNCH_CHECK();
+}
+template <typename R>
+void launch_unpack_fine(double2* ext, const cplx<R>* in, const int* perm, int V, int nrhs, cudaStream_t st) {
+  k_unpack_fine<R><<<dim3(nblk(V, 128), nrhs), 128, 0, st>>>(ext, in, perm, V, nrhs);
+  WCMG_LAUNCH_CHECK();
+}
+template <typename R>
+void launch_pack_gauge(cplx<R>* out, const double2* ext, const int* perm, int V, cudaStream_t st) {
+  k_pack_gauge<R><<<dim3(nblk(V, 128), 4), 128, 0, st>>>(out, ext, perm, V);
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---------------- clover term (K0, FP64, once per gauge field) ----------------
+struct Su3 { double2 m[9]; };
+
+__device__ __forceinline__ Su3 load_u(const double2* __restrict__ g, int V, int mu, int s) {
+  Su3 u;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u.m[k] = g[((long long)mu * 9 + k) * V + s];
+  return u;
+}
+__device__ __forceinline__ Su3 dag(const Su3& a) {
+  Su3 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r.m[3 * i + j] = conjg(a.m[3 * j + i]);
+  return r;
+}
+__device__ __forceinline__ Su3 mm(const Su3& a, const Su3& b) {
+  Su3 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double2 acc = make_double2(0, 0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cmac(acc, a.m[3 * i + k], b.m[3 * k + j]);
+      r.m[3 * i + j] = acc;
+    }
+  return r;
+}
+
+// S[plane][chirality][2x2]: the chiral blocks of sigma_{mu nu} = i gamma_mu gamma_nu
+// (upper: i B_mu B_nu^dag, lower: i B_mu^dag B_nu), planes in the order
+// (0,1) (0,2) (0,3) (1,2) (1,3) (2,3).
+struct CloverSigma { double2 S[6][2][4]; };
+
+__global__ void k_clover_build(double2* __restrict__ clov, const double2* __restrict__ g, const int* __restrict__ nbr,
+                               int V, double diag, double half_csw, CloverSigma sig) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  double2 C[2][6][6];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) C[h][i][j] = make_double2(i == j ? diag : 0.0, 0.0);
+  int plane = 0;
+  for (int mu = 0; mu < 4; ++mu) {
+    for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+      const int xpm = nbr[(2 * mu) * V + s], xmm = nbr[(2 * mu + 1) * V + s];
+      const int xpn = nbr[(2 * nu) * V + s], xmn = nbr[(2 * nu + 1) * V + s];
+      const int xmm_pn = nbr[(2 * nu) * V + xmm];      // x - mu + nu
+      const int xmm_mn = nbr[(2 * nu + 1) * V + xmm];  // x - mu - nu
+      const int xpm_mn = nbr[(2 * nu + 1) * V + xpm];  // x + mu - nu
+      Su3 Umx = load_u(g, V, mu, s), Unx = load_u(g, V, nu, s);
+      Su3 Um_mm = load_u(g, V, mu, xmm), Un_mn = load_u(g, V, nu, xmn);
+      // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+      Su3 Q = mm(mm(Umx, load_u(g, V, nu, xpm)), mm(dag(load_u(g, V, mu, xpn)), dag(Unx)));
+      // leaf 2: U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag U_mu(x-mu)
+      Su3 L = mm(mm(Unx, dag(load_u(g, V, mu, xmm_pn))), mm(dag(load_u(g, V, nu, xmm)), Um_mm));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Q.m[k] += L.m[k];
+      // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
+      L = mm(mm(dag(Um_mm), dag(load_u(g, V, nu, xmm_mn))), mm(load_u(g, V, mu, xmm_mn), Un_mn));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Q.m[k] += L.m[k];
+      // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x+mu-nu) U_mu(x)^dag
+      L = mm(mm(dag(Un_mn), load_u(g, V, mu, xmn)), mm(load_u(g, V, nu, xpm_mn), dag(Umx)));
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Q.m[k] += L.m[k];
+      // i Fhat = i (Q - Q^dag) / 8  (Hermitian)
+      double2 iF[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) iF[3 * a + b] = mul_i(0.125 * (Q.m[3 * a + b] - conjg(Q.m[3 * b + a])));
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const double2 sp = half_csw * sig.S[plane][h][2 * p + q];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b = 0; b < 3; ++b) cmac(C[h][3 * p + a][3 * q + b], sp, iF[3 * a + b]);
+          }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      clov[(long long)(18 * h + k) * V + s] = make_double2(C[h][2 * k][2 * k].x, C[h][2 * k + 1][2 * k + 1].x);
+    int o = 3;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) clov[(long long)(18 * h + o++) * V + s] = C[h][i][j];
+  }
+}
+
+__global__ void k_clover_expand(double2* __restrict__ ext, const double2* __restrict__ clov,
+                                const int* __restrict__ perm, int V) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  double2* e = ext + (long long)perm[s] * 144;
+  for (int k = 0; k < 144; ++k) e[k] = make_double2(0, 0);
+  for (int h = 0; h < 2; ++h) {
+    for (int k = 0; k < 3; ++k) {
+      double2 d = clov[(long long)(18 * h + k) * V + s];
+      e[(6 * h + 2 * k) * 12 + 6 * h + 2 * k] = make_double2(d.x, 0);
+      e[(6 * h + 2 * k + 1) * 12 + 6 * h + 2 * k + 1] = make_double2(d.y, 0);
+    }
+    int o = 3;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j) {
+        double2 c = clov[(long long)(18 * h + o++) * V + s];
+        e[(6 * h + i) * 12 + 6 * h + j] = c;
+        e[(6 * h + j) * 12 + 6 * h + i] = conjg(c);
+      }
+  }
+}
+
+static CloverSigma make_sigma() {
+  // B_mu as 2x2 complex (row-major)
+  double2 B[4][4];
+  const double2 z = make_double2(0, 0), one = make_double2(1, 0), mi = make_double2(0, -1);
+  // B_x = -i sigma_1 ; B_y = -i sigma_2 ; B_z = -i sigma_3 ; B_t = 1
+  double2 Bx[4] = {z, mi, mi, z};
+  double2 By[4] = {z, make_double2(-1, 0), one, z};
+  double2 Bz[4] = {mi, z, z, make_double2(0, 1)};
+  double2 Bt[4] = {one, z, z, one};
+  for (int k = 0; k < 4; ++k) { B[0][k] = Bx[k]; B[1][k] = By[k]; B[2][k] = Bz[k]; B[3][k] = Bt[k]; }
+  auto mul = [](const double2* a, const double2* b, double2* r, bool dag_a, bool dag_b) {
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        double2 acc = make_double2(0, 0);
+        for (int k = 0; k < 2; ++k) {
+          double2 x = dag_a ? conjg(a[2 * k + i]) : a[2 * i + k];
+          double2 y = dag_b ? conjg(b[2 * j + k]) : b[2 * k + j];
+          acc += cmul(x, y);
+        }
+        r[2 * i + j] = mul_i(acc);
+      }
+  };
+  CloverSigma cs;
+  int plane = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+      mul(B[mu], B[nu], cs.S[plane][0], false, true);   // i B_mu B_nu^dag
+      mul(B[mu], B[nu], cs.S[plane][1], true, false);   // i B_mu^dag B_nu
+    }
+  return cs;
+}
+
+void launch_clover_build(double2* clov, const double2* gauge64, const int* nbr, int V, double m0, double csw,
+                         cudaStream_t st) {
+  static const CloverSigma sig = make_sigma();
+  k_clover_build<<<nblk(V, 64), 64, 0, st>>>(clov, gauge64, nbr, V, 4.0 + m0, 0.5 * csw, sig);
+  WCMG_LAUNCH_CHECK();
+}
+void launch_clover_expand(double2* ext, const double2* clov, const int* perm, int V, cudaStream_t st) {
+  k_clover_expand<<<nblk(V, 128), 128, 0, st>>>(ext, clov, perm, V);
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---------------- Dslash (K1) ----------------
+// apply B_mu (or B_mu^dag) to a 2-spin x 3-colour half spinor v[2][3]
+template <int MU, typename T>
+__device__ __forceinline__ void applyB(T (&out)[2][3], const T (&v)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) { out[0][c] = mul_mi(v[1][c]); out[1][c] = mul_mi(v[0][c]); }
+    if (MU == 1) { out[0][c] = -v[1][c]; out[1][c] = v[0][c]; }
+    if (MU == 2) { out[0][c] = mul_mi(v[0][c]); out[1][c] = mul_i(v[1][c]); }
+    if (MU == 3) { out[0][c] = v[0][c]; out[1][c] = v[1][c]; }
+  }
+}
+template <int MU, typename T>
+__device__ __forceinline__ void applyBdag(T (&out)[2][3], const T (&v)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) { out[0][c] = mul_i(v[1][c]); out[1][c] = mul_i(v[0][c]); }
+    if (MU == 1) { out[0][c] = v[1][c]; out[1][c] = -v[0][c]; }
+    if (MU == 2) { out[0][c] = mul_i(v[0][c]); out[1][c] = mul_mi(v[1][c]); }
+    if (MU == 3) { out[0][c] = v[0][c]; out[1][c] = v[1][c]; }
+  }
+}
+
+template <typename R, int MU, bool FWD>
+__device__ __forceinline__ void hop(cplx<R> (&acc)[12], const cplx<R>* __restrict__ in, const cplx<R>* __restrict__ U,
+                                    int V, int s, int y) {
+  using T = cplx<R>;
+  T pu[2][3], pl[2][3];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pu[sp][c] = in[(long long)(3 * sp + c) * V + y];
+      pl[sp][c] = in[(long long)(6 + 3 * sp + c) * V + y];
+    }
+  T Bpl[2][3], h[2][3];
+  applyB<MU>(Bpl, pl);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[sp][c] = FWD ? pu[sp][c] - Bpl[sp][c] : pu[sp][c] + Bpl[sp][c];
+  const int ls = FWD ? s : y;  // link U_mu(x) forward, U_mu(x - mu) backward
+  T u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = U[((long long)MU * 9 + k) * V + ls];
+  T w[2][3];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T t = czero<R>();
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (FWD) cmac(t, u[3 * a + b], h[sp][b]);
+        else cjmac(t, u[3 * b + a], h[sp][b]);
+      }
+      w[sp][a] = t;
+    }
+  T Bw[2][3];
+  applyBdag<MU>(Bw, w);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[3 * sp + c] += w[sp][c];
+      if (FWD) acc[6 + 3 * sp + c] -= Bw[sp][c];
+      else acc[6 + 3 * sp + c] += Bw[sp][c];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void clover_apply(cplx<R> (&out)[12], const cplx<R>* __restrict__ clov,
+                                             const cplx<R>* __restrict__ in, int V, int s) {
+  using T = cplx<R>;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    T p[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) p[i] = in[(long long)(6 * h + i) * V + s];
+    T y[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      T d = clov[(long long)(18 * h + k) * V + s];
+      y[2 * k] = d.x * p[2 * k];
+      y[2 * k + 1] = d.y * p[2 * k + 1];
+    }
+    int o = 3;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        T c = clov[(long long)(18 * h + o++) * V + s];
+        cmac(y[i], c, p[j]);
+        cjmac(y[j], c, p[i]);
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[6 * h + i] = y[i];
+  }
+}
+
+struct BlockInfo { int b[4]; int bvol; };
+
+__device__ __forceinline__ bool on_face(const BlockInfo& bi, int s, int d) {
+  int loc = s % bi.bvol;
+  int l[4];
+  l[0] = loc % bi.b[0]; loc /= bi.b[0];
+  l[1] = loc % bi.b[1]; loc /= bi.b[1];
+  l[2] = loc % bi.b[2];
+  l[3] = loc / bi.b[2];
+  const int mu = d >> 1;
+  return (d & 1) ? (l[mu] == 0) : (l[mu] == bi.b[mu] - 1);
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(128) k_dslash(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                const cplx<R>* __restrict__ U, const cplx<R>* __restrict__ clov,
+                                                const int* __restrict__ nbr, int V, BlockInfo bi, int hopdir) {
+  using T = cplx<R>;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const long long off = (long long)blockIdx.y * 12 * V;
+  in += off;
+  out += off;
+  T acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = czero<R>();
+  auto use = [&](int d) -> bool {
+    if (MODE == ST_FULL) return true;
+    if (MODE == ST_BLOCK_INTERIOR) return !on_face(bi, s, d);
+    return d == hopdir && on_face(bi, s, d);
+  };
+#define WCMG_HOP(MU)                                                               \
+  if (use(2 * MU)) hop<R, MU, true>(acc, in, U, V, s, nbr[(2 * MU) * V + s]);       \
+  if (use(2 * MU + 1)) hop<R, MU, false>(acc, in, U, V, s, nbr[(2 * MU + 1) * V + s]);
+  WCMG_HOP(0)
+  WCMG_HOP(1)
+  WCMG_HOP(2)
+  WCMG_HOP(3)
+#undef WCMG_HOP
+  T res[12];
+  if (MODE != ST_FACE_HOP) {
+    clover_apply<R>(res, clov, in, V, s);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) res[c] = czero<R>();
+  }
+#pragma unroll
+  for (int c = 0; c < 12; ++c) out[(long long)c * V + s] = res[c] + R(-0.5) * acc[c];
+}
+
+template <typename R>
+void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
+                   int nrhs, int mode, int hopdir, cudaStream_t st) {
+  BlockInfo bi;
+  for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
+  bi.bvol = g.bvol;
+  dim3 grid(nblk(g.V, 128), nrhs);
+  if (mode == ST_FULL) k_dslash<R, ST_FULL><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir);
+  else if (mode == ST_BLOCK_INTERIOR)
+    k_dslash<R, ST_BLOCK_INTERIOR><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir);
+  else k_dslash<R, ST_FACE_HOP><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir);
+  WCMG_LAUNCH_CHECK();
+}
+
+#define WCMG_INST(R)                                                                                          \
+  template void launch_pack_fine<R>(cplx<R>*, const double2*, const int*, int, int, cudaStream_t);            \
+  template void launch_unpack_fine<R>(double2*, const cplx<R>*, const int*, int, int, cudaStream_t);          \
+  template void launch_pack_gauge<R>(cplx<R>*, const double2*, const int*, int, cudaStream_t);                \
+  template void launch_dslash<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
+                                 int, int, int, cudaStream_t);
+WCMG_INST(double)
+WCMG_INST(float)
+#undef WCMG_INST
+
+}  // namespace wcmg

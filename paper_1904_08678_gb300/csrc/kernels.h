@@ -1,0 +1,134 @@
+// Host-side launchers of the wcmg CUDA kernels (one declaration per kernel family).
+#pragma once
+#include "common.cuh"
+
+namespace wcmg {
+
+// Geometry of one level as seen by its stencil kernels.  Sites are stored in
+// hierarchical block-major order: the |B| sites of one aggregate of the next
+// coarser level are contiguous, so transfers need no index tables.
+struct LevelGeom {
+  int V;            // sites
+  const int* nbr;   // [8][V] storage index of x + mu (2 mu) and x - mu (2 mu + 1)
+  int b[4];         // aggregate extents towards the next level (1s on the coarsest)
+  int bvol;         // b0 * b1 * b2 * b3
+};
+
+enum StencilMode { ST_FULL = 0, ST_BLOCK_INTERIOR = 1, ST_FACE_HOP = 2 };
+
+// ---- fine level (fine.cu) ----
+template <typename R>
+void launch_pack_fine(cplx<R>* out, const double2* ext, const int* perm, int V, int nrhs, cudaStream_t st);
+template <typename R>
+void launch_unpack_fine(double2* ext, const cplx<R>* in, const int* perm, int V, int nrhs, cudaStream_t st);
+template <typename R>
+void launch_pack_gauge(cplx<R>* out, const double2* ext, const int* perm, int V, cudaStream_t st);
+void launch_clover_build(double2* clov, const double2* gauge64, const int* nbr, int V, double m0, double csw,
+                         cudaStream_t st);
+void launch_clover_expand(double2* ext, const double2* clov, const int* perm, int V, cudaStream_t st);
+template <typename R>
+void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
+                   int nrhs, int mode, int hopdir, cudaStream_t st);
+
+// ---- transfers (transfer.cu) ----
+// `fine` selects the component-major fine layout [ncomp][V]; otherwise fields are
+// site-major [V][ncomp].  Vectors and fields of one level share the layout.
+template <typename R>
+void launch_restrict(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
+                     int nrhs, bool fine, cudaStream_t st);
+template <typename R>
+void launch_prolong(cplx<R>* out, const cplx<R>* coarse, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
+                    int nrhs, bool fine, cudaStream_t st);
+// FP64 block orthonormalisation in place; err receives 1 on a rank-deficient panel.
+void launch_block_ortho(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st);
+// cols[b] = Pi_s v_i with (s, i) = divmod(b0 + b, nvec), for b < ncols.
+template <typename R>
+void launch_make_columns(cplx<R>* cols, const cplx<R>* vecs, int Vf, int nc, int nvec, int b0, int ncols, bool fine,
+                         cudaStream_t st);
+
+// ---- coarse levels (coarse.cu) ----
+// Coarse links: per site a row-major nb x ld matrix, ld = round_up(9 nb, 4),
+// column d*nb + c of row a holds A_d(x)[a][c].
+inline int links_ld(int nb) { return (9 * nb + 3) / 4 * 4; }
+template <typename L>
+void launch_pack_links(L* links, const double2* ext, const int* perm, int Vc, int nb, cudaStream_t st);
+template <typename L>
+void launch_unpack_links(double2* ext, const L* links, const int* perm, int Vc, int nb, cudaStream_t st);
+template <typename R>
+void launch_pack_coarse(cplx<R>* out, const double2* ext, const int* perm, int V, int nc, int nrhs, cudaStream_t st);
+template <typename R>
+void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int V, int nc, int nrhs, cudaStream_t st);
+template <typename R, typename L>
+void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
+                         int mode, int hopdir, cudaStream_t st);
+// links[x][a][d*nb + b0 + j] = res[j][x][a] for j < ncols (res: restrict output of the column fields)
+template <typename R, typename L>
+void launch_scatter_links(L* links, const cplx<R>* res, int Vc, int nb, int d, int b0, int ncols, cudaStream_t st);
+template <typename Lin, typename Lout>
+void launch_convert_links(Lout* out, const Lin* in, long long n, cudaStream_t st);
+
+// ---- BLAS-1 and Krylov helpers (blas.cu); fields are [nrhs][n] complex ----
+template <typename A, typename B>
+void launch_convert(cplx<B>* out, const cplx<A>* in, long long n, cudaStream_t st);
+template <typename R>
+void launch_dot(double2* out, const cplx<R>* a, const cplx<R>* b, long long n, int nrhs, double2* partial,
+                cudaStream_t st);
+template <typename R>
+void launch_norm2(double* out, const cplx<R>* a, long long n, int nrhs, double* partial, cudaStream_t st);
+// out[r][i] = <basis_i, w> for i < k; basis_i at basis + i * bstride (each [nrhs][n])
+template <typename R>
+void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int k, int ldo, const cplx<R>* w,
+                     long long n, int nrhs, double2* partial, cudaStream_t st);
+// w[r] += sign * sum_{i<k} coef[r*ldc + i] * basis_i[r]
+template <typename R>
+void launch_multiaxpy(cplx<R>* w, const cplx<R>* basis, long long bstride, int k, const double2* coef, int ldc,
+                      double sign, long long n, int nrhs, cudaStream_t st);
+template <typename R>
+void launch_axpby(cplx<R>* y, double a, const cplx<R>* x, double b, long long n, int nrhs, cudaStream_t st);
+// y[r] = x[r] * s[r] (s real, device)
+template <typename R>
+void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqrt, long long n, int nrhs,
+                      cudaStream_t st);
+// MR update with alpha[r] = pr[r] / pp[r] (0 if pp = 0), pr = <p, r>, pp = <p, p>:
+//   x += alpha r ; r -= alpha p
+template <typename R>
+void launch_mr_update(cplx<R>* x, cplx<R>* r, const cplx<R>* p, const double2* pr, const double* pp, long long n,
+                      int nrhs, cudaStream_t st);
+// x[r] = mask[r] ? 0 : x[r]
+template <typename R>
+void launch_mask_rhs(cplx<R>* x, const int* mask, long long n, int nrhs, cudaStream_t st);
+template <typename R>
+void launch_fill_zero(cplx<R>* x, long long n, cudaStream_t st);
+
+// Arnoldi/Givens bookkeeping for batched (F)GMRES, one thread per rhs.
+struct GmresState {
+  double2* H;      // [nrhs][m+1][m]
+  double* cs;      // [nrhs][m]
+  double2* sn;     // [nrhs][m]
+  double2* g;      // [nrhs][m+1]
+  double2* y;      // [nrhs][m]
+  double* hnorm;   // [nrhs]
+  double* bnorm;   // [nrhs]
+  double* resid;   // [nrhs]  |g_{j+1}|
+  int* active;     // [nrhs]  1 while iterating in this cycle
+  int* jdone;      // [nrhs]  steps taken in this cycle
+  int* done;       // [nrhs]  finished for good (frozen in later cycles)
+  int m;
+};
+// h column j is in H (entries 0..j from multidot); hnorm holds ||w||.
+// h1, h2: the two CGS passes' coefficients [nrhs][m+1]; hnorm2 = ||w||^2 after both.
+// `final_done`: a recurrence convergence also marks the rhs done (no true-residual check).
+void launch_gmres_step(const GmresState& s, int j, const double2* h1, const double2* h2, const double* hnorm2,
+                       double tol, int final_done, int nrhs, double* inv_h, cudaStream_t st);
+// done[r] |= nrm2[r] <= (tol * bnorm[r])^2
+void launch_gmres_mark_done(const GmresState& s, const double* nrm2, double tol, int nrhs, cudaStream_t st);
+void launch_gmres_solve_y(const GmresState& s, int nrhs, cudaStream_t st);
+// start a cycle: beta[r] = sqrt(nrm2[r]); g = (beta, 0...); active = beta > tol*bnorm; inv_beta
+void launch_gmres_start(const GmresState& s, const double* nrm2, double tol, int nrhs, double* inv_beta,
+                        cudaStream_t st);
+
+}  // namespace wcmg
+
+namespace wcmg {
+void launch_sqrt_inplace(double* x, int n, cudaStream_t st);
+}

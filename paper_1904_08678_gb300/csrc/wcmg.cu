@@ -1,0 +1,1383 @@
+// Host orchestration and C-ABI of the multigrid library (include/wcmg.h).
+//
+// Sec. 2.1 of the paper: the solver class calls itself recursively over the
+// levels; the coarse operator of each level is applied through Mdiag + Mdir
+// and can be coarsened again; MR is the smoother, GMRES the coarsest solver,
+// FGMRES the outer solver; the setup is the smoother-based initial setup
+// followed by iterative refinement with the whole MG preconditioner.  The
+// precision change of the paper (double outer solver, single preconditioner) is
+// the inner_prec = F32 mode, here with FP64 defect correction at every restart.
+//
+// Every Krylov loop is batched over right-hand sides: the setup runs all Nvec
+// near-null candidates of a level as one batch, and each rhs keeps its own
+// Hessenberg matrix and stopping state on the device.
+#include "../../include/wcmg.h"
+#include "kernels.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace wcmg {
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  T* ensure(size_t count) {
+    if (count <= n && p) return p;
+    release();
+    WCMG_CUDA(cudaMalloc(&p, (count ? count : 1) * sizeof(T)));
+    n = count;
+    return p;
+  }
+};
+
+struct HostGeom {
+  int dims[4] = {1, 1, 1, 1};
+  int V = 1;
+  int b[4] = {1, 1, 1, 1};
+  int bvol = 1;
+  std::vector<int> perm, inv, nbr;
+  DevBuf<int> d_perm, d_nbr;
+  LevelGeom lg() const {
+    LevelGeom g;
+    g.V = V;
+    g.nbr = d_nbr.p;
+    for (int k = 0; k < 4; ++k) g.b[k] = b[k];
+    g.bvol = bvol;
+    return g;
+  }
+};
+
+static inline int lexi(const int* x, const int* d) { return x[0] + d[0] * (x[1] + d[1] * (x[2] + d[2] * x[3])); }
+static inline void coords(int s, const int* d, int* x) {
+  x[0] = s % d[0]; s /= d[0];
+  x[1] = s % d[1]; s /= d[1];
+  x[2] = s % d[2];
+  x[3] = s / d[2];
+}
+
+// Scalars of one level's Krylov loops (device) and its (F)GMRES state.
+struct LevelScalars {
+  int cap_rhs = 0, cap_m = 0;
+  DevBuf<double2> c2;  // h1, h2 [2][rhs][m+1]; pr [rhs]
+  DevBuf<double> d;    // hn2, nrm2, inv_beta, inv_h, pp, bnorm, resid, cs... [slots][rhs]
+  DevBuf<double2> H, sn, g, y;
+  DevBuf<double> cs;
+  DevBuf<int> ints;    // active, jdone, done
+  void ensure(int rhs, int m) {
+    if (rhs <= cap_rhs && m <= cap_m) return;
+    rhs = std::max(rhs, cap_rhs);
+    m = std::max(m, cap_m);
+    c2.ensure((size_t)rhs * (2 * (m + 1) + 1));
+    d.ensure((size_t)rhs * 8);
+    H.ensure((size_t)rhs * (m + 1) * m);
+    sn.ensure((size_t)rhs * m);
+    g.ensure((size_t)rhs * (m + 1));
+    y.ensure((size_t)rhs * m);
+    cs.ensure((size_t)rhs * m);
+    ints.ensure((size_t)rhs * 3);
+    cap_rhs = rhs;
+    cap_m = m;
+  }
+  double2* h1() { return c2.p; }
+  double2* h2() { return c2.p + (size_t)cap_rhs * (cap_m + 1); }
+  double2* pr() { return c2.p + (size_t)2 * cap_rhs * (cap_m + 1); }
+  double* slot(int k) { return d.p + (size_t)k * cap_rhs; }
+  GmresState state(int m) {
+    GmresState s;
+    s.H = H.p; s.cs = cs.p; s.sn = sn.p; s.g = g.p; s.y = y.p;
+    s.hnorm = slot(0); s.bnorm = slot(5); s.resid = slot(6);
+    s.active = ints.p; s.jdone = ints.p + cap_rhs; s.done = ints.p + 2 * cap_rhs;
+    s.m = m;
+    return s;
+  }
+};
+// slot map: 0 hn2, 1 nrm2, 2 inv_beta, 3 inv_h, 4 pp, 5 bnorm, 6 resid, 7 misc
+
+struct Level {
+  HostGeom g;
+  int nc = 12;
+  bool fine = true;
+  int nvec = 0;  // towards the next level
+  DevBuf<double2> v64;
+  DevBuf<float2> v32;
+  bool have_P = false, v32_valid = false;
+  DevBuf<double2> raw64;
+  DevBuf<float2> raw32;
+  // coarse operator of this level (level >= 1)
+  bool have_op = false;
+  bool op64 = false;  // FP64 links present (else FP32)
+  DevBuf<double2> L64;
+  DevBuf<float2> L32;
+  DevBuf<bf16c> Lbf;
+  DevBuf<f16c> Lh;
+  bool L32_valid = false, low_valid = false;
+  LevelScalars sc;
+  std::map<std::string, DevBuf<unsigned char>> ws;
+  long long n() const { return (long long)g.V * nc; }
+};
+
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Pend { int cls; cudaEvent_t a, b; double bytes, flops; };
+  std::vector<Pend> pend;
+  wcmg_kstat k[WCMG_NKCLASS];
+  Prof() { reset(); }
+  void reset() { std::memset(k, 0, sizeof(k)); }
+  cudaEvent_t get() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      WCMG_CUDA(cudaEventCreate(&e));
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  void flush() {
+    for (auto& p : pend) {
+      WCMG_CUDA(cudaEventSynchronize(p.b));
+      float ms = 0;
+      WCMG_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+      k[p.cls].launches += 1;
+      k[p.cls].ms += ms;
+      k[p.cls].bytes += p.bytes;
+      k[p.cls].flops += p.flops;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pend.clear();
+  }
+  ~Prof() {
+    for (auto& p : pend) { pool.push_back(p.a); pool.push_back(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace wcmg
+
+using namespace wcmg;
+
+struct wcmg_ctx {
+  wcmg_params p;
+  std::string err;
+  std::vector<Level> L;
+  DevBuf<double2> gauge64, clover64;
+  DevBuf<float2> gauge32, clover32;
+  bool have_gauge = false;
+  DevBuf<double2> partial;
+  DevBuf<double> partial_d;
+  DevBuf<unsigned char> stage[3];
+  DevBuf<int> errflag;
+  int* h_flags = nullptr;   // pinned host mirror of per-rhs flags
+  double* h_vals = nullptr; // pinned host mirror of per-rhs values
+  int hcap = 0;
+  Prof prof;
+  cudaStream_t st = nullptr;
+  long long coarse_its = 0;
+  ~wcmg_ctx() {
+    if (h_flags) cudaFreeHost(h_flags);
+    if (h_vals) cudaFreeHost(h_vals);
+  }
+};
+
+namespace wcmg {
+
+#define KPROF(c, cls, bytes, flops, call)                                     \
+  do {                                                                        \
+    cudaEvent_t a_ = nullptr, b_ = nullptr;                                   \
+    if ((c)->prof.on) { a_ = (c)->prof.get(); WCMG_CUDA(cudaEventRecord(a_, (c)->st)); } \
+    call;                                                                     \
+    if ((c)->prof.on) {                                                       \
+      b_ = (c)->prof.get();                                                   \
+      WCMG_CUDA(cudaEventRecord(b_, (c)->st));                                \
+      (c)->prof.pend.push_back({(cls), a_, b_, (double)(bytes), (double)(flops)}); \
+    }                                                                         \
+  } while (0)
+
+static void host_mirrors(wcmg_ctx* c, int n) {
+  if (n <= c->hcap) return;
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  if (c->h_vals) cudaFreeHost(c->h_vals);
+  c->h_flags = nullptr;
+  c->h_vals = nullptr;
+  WCMG_CUDA(cudaMallocHost(&c->h_flags, sizeof(int) * n));
+  WCMG_CUDA(cudaMallocHost(&c->h_vals, sizeof(double) * n));
+  c->hcap = n;
+}
+static const int* read_ints(wcmg_ctx* c, const int* d, int n) {
+  host_mirrors(c, n);
+  WCMG_CUDA(cudaMemcpyAsync(c->h_flags, d, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st));
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  return c->h_flags;
+}
+static const double* read_doubles(wcmg_ctx* c, const double* d, int n) {
+  host_mirrors(c, n);
+  WCMG_CUDA(cudaMemcpyAsync(c->h_vals, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  return c->h_vals;
+}
+
+template <typename R>
+static cplx<R>* ws(Level& L, const char* name, long long nfields) {
+  std::string key = std::string(name) + (sizeof(R) == 8 ? "/64" : "/32");
+  auto& b = L.ws[key];
+  return reinterpret_cast<cplx<R>*>(b.ensure((size_t)nfields * L.n() * sizeof(cplx<R>)));
+}
+
+static int max_rhs_all(const wcmg_ctx* c) {
+  int m = std::max(1, c->p.max_rhs);
+  for (int l = 0; l + 1 < c->p.n_levels; ++l) m = std::max(m, c->p.nvec[l]);
+  return m;
+}
+static void ensure_partials(wcmg_ctx* c) {
+  const int r = std::max(max_rhs_all(c), 2 * c->p.nvec[0] + 1);
+  const int k = std::max(c->p.outer_restart, c->p.coarse_restart) + 1 + 8;
+  c->partial.ensure((size_t)r * k * 608);
+  c->partial_d.ensure((size_t)r * 608);
+}
+
+// ---------------- accessors at a precision ----------------
+template <typename R> struct Prec;
+template <> struct Prec<double> {
+  static double2* gauge(wcmg_ctx* c) { return c->gauge64.p; }
+  static double2* clover(wcmg_ctx* c) { return c->clover64.p; }
+  static double2* vecs(wcmg_ctx*, Level& L) { return L.v64.p; }
+  static DevBuf<double2>& raw(Level& L) { return L.raw64; }
+};
+template <> struct Prec<float> {
+  static float2* gauge(wcmg_ctx* c) { return c->gauge32.p; }
+  static float2* clover(wcmg_ctx* c) { return c->clover32.p; }
+  static float2* vecs(wcmg_ctx* c, Level& L) {
+    if (!L.v32_valid) {
+      L.v32.ensure((size_t)L.nvec * L.n());
+      launch_convert<double, float>(L.v32.p, L.v64.p, (long long)L.nvec * L.n(), c->st);
+      L.v32_valid = true;
+    }
+    return L.v32.p;
+  }
+  static DevBuf<float2>& raw(Level& L) { return L.raw32; }
+};
+
+static double sz(int prec) { return prec == WCMG_F64 ? 16.0 : prec == WCMG_F32 ? 8.0 : 4.0; }
+
+// ---------------- operators ----------------
+template <typename R>
+static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nrhs, int mode = ST_FULL,
+                     int hopdir = 0) {
+  Level& L = c->L[l];
+  if (l == 0) {
+    if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+    const double V = L.g.V, s = sizeof(cplx<R>);
+    const int cls = sizeof(R) == 8 ? WCMG_K_DSLASH64 : WCMG_K_DSLASH;
+    KPROF(c, cls, V * s * (24.0 * nrhs + 72.0), V * 1872.0 * nrhs,
+          launch_dslash<R>(out, in, Prec<R>::gauge(c), Prec<R>::clover(c), L.g.lg(), nrhs, mode, hopdir, c->st));
+    return;
+  }
+  if (!L.have_op) throw Error(WCMG_ERR_STATE, "coarse operator of level not built");
+  const int nb = L.nc;
+  const double Vc = L.g.V, nb2 = (double)nb * nb;
+  const double flops = Vc * 8.0 * 9.0 * nb2 * nrhs;
+  if (sizeof(R) == 8) {
+    if (!L.op64) throw Error(WCMG_ERR_ARG, "FP64 coarse apply needs FP64 links");
+    KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 16.0 + 2.0 * nb * 16.0 * nrhs), flops,
+          (launch_coarse_apply<double, double2>((double2*)out, (const double2*)in, L.L64.p, L.g.lg(), nb, nrhs,
+                                                mode, hopdir, c->st)));
+    return;
+  }
+  const int lp = c->p.coarse_link_prec;
+  if (mode == ST_FULL && L.low_valid && (lp == WCMG_BF16 || lp == WCMG_F16)) {
+    if (lp == WCMG_BF16)
+      KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
+            (launch_coarse_apply<float, bf16c>((float2*)out, (const float2*)in, L.Lbf.p, L.g.lg(), nb, nrhs, mode,
+                                               hopdir, c->st)));
+    else
+      KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
+            (launch_coarse_apply<float, f16c>((float2*)out, (const float2*)in, L.Lh.p, L.g.lg(), nb, nrhs, mode,
+                                              hopdir, c->st)));
+    return;
+  }
+  if (!L.L32_valid) {
+    const long long n = (long long)L.g.V * nb * links_ld(nb);
+    L.L32.ensure(n);
+    launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
+    L.L32_valid = true;
+  }
+  KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 8.0 + 2.0 * nb * 8.0 * nrhs), flops,
+        (launch_coarse_apply<float, float2>((float2*)out, (const float2*)in, L.L32.p, L.g.lg(), nb, nrhs, mode,
+                                            hopdir, c->st)));
+}
+
+template <typename R>
+static void restrict_op(wcmg_ctx* c, int l, cplx<R>* coarse, const cplx<R>* fine, int nrhs) {
+  Level& L = c->L[l];
+  if (!L.have_P) throw Error(WCMG_ERR_STATE, "prolongator of level not built");
+  const double s = sizeof(cplx<R>);
+  KPROF(c, WCMG_K_RESTRICT, (double)L.n() * s * (L.nvec + nrhs) + (double)L.g.V / L.g.bvol * 2 * L.nvec * s * nrhs,
+        (double)L.n() * 8.0 * L.nvec * nrhs,
+        launch_restrict<R>(coarse, fine, Prec<R>::vecs(c, L), L.g.V, L.nc, L.g.bvol, L.nvec, nrhs, L.fine, c->st));
+}
+template <typename R>
+static void prolong_op(wcmg_ctx* c, int l, cplx<R>* fine, const cplx<R>* coarse, int nrhs) {
+  Level& L = c->L[l];
+  if (!L.have_P) throw Error(WCMG_ERR_STATE, "prolongator of level not built");
+  const double s = sizeof(cplx<R>);
+  KPROF(c, WCMG_K_PROLONG, (double)L.n() * s * (L.nvec + nrhs) + (double)L.g.V / L.g.bvol * 2 * L.nvec * s * nrhs,
+        (double)L.n() * 8.0 * L.nvec * nrhs,
+        launch_prolong<R>(fine, coarse, Prec<R>::vecs(c, L), L.g.V, L.nc, L.g.bvol, L.nvec, nrhs, L.fine, c->st));
+}
+
+template <typename R>
+static void copy_fields(wcmg_ctx* c, cplx<R>* dst, const cplx<R>* src, long long n) {
+  WCMG_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(cplx<R>), cudaMemcpyDeviceToDevice, c->st));
+}
+
+// ---------------- BLAS wrappers (profiled) ----------------
+template <typename R>
+static void norm2_op(wcmg_ctx* c, double* out, const cplx<R>* a, long long n, int nrhs) {
+  KPROF(c, WCMG_K_BLAS, (double)n * nrhs * sizeof(cplx<R>), 4.0 * n * nrhs,
+        launch_norm2<R>(out, a, n, nrhs, c->partial_d.p, c->st));
+}
+template <typename R>
+static void dot_op(wcmg_ctx* c, double2* out, const cplx<R>* a, const cplx<R>* b, long long n, int nrhs) {
+  KPROF(c, WCMG_K_BLAS, 2.0 * n * nrhs * sizeof(cplx<R>), 8.0 * n * nrhs,
+        launch_dot<R>(out, a, b, n, nrhs, c->partial.p, c->st));
+}
+
+// ---------------- MR (smoother) ----------------
+// Sec. 2.1 MinimalResidual, zero initial guess, fixed number of steps:
+//   r = b; k times: p = A r, alpha = <p, r>/<p, p>, x += alpha r, r -= alpha p.
+template <typename R>
+static void mr(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int steps) {
+  Level& L = c->L[l];
+  const long long n = L.n();
+  cplx<R>* r = ws<R>(L, "mr_r", nrhs);
+  cplx<R>* p = ws<R>(L, "mr_p", nrhs);
+  L.sc.ensure(max_rhs_all(c), std::max(c->p.outer_restart, c->p.coarse_restart));
+  copy_fields<R>(c, r, b, n * nrhs);
+  launch_fill_zero<R>(x, n * nrhs, c->st);
+  for (int k = 0; k < steps; ++k) {
+    apply_op<R>(c, l, p, r, nrhs);
+    dot_op<R>(c, L.sc.pr(), p, r, n, nrhs);
+    norm2_op<R>(c, L.sc.slot(4), p, n, nrhs);
+    KPROF(c, WCMG_K_BLAS, 5.0 * n * nrhs * sizeof(cplx<R>), 16.0 * n * nrhs,
+          launch_mr_update<R>(x, r, p, L.sc.pr(), L.sc.slot(4), n, nrhs, c->st));
+  }
+}
+
+template <typename R> static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs);
+
+// ---------------- (F)GMRES ----------------
+struct KrylovOut {
+  int iterations = 0;
+  bool converged = false;
+};
+
+// Batched right-preconditioned flexible GMRES(m) on level l (GMRES when
+// precond = false).  Arnoldi by classical Gram-Schmidt applied twice (CGS2,
+// equal to modified Gram-Schmidt in exact arithmetic), complex Givens
+// rotations and the least-squares update in FP64 on the device.  Each rhs stops
+// when its recurrence residual is <= tol * ||b||; with verify the true residual
+// b - A x decides at the end of a cycle.  max_cycles = 0: unlimited restarts.
+template <typename R>
+static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int m, double tol, int maxiter,
+                        bool x_zero, bool verify, bool precond, int max_cycles = 0) {
+  Level& L = c->L[l];
+  const long long n = L.n();
+  const int mr_ = max_rhs_all(c);
+  L.sc.ensure(mr_, std::max(m, std::max(c->p.outer_restart, c->p.coarse_restart)));
+  cplx<R>* Vb = ws<R>(L, precond ? "fg_V" : "gm_V", (long long)(m + 1) * nrhs);
+  cplx<R>* Zb = precond ? ws<R>(L, "fg_Z", (long long)m * nrhs) : nullptr;
+  cplx<R>* w = ws<R>(L, precond ? "fg_w" : "gm_w", nrhs);
+  cplx<R>* r = ws<R>(L, precond ? "fg_r" : "gm_r", nrhs);
+  const long long bstride = n * nrhs;
+  GmresState S = L.sc.state(m);
+  const int ldh = m + 1;
+  norm2_op<R>(c, S.bnorm, b, n, nrhs);
+  launch_sqrt_inplace(S.bnorm, nrhs, c->st);
+  WCMG_CUDA(cudaMemsetAsync(S.done, 0, sizeof(int) * nrhs, c->st));
+  if (x_zero) {
+    launch_fill_zero<R>(x, n * nrhs, c->st);
+    copy_fields<R>(c, r, b, n * nrhs);
+  } else {
+    apply_op<R>(c, l, r, x, nrhs);
+    launch_axpby<R>(r, 1.0, b, -1.0, n, nrhs, c->st);  // r = b - A x
+  }
+  KrylovOut out;
+  int cycles = 0;
+  norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
+  while (true) {
+    launch_gmres_start(S, L.sc.slot(1), tol, nrhs, L.sc.slot(2), c->st);
+    launch_scale_dev<R>(Vb, r, L.sc.slot(2), 0, n, nrhs, c->st);
+    int steps = 0;
+    const int* act = read_ints(c, S.active, nrhs);
+    bool any = false;
+    for (int q = 0; q < nrhs; ++q) any |= act[q] != 0;
+    for (int j = 0; j < m && any; ++j) {
+      cplx<R>* vj = Vb + (long long)j * bstride;
+      cplx<R>* z = vj;
+      if (precond) {
+        z = Zb + (long long)j * bstride;
+        cycle<R>(c, l, z, vj, nrhs);
+      }
+      apply_op<R>(c, l, w, z, nrhs);
+      KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+            launch_multidot<R>(L.sc.h1(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
+      KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+            launch_multiaxpy<R>(w, Vb, bstride, j + 1, L.sc.h1(), ldh, -1.0, n, nrhs, c->st));
+      KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+            launch_multidot<R>(L.sc.h2(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
+      KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+            launch_multiaxpy<R>(w, Vb, bstride, j + 1, L.sc.h2(), ldh, -1.0, n, nrhs, c->st));
+      norm2_op<R>(c, L.sc.slot(0), w, n, nrhs);
+      launch_gmres_step(S, j, L.sc.h1(), L.sc.h2(), L.sc.slot(0), tol, verify ? 0 : 1, nrhs, L.sc.slot(3), c->st);
+      launch_scale_dev<R>(Vb + (long long)(j + 1) * bstride, w, L.sc.slot(3), 0, n, nrhs, c->st);
+      ++steps;
+      ++out.iterations;
+      act = read_ints(c, S.active, nrhs);
+      any = false;
+      for (int q = 0; q < nrhs; ++q) any |= act[q] != 0;
+      if (out.iterations >= maxiter) break;
+    }
+    ++cycles;
+    if (steps > 0) {
+      launch_gmres_solve_y(S, nrhs, c->st);
+      KPROF(c, WCMG_K_KRYLOV, (double)(steps + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * steps * n * nrhs,
+            launch_multiaxpy<R>(x, precond ? Zb : Vb, bstride, steps, S.y, m, 1.0, n, nrhs, c->st));
+    }
+    if (max_cycles > 0 && cycles >= max_cycles) {
+      out.converged = false;
+      return out;
+    }
+    const int* dn = read_ints(c, S.done, nrhs);
+    bool all = true;
+    for (int q = 0; q < nrhs; ++q) all &= dn[q] != 0;
+    if (all && !verify) { out.converged = true; return out; }
+    apply_op<R>(c, l, r, x, nrhs);
+    launch_axpby<R>(r, 1.0, b, -1.0, n, nrhs, c->st);
+    norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
+    launch_gmres_mark_done(S, L.sc.slot(1), tol, nrhs, c->st);
+    const double* nr = read_doubles(c, L.sc.slot(1), nrhs);
+    for (int q = 0; q < nrhs; ++q)
+      if (!std::isfinite(nr[q])) throw Error(WCMG_ERR_NAN, "non-finite residual in Krylov solver");
+    dn = read_ints(c, S.done, nrhs);
+    all = true;
+    for (int q = 0; q < nrhs; ++q) all &= dn[q] != 0;
+    if (all) { out.converged = true; return out; }
+    if (out.iterations >= maxiter || steps == 0) return out;
+  }
+}
+
+// ---------------- multigrid cycle ----------------
+// M_l(r): e = P_l CoarseSolve_{l+1}(P_l^dag r); e += MR_k(D_l; r - D_l e).
+// CoarseSolve is GMRES at the coarsest level and one cycle of level l+1 between.
+template <typename R>
+static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
+  Level& L = c->L[l];
+  Level& C = c->L[l + 1];
+  const long long n = L.n();
+  cplx<R>* rc = ws<R>(C, "cyc_rc", nrhs);
+  cplx<R>* ec = ws<R>(C, "cyc_ec", nrhs);
+  restrict_op<R>(c, l, rc, r, nrhs);
+  if (l + 1 == c->p.n_levels - 1) {
+    KrylovOut k = fgmres<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter, true,
+                            false, false);
+    c->coarse_its += k.iterations;
+  } else {
+    cycle<R>(c, l + 1, ec, rc, nrhs);
+  }
+  prolong_op<R>(c, l, e, ec, nrhs);
+  cplx<R>* t = ws<R>(L, "cyc_t", nrhs);
+  cplx<R>* s = ws<R>(L, "cyc_s", nrhs);
+  apply_op<R>(c, l, t, e, nrhs);
+  launch_axpby<R>(t, 1.0, r, -1.0, n, nrhs, c->st);  // t = r - D e
+  mr<R>(c, l, s, t, nrhs, c->p.smoother_steps);
+  launch_axpby<R>(e, 1.0, s, 1.0, n, nrhs, c->st);
+}
+
+// ---------------- setup ----------------
+template <typename R>
+static void coarsen(wcmg_ctx* c, int l) {
+  Level& F = c->L[l];
+  Level& C = c->L[l + 1];
+  const int nb = 2 * F.nvec, Vc = C.g.V;
+  const long long nl = (long long)Vc * nb * links_ld(nb);
+  cplx<R>* links;
+  if (sizeof(R) == 8) {
+    links = (cplx<R>*)C.L64.ensure(nl);
+    C.op64 = true;
+    C.L32_valid = false;
+  } else {
+    links = (cplx<R>*)C.L32.ensure(nl);
+    C.op64 = false;
+    C.L32_valid = true;
+  }
+  WCMG_CUDA(cudaMemsetAsync(links, 0, (size_t)nl * sizeof(cplx<R>), c->st));
+  const int chunk = std::min(nb, 48);
+  cplx<R>* cols = ws<R>(F, "co_cols", chunk);
+  cplx<R>* T = ws<R>(F, "co_T", chunk);
+  cplx<R>* res = ws<R>(C, "co_res", chunk);
+  for (int b0 = 0; b0 < nb; b0 += chunk) {
+    const int ncols = std::min(chunk, nb - b0);
+    KPROF(c, WCMG_K_COARSEN, 2.0 * F.n() * ncols * sizeof(cplx<R>), 0.0,
+          launch_make_columns<R>(cols, Prec<R>::vecs(c, F), F.g.V, F.nc, F.nvec, b0, ncols, F.fine, c->st));
+    for (int dm = 0; dm < 9; ++dm) {
+      const int mode = dm == 0 ? ST_BLOCK_INTERIOR : ST_FACE_HOP;
+      const int hop = dm == 0 ? 0 : dm - 1;
+      apply_op<R>(c, l, T, cols, ncols, mode, hop);
+      restrict_op<R>(c, l, res, T, ncols);
+      KPROF(c, WCMG_K_COARSEN, (double)Vc * nb * ncols * 2.0 * sizeof(cplx<R>), 0.0,
+            (launch_scatter_links<R, cplx<R>>(links, res, Vc, nb, dm == 0 ? 0 : dm, b0, ncols, c->st)));
+    }
+  }
+  C.have_op = true;
+  C.low_valid = false;
+  if (sizeof(R) == 4 && (c->p.coarse_link_prec == WCMG_BF16 || c->p.coarse_link_prec == WCMG_F16)) {
+    if (c->p.coarse_link_prec == WCMG_BF16) {
+      C.Lbf.ensure(nl);
+      launch_convert_links<float2, bf16c>(C.Lbf.p, C.L32.p, nl, c->st);
+    } else {
+      C.Lh.ensure(nl);
+      launch_convert_links<float2, f16c>(C.Lh.p, C.L32.p, nl, c->st);
+    }
+    C.low_valid = true;
+  }
+}
+
+// P_l from the level's raw vectors at precision R: FP64 block orthonormalisation.
+template <typename R>
+static void build_P(wcmg_ctx* c, int l) {
+  Level& L = c->L[l];
+  const long long n = (long long)L.nvec * L.n();
+  L.v64.ensure(n);
+  launch_convert<R, double>(L.v64.p, Prec<R>::raw(L).p, n, c->st);
+  WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
+  const double V = L.g.V;
+  KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0 * L.nvec, 2.0 * 2.0 * 8.0 * n * L.nvec / 2.0,
+        launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
+  (void)V;
+  const int* e = read_ints(c, c->errflag.p, 1);
+  if (e[0]) throw Error(WCMG_ERR_NAN, "rank-deficient aggregate in block orthonormalisation");
+  L.v32_valid = false;
+  L.have_P = true;
+}
+
+template <typename R>
+static void smooth_sweep(wcmg_ctx* c, int l) {
+  Level& L = c->L[l];
+  const int nv = L.nvec;
+  cplx<R>* raw = Prec<R>::raw(L).p;
+  cplx<R>* x = ws<R>(L, "sw_x", nv);
+  mr<R>(c, l, x, raw, nv, c->p.smoother_steps);
+  norm2_op<R>(c, L.sc.slot(7), x, L.n(), nv);
+  launch_scale_dev<R>(raw, x, L.sc.slot(7), 1, L.n(), nv, c->st);
+}
+
+template <typename R>
+static void setup_all(wcmg_ctx* c, const double2* init, wcmg_stats* st) {
+  const int nl = c->p.n_levels;
+  auto t0 = std::chrono::steady_clock::now();
+  long long off = 0;
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level& L = c->L[l];
+    auto& raw = Prec<R>::raw(L);
+    raw.ensure((size_t)L.nvec * L.n());
+    if (L.fine) launch_pack_fine<R>(raw.p, init + off, L.g.d_perm.p, L.g.V, L.nvec, c->st);
+    else launch_pack_coarse<R>(raw.p, init + off, L.g.d_perm.p, L.g.V, L.nc, L.nvec, c->st);
+    off += (long long)L.nvec * L.n();
+    for (int s = 0; s < c->p.setup_init_sweeps; ++s) smooth_sweep<R>(c, l);
+    build_P<R>(c, l);
+    coarsen<R>(c, l);
+  }
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  auto t1 = std::chrono::steady_clock::now();
+  for (int s = 0; s < c->p.setup_refine_sweeps; ++s) {
+    Level& L = c->L[0];
+    const int nv = L.nvec;
+    cplx<R>* raw = Prec<R>::raw(L).p;
+    cplx<R>* e = ws<R>(L, "ref_e", nv);
+    cycle<R>(c, 0, e, raw, nv);
+    norm2_op<R>(c, L.sc.slot(7), e, L.n(), nv);
+    launch_scale_dev<R>(raw, e, L.sc.slot(7), 1, L.n(), nv, c->st);
+    build_P<R>(c, 0);
+    coarsen<R>(c, 0);
+    for (int l = 1; l + 1 < nl; ++l) {
+      smooth_sweep<R>(c, l);
+      build_P<R>(c, l);
+      coarsen<R>(c, l);
+    }
+  }
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  auto t2 = std::chrono::steady_clock::now();
+  if (st) {
+    st->ms_setup_init = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    st->ms_setup_refine = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  }
+}
+
+// ---------------- outer solve ----------------
+static void solve_f64(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcmg_stats* st) {
+  KrylovOut k = fgmres<double>(c, 0, x, b, nrhs, c->p.outer_restart, c->p.outer_tol, c->p.outer_maxiter, true, true,
+                               true);
+  st->outer_iterations = k.iterations;
+  st->converged = k.converged;
+}
+
+// Precision change (Sec. 2.1): FP64 iterate and true residual, FP32 FGMRES cycles
+// preconditioned by the FP32 multigrid; every restart is a defect correction.
+static void solve_mixed(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcmg_stats* st) {
+  Level& L = c->L[0];
+  const long long n = L.n();
+  double2* r64 = ws<double>(L, "mx_r", nrhs);
+  double2* t64 = ws<double>(L, "mx_t", nrhs);
+  float2* r32 = ws<float>(L, "mx_r32", nrhs);
+  float2* e32 = ws<float>(L, "mx_e32", nrhs);
+  L.sc.ensure(max_rhs_all(c), std::max(c->p.outer_restart, c->p.coarse_restart));
+  double* bn2 = L.sc.slot(7);
+  norm2_op<double>(c, bn2, b, n, nrhs);
+  std::vector<double> bnorm(nrhs);
+  {
+    const double* h = read_doubles(c, bn2, nrhs);
+    for (int q = 0; q < nrhs; ++q) bnorm[q] = std::sqrt(h[q]);
+  }
+  launch_fill_zero<double>(x, n * nrhs, c->st);
+  copy_fields<double>(c, r64, b, n * nrhs);
+  DevBuf<int>& mask = c->errflag;  // errflag has room for max rhs + 1
+  std::vector<int> done(nrhs, 0);
+  int its = 0, restarts = 0;
+  const double inner_tol = 1e-5;
+  while (true) {
+    norm2_op<double>(c, L.sc.slot(1), r64, n, nrhs);
+    const double* h = read_doubles(c, L.sc.slot(1), nrhs);
+    bool all = true;
+    double worst = 0;
+    for (int q = 0; q < nrhs; ++q) {
+      if (!std::isfinite(h[q])) throw Error(WCMG_ERR_NAN, "non-finite residual");
+      const double rel = bnorm[q] > 0 ? std::sqrt(h[q]) / bnorm[q] : 0.0;
+      worst = std::max(worst, rel);
+      done[q] = rel <= c->p.outer_tol;
+      all &= done[q] != 0;
+    }
+    st->true_residual = worst;
+    if (all) { st->converged = 1; break; }
+    if (its >= c->p.outer_maxiter) { st->converged = 0; break; }
+    WCMG_CUDA(cudaMemcpyAsync(mask.p + 1, done.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, c->st));
+    launch_convert<double, float>(r32, r64, n * nrhs, c->st);
+    launch_mask_rhs<float>(r32, mask.p + 1, n, nrhs, c->st);
+    KrylovOut k = fgmres<float>(c, 0, e32, r32, nrhs, c->p.outer_restart, inner_tol,
+                                std::min(c->p.outer_restart, c->p.outer_maxiter - its), true, false, true, 1);
+    its += k.iterations;
+    ++restarts;
+    launch_convert<float, double>(t64, e32, n * nrhs, c->st);
+    launch_axpby<double>(x, 1.0, t64, 1.0, n, nrhs, c->st);
+    apply_op<double>(c, 0, t64, x, nrhs);
+    copy_fields<double>(c, r64, b, n * nrhs);
+    launch_axpby<double>(r64, -1.0, t64, 1.0, n, nrhs, c->st);
+  }
+  st->outer_iterations = its;
+  st->restarts = restarts - 1 > 0 ? restarts - 1 : 0;
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+}
+
+// true residual max_r ||b - D x|| / ||b|| in FP64
+static double true_residual(wcmg_ctx* c, const double2* x, const double2* b, int nrhs) {
+  Level& L = c->L[0];
+  const long long n = L.n();
+  double2* t = ws<double>(L, "tr_t", nrhs);
+  apply_op<double>(c, 0, t, x, nrhs);
+  launch_axpby<double>(t, 1.0, b, -1.0, n, nrhs, c->st);
+  L.sc.ensure(max_rhs_all(c), std::max(c->p.outer_restart, c->p.coarse_restart));
+  norm2_op<double>(c, L.sc.slot(1), t, n, nrhs);
+  norm2_op<double>(c, L.sc.slot(7), b, n, nrhs);
+  std::vector<double> rn(nrhs);
+  const double* h = read_doubles(c, L.sc.slot(1), nrhs);
+  for (int q = 0; q < nrhs; ++q) rn[q] = h[q];
+  h = read_doubles(c, L.sc.slot(7), nrhs);
+  double worst = 0;
+  for (int q = 0; q < nrhs; ++q) worst = std::max(worst, h[q] > 0 ? std::sqrt(rn[q] / h[q]) : 0.0);
+  return worst;
+}
+
+// ---------------- external I/O ----------------
+static const double2* in_dev(wcmg_ctx* c, const void* ptr, size_t bytes, int where, int slot) {
+  if (where == WCMG_DEVICE) return (const double2*)ptr;
+  if (where != WCMG_HOST) throw Error(WCMG_ERR_ARG, "where must be WCMG_HOST or WCMG_DEVICE");
+  auto* d = c->stage[slot].ensure(bytes);
+  WCMG_CUDA(cudaMemcpyAsync(d, ptr, bytes, cudaMemcpyHostToDevice, c->st));
+  return (const double2*)d;
+}
+static double2* out_dev(wcmg_ctx* c, void* ptr, size_t bytes, int where, int slot) {
+  if (where == WCMG_DEVICE) return (double2*)ptr;
+  if (where != WCMG_HOST) throw Error(WCMG_ERR_ARG, "where must be WCMG_HOST or WCMG_DEVICE");
+  return (double2*)c->stage[slot].ensure(bytes);
+}
+static void out_finish(wcmg_ctx* c, void* ptr, const double2* d, size_t bytes, int where) {
+  if (where == WCMG_HOST) {
+    WCMG_CUDA(cudaMemcpyAsync(ptr, d, bytes, cudaMemcpyDeviceToHost, c->st));
+    WCMG_CUDA(cudaStreamSynchronize(c->st));
+  }
+}
+
+template <typename R>
+static void pack_level(wcmg_ctx* c, int l, cplx<R>* out, const double2* ext, int nrhs) {
+  Level& L = c->L[l];
+  KPROF(c, WCMG_K_PACK, (double)L.n() * nrhs * (16.0 + sizeof(cplx<R>)), 0.0,
+        (L.fine ? launch_pack_fine<R>(out, ext, L.g.d_perm.p, L.g.V, nrhs, c->st)
+                : launch_pack_coarse<R>(out, ext, L.g.d_perm.p, L.g.V, L.nc, nrhs, c->st)));
+}
+template <typename R>
+static void unpack_level(wcmg_ctx* c, int l, double2* ext, const cplx<R>* in, int nrhs) {
+  Level& L = c->L[l];
+  KPROF(c, WCMG_K_PACK, (double)L.n() * nrhs * (16.0 + sizeof(cplx<R>)), 0.0,
+        (L.fine ? launch_unpack_fine<R>(ext, in, L.g.d_perm.p, L.g.V, nrhs, c->st)
+                : launch_unpack_coarse<R>(ext, in, L.g.d_perm.p, L.g.V, L.nc, nrhs, c->st)));
+}
+
+static bool inner64(const wcmg_ctx* c) { return c->p.inner_prec == WCMG_F64; }
+
+static void check_level(const wcmg_ctx* c, int l, int lo, int hi) {
+  if (l < lo || l > hi) throw Error(WCMG_ERR_ARG, "level out of range");
+  (void)c;
+}
+static void check_rhs(const wcmg_ctx* c, int nrhs) {
+  if (nrhs < 1 || nrhs > max_rhs_all(c)) throw Error(WCMG_ERR_ARG, "nrhs out of range (1 .. max_rhs)");
+}
+
+}  // namespace wcmg
+
+// =====================================================================
+// C-ABI
+// =====================================================================
+#define API_BEGIN(ctx)                    \
+  if (!(ctx)) return WCMG_ERR_ARG;        \
+  try {
+#define API_END(ctx)                                                     \
+  }                                                                      \
+  catch (const wcmg::Error& e) {                                         \
+    (ctx)->err = e.what();                                               \
+    (ctx)->prof.pend.clear();                                            \
+    return e.code;                                                       \
+  }                                                                      \
+  catch (const std::exception& e) {                                      \
+    (ctx)->err = e.what();                                               \
+    return WCMG_ERR_ARG;                                                 \
+  }                                                                      \
+  return WCMG_OK;
+
+extern "C" {
+
+int wcmg_default_params(wcmg_params* p) {
+  if (!p) return WCMG_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  for (int k = 0; k < 4; ++k) p->dims[k] = 4;
+  p->n_levels = 2;
+  for (int l = 0; l < WCMG_MAX_LEVELS - 1; ++l) {
+    for (int k = 0; k < 4; ++k) p->block[l][k] = 2;
+    p->nvec[l] = 8;
+  }
+  p->m0 = -0.1;
+  p->csw = 1.0;
+  p->smoother_steps = 4;
+  p->setup_init_sweeps = 3;
+  p->setup_refine_sweeps = 0;
+  p->coarse_restart = 20;
+  p->coarse_maxiter = 100;
+  p->coarse_tol = 0.05;
+  p->outer_restart = 20;
+  p->outer_maxiter = 1000;
+  p->outer_tol = 1e-10;
+  p->inner_prec = WCMG_F64;
+  p->coarse_link_prec = WCMG_F32;
+  p->max_rhs = 1;
+  p->profile = 0;
+  return WCMG_OK;
+}
+
+int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
+  if (!p || !out) return WCMG_ERR_ARG;
+  *out = nullptr;
+  wcmg_ctx* c = new (std::nothrow) wcmg_ctx();
+  if (!c) return WCMG_ERR_OOM;
+  c->p = *p;
+  try {
+    const int nl = p->n_levels;
+    if (nl < 2 || nl > WCMG_MAX_LEVELS) throw Error(WCMG_ERR_ARG, "n_levels must be 2..4");
+    if (p->inner_prec != WCMG_F64 && p->inner_prec != WCMG_F32) throw Error(WCMG_ERR_ARG, "inner_prec");
+    if (p->coarse_link_prec != WCMG_F32 && p->coarse_link_prec != WCMG_BF16 && p->coarse_link_prec != WCMG_F16 &&
+        p->coarse_link_prec != WCMG_F64)
+      throw Error(WCMG_ERR_ARG, "coarse_link_prec");
+    if (p->smoother_steps < 0 || p->coarse_restart < 1 || p->outer_restart < 1 || p->coarse_restart > 64 ||
+        p->outer_restart > 64 || p->max_rhs < 1 || p->max_rhs > 1024)
+      throw Error(WCMG_ERR_ARG, "solver parameters out of range");
+    c->L.resize(nl);
+    int dims[4];
+    for (int k = 0; k < 4; ++k) dims[k] = p->dims[k];
+    for (int l = 0; l < nl; ++l) {
+      Level& L = c->L[l];
+      for (int k = 0; k < 4; ++k) {
+        if (dims[k] < 1) throw Error(WCMG_ERR_ARG, "lattice extent < 1");
+        L.g.dims[k] = dims[k];
+      }
+      L.g.V = dims[0] * dims[1] * dims[2] * dims[3];
+      L.fine = l == 0;
+      L.nc = l == 0 ? 12 : 2 * p->nvec[l - 1];
+      if (l + 1 < nl) {
+        L.nvec = p->nvec[l];
+        if (L.nvec < 1 || L.nvec > 32) throw Error(WCMG_ERR_ARG, "nvec must be 1..32");
+        for (int k = 0; k < 4; ++k) {
+          const int b = p->block[l][k];
+          if (b < 1 || dims[k] % b) throw Error(WCMG_ERR_ARG, "extent not divisible by block");
+          L.g.b[k] = b;
+          dims[k] /= b;
+        }
+        L.g.bvol = L.g.b[0] * L.g.b[1] * L.g.b[2] * L.g.b[3];
+        if (L.g.bvol * (L.nc / 2) < L.nvec) throw Error(WCMG_ERR_ARG, "aggregate too small for nvec (rank)");
+        if (L.g.bvol * (L.nc / 2) > 2048) throw Error(WCMG_ERR_ARG, "aggregate panel larger than 2048 rows");
+      }
+    }
+    // storage orders, coarsest first
+    for (int l = nl - 1; l >= 0; --l) {
+      HostGeom& G = c->L[l].g;
+      G.perm.assign(G.V, 0);
+      G.inv.assign(G.V, 0);
+      for (int s = 0; s < G.V; ++s) {
+        int x[4];
+        coords(s, G.dims, x);
+        int stg;
+        if (l == nl - 1) {
+          stg = s;
+        } else {
+          const HostGeom& Cg = c->L[l + 1].g;
+          int xc[4], lo[4];
+          for (int k = 0; k < 4; ++k) { xc[k] = x[k] / G.b[k]; lo[k] = x[k] % G.b[k]; }
+          stg = Cg.inv[lexi(xc, Cg.dims)] * G.bvol + lexi(lo, G.b);
+        }
+        G.inv[s] = stg;
+        G.perm[stg] = s;
+      }
+      G.nbr.assign((size_t)8 * G.V, 0);
+      for (int st = 0; st < G.V; ++st) {
+        int x[4];
+        coords(G.perm[st], G.dims, x);
+        for (int mu = 0; mu < 4; ++mu)
+          for (int dir = 0; dir < 2; ++dir) {
+            int y[4] = {x[0], x[1], x[2], x[3]};
+            y[mu] = (y[mu] + (dir == 0 ? 1 : G.dims[mu] - 1)) % G.dims[mu];
+            G.nbr[(size_t)(2 * mu + dir) * G.V + st] = G.inv[lexi(y, G.dims)];
+          }
+      }
+      G.d_perm.ensure(G.V);
+      G.d_nbr.ensure((size_t)8 * G.V);
+      WCMG_CUDA(cudaMemcpy(G.d_perm.p, G.perm.data(), sizeof(int) * G.V, cudaMemcpyHostToDevice));
+      WCMG_CUDA(cudaMemcpy(G.d_nbr.p, G.nbr.data(), sizeof(int) * 8 * G.V, cudaMemcpyHostToDevice));
+    }
+    ensure_partials(c);
+    c->errflag.ensure((size_t)max_rhs_all(c) + 1);
+    c->prof.on = p->profile != 0;
+  } catch (const Error& e) {
+    int code = e.code;
+    delete c;
+    return code;
+  }
+  *out = c;
+  return WCMG_OK;
+}
+
+void wcmg_destroy(wcmg_ctx* ctx) { delete ctx; }
+
+const char* wcmg_last_error(const wcmg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int wcmg_set_gauge(wcmg_ctx* c, const void* U, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  Level& L = c->L[0];
+  const int V = L.g.V;
+  const double2* u = in_dev(c, U, (size_t)4 * V * 9 * 16, where, 0);
+  c->gauge64.ensure((size_t)36 * V);
+  c->gauge32.ensure((size_t)36 * V);
+  c->clover64.ensure((size_t)36 * V);
+  c->clover32.ensure((size_t)36 * V);
+  KPROF(c, WCMG_K_PACK, 36.0 * V * 32, 0, launch_pack_gauge<double>(c->gauge64.p, u, L.g.d_perm.p, V, c->st));
+  launch_pack_gauge<float>(c->gauge32.p, u, L.g.d_perm.p, V, c->st);
+  KPROF(c, WCMG_K_CLOVER, 36.0 * V * 16 * 5, 0,
+        launch_clover_build(c->clover64.p, c->gauge64.p, L.g.d_nbr.p, V, c->p.m0, c->p.csw, c->st));
+  launch_convert<double, float>(c->clover32.p, c->clover64.p, (long long)36 * V, c->st);
+  c->have_gauge = true;
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_get_clover(wcmg_ctx* c, void* C, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+  const int V = c->L[0].g.V;
+  const size_t bytes = (size_t)V * 144 * 16;
+  double2* o = out_dev(c, C, bytes, where, 1);
+  launch_clover_expand(o, c->clover64.p, c->L[0].g.d_perm.p, V, c->st);
+  out_finish(c, C, o, bytes, where);
+  API_END(c)
+}
+
+extern "C++" {
+template <typename R>
+static void apply_D_ext(wcmg_ctx* c, const double2* in, double2* out, int nrhs) {
+  Level& L = c->L[0];
+  cplx<R>* a = ws<R>(L, "io_a", nrhs);
+  cplx<R>* b = ws<R>(L, "io_b", nrhs);
+  pack_level<R>(c, 0, a, in, nrhs);
+  apply_op<R>(c, 0, b, a, nrhs);
+  unpack_level<R>(c, 0, out, b, nrhs);
+}
+}  // extern "C++"
+
+int wcmg_apply_D(wcmg_ctx* c, const void* in, void* out, int nrhs, int prec, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_rhs(c, nrhs);
+  const size_t bytes = (size_t)nrhs * c->L[0].n() * 16;
+  const double2* i = in_dev(c, in, bytes, where, 0);
+  double2* o = out_dev(c, out, bytes, where, 1);
+  if (prec == WCMG_F64) apply_D_ext<double>(c, i, o, nrhs);
+  else if (prec == WCMG_F32) apply_D_ext<float>(c, i, o, nrhs);
+  else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
+  out_finish(c, out, o, bytes, where);
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_set_nullvecs(wcmg_ctx* c, int level, const void* vecs, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 0, c->p.n_levels - 2);
+  Level& L = c->L[level];
+  const size_t bytes = (size_t)L.nvec * L.n() * 16;
+  const double2* v = in_dev(c, vecs, bytes, where, 0);
+  if (inner64(c)) {
+    L.raw64.ensure((size_t)L.nvec * L.n());
+    pack_level<double>(c, level, L.raw64.p, v, L.nvec);
+    build_P<double>(c, level);
+  } else {
+    L.raw32.ensure((size_t)L.nvec * L.n());
+    L.raw64.ensure((size_t)L.nvec * L.n());
+    pack_level<double>(c, level, L.raw64.p, v, L.nvec);
+    // orthonormalise from the FP64 input directly
+    L.v64.ensure((size_t)L.nvec * L.n());
+    copy_fields<double>(c, L.v64.p, L.raw64.p, (long long)L.nvec * L.n());
+    WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
+    launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st);
+    const int* e = read_ints(c, c->errflag.p, 1);
+    if (e[0]) throw Error(WCMG_ERR_NAN, "rank-deficient aggregate in block orthonormalisation");
+    launch_convert<double, float>(L.raw32.p, L.raw64.p, (long long)L.nvec * L.n(), c->st);
+    L.v32_valid = false;
+    L.have_P = true;
+  }
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_get_nullvecs(wcmg_ctx* c, int level, void* vecs, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 0, c->p.n_levels - 2);
+  Level& L = c->L[level];
+  if (!L.have_P) throw Error(WCMG_ERR_STATE, "prolongator of level not built");
+  const size_t bytes = (size_t)L.nvec * L.n() * 16;
+  double2* o = out_dev(c, vecs, bytes, where, 1);
+  unpack_level<double>(c, level, o, L.v64.p, L.nvec);
+  out_finish(c, vecs, o, bytes, where);
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_coarsen(wcmg_ctx* c, int level, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 0, c->p.n_levels - 2);
+  if (inner64(c)) coarsen<double>(c, level);
+  else coarsen<float>(c, level);
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_get_coarse_links(wcmg_ctx* c, int level, void* A, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 1, c->p.n_levels - 1);
+  Level& L = c->L[level];
+  if (!L.have_op) throw Error(WCMG_ERR_STATE, "coarse operator of level not built");
+  const int nb = L.nc;
+  const size_t bytes = (size_t)9 * L.g.V * nb * nb * 16;
+  double2* o = out_dev(c, A, bytes, where, 1);
+  if (L.op64) launch_unpack_links<double2>(o, L.L64.p, L.g.d_perm.p, L.g.V, nb, c->st);
+  else if (L.low_valid && c->p.coarse_link_prec == WCMG_BF16)
+    launch_unpack_links<bf16c>(o, L.Lbf.p, L.g.d_perm.p, L.g.V, nb, c->st);
+  else if (L.low_valid && c->p.coarse_link_prec == WCMG_F16)
+    launch_unpack_links<f16c>(o, L.Lh.p, L.g.d_perm.p, L.g.V, nb, c->st);
+  else launch_unpack_links<float2>(o, L.L32.p, L.g.d_perm.p, L.g.V, nb, c->st);
+  out_finish(c, A, o, bytes, where);
+  API_END(c)
+}
+
+int wcmg_set_coarse_links(wcmg_ctx* c, int level, const void* A, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 1, c->p.n_levels - 1);
+  Level& L = c->L[level];
+  const int nb = L.nc;
+  const size_t bytes = (size_t)9 * L.g.V * nb * nb * 16;
+  const double2* a = in_dev(c, A, bytes, where, 0);
+  const long long nl = (long long)L.g.V * nb * links_ld(nb);
+  L.L64.ensure(nl);
+  launch_pack_links<double2>(L.L64.p, a, L.g.d_perm.p, L.g.V, nb, c->st);
+  L.op64 = true;
+  L.L32_valid = false;
+  L.low_valid = false;
+  if (!inner64(c)) {
+    L.L32.ensure(nl);
+    launch_convert_links<double2, float2>(L.L32.p, L.L64.p, nl, c->st);
+    L.L32_valid = true;
+    if (c->p.coarse_link_prec == WCMG_BF16) {
+      L.Lbf.ensure(nl);
+      launch_convert_links<double2, bf16c>(L.Lbf.p, L.L64.p, nl, c->st);
+      L.low_valid = true;
+    } else if (c->p.coarse_link_prec == WCMG_F16) {
+      L.Lh.ensure(nl);
+      launch_convert_links<double2, f16c>(L.Lh.p, L.L64.p, nl, c->st);
+      L.low_valid = true;
+    }
+  }
+  L.have_op = true;
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  API_END(c)
+}
+
+extern "C++" {
+template <typename R>
+static void transfer_ext(wcmg_ctx* c, int level, const double2* in, double2* out, int nrhs, bool restrict_dir) {
+  Level& F = c->L[level];
+  Level& C = c->L[level + 1];
+  cplx<R>* f = ws<R>(F, "io_a", nrhs);
+  cplx<R>* q = ws<R>(C, "io_a", nrhs);
+  if (restrict_dir) {
+    pack_level<R>(c, level, f, in, nrhs);
+    restrict_op<R>(c, level, q, f, nrhs);
+    unpack_level<R>(c, level + 1, out, q, nrhs);
+  } else {
+    pack_level<R>(c, level + 1, q, in, nrhs);
+    prolong_op<R>(c, level, f, q, nrhs);
+    unpack_level<R>(c, level, out, f, nrhs);
+  }
+}
+}  // extern "C++"
+
+int wcmg_restrict(wcmg_ctx* c, int level, const void* fine, void* coarse, int nrhs, int prec, int where,
+                  void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 0, c->p.n_levels - 2);
+  check_rhs(c, nrhs);
+  const size_t bi = (size_t)nrhs * c->L[level].n() * 16, bo = (size_t)nrhs * c->L[level + 1].n() * 16;
+  const double2* i = in_dev(c, fine, bi, where, 0);
+  double2* o = out_dev(c, coarse, bo, where, 1);
+  if (prec == WCMG_F64) transfer_ext<double>(c, level, i, o, nrhs, true);
+  else if (prec == WCMG_F32) transfer_ext<float>(c, level, i, o, nrhs, true);
+  else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
+  out_finish(c, coarse, o, bo, where);
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_prolong(wcmg_ctx* c, int level, const void* coarse, void* fine, int nrhs, int prec, int where,
+                 void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 0, c->p.n_levels - 2);
+  check_rhs(c, nrhs);
+  const size_t bi = (size_t)nrhs * c->L[level + 1].n() * 16, bo = (size_t)nrhs * c->L[level].n() * 16;
+  const double2* i = in_dev(c, coarse, bi, where, 0);
+  double2* o = out_dev(c, fine, bo, where, 1);
+  if (prec == WCMG_F64) transfer_ext<double>(c, level, i, o, nrhs, false);
+  else if (prec == WCMG_F32) transfer_ext<float>(c, level, i, o, nrhs, false);
+  else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
+  out_finish(c, fine, o, bo, where);
+  c->prof.flush();
+  API_END(c)
+}
+
+extern "C++" {
+template <typename R>
+static void coarse_ext(wcmg_ctx* c, int level, const double2* in, double2* out, int nrhs) {
+  Level& L = c->L[level];
+  cplx<R>* a = ws<R>(L, "io_a", nrhs);
+  cplx<R>* b = ws<R>(L, "io_b", nrhs);
+  pack_level<R>(c, level, a, in, nrhs);
+  apply_op<R>(c, level, b, a, nrhs);
+  unpack_level<R>(c, level, out, b, nrhs);
+}
+}  // extern "C++"
+
+int wcmg_apply_coarse(wcmg_ctx* c, int level, const void* in, void* out, int nrhs, int prec, int where,
+                      void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 1, c->p.n_levels - 1);
+  check_rhs(c, nrhs);
+  const size_t bytes = (size_t)nrhs * c->L[level].n() * 16;
+  const double2* i = in_dev(c, in, bytes, where, 0);
+  double2* o = out_dev(c, out, bytes, where, 1);
+  if (prec == WCMG_F64) coarse_ext<double>(c, level, i, o, nrhs);
+  else if (prec == WCMG_F32) coarse_ext<float>(c, level, i, o, nrhs);
+  else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
+  out_finish(c, out, o, bytes, where);
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_setup(wcmg_ctx* c, const void* init_vecs, int where, void* stream, wcmg_stats* st) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+  if (!init_vecs) throw Error(WCMG_ERR_ARG, "init_vecs is required");
+  size_t tot = 0;
+  for (int l = 0; l + 1 < c->p.n_levels; ++l) tot += (size_t)c->L[l].nvec * c->L[l].n() * 16;
+  const double2* iv = in_dev(c, init_vecs, tot, where, 2);
+  if (st) std::memset(st, 0, sizeof(*st));
+  c->prof.flush();
+  c->prof.reset();
+  c->coarse_its = 0;
+  if (inner64(c)) setup_all<double>(c, iv, st);
+  else setup_all<float>(c, iv, st);
+  c->prof.flush();
+  if (st) {
+    std::memcpy(st->k, c->prof.k, sizeof(st->k));
+    st->coarse_iterations = c->coarse_its;
+  }
+  API_END(c)
+}
+
+int wcmg_mg_cycle(wcmg_ctx* c, const void* r, void* e, int nrhs, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_rhs(c, nrhs);
+  const size_t bytes = (size_t)nrhs * c->L[0].n() * 16;
+  const double2* i = in_dev(c, r, bytes, where, 0);
+  double2* o = out_dev(c, e, bytes, where, 1);
+  Level& L = c->L[0];
+  if (inner64(c)) {
+    double2* a = ws<double>(L, "io_a", nrhs);
+    double2* b = ws<double>(L, "io_b", nrhs);
+    pack_level<double>(c, 0, a, i, nrhs);
+    cycle<double>(c, 0, b, a, nrhs);
+    unpack_level<double>(c, 0, o, b, nrhs);
+  } else {
+    float2* a = ws<float>(L, "io_a", nrhs);
+    float2* b = ws<float>(L, "io_b", nrhs);
+    pack_level<float>(c, 0, a, i, nrhs);
+    cycle<float>(c, 0, b, a, nrhs);
+    unpack_level<float>(c, 0, o, b, nrhs);
+  }
+  out_finish(c, e, o, bytes, where);
+  c->prof.flush();
+  API_END(c)
+}
+
+extern "C++" {
+template <typename R>
+static int krylov_ext(wcmg_ctx* c, int level, int kind, const double2* b, double2* x, int nrhs, int sr, double tol,
+                      int maxiter) {
+  Level& L = c->L[level];
+  cplx<R>* a = ws<R>(L, "io_a", nrhs);
+  cplx<R>* y = ws<R>(L, "io_b", nrhs);
+  pack_level<R>(c, level, a, b, nrhs);
+  int its = 0;
+  if (kind == 0) {
+    mr<R>(c, level, y, a, nrhs, sr);
+    its = sr;
+  } else {
+    KrylovOut k = fgmres<R>(c, level, y, a, nrhs, sr, tol, maxiter, true, false, false);
+    its = k.iterations;
+  }
+  unpack_level<R>(c, level, x, y, nrhs);
+  return its;
+}
+}  // extern "C++"
+
+int wcmg_krylov(wcmg_ctx* c, int level, int kind, const void* b, void* x, int nrhs, int steps_or_restart, double tol,
+                int maxiter, int where, void* stream, int* iters_out) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 0, c->p.n_levels - 1);
+  check_rhs(c, nrhs);
+  if (kind != 0 && kind != 1) throw Error(WCMG_ERR_ARG, "kind must be 0 (MR) or 1 (GMRES)");
+  if (steps_or_restart < 1 || steps_or_restart > 64) throw Error(WCMG_ERR_ARG, "steps/restart out of range");
+  const size_t bytes = (size_t)nrhs * c->L[level].n() * 16;
+  const double2* i = in_dev(c, b, bytes, where, 0);
+  double2* o = out_dev(c, x, bytes, where, 1);
+  int its = inner64(c) ? krylov_ext<double>(c, level, kind, i, o, nrhs, steps_or_restart, tol, maxiter)
+                       : krylov_ext<float>(c, level, kind, i, o, nrhs, steps_or_restart, tol, maxiter);
+  out_finish(c, x, o, bytes, where);
+  if (iters_out) *iters_out = its;
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* stream, wcmg_stats* st) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_rhs(c, nrhs);
+  for (int l = 0; l + 1 < c->p.n_levels; ++l)
+    if (!c->L[l].have_P || !c->L[l + 1].have_op) throw Error(WCMG_ERR_STATE, "setup not done");
+  wcmg_stats local;
+  if (!st) st = &local;
+  const double ms_i = st->ms_setup_init, ms_r = st->ms_setup_refine;
+  std::memset(st, 0, sizeof(*st));
+  st->ms_setup_init = ms_i;
+  st->ms_setup_refine = ms_r;
+  c->prof.flush();
+  c->prof.reset();
+  c->coarse_its = 0;
+  auto t0 = std::chrono::steady_clock::now();
+  Level& L = c->L[0];
+  const size_t bytes = (size_t)nrhs * L.n() * 16;
+  const double2* bi = in_dev(c, b, bytes, where, 0);
+  double2* xo = out_dev(c, x, bytes, where, 1);
+  double2* b64 = ws<double>(L, "sv_b", nrhs);
+  double2* x64 = ws<double>(L, "sv_x", nrhs);
+  pack_level<double>(c, 0, b64, bi, nrhs);
+  if (inner64(c)) solve_f64(c, x64, b64, nrhs, st);
+  else solve_mixed(c, x64, b64, nrhs, st);
+  st->true_residual = true_residual(c, x64, b64, nrhs);
+  st->converged = st->true_residual <= c->p.outer_tol;
+  unpack_level<double>(c, 0, xo, x64, nrhs);
+  out_finish(c, x, xo, bytes, where);
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  auto t1 = std::chrono::steady_clock::now();
+  st->ms_solve = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  c->prof.flush();
+  std::memcpy(st->k, c->prof.k, sizeof(st->k));
+  st->coarse_iterations = c->coarse_its;
+  if (!st->converged) {
+    c->err = "outer solver reached outer_maxiter";
+    return WCMG_ERR_NOT_CONVERGED;
+  }
+  API_END(c)
+}
+
+int wcmg_save_setup(wcmg_ctx* c, const char* path) {
+  API_BEGIN(c)
+  if (!path) throw Error(WCMG_ERR_ARG, "path");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) throw Error(WCMG_ERR_ARG, std::string("cannot open ") + path);
+  const char magic[8] = {'W', 'C', 'M', 'G', 'S', 'E', 'T', '1'};
+  std::fwrite(magic, 1, 8, f);
+  std::fwrite(&c->p.n_levels, sizeof(int), 1, f);
+  std::fwrite(c->p.dims, sizeof(int), 4, f);
+  std::fwrite(c->p.nvec, sizeof(int), WCMG_MAX_LEVELS - 1, f);
+  std::vector<double2> h;
+  for (int l = 0; l + 1 < c->p.n_levels; ++l) {
+    Level& L = c->L[l];
+    if (!L.have_P || !c->L[l + 1].have_op) { std::fclose(f); throw Error(WCMG_ERR_STATE, "setup not done"); }
+    const size_t nv = (size_t)L.nvec * L.n();
+    h.resize(nv);
+    double2* d = ws<double>(L, "io_a", L.nvec);
+    if (L.fine) launch_unpack_fine<double>(d, L.v64.p, L.g.d_perm.p, L.g.V, L.nvec, c->st);
+    else launch_unpack_coarse<double>(d, L.v64.p, L.g.d_perm.p, L.g.V, L.nc, L.nvec, c->st);
+    WCMG_CUDA(cudaMemcpyAsync(h.data(), d, nv * 16, cudaMemcpyDeviceToHost, c->st));
+    WCMG_CUDA(cudaStreamSynchronize(c->st));
+    std::fwrite(h.data(), 16, nv, f);
+  }
+  for (int l = 1; l < c->p.n_levels; ++l) {
+    Level& L = c->L[l];
+    const int nb = L.nc;
+    const size_t na = (size_t)9 * L.g.V * nb * nb;
+    h.resize(na);
+    DevBuf<double2> tmp;
+    tmp.ensure(na);
+    if (L.op64) launch_unpack_links<double2>(tmp.p, L.L64.p, L.g.d_perm.p, L.g.V, nb, c->st);
+    else launch_unpack_links<float2>(tmp.p, L.L32.p, L.g.d_perm.p, L.g.V, nb, c->st);
+    WCMG_CUDA(cudaMemcpyAsync(h.data(), tmp.p, na * 16, cudaMemcpyDeviceToHost, c->st));
+    WCMG_CUDA(cudaStreamSynchronize(c->st));
+    std::fwrite(h.data(), 16, na, f);
+  }
+  std::fclose(f);
+  API_END(c)
+}
+
+int wcmg_load_setup(wcmg_ctx* c, const char* path) {
+  API_BEGIN(c)
+  if (!path) throw Error(WCMG_ERR_ARG, "path");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) throw Error(WCMG_ERR_ARG, std::string("cannot open ") + path);
+  char magic[8];
+  int nl, dims[4], nvec[WCMG_MAX_LEVELS - 1];
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "WCMGSET1", 8) == 0 &&
+            std::fread(&nl, sizeof(int), 1, f) == 1 && std::fread(dims, sizeof(int), 4, f) == 4 &&
+            std::fread(nvec, sizeof(int), WCMG_MAX_LEVELS - 1, f) == WCMG_MAX_LEVELS - 1;
+  ok = ok && nl == c->p.n_levels && std::memcmp(dims, c->p.dims, sizeof(dims)) == 0;
+  for (int l = 0; ok && l + 1 < nl; ++l) ok = nvec[l] == c->p.nvec[l];
+  if (!ok) { std::fclose(f); throw Error(WCMG_ERR_ARG, "setup file does not match the context"); }
+  std::vector<double2> h;
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level& L = c->L[l];
+    const size_t nv = (size_t)L.nvec * L.n();
+    h.resize(nv);
+    if (std::fread(h.data(), 16, nv, f) != nv) { std::fclose(f); throw Error(WCMG_ERR_ARG, "truncated setup file"); }
+    double2* d = ws<double>(L, "io_a", L.nvec);
+    WCMG_CUDA(cudaMemcpyAsync(d, h.data(), nv * 16, cudaMemcpyHostToDevice, c->st));
+    L.v64.ensure(nv);
+    if (L.fine) launch_pack_fine<double>(L.v64.p, d, L.g.d_perm.p, L.g.V, L.nvec, c->st);
+    else launch_pack_coarse<double>(L.v64.p, d, L.g.d_perm.p, L.g.V, L.nc, L.nvec, c->st);
+    L.raw64.ensure(nv);
+    copy_fields<double>(c, L.raw64.p, L.v64.p, (long long)nv);
+    if (!inner64(c)) {
+      L.raw32.ensure(nv);
+      launch_convert<double, float>(L.raw32.p, L.v64.p, (long long)nv, c->st);
+    }
+    L.v32_valid = false;
+    L.have_P = true;
+    WCMG_CUDA(cudaStreamSynchronize(c->st));
+  }
+  for (int l = 1; l < nl; ++l) {
+    Level& L = c->L[l];
+    const int nb = L.nc;
+    const size_t na = (size_t)9 * L.g.V * nb * nb;
+    h.resize(na);
+    if (std::fread(h.data(), 16, na, f) != na) { std::fclose(f); throw Error(WCMG_ERR_ARG, "truncated setup file"); }
+    int rc = wcmg_set_coarse_links(c, l, h.data(), WCMG_HOST, c->st);
+    if (rc) { std::fclose(f); throw Error(rc, c->err); }
+    if (!inner64(c)) {
+      // links were produced in FP32: keep FP32 arithmetic on the FP32-rounded values
+      L.op64 = false;
+    }
+  }
+  std::fclose(f);
+  API_END(c)
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libwcmg.so (include/wcmg.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Functions keep the C names; ``Context`` bundles a context handle with
+the same calls for convenience.  Buffers may be numpy arrays (host memory,
+complex128, C-contiguous) or torch CUDA tensors (device memory, complex128,
+contiguous); the binding passes the pointer and the matching ``where`` flag.
+
+Importing this module raises ImportError when the built library is missing:
+there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwcmg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "wcmg.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run paper_1904_08678_gb300/build.py (or __graft_entry__.build())")
+_lib = ctypes.CDLL(LIB_PATH)
+
+MAX_LEVELS = 4
+NKCLASS = 12
+OK, ERR_ARG, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7
+F64, F32, BF16, F16 = 0, 1, 2, 3
+HOST, DEVICE = 0, 1
+KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen", "clover", "pack", "krylov",
+          "dslash64", "other"]
+
+
+class wcmg_params(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int * 4),
+        ("n_levels", ctypes.c_int),
+        ("block", (ctypes.c_int * 4) * (MAX_LEVELS - 1)),
+        ("nvec", ctypes.c_int * (MAX_LEVELS - 1)),
+        ("m0", ctypes.c_double),
+        ("csw", ctypes.c_double),
+        ("smoother_steps", ctypes.c_int),
+        ("setup_init_sweeps", ctypes.c_int),
+        ("setup_refine_sweeps", ctypes.c_int),
+        ("coarse_restart", ctypes.c_int),
+        ("coarse_maxiter", ctypes.c_int),
+        ("coarse_tol", ctypes.c_double),
+        ("outer_restart", ctypes.c_int),
+        ("outer_maxiter", ctypes.c_int),
+        ("outer_tol", ctypes.c_double),
+        ("inner_prec", ctypes.c_int),
+        ("coarse_link_prec", ctypes.c_int),
+        ("max_rhs", ctypes.c_int),
+        ("profile", ctypes.c_int),
+    ]
+
+
+class wcmg_kstat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+
+class wcmg_stats(ctypes.Structure):
+    _fields_ = [
+        ("outer_iterations", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("true_residual", ctypes.c_double),
+        ("coarse_iterations", ctypes.c_longlong),
+        ("ms_setup_init", ctypes.c_double),
+        ("ms_setup_refine", ctypes.c_double),
+        ("ms_solve", ctypes.c_double),
+        ("k", wcmg_kstat * NKCLASS),
+    ]
+
+    def kernels(self):
+        return {KCLASS[i]: dict(launches=self.k[i].launches, ms=self.k[i].ms, bytes=self.k[i].bytes,
+                                flops=self.k[i].flops) for i in range(NKCLASS) if self.k[i].launches}
+
+
+_vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_PCTX = ctypes.c_void_p
+_SIGS = {
+    "wcmg_default_params": ([ctypes.POINTER(wcmg_params)], _i),
+    "wcmg_create": ([ctypes.POINTER(wcmg_params), ctypes.POINTER(_PCTX)], _i),
+    "wcmg_destroy": ([_PCTX], None),
+    "wcmg_last_error": ([_PCTX], ctypes.c_char_p),
+    "wcmg_set_gauge": ([_PCTX, _vp, _i, _vp], _i),
+    "wcmg_get_clover": ([_PCTX, _vp, _i, _vp], _i),
+    "wcmg_apply_D": ([_PCTX, _vp, _vp, _i, _i, _i, _vp], _i),
+    "wcmg_set_nullvecs": ([_PCTX, _i, _vp, _i, _vp], _i),
+    "wcmg_get_nullvecs": ([_PCTX, _i, _vp, _i, _vp], _i),
+    "wcmg_coarsen": ([_PCTX, _i, _vp], _i),
+    "wcmg_get_coarse_links": ([_PCTX, _i, _vp, _i, _vp], _i),
+    "wcmg_set_coarse_links": ([_PCTX, _i, _vp, _i, _vp], _i),
+    "wcmg_restrict": ([_PCTX, _i, _vp, _vp, _i, _i, _i, _vp], _i),
+    "wcmg_prolong": ([_PCTX, _i, _vp, _vp, _i, _i, _i, _vp], _i),
+    "wcmg_apply_coarse": ([_PCTX, _i, _vp, _vp, _i, _i, _i, _vp], _i),
+    "wcmg_setup": ([_PCTX, _vp, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
+    "wcmg_mg_cycle": ([_PCTX, _vp, _vp, _i, _i, _vp], _i),
+    "wcmg_krylov": ([_PCTX, _i, _i, _vp, _vp, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_i)], _i),
+    "wcmg_solve": ([_PCTX, _vp, _vp, _i, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
+    "wcmg_save_setup": ([_PCTX, ctypes.c_char_p], _i),
+    "wcmg_load_setup": ([_PCTX, ctypes.c_char_p], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+    globals()[_name] = _f
+
+
+def header_functions():
+    """Names of the functions include/wcmg.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(wcmg_\w+)\s*\(", txt, re.M)))
+
+
+def exported(name: str) -> bool:
+    return hasattr(_lib, name)
+
+
+class WcmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"wcmg error {code}: {msg}")
+        self.code = code
+
+
+def _buf(a, writable=False):
+    """(pointer, where) of a numpy host array or a torch CUDA tensor (complex128)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.complex128 or not a.flags.c_contiguous:
+            raise TypeError("host buffers must be C-contiguous complex128 numpy arrays")
+        if writable and not a.flags.writeable:
+            raise TypeError("output array is read-only")
+        return a.ctypes.data, HOST
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous() or str(a.dtype) != "torch.complex128":
+            raise TypeError("device buffers must be contiguous complex128 torch tensors")
+        return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def default_params(**kw) -> wcmg_params:
+    p = wcmg_params()
+    wcmg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("dims", "nvec"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = int(x)
+        elif k == "blocks":
+            for l, b in enumerate(v):
+                for i, x in enumerate(b):
+                    p.block[l][i] = int(x)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Context:
+    """Owns one wcmg_ctx; methods map one-to-one onto the C calls."""
+
+    def __init__(self, params: wcmg_params):
+        self.params = params
+        h = _PCTX()
+        rc = wcmg_create(ctypes.byref(params), ctypes.byref(h))
+        if rc != OK:
+            raise WcmgError(rc, "wcmg_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            wcmg_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _check(self, rc, allow=()):
+        if rc != OK and rc not in allow:
+            raise WcmgError(rc, wcmg_last_error(self.h).decode())
+        return rc
+
+    def set_gauge(self, U, stream=None):
+        p, w = _buf(U)
+        return self._check(wcmg_set_gauge(self.h, p, w, _stream(stream)))
+
+    def get_clover(self, C, stream=None):
+        p, w = _buf(C, True)
+        return self._check(wcmg_get_clover(self.h, p, w, _stream(stream)))
+
+    def apply_D(self, inp, out, nrhs=1, prec=F64, stream=None):
+        pi, wi = _buf(inp)
+        po, wo = _buf(out, True)
+        assert wi == wo
+        return self._check(wcmg_apply_D(self.h, pi, po, nrhs, prec, wi, _stream(stream)))
+
+    def set_nullvecs(self, level, vecs, stream=None):
+        p, w = _buf(vecs)
+        return self._check(wcmg_set_nullvecs(self.h, level, p, w, _stream(stream)))
+
+    def get_nullvecs(self, level, vecs, stream=None):
+        p, w = _buf(vecs, True)
+        return self._check(wcmg_get_nullvecs(self.h, level, p, w, _stream(stream)))
+
+    def coarsen(self, level, stream=None):
+        return self._check(wcmg_coarsen(self.h, level, _stream(stream)))
+
+    def get_coarse_links(self, level, A, stream=None):
+        p, w = _buf(A, True)
+        return self._check(wcmg_get_coarse_links(self.h, level, p, w, _stream(stream)))
+
+    def set_coarse_links(self, level, A, stream=None):
+        p, w = _buf(A)
+        return self._check(wcmg_set_coarse_links(self.h, level, p, w, _stream(stream)))
+
+    def restrict(self, level, fine, coarse, nrhs=1, prec=F64, stream=None):
+        pi, wi = _buf(fine)
+        po, wo = _buf(coarse, True)
+        assert wi == wo
+        return self._check(wcmg_restrict(self.h, level, pi, po, nrhs, prec, wi, _stream(stream)))
+
+    def prolong(self, level, coarse, fine, nrhs=1, prec=F64, stream=None):
+        pi, wi = _buf(coarse)
+        po, wo = _buf(fine, True)
+        assert wi == wo
+        return self._check(wcmg_prolong(self.h, level, pi, po, nrhs, prec, wi, _stream(stream)))
+
+    def apply_coarse(self, level, inp, out, nrhs=1, prec=F64, stream=None):
+        pi, wi = _buf(inp)
+        po, wo = _buf(out, True)
+        assert wi == wo
+        return self._check(wcmg_apply_coarse(self.h, level, pi, po, nrhs, prec, wi, _stream(stream)))
+
+    def setup(self, init_vecs, stream=None):
+        p, w = _buf(init_vecs)
+        st = wcmg_stats()
+        self._check(wcmg_setup(self.h, p, w, _stream(stream), ctypes.byref(st)))
+        return st
+
+    def mg_cycle(self, r, e, nrhs=1, stream=None):
+        pi, wi = _buf(r)
+        po, wo = _buf(e, True)
+        assert wi == wo
+        return self._check(wcmg_mg_cycle(self.h, pi, po, nrhs, wi, _stream(stream)))
+
+    def krylov(self, level, kind, b, x, nrhs=1, steps_or_restart=4, tol=0.0, maxiter=100, stream=None):
+        pi, wi = _buf(b)
+        po, wo = _buf(x, True)
+        assert wi == wo
+        its = ctypes.c_int(0)
+        self._check(wcmg_krylov(self.h, level, kind, pi, po, nrhs, steps_or_restart, tol, maxiter, wi,
+                                _stream(stream), ctypes.byref(its)))
+        return its.value
+
+    def solve(self, b, x, nrhs=1, stream=None, allow_not_converged=False):
+        pi, wi = _buf(b)
+        po, wo = _buf(x, True)
+        assert wi == wo
+        st = wcmg_stats()
+        self._check(wcmg_solve(self.h, pi, po, nrhs, wi, _stream(stream), ctypes.byref(st)),
+                    allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return st
+
+    def save_setup(self, path):
+        return self._check(wcmg_save_setup(self.h, path.encode()))
+
+    def load_setup(self, path):
+        return self._check(wcmg_load_setup(self.h, path.encode()))
