@@ -1,0 +1,471 @@
+"""Benchmark: Wilson-clover multigrid time-to-solution on one GB300 per rank.
+
+One step = one full pass of the hot path on the 16^3x32 two-level workload:
+set the gauge field (clover term built on the device), initial setup (3 MR(4)
+sweeps over 24 near-null vectors), 2 iterative-refinement sweeps (multigrid
+cycle over all 24 vectors), and the FGMRES(20) solve of D x = b to a true
+relative residual of 1e-10.  `value` is the time-to-solution in seconds
+(device CUDA events on the call's stream, max over ranks), inputs resident in
+HBM, L2 flushed (256 MiB write) between steps.  `e2e` is the same step through
+the same C-ABI calls with pinned host buffers, copies included.
+
+Multi-GPU: the path does not shard (one lattice per GPU): N ranks run
+independent replicas; the step time is the max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--inner f32|f64] [--links f32|bf16|f16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+WORKLOAD = dict(
+    workload="wilson-clover 2-level MG, 16^3x32, eps 0.25, m0 -0.2, csw 1.0, blocks 4^4 -> 4^3x8, "
+             "Nvec 24 (nbasis 48), 3 initial + 2 refinement sweeps, MR(4) smoother, GMRES(20) coarse to 0.05, "
+             "FGMRES(20) to 1e-10, 1 Gaussian rhs",
+    dims=(16, 16, 16, 32), eps=0.25, m0=-0.2, csw=1.0, blocks=[(4, 4, 4, 4)], nvec=[24],
+    init_sweeps=3, refine_sweeps=2, gauge_seed=1002, source_seed=0,
+)
+# Reduced-volume sample of the same workload for the CPU oracle (same blocks,
+# Nvec and parameters; time scaled by the volume ratio).
+ORACLE_SAMPLE_DIMS = (8, 8, 8, 8)
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
+# for the kernel sources it was taken on (sha256 prefix of csrc/*.cu, *.cuh, *.h).
+NCU_TRAFFIC = {}  # {"<class>": {"src": "<hash>", "bytes_per_launch": B, "profile": "profiles/<file>"}}
+
+KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen", "clover", "pack", "krylov",
+          "dslash64", "other"]
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1904_08678_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), float(m["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+# FP64 / FP32 non-tensor ALU peaks of GB300 derived from unit counts and the
+# maximum SM clock: 152 SMs x 2070 MHz x 2 flop/FMA x (2 FP64 / 128 FP32) FMA per SM per clock.
+ALU_PEAK_TFLOPS = {"f64": 152 * 2.070e9 * 2 * 2 / 1e12, "f32": 152 * 2.070e9 * 2 * 128 / 1e12}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend, init_method="env://")
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity at world size 1)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- inputs
+def make_inputs(cfg):
+    from paper_1904_08678_gb300 import inputs
+    dims = cfg["dims"]
+    U = inputs.random_gauge(dims, cfg["eps"], cfg["gauge_seed"])
+    iv = inputs.setup_vectors(dims, 12, cfg["nvec"][0], 0, cfg["gauge_seed"])
+    b = inputs.source(dims, cfg["source_seed"])
+    return U, iv, b
+
+
+def params(wcmg, cfg, inner, links, profile=0):
+    p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
+                            setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
+                            n_levels=len(cfg["blocks"]) + 1, max_rhs=1, profile=profile)
+    p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
+    p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
+    return p
+
+
+def add_stats(acc, st):
+    for i in range(len(KCLASS)):
+        k = st.k[i]
+        a = acc.setdefault(KCLASS[i], [0, 0.0, 0.0, 0.0])
+        a[0] += k.launches
+        a[1] += k.ms
+        a[2] += k.bytes
+        a[3] += k.flops
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_1904_08678_gb300 import wcmg
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    cfg = WORKLOAD
+    U, iv, b = make_inputs(cfg)
+    Ud = torch.from_numpy(U).to(dev)
+    ivd = torch.from_numpy(iv).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctx = wcmg.Context(params(wcmg, cfg, args.inner, args.links, profile=-1))
+
+    def step(x, U_, iv_, b_):
+        ctx.set_gauge(U_, stream)
+        s1 = ctx.setup(iv_, stream)
+        s2 = ctx.solve(b_, x, stream=stream)
+        return s1, s2
+
+    # warm-up, all kernel classes timed: find the dominant class
+    acc = {}
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        s1, s2 = step(xd, Ud, ivd, bd)
+        add_stats(acc, s1)
+        add_stats(acc, s2)
+    torch.cuda.synchronize()
+    dominant = max(acc, key=lambda k: acc[k][1])
+    mask = (1 << KCLASS.index(dominant)) | (1 << KCLASS.index("coarse"))
+    ctx.set_profile(mask)
+
+    # timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    acc = {}
+    its, res, launches = [], [], 0
+    phases = {"setup_init": [], "setup_refine": [], "solve": []}
+    barrier(dist, local)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            starts[i].record(stream)
+            s1, s2 = step(xd, Ud, ivd, bd)
+            ends[i].record(stream)
+            add_stats(acc, s1)
+            add_stats(acc, s2)
+            its.append(s2.outer_iterations)
+            res.append(s2.true_residual)
+            launches += s1.kernel_launches + s2.kernel_launches + 2  # + set_gauge's pack/clover kernels
+            phases["setup_init"].append(s1.ms_setup_init)
+            phases["setup_refine"].append(s1.ms_setup_refine)
+            phases["solve"].append(s2.ms_solve)
+        torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(dist, local)
+    step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+    ms_local = sum(step_ms) / len(step_ms)
+    ms = max_over_ranks(dist, ms_local, dev)
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel class (live CUDA-event timing in the timed region)
+    hbm, bf16, peak_kind = peaks()
+    d = acc[dominant]
+    bound = "hbm"
+    if dominant in ("dslash64", "ortho"):
+        bound = "alu"
+    if bound == "hbm":
+        achieved = d[2] / (d[1] * 1e-3) / 1e9
+        peak, unit = hbm, "GB/s"
+    else:
+        achieved = d[3] / (d[1] * 1e-3) / 1e12
+        peak, unit = ALU_PEAK_TFLOPS["f64"], "TFLOP/s"
+    tr = NCU_TRAFFIC.get(dominant)
+    traffic = tr["bytes_per_launch"] if tr and tr["src"] == src_hash() else None
+    roofline = {"kernel": dominant, "bound": bound, "achieved": round(achieved, 2), "peak": peak, "unit": unit,
+                "frac": round(achieved / peak, 4),
+                "peak_source": f"{'MEASURED_PEAKS.json hbm_gbs (of measured)' if (bound == 'hbm' and peak_kind == 'measured') else ('fallback' if bound == 'hbm' else 'FP64 unit count x max SM clock (derived)')}",
+                "traffic": traffic, "launches": d[0], "avg_launch_us": round(d[1] / max(d[0], 1) * 1e3, 2),
+                "algorithmic_bytes_per_launch": d[2] / max(d[0], 1), "share_of_step": round(d[1] / (ms * args.steps), 4)}
+    co = acc["coarse"]
+    coarse_live = {"launches": co[0], "avg_launch_us": round(co[1] / max(co[0], 1) * 1e3, 2),
+                   "GB/s": round(co[2] / (co[1] * 1e-3) / 1e9, 1) if co[1] else None,
+                   "frac_of_hbm": round(co[2] / (co[1] * 1e-3) / 1e9 / hbm, 4) if co[1] else None}
+
+    # isolated coarse stencil (1 rhs), L2 flushed before every apply
+    coarse_iso = measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg)
+
+    # e2e: same step through the C-ABI with pinned host buffers
+    Uh = torch.from_numpy(U).pin_memory()
+    ivh = torch.from_numpy(iv).pin_memory()
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    ctx.set_profile(0)
+    e_ms = []
+    for i in range(args.steps):
+        flush.fill_(2)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(xh, Uh, ivh, bh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms.append(e0.elapsed_time(e1))
+    e2e_ms = max_over_ranks(dist, sum(e_ms) / len(e_ms), dev)
+    h2d = U.nbytes + iv.nbytes + b.nbytes
+    d2h = b.nbytes
+
+    # plain FP64 GPU multigrid on the same field, source and setup parameters (one step)
+    fp64 = None
+    if args.inner != "f64" and not args.no_fp64_compare:
+        ctx64 = wcmg.Context(params(wcmg, cfg, "f64", "f32", profile=0))
+        x64 = torch.zeros_like(bd)
+        ctx64.set_gauge(Ud, stream)
+        ctx64.setup(ivd, stream)
+        ctx64.solve(bd, x64, stream=stream)  # warm
+        flush.fill_(3)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ctx64.set_gauge(Ud, stream)
+        s1 = ctx64.setup(ivd, stream)
+        s2 = ctx64.solve(bd, x64, stream=stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"time_to_solution_s": round(f0.elapsed_time(f1) / 1e3, 4), "outer_iterations": s2.outer_iterations,
+                "true_residual": s2.true_residual, "setup_init_ms": round(s1.ms_setup_init, 2),
+                "setup_refine_ms": round(s1.ms_setup_refine, 2), "solve_ms": round(s2.ms_solve, 2)}
+        ctx64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+
+    if rank == 0:
+        med = lambda v: round(statistics.median(v), 2)
+        line = {
+            "metric": "time_to_solution_1e-10", "value": round(ms / 1e3, 5), "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.inner == "f32" else "f64", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "dims": list(cfg["dims"]), "inner_prec": args.inner,
+                       "coarse_links": args.links if args.inner == "f32" else "f64",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
+                       "gauge": "U = exp(i eps X), X = sum_a xi_a lambda_a, seed 1002"},
+            "outer_iterations": its[-1], "true_residual": max(res), "phases_ms": {k: med(v) for k, v in phases.items()},
+            "solves_per_s": round(sum_over_ranks(dist, args.steps, dev) / (ms * args.steps / 1e3), 3),
+            "roofline": roofline, "coarse_stencil": {"in_solve": coarse_live, "isolated": coarse_iso},
+            "e2e": {"value": round(e2e_ms / 1e3, 5), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
+            "clocks": clocks, "wall_s_timed": round(t_wall, 3), "fp64_inner": fp64, "cpu_baseline": cpu,
+            "kernel_shares": {k: round(v[1] / (ms * args.steps), 4) for k, v in acc.items() if v[1] > 0},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg, reps=200):
+    """K4 alone: 1 rhs on the workload's coarse operator, L2 flushed before each apply."""
+    nb = 2 * cfg["nvec"][0]
+    cd = [L // b for L, b in zip(cfg["dims"], cfg["blocks"][0])]
+    Vc = int(np.prod(cd))
+    from paper_1904_08678_gb300 import inputs
+    phi = torch.from_numpy(inputs.complex_gaussian(5, 5, (1, Vc, nb))).to(dev)
+    out = torch.zeros_like(phi)
+    ctx.set_profile(1 << KCLASS.index("coarse"))
+    prec = wcmg.F32 if ctx.params.inner_prec == wcmg.F32 else wcmg.F64
+    for _ in range(5):
+        ctx.apply_coarse(1, phi, out, prec=prec, stream=stream)
+    k0 = ctx.kstats()["coarse"]
+    for _ in range(reps):
+        flush.fill_(5)
+        ctx.apply_coarse(1, phi, out, prec=prec, stream=stream)
+    torch.cuda.synchronize()
+    k1 = ctx.kstats()["coarse"]
+    n = k1["launches"] - k0["launches"]
+    kms = (k1["ms"] - k0["ms"]) / max(n, 1)
+    kbytes = (k1["bytes"] - k0["bytes"]) / max(n, 1)
+    link_b = {"f32": 8, "bf16": 4, "f16": 4}[{wcmg.F32: "f32", wcmg.BF16: "bf16", wcmg.F16: "f16"}.get(
+        ctx.params.coarse_link_prec, "f32")] if prec == wcmg.F32 else 16
+    vec_b = 8 if prec == wcmg.F32 else 16
+    algo = Vc * (9 * nb * nb * link_b + 2 * nb * vec_b)
+    return {"sites": Vc, "nbasis": nb, "link_bytes": link_b, "algorithmic_bytes": algo, "launches": n,
+            "kernel_us": round(kms * 1e3, 2), "GB/s": round(kbytes / (kms * 1e-3) / 1e9, 1),
+            "frac_of_hbm": round(kbytes / (kms * 1e-3) / 1e9 / hbm, 4), "l2": "flushed before every apply"}
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample():
+    """The FP64 numpy oracle on a reduced-volume sample of the workload, scaled by volume."""
+    from oracle.lattice import to_grid
+    from oracle.mg import MGParams, Multigrid
+    from oracle.wilson import WilsonClover
+    from paper_1904_08678_gb300 import inputs
+    cfg = WORKLOAD
+    dims = ORACLE_SAMPLE_DIMS
+    V = int(np.prod(dims))
+    U = inputs.random_gauge(dims, cfg["eps"], cfg["gauge_seed"])
+    iv = inputs.setup_vectors(dims, 12, cfg["nvec"][0], 0, cfg["gauge_seed"])
+    b = inputs.source(dims, cfg["source_seed"])
+    c0, t0 = time.process_time(), time.perf_counter()
+    D = WilsonClover(U, dims, cfg["m0"], cfg["csw"])
+    mg = Multigrid(D, MGParams(blocks=cfg["blocks"], nvecs=cfg["nvec"], init_sweeps=cfg["init_sweeps"],
+                               refine_sweeps=cfg["refine_sweeps"]), [[to_grid(v, dims) for v in iv]])
+    x, info = mg.solve(to_grid(b[0].reshape(V, 12), dims))
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    scale = int(np.prod(cfg["dims"])) / V
+    return {"value": round(wall * scale, 2), "unit": "s", "cores": max(1, round(cpu / wall)), "kind": "oracle",
+            "sample": f"full oracle setup+solve on {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} (1/{int(scale)} of the "
+                      f"volume, same blocks/Nvec/sweeps/tolerances): {wall:.1f} s wall, {info.iterations} outer its, "
+                      f"scaled x{int(scale)} by volume", "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args, rank, world):
+    if world > 1:
+        dist = dist_init(world, "gloo")
+        if rank != 0:
+            barrier(dist)
+            dist.destroy_process_group()
+            return
+    else:
+        dist = None
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample()
+        if i >= args.warmup:
+            vals.append(r)
+    v = sum(r["value"] for r in vals) / len(vals)
+    line = {"impl": "reference", "metric": "time_to_solution_1e-10", "value": round(v, 2), "unit": "s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["workload"], "dims": list(WORKLOAD["dims"]), "inner_prec": "f64"},
+            "cpu_baseline": {"value": round(v, 2), "unit": "s", "cores": vals[-1]["cores"], "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": round(v, 2), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        barrier(dist)
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--inner", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--links", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

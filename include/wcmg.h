@@ -80,7 +80,9 @@ typedef struct wcmg_params {
   int coarse_link_prec;                 /* storage of coarse links when inner_prec = F32:
                                            WCMG_F32, WCMG_BF16 or WCMG_F16 (FP32 accumulate) */
   int max_rhs;                          /* largest nrhs of any call */
-  int profile;                          /* nonzero: time every kernel launch with CUDA events */
+  int profile;                          /* bitmask of (1 << wcmg_kclass): kernel classes whose
+                                           launches are timed with CUDA events (-1: all, 0: none);
+                                           launch, byte and flop counts are always kept */
 } wcmg_params;
 
 /* Per-kernel-class counters, filled when params.profile != 0. */
@@ -98,6 +100,7 @@ typedef struct wcmg_stats {
   int converged;                        /* 1 if every rhs met outer_tol */
   double true_residual;                 /* max over rhs of ||b - D x|| / ||b|| (FP64) */
   long long coarse_iterations;          /* coarsest-level GMRES iterations, summed */
+  long long kernel_launches;            /* CUDA kernels this library launched during the call */
   double ms_setup_init;                 /* wall time of the phases (host clock around synced work) */
   double ms_setup_refine;
   double ms_solve;
@@ -174,6 +177,12 @@ int wcmg_krylov(wcmg_ctx* ctx, int level, int kind, const void* b, void* x, int 
  * and the FP64 residual is recomputed at every restart (defect correction).
  * Returns ERR_NOT_CONVERGED (x and *st valid) at outer_maxiter. */
 int wcmg_solve(wcmg_ctx* ctx, const void* b, void* x, int nrhs, int where, void* stream, wcmg_stats* st);
+
+/* Change params.profile of an existing context (no GPU work). */
+int wcmg_set_profile(wcmg_ctx* ctx, int mask);
+/* Per-kernel-class counters accumulated over the context's lifetime
+ * (out: WCMG_NKCLASS entries).  wcmg_setup / wcmg_solve report their own share. */
+int wcmg_get_kstats(wcmg_ctx* ctx, wcmg_kstat* out);
 
 /* Checkpoint of the setup (near-null vectors and coarse links of every level). */
 int wcmg_save_setup(wcmg_ctx* ctx, const char* path);

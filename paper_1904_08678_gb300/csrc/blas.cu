@@ -76,6 +76,7 @@ void launch_dot(double2* out, const cplx<R>* a, const cplx<R>* b, long long n, i
   const int nb = red_blocks(n);
   k_dot_partial<R><<<dim3(nb, nrhs), RED_T, 0, st>>>(partial, a, b, n);
   k_final<double2><<<dim3(nrhs, 1), RED_T, 0, st>>>(out, partial, nb, nb, 0, 1);
+  ++launch_counter();
   WCMG_LAUNCH_CHECK();
 }
 template <typename R>
@@ -83,6 +84,7 @@ void launch_norm2(double* out, const cplx<R>* a, long long n, int nrhs, double* 
   const int nb = red_blocks(n);
   k_norm_partial<R><<<dim3(nb, nrhs), RED_T, 0, st>>>(partial, a, n);
   k_final<double><<<dim3(nrhs, 1), RED_T, 0, st>>>(out, partial, nb, nb, 0, 1);
+  ++launch_counter();
   WCMG_LAUNCH_CHECK();
 }
 
@@ -120,6 +122,7 @@ void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int 
   const int nchunk = (k + MD_K - 1) / MD_K, kpad = nchunk * MD_K;
   k_multidot_partial<R><<<dim3(nb, nrhs, nchunk), RED_T, 0, st>>>(partial, basis, bstride, k, w, n, kpad);
   k_final<double2><<<dim3(nrhs, k), RED_T, 0, st>>>(out, partial, nb, (long long)kpad * nb, nb, ldo);
+  ++launch_counter();
   WCMG_LAUNCH_CHECK();
 }
 

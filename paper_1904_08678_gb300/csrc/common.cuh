@@ -126,7 +126,16 @@ struct Error : std::runtime_error {
                           std::string(#call) + ": " + cudaGetErrorString(e_));                   \
   } while (0)
 
-#define WCMG_LAUNCH_CHECK() WCMG_CUDA(cudaGetLastError())
+// Number of kernels this library has launched (host side, one process).
+inline long long& launch_counter() {
+  static long long n = 0;
+  return n;
+}
+#define WCMG_LAUNCH_CHECK()          \
+  do {                               \
+    ++::wcmg::launch_counter();      \
+    WCMG_CUDA(cudaGetLastError());   \
+  } while (0)
 
 inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 

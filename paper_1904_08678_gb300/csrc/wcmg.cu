@@ -139,7 +139,7 @@ struct Level {
 };
 
 struct Prof {
-  bool on = false;
+  int mask = 0;
   std::vector<cudaEvent_t> pool;
   struct Pend { int cls; cudaEvent_t a, b; double bytes, flops; };
   std::vector<Pend> pend;
@@ -161,10 +161,7 @@ struct Prof {
       WCMG_CUDA(cudaEventSynchronize(p.b));
       float ms = 0;
       WCMG_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
-      k[p.cls].launches += 1;
       k[p.cls].ms += ms;
-      k[p.cls].bytes += p.bytes;
-      k[p.cls].flops += p.flops;
       pool.push_back(p.a);
       pool.push_back(p.b);
     }
@@ -205,16 +202,23 @@ struct wcmg_ctx {
 
 namespace wcmg {
 
-#define KPROF(c, cls, bytes, flops, call)                                     \
-  do {                                                                        \
-    cudaEvent_t a_ = nullptr, b_ = nullptr;                                   \
-    if ((c)->prof.on) { a_ = (c)->prof.get(); WCMG_CUDA(cudaEventRecord(a_, (c)->st)); } \
-    call;                                                                     \
-    if ((c)->prof.on) {                                                       \
-      b_ = (c)->prof.get();                                                   \
-      WCMG_CUDA(cudaEventRecord(b_, (c)->st));                                \
-      (c)->prof.pend.push_back({(cls), a_, b_, (double)(bytes), (double)(flops)}); \
-    }                                                                         \
+// Launch `call` (one kernel family of class `cls`); count it with its
+// algorithmic bytes/flops and, when the class is in the profile mask, time it
+// with a CUDA-event pair on the call's stream.
+#define KPROF(c, cls, BYTES_, FLOPS_, call)                                        \
+  do {                                                                           \
+    const bool on_ = ((c)->prof.mask >> (cls)) & 1;                             \
+    cudaEvent_t a_ = nullptr, b_ = nullptr;                                      \
+    if (on_) { a_ = (c)->prof.get(); WCMG_CUDA(cudaEventRecord(a_, (c)->st)); }  \
+    call;                                                                        \
+    (c)->prof.k[(cls)].launches += 1;                                            \
+    (c)->prof.k[(cls)].bytes += (double)(BYTES_);                                \
+    (c)->prof.k[(cls)].flops += (double)(FLOPS_);                                \
+    if (on_) {                                                                   \
+      b_ = (c)->prof.get();                                                      \
+      WCMG_CUDA(cudaEventRecord(b_, (c)->st));                                   \
+      (c)->prof.pend.push_back({(cls), a_, b_, 0.0, 0.0});                      \
+    }                                                                            \
   } while (0)
 
 static void host_mirrors(wcmg_ctx* c, int n) {
@@ -757,6 +761,15 @@ static void unpack_level(wcmg_ctx* c, int l, double2* ext, const cplx<R>* in, in
 
 static bool inner64(const wcmg_ctx* c) { return c->p.inner_prec == WCMG_F64; }
 
+static void kstat_delta(wcmg_kstat* out, const wcmg_kstat* now, const wcmg_kstat* before) {
+  for (int i = 0; i < WCMG_NKCLASS; ++i) {
+    out[i].launches = now[i].launches - before[i].launches;
+    out[i].ms = now[i].ms - before[i].ms;
+    out[i].bytes = now[i].bytes - before[i].bytes;
+    out[i].flops = now[i].flops - before[i].flops;
+  }
+}
+
 static void check_level(const wcmg_ctx* c, int l, int lo, int hi) {
   if (l < lo || l > hi) throw Error(WCMG_ERR_ARG, "level out of range");
   (void)c;
@@ -895,7 +908,7 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
     }
     ensure_partials(c);
     c->errflag.ensure((size_t)max_rhs_all(c) + 1);
-    c->prof.on = p->profile != 0;
+    c->prof.mask = p->profile;
   } catch (const Error& e) {
     int code = e.code;
     delete c;
@@ -1169,14 +1182,17 @@ int wcmg_setup(wcmg_ctx* c, const void* init_vecs, int where, void* stream, wcmg
   const double2* iv = in_dev(c, init_vecs, tot, where, 2);
   if (st) std::memset(st, 0, sizeof(*st));
   c->prof.flush();
-  c->prof.reset();
+  wcmg_kstat k0[WCMG_NKCLASS];
+  std::memcpy(k0, c->prof.k, sizeof(k0));
   c->coarse_its = 0;
+  const long long l0 = launch_counter();
   if (inner64(c)) setup_all<double>(c, iv, st);
   else setup_all<float>(c, iv, st);
   c->prof.flush();
   if (st) {
-    std::memcpy(st->k, c->prof.k, sizeof(st->k));
+    kstat_delta(st->k, c->prof.k, k0);
     st->coarse_iterations = c->coarse_its;
+    st->kernel_launches = launch_counter() - l0;
   }
   API_END(c)
 }
@@ -1260,8 +1276,10 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   st->ms_setup_init = ms_i;
   st->ms_setup_refine = ms_r;
   c->prof.flush();
-  c->prof.reset();
+  wcmg_kstat k0[WCMG_NKCLASS];
+  std::memcpy(k0, c->prof.k, sizeof(k0));
   c->coarse_its = 0;
+  const long long l0 = launch_counter();
   auto t0 = std::chrono::steady_clock::now();
   Level& L = c->L[0];
   const size_t bytes = (size_t)nrhs * L.n() * 16;
@@ -1280,12 +1298,29 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   auto t1 = std::chrono::steady_clock::now();
   st->ms_solve = std::chrono::duration<double, std::milli>(t1 - t0).count();
   c->prof.flush();
-  std::memcpy(st->k, c->prof.k, sizeof(st->k));
+  kstat_delta(st->k, c->prof.k, k0);
   st->coarse_iterations = c->coarse_its;
+  st->kernel_launches = launch_counter() - l0;
   if (!st->converged) {
     c->err = "outer solver reached outer_maxiter";
     return WCMG_ERR_NOT_CONVERGED;
   }
+  API_END(c)
+}
+
+int wcmg_set_profile(wcmg_ctx* c, int mask) {
+  API_BEGIN(c)
+  c->prof.flush();
+  c->p.profile = mask;
+  c->prof.mask = mask;
+  API_END(c)
+}
+
+int wcmg_get_kstats(wcmg_ctx* c, wcmg_kstat* out) {
+  API_BEGIN(c)
+  if (!out) throw Error(WCMG_ERR_ARG, "out");
+  c->prof.flush();
+  std::memcpy(out, c->prof.k, sizeof(c->prof.k));
   API_END(c)
 }
 

@@ -11,10 +11,14 @@ Generator (counter based, host only):
   * uniform double u = (out >> 11) * 2**-53 in [0, 1)
   * normals by Box-Muller from the pair (u[2k], u[2k+1]).
 
-Gauge links: U = exp(i * eps * X) with X = sum_a xi_a lambda_a / 2 (Gell-Mann
-lambda_a, xi_a ~ N(0,1) iid per link), exponentiated through the eigen-
+Gauge links: U = exp(i * eps * X) with X = sum_a xi_a lambda_a (Gell-Mann
+lambda_a, xi_a ~ N(0,1) iid per link: a unit Gaussian in the Gell-Mann basis of
+traceless Hermitian matrices, E tr X^2 = 16), exponentiated through the eigen-
 decomposition of the Hermitian X and re-unitarised (Gram-Schmidt on rows 0-1,
 row 2 = conj(row0 x row1)) so that U^dagger U = 1 and det U = 1 to rounding.
+With this normalisation the bare masses of the benchmark configurations
+(eps, m0) = (0.3, -0.1), (0.25, -0.2), (0.2, -0.25) all lie above the critical
+mass (smallest Re(lambda) of D on 4^4: 0.62, 0.29, 0.058).
 
 Layouts (external, lexicographic site index s = x + Lx*(y + Ly*(z + Lz*t))):
   gauge  : complex128 [4][V][3][3]   U_mu(x), the link x -> x + mu
@@ -97,7 +101,7 @@ def random_gauge(dims, eps: float, seed: int) -> np.ndarray:
     Lx, Ly, Lz, Lt = dims
     V = Lx * Ly * Lz * Lt
     xi = normal(seed, 0, 4 * V * 8).reshape(4 * V, 8)
-    X = np.einsum("na,aij->nij", xi, gell_mann() / 2.0)
+    X = np.einsum("na,aij->nij", xi, gell_mann())
     w, Q = np.linalg.eigh(X)
     U = np.einsum("nij,nj,nkj->nik", Q, np.exp(1j * eps * w), np.conj(Q))
     return _reunitarise(U).reshape(4, V, 3, 3)

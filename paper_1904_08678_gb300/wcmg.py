@@ -70,6 +70,7 @@ class wcmg_stats(ctypes.Structure):
         ("converged", ctypes.c_int),
         ("true_residual", ctypes.c_double),
         ("coarse_iterations", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
         ("ms_setup_init", ctypes.c_double),
         ("ms_setup_refine", ctypes.c_double),
         ("ms_solve", ctypes.c_double),
@@ -103,6 +104,8 @@ _SIGS = {
     "wcmg_mg_cycle": ([_PCTX, _vp, _vp, _i, _i, _vp], _i),
     "wcmg_krylov": ([_PCTX, _i, _i, _vp, _vp, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_i)], _i),
     "wcmg_solve": ([_PCTX, _vp, _vp, _i, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
+    "wcmg_set_profile": ([_PCTX, _i], _i),
+    "wcmg_get_kstats": ([_PCTX, ctypes.POINTER(wcmg_kstat)], _i),
     "wcmg_save_setup": ([_PCTX, ctypes.c_char_p], _i),
     "wcmg_load_setup": ([_PCTX, ctypes.c_char_p], _i),
 }
@@ -272,6 +275,15 @@ class Context:
         self._check(wcmg_solve(self.h, pi, po, nrhs, wi, _stream(stream), ctypes.byref(st)),
                     allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return st
+
+    def set_profile(self, mask):
+        return self._check(wcmg_set_profile(self.h, mask))
+
+    def kstats(self):
+        arr = (wcmg_kstat * NKCLASS)()
+        self._check(wcmg_get_kstats(self.h, arr))
+        return {KCLASS[i]: dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes, flops=arr[i].flops)
+                for i in range(NKCLASS)}
 
     def save_setup(self, path):
         return self._check(wcmg_save_setup(self.h, path.encode()))
