@@ -184,6 +184,33 @@ int wcmg_set_profile(wcmg_ctx* ctx, int mask);
  * (out: WCMG_NKCLASS entries).  wcmg_setup / wcmg_solve report their own share. */
 int wcmg_get_kstats(wcmg_ctx* ctx, wcmg_kstat* out);
 
+/* Allocation-free block orthonormalisation of fine-level near-null vectors.
+ * The paper has no counterpart.  It is for callers that cannot allocate device
+ * memory: code whose device memory all belongs to another allocator (for example
+ * a host framework's caching pool) and that must not call cudaMalloc/cudaFree,
+ * which synchronise the whole device and can fail at run time once the pool
+ * holds the memory.  Result: what wcmg_set_nullvecs followed by
+ * wcmg_get_nullvecs return on the fine level (FP64 Q factor with positive real
+ * diag(R) for every aggregate and chirality), with no context.
+ *   vecs_in   device pointer, complex128 [nvec][V][4][3], V = product of dims
+ *   vecs_out  device pointer, same layout (may equal vecs_in)
+ *   dims      host int[4], fine extents Lx, Ly, Lz, Lt
+ *   block     host int[4], aggregate extents (each divides its extent)
+ * Working memory: a file-scope device array of WCMG_NOALLOC_MAX_ELEMS complex128
+ * entries (4 MiB) that every device which loads the library keeps until the
+ * process exits; nvec * V * 12 > WCMG_NOALLOC_MAX_ELEMS returns WCMG_ERR_ARG.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current: make the first call on each
+ * device before any stream capture.  Every call uses the same array, which keeps
+ * the last call's contents: calls whose GPU work overlaps (several streams or
+ * host threads) race and must be serialised by the caller.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  Synchronises `stream` to
+ * read the rank check.  Errors: WCMG_ERR_ARG (null pointer, sizes, nvec outside
+ * 1..32), WCMG_ERR_NAN (rank-deficient aggregate), WCMG_ERR_CUDA. */
+#define WCMG_NOALLOC_MAX_ELEMS 262144
+int wcmg_block_orthonormalise_noalloc(const void* vecs_in, void* vecs_out, const int dims[4], const int block[4],
+                                      int nvec, void* stream);
+
 /* Checkpoint of the setup (near-null vectors and coarse links of every level). */
 int wcmg_save_setup(wcmg_ctx* ctx, const char* path);
 int wcmg_load_setup(wcmg_ctx* ctx, const char* path);

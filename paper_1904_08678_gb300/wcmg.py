@@ -26,6 +26,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 MAX_LEVELS = 4
+NOALLOC_MAX_ELEMS = 262144
 NKCLASS = 12
 OK, ERR_ARG, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7
 F64, F32, BF16, F16 = 0, 1, 2, 3
@@ -106,6 +107,7 @@ _SIGS = {
     "wcmg_solve": ([_PCTX, _vp, _vp, _i, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
     "wcmg_set_profile": ([_PCTX, _i], _i),
     "wcmg_get_kstats": ([_PCTX, ctypes.POINTER(wcmg_kstat)], _i),
+    "wcmg_block_orthonormalise_noalloc": ([_vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp], _i),
     "wcmg_save_setup": ([_PCTX, ctypes.c_char_p], _i),
     "wcmg_load_setup": ([_PCTX, ctypes.c_char_p], _i),
 }
