@@ -128,23 +128,27 @@ void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int 
 
 template <typename R>
 __global__ void k_multiaxpy(cplx<R>* __restrict__ w, const cplx<R>* __restrict__ basis, long long bstride, int k,
-                           const double2* __restrict__ coef, int ldc, R sign, long long n) {
+                           const double2* __restrict__ coef, int ldc, double sign, long long n) {
+  __shared__ cplx<R> cf[80];  // k <= 65 (restart <= 64)
   const int r = blockIdx.y;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double2 c = coef[(long long)r * ldc + i];
+    cf[i] = cmk(R(sign * c.x), R(sign * c.y));
+  }
+  __syncthreads();
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= n) return;
   const long long off = (long long)r * n + e;
   cplx<R> acc = w[off];
-  for (int i = 0; i < k; ++i) {
-    const double2 c = coef[(long long)r * ldc + i];
-    cmac(acc, cmk(R(sign * c.x), R(sign * c.y)), basis[i * bstride + off]);
-  }
+  for (int i = 0; i < k; ++i) cmac(acc, cf[i], basis[i * bstride + off]);
   w[off] = acc;
 }
 template <typename R>
 void launch_multiaxpy(cplx<R>* w, const cplx<R>* basis, long long bstride, int k, const double2* coef, int ldc,
                       double sign, long long n, int nrhs, cudaStream_t st) {
   if (k <= 0) return;
-  k_multiaxpy<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(w, basis, bstride, k, coef, ldc, (R)sign, n);
+  if (k > 80) throw Error(-1, "multiaxpy supports k <= 80");
+  k_multiaxpy<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(w, basis, bstride, k, coef, ldc, sign, n);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -163,12 +167,17 @@ void launch_axpby(cplx<R>* y, double a, const cplx<R>* x, double b, long long n,
 template <typename R>
 __global__ void k_scale_dev(cplx<R>* __restrict__ y, const cplx<R>* __restrict__ x, const double* __restrict__ s,
                             int inv_sqrt, long long n) {
+  __shared__ R f_s;
   const int r = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double f = s[r];
+    if (inv_sqrt) f = f > 0.0 ? 1.0 / sqrt(f) : 0.0;
+    f_s = (R)f;
+  }
+  __syncthreads();
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  double f = s[r];
-  if (inv_sqrt) f = f > 0.0 ? 1.0 / sqrt(f) : 0.0;
-  y[(long long)r * n + e] = (R)f * x[(long long)r * n + e];
+  y[(long long)r * n + e] = f_s * x[(long long)r * n + e];
 }
 template <typename R>
 void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqrt, long long n, int nrhs,
@@ -180,12 +189,16 @@ void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqr
 template <typename R>
 __global__ void k_mr_update(cplx<R>* __restrict__ x, cplx<R>* __restrict__ r, const cplx<R>* __restrict__ p,
                             const double2* __restrict__ pr, const double* __restrict__ pp, long long n) {
+  __shared__ cplx<R> a_s;
   const int q = blockIdx.y;
+  if (threadIdx.x == 0) {
+    const double d = pp[q];
+    a_s = d != 0.0 ? cmk((R)(pr[q].x / d), (R)(pr[q].y / d)) : czero<R>();
+  }
+  __syncthreads();
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const double d = pp[q];
-  const double2 al = d != 0.0 ? make_double2(pr[q].x / d, pr[q].y / d) : make_double2(0, 0);
-  const cplx<R> a = cmk((R)al.x, (R)al.y);
+  const cplx<R> a = a_s;
   const long long o = (long long)q * n + e;
   const cplx<R> rv = r[o];
   cmac(x[o], a, rv);

@@ -9,6 +9,8 @@
 // warp per row, lanes split the row, warp-shuffle reduction.  The same kernel,
 // with masked gathers, gives the block-interior and single-face parts that the
 // Galerkin construction (CoarsenOperator) of the next level needs.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace wcmg {
@@ -36,7 +38,12 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
   using T = cplx<R>;
   extern __shared__ unsigned char smem_raw[];
   T* phi = reinterpret_cast<T*>(smem_raw);  // [RR][ld]
-  const int site = blockIdx.x, r0 = blockIdx.y * RR;
+  // grid.x = sites x row parts: CTA (site, part) computes rows [row0, row1) of y(site)
+  const int parts = gridDim.x / Vc;
+  const int site = blockIdx.x / parts, part = blockIdx.x % parts;
+  const int rpc = (nb + parts - 1) / parts;
+  const int row0 = part * rpc, row1 = min(nb, row0 + rpc);
+  const int r0 = blockIdx.y * RR;
   const int K = 9 * nb;
   for (int idx = threadIdx.x; idx < RR * ld; idx += blockDim.x) {
     const int r = idx / ld, k = idx % ld;
@@ -55,11 +62,12 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int row = warp; row < nb; row += nw) {
+  for (int row = row0 + warp; row < row1; row += nw) {
     const L* lr = links + ((long long)site * nb + row) * ld;
     T acc[RR];
 #pragma unroll
     for (int r = 0; r < RR; ++r) acc[r] = czero<R>();
+#pragma unroll 4
     for (int k0 = lane * VEC; k0 < ld; k0 += 32 * VEC) {
       const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + k0);
 #pragma unroll
@@ -77,6 +85,63 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
   }
 }
 
+// Single-rhs coarse apply.  One CTA per (site, block of rows): the nine
+// neighbour vectors are gathered once into shared memory; each warp owns rows
+// and loads a whole row (NK 16-byte chunks per lane) before reducing it; the
+// first row is requested before the gather and the barrier, so every warp has
+// a full row (NK x 512 B) of the link stream in flight.
+template <typename R, typename L, int VEC, int NK>
+__global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                       const L* __restrict__ links, const int* __restrict__ nbr,
+                                                       int Vc, int nb, int ld, int parts) {
+  using T = cplx<R>;
+  extern __shared__ unsigned char smem_raw[];
+  T* phi = reinterpret_cast<T*>(smem_raw);  // [ld]
+  const int site = blockIdx.x / parts, part = blockIdx.x % parts;
+  const int rpc = (nb + parts - 1) / parts;
+  const int row0 = part * rpc, row1 = min(nb, row0 + rpc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const L* base = links + (long long)site * nb * ld;
+  LinkVec<L, VEC> cur[NK];
+  int row = row0 + warp;
+#pragma unroll
+  for (int j = 0; j < NK; ++j) {
+    const int k0 = VEC * (lane + 32 * j);
+    if (row < row1 && k0 < ld) cur[j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)row * ld + k0);
+  }
+  const int K = 9 * nb;
+  for (int idx = threadIdx.x; idx < ld; idx += blockDim.x) {
+    T v = czero<R>();
+    if (idx < K) {
+      const int d = idx / nb, c = idx - d * nb;
+      const int n = d == 0 ? site : nbr[(d - 1) * Vc + site];
+      v = in[(long long)n * nb + c];
+    }
+    phi[idx] = v;
+  }
+  __syncthreads();
+  for (; row < row1; row += nw) {
+    if (row != row0 + warp) {
+#pragma unroll
+      for (int j = 0; j < NK; ++j) {
+        const int k0 = VEC * (lane + 32 * j);
+        if (k0 < ld) cur[j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)row * ld + k0);
+      }
+    }
+    T acc = czero<R>();
+#pragma unroll
+    for (int j = 0; j < NK; ++j) {
+      const int k0 = VEC * (lane + 32 * j);
+      if (k0 < ld) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(cur[j].v[v]), phi[k0 + v]);
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[(long long)site * nb + row] = acc;
+  }
+}
+
 template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
 
 template <typename R, typename L, int RR>
@@ -90,16 +155,47 @@ static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, con
   const size_t smem = (size_t)RR * ld * sizeof(cplx<R>);
   auto kern = k_coarse_apply<R, L, RR, VEC>;
   if (smem > 48 * 1024) WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int threads = nb >= 32 ? 512 : 256;
-  kern<<<dim3(g.V, (nrhs + RR - 1) / RR), threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, nrhs, mode,
-                                                               hopdir, bi);
+  // enough CTAs to fill every SM several times over: split the rows of a site
+  int parts = 1;
+  const long long want = 6LL * 152;
+  const long long ncta_y = (nrhs + RR - 1) / RR;
+  while (parts < nb / 4 && (long long)g.V * parts * ncta_y < want) parts *= 2;
+  const int rpc = (nb + parts - 1) / parts;
+  const int rpw = (rpc + 15) / 16;  // rows per warp, at most 16 warps
+  const int threads = std::max(64, 32 * ((rpc + rpw - 1) / rpw));
+  kern<<<dim3(g.V * parts, ncta_y), threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, nrhs, mode, hopdir,
+                                                          bi);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R, typename L>
+static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb,
+                          cudaStream_t st) {
+  constexpr int VEC = VecOf<L>::v;
+  const int ld = links_ld(nb);
+  const int nk = (ld + 32 * VEC - 1) / (32 * VEC);
+  // one site per CTA, 16 warps; split a site only when there are too few sites
+  int parts = 1;
+  while (parts < 4 && (long long)g.V * parts < 2LL * 152) parts *= 2;
+  const size_t smem = (size_t)ld * sizeof(cplx<R>);
+  const unsigned grid = (unsigned)(g.V * parts);
+#define WCMG_C1(NKV) \
+  k_coarse_apply1<R, L, VEC, NKV><<<grid, 512, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, parts)
+  if (nk <= 4) WCMG_C1(4);
+  else if (nk <= 8) WCMG_C1(8);
+  else if (nk <= 12) WCMG_C1(12);
+  else if (nk <= 18) WCMG_C1(18);
+  else throw Error(-1, "coarse apply: nbasis too large");
+#undef WCMG_C1
   WCMG_LAUNCH_CHECK();
 }
 
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
-                         int mode, int hopdir, cudaStream_t st) {
-  if (nrhs == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, st);
+                         int mode, int hopdir, cudaStream_t st, int* err) {
+  (void)err;
+  if (nrhs == 1 && mode == ST_FULL) coarse_apply1<R, L>(out, in, links, g, nb, st);
+  else if (nrhs == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, st);
   else if (nrhs <= 4 || sizeof(R) == 8) coarse_apply_rr<R, L, 4>(out, in, links, g, nb, nrhs, mode, hopdir, st);
   else coarse_apply_rr<R, L, 8>(out, in, links, g, nb, nrhs, mode, hopdir, st);
 }
@@ -207,13 +303,13 @@ void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int 
 }
 
 template void launch_coarse_apply<double, double2>(double2*, const double2*, const double2*, const LevelGeom&, int,
-                                                   int, int, int, cudaStream_t);
+                                                   int, int, int, cudaStream_t, int*);
 template void launch_coarse_apply<float, float2>(float2*, const float2*, const float2*, const LevelGeom&, int, int,
-                                                 int, int, cudaStream_t);
+                                                 int, int, cudaStream_t, int*);
 template void launch_coarse_apply<float, bf16c>(float2*, const float2*, const bf16c*, const LevelGeom&, int, int, int,
-                                                int, cudaStream_t);
+                                                int, cudaStream_t, int*);
 template void launch_coarse_apply<float, f16c>(float2*, const float2*, const f16c*, const LevelGeom&, int, int, int,
-                                               int, cudaStream_t);
+                                               int, cudaStream_t, int*);
 #define WCMG_INST_L(L)                                                                                   \
   template void launch_pack_links<L>(L*, const double2*, const int*, int, int, cudaStream_t);           \
   template void launch_unpack_links<L>(double2*, const L*, const int*, int, int, cudaStream_t);

@@ -44,6 +44,11 @@ template <typename R> __host__ __device__ __forceinline__ cplx<R> czero() { retu
     acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);                                     \
     acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);                                    \
   }                                                                                                 \
+  /* acc -= a * b  (four fused multiply-adds) */                                                    \
+  __host__ __device__ __forceinline__ void cnmac(T& acc, T a, T b) {                                \
+    acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);                                    \
+    acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);                                   \
+  }                                                                                                 \
   __host__ __device__ __forceinline__ T conjg(T a) { return cmk(a.x, -a.y); }                       \
   /* i * a, -i * a */                                                                               \
   __host__ __device__ __forceinline__ T mul_i(T a) { return cmk(-a.y, a.x); }                       \
@@ -110,6 +115,63 @@ __device__ __forceinline__ void block_sum_many(T* vals, int n, T* scratch, T* re
     red[k] = s;
   }
   __syncthreads();
+}
+
+// Register-resident variant: vals has a compile-time size N (fully unrolled, so
+// the array stays in registers); the first n entries are summed into red[0..n).
+// scratch must hold (blockDim/32) * N values.
+template <typename T, int N>
+__device__ __forceinline__ void block_sum_regs(const T (&vals)[N], int n, T* scratch, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k < n) {
+      T s = warp_sum(vals[k]);
+      if (lane == 0) scratch[warp * N + k] = s;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    T s = scratch[k];
+    for (int w = 1; w < nw; ++w) s += scratch[w * N + k];
+    red[k] = s;
+  }
+  __syncthreads();
+}
+
+// ---- TMA bulk copies and mbarriers (inline PTX, sm_90+ / sm_103a) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// one arrival that also announces `bytes` of transaction to complete the phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase: gives up after `limit` polls (returns false).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = (1LL << 26)) {
+  for (long long i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // ---- host-side error plumbing ----

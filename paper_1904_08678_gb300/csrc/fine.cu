@@ -356,13 +356,19 @@ __device__ __forceinline__ bool on_face(const BlockInfo& bi, int s, int d) {
 }
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(128) k_dslash(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 1) k_dslash(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
                                                 const cplx<R>* __restrict__ U, const cplx<R>* __restrict__ clov,
-                                                const int* __restrict__ nbr, int V, BlockInfo bi, int hopdir) {
+                                                const int* __restrict__ nbr, int V, BlockInfo bi, int hopdir,
+                                                int nrhs) {
   using T = cplx<R>;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  // right-hand side fastest in the grid: the CTAs running together cover the same
+  // sites for every rhs, so links and clover are fetched from HBM once
+  const int rhs = blockIdx.x % nrhs;
+  const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
   if (s >= V) return;
-  const long long off = (long long)blockIdx.y * 12 * V;
+  // single-face mode: sites off the face are never read by the face restriction
+  if (MODE == ST_FACE_HOP && !on_face(bi, s, hopdir)) return;
+  const long long off = (long long)rhs * 12 * V;
   in += off;
   out += off;
   T acc[12];
@@ -398,11 +404,11 @@ void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const 
   BlockInfo bi;
   for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
   bi.bvol = g.bvol;
-  dim3 grid(nblk(g.V, 128), nrhs);
-  if (mode == ST_FULL) k_dslash<R, ST_FULL><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir);
+  const dim3 grid((unsigned)(nblk(g.V, 128) * (long long)nrhs));
+  if (mode == ST_FULL) k_dslash<R, ST_FULL><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs);
   else if (mode == ST_BLOCK_INTERIOR)
-    k_dslash<R, ST_BLOCK_INTERIOR><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir);
-  else k_dslash<R, ST_FACE_HOP><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir);
+    k_dslash<R, ST_BLOCK_INTERIOR><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs);
+  else k_dslash<R, ST_FACE_HOP><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs);
   WCMG_LAUNCH_CHECK();
 }
 

@@ -33,9 +33,11 @@ void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const 
 // ---- transfers (transfer.cu) ----
 // `fine` selects the component-major fine layout [ncomp][V]; otherwise fields are
 // site-major [V][ncomp].  Vectors and fields of one level share the layout.
+// face >= 0 restricts only the sites on that face of every aggregate (2 mu: +mu
+// face, 2 mu + 1: -mu face; `block` = aggregate extents); other sites are not read.
 template <typename R>
 void launch_restrict(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
-                     int nrhs, bool fine, cudaStream_t st);
+                     int nrhs, bool fine, cudaStream_t st, int face = -1, const int* block = nullptr);
 template <typename R>
 void launch_prolong(cplx<R>* out, const cplx<R>* coarse, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
                     int nrhs, bool fine, cudaStream_t st);
@@ -58,9 +60,11 @@ template <typename R>
 void launch_pack_coarse(cplx<R>* out, const double2* ext, const int* perm, int V, int nc, int nrhs, cudaStream_t st);
 template <typename R>
 void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int V, int nc, int nrhs, cudaStream_t st);
+// err (device int, may be null): receives 2 if a bounded wait of the TMA path
+// gave up; a null err selects the plain load path.
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
-                         int mode, int hopdir, cudaStream_t st);
+                         int mode, int hopdir, cudaStream_t st, int* err = nullptr);
 // links[x][a][d*nb + b0 + j] = res[j][x][a] for j < ncols (res: restrict output of the column fields)
 template <typename R, typename L>
 void launch_scatter_links(L* links, const cplx<R>* res, int Vc, int nb, int d, int b0, int ncols, cudaStream_t st);

@@ -27,45 +27,98 @@ __device__ __forceinline__ long long elem_addr(bool fine, int blk, int e, int s,
   return (long long)site * nc + c;
 }
 
-template <typename R, int RR, int NV>
+// Face restriction (coarsening): only the sites of an aggregate whose neighbour
+// across face `fd` (2 mu for +mu, 2 mu + 1 for -mu) lies in the next aggregate.
+struct FaceSel {
+  int fd;     // -1: whole aggregate
+  int b[4];   // aggregate extents
+};
+
+// local site of the aggregate for index f over the selected sites
+__device__ __forceinline__ int face_site(const FaceSel& fs, int f) {
+  if (fs.fd < 0) return f;
+  const int mu = fs.fd >> 1, fixed = (fs.fd & 1) ? 0 : fs.b[mu] - 1;
+  int l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k == mu) { l[k] = fixed; continue; }
+    l[k] = f % fs.b[k];
+    f /= fs.b[k];
+  }
+  return l[0] + fs.b[0] * (l[1] + fs.b[1] * (l[2] + fs.b[2] * l[3]));
+}
+
+// One CTA (8 warps) per (aggregate, tile of RR right-hand sides).  The CTA walks
+// the selected elements of one chirality in chunks of 256; each chunk of the RR
+// fine fields is staged once in shared memory.  Warp w owns the near-null
+// vectors i = w, w + 8, ... (VPW of them): every vector element is loaded once
+// from global memory and each lane keeps RR x VPW complex partial sums; the only
+// reduction is a warp shuffle at the end.
+template <typename R, int RR, int VPW>
 __global__ void __launch_bounds__(256) k_restrict(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
                                                   const cplx<R>* __restrict__ vecs, int Vf, int nc, int bvol,
-                                                  int nvec, int nrhs, bool fine) {
+                                                  int nvec, int nrhs, bool fine, FaceSel fs) {
   using T = cplx<R>;
-  __shared__ T scratch[8 * RR * NV];
-  __shared__ T red[RR * NV];
-  const int blk = blockIdx.x, r0 = blockIdx.y * RR;
-  const int half = nc >> 1, nelem = bvol * half, nb = 2 * nvec;
+  constexpr int CH = 256;
+  __shared__ T ps[RR][CH];
+  __shared__ int off_s[CH];
+  // rhs tile fastest in the grid: CTAs running together share an aggregate's vectors in L2
+  const int ntile = (nrhs + RR - 1) / RR;
+  const int blk = blockIdx.x / ntile, r0 = (blockIdx.x % ntile) * RR, s = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int half = nc >> 1, nb = 2 * nvec;
+  const int nsite = fs.fd < 0 ? bvol : bvol / fs.b[fs.fd >> 1];
+  const int nelem = nsite * half;
   const int Vc = Vf / bvol;
   const long long fstride = (long long)Vf * nc;
-  for (int s = 0; s < 2; ++s) {
-    for (int i0 = 0; i0 < nvec; i0 += NV) {
-      T acc[RR * NV];
+  const T* vb[VPW];
 #pragma unroll
-      for (int k = 0; k < RR * NV; ++k) acc[k] = czero<R>();
-      for (int e = threadIdx.x; e < nelem; e += blockDim.x) {
-        const long long a = elem_addr(fine, blk, e, s, Vf, nc, bvol);
-        T p[RR];
+  for (int j = 0; j < VPW; ++j) {
+    const int i = warp + nw * j;
+    vb[j] = i < nvec ? vecs + i * fstride : nullptr;
+  }
+  T acc[RR][VPW];
 #pragma unroll
-        for (int r = 0; r < RR; ++r) p[r] = (r0 + r < nrhs) ? in[(r0 + r) * fstride + a] : czero<R>();
+  for (int r = 0; r < RR; ++r)
 #pragma unroll
-        for (int i = 0; i < NV; ++i) {
-          if (i0 + i < nvec) {
-            const T v = vecs[(i0 + i) * fstride + a];
+    for (int j = 0; j < VPW; ++j) acc[r][j] = czero<R>();
+  for (int c0 = 0; c0 < nelem; c0 += CH) {
+    // stage: element -> offset (fast index of the layout first), and the rhs values
+    const int e = c0 + threadIdx.x;
+    if (e < nelem) {
+      int c, f;
+      if (fine) { c = s * half + e / nsite; f = e % nsite; }
+      else { f = e / half; c = s * half + e % half; }
+      const int site = blk * bvol + face_site(fs, f);
+      const int a = fine ? c * Vf + site : site * nc + c;
+      off_s[threadIdx.x] = a;
 #pragma unroll
-            for (int r = 0; r < RR; ++r) cjmac(acc[r * NV + i], v, p[r]);
-          }
+      for (int r = 0; r < RR; ++r) ps[r][threadIdx.x] = (r0 + r < nrhs) ? in[(r0 + r) * fstride + a] : czero<R>();
+    }
+    __syncthreads();
+    const int cn = min(CH, nelem - c0);
+#pragma unroll 4
+    for (int t = lane; t < cn; t += 32) {
+      const int a = off_s[t];
+#pragma unroll
+      for (int j = 0; j < VPW; ++j) {
+        if (vb[j]) {
+          const T v = vb[j][a];
+#pragma unroll
+          for (int r = 0; r < RR; ++r) cjmac(acc[r][j], v, ps[r][t]);
         }
       }
-      block_sum_many<T>(acc, RR * NV, scratch, red);
-      for (int k = threadIdx.x; k < RR * NV; k += blockDim.x) {
-        const int r = k / NV, i = k % NV;
-        if (r0 + r < nrhs && i0 + i < nvec)
-          out[((long long)(r0 + r) * Vc + blk) * nb + s * nvec + i0 + i] = red[k];
-      }
-      __syncthreads();
     }
+    __syncthreads();
   }
+#pragma unroll
+  for (int r = 0; r < RR; ++r)
+#pragma unroll
+    for (int j = 0; j < VPW; ++j) {
+      const T t = warp_sum(acc[r][j]);
+      const int i = warp + nw * j;
+      if (lane == 0 && i < nvec && r0 + r < nrhs) out[((long long)(r0 + r) * Vc + blk) * nb + s * nvec + i] = t;
+    }
 }
 
 template <typename R, int RR>
@@ -75,7 +128,8 @@ __global__ void __launch_bounds__(256) k_prolong(cplx<R>* __restrict__ out, cons
   using T = cplx<R>;
   extern __shared__ unsigned char smem_raw[];
   T* phi = reinterpret_cast<T*>(smem_raw);  // [RR][nb]
-  const int blk = blockIdx.x, r0 = blockIdx.y * RR;
+  const int ntile = (nrhs + RR - 1) / RR;  // rhs tile fastest: the vectors are shared in L2
+  const int blk = blockIdx.x / ntile, r0 = (blockIdx.x % ntile) * RR;
   const int nb = 2 * nvec, half = nc >> 1, Vc = Vf / bvol;
   const long long fstride = (long long)Vf * nc;
   for (int k = threadIdx.x; k < RR * nb; k += blockDim.x) {
@@ -104,16 +158,110 @@ __global__ void __launch_bounds__(256) k_prolong(cplx<R>* __restrict__ out, cons
   }
 }
 
+// Few right-hand sides: one warp per (aggregate, chirality, vector) dot
+// product.  A CTA holds 8 warps = 8 vectors of one (aggregate, chirality), so
+// the fine-field entries they all read come from L1; each lane streams its
+// elements of one vector with UNR independent loads in flight.  No shared
+// memory, no block barrier, a warp shuffle at the end.  Fine layout: the
+// aggregate's chirality half is `half` runs of bvol consecutive sites.
+template <typename R, int UNR>
+__global__ void __launch_bounds__(256) k_restrict_few(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                      const cplx<R>* __restrict__ vecs, int Vf, int nc, int bvol,
+                                                      int nvec, int nrhs, bool fine, FaceSel fs) {
+  using T = cplx<R>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int vgroups = (nvec + 7) / 8;
+  const int g = blockIdx.x % vgroups;
+  const int s = (blockIdx.x / vgroups) & 1;
+  const int blk = blockIdx.x / (2 * vgroups);
+  const int i = g * 8 + warp;
+  if (i >= nvec) return;
+  const int half = nc >> 1, nb = 2 * nvec;
+  const int Vc = Vf / bvol;
+  const long long fstride = (long long)Vf * nc;
+  const T* v = vecs + i * fstride;
+  const bool plain = fine && fs.fd < 0;
+  const int nsite = fs.fd < 0 ? bvol : bvol / fs.b[fs.fd >> 1];
+  const int nelem = nsite * half;
+  for (int r = 0; r < nrhs; ++r) {
+    const T* p = in + r * fstride;
+    T acc = czero<R>();
+    if (plain) {
+      // element (c, site): offset (s half + c) Vf + blk bvol + site
+      const long long base = (long long)(s * half) * Vf + (long long)blk * bvol;
+      for (int c = 0; c < half; ++c) {
+        const long long rowb = base + (long long)c * Vf;
+        for (int q0 = lane; q0 < bvol; q0 += 32 * UNR) {
+          T vv[UNR], pp[UNR];
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            const int q = q0 + 32 * u;
+            vv[u] = q < bvol ? v[rowb + q] : czero<R>();
+            pp[u] = q < bvol ? p[rowb + q] : czero<R>();
+          }
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) cjmac(acc, vv[u], pp[u]);
+        }
+      }
+    } else {
+      for (int e0 = lane; e0 < nelem; e0 += 32 * UNR) {
+        T vv[UNR], pp[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int e = e0 + 32 * u;
+          vv[u] = czero<R>();
+          pp[u] = czero<R>();
+          if (e < nelem) {
+            int c, f;
+            if (fine) { c = s * half + e / nsite; f = e % nsite; }
+            else { f = e / half; c = s * half + e % half; }
+            const int site = blk * bvol + face_site(fs, f);
+            const long long a = fine ? (long long)c * Vf + site : (long long)site * nc + c;
+            vv[u] = v[a];
+            pp[u] = p[a];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) cjmac(acc, vv[u], pp[u]);
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[((long long)r * Vc + blk) * nb + s * nvec + i] = acc;
+  }
+}
+
+template <typename R>
+static void restrict_few(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
+                         int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
+  const int vgroups = (nvec + 7) / 8;
+  const unsigned grid = (unsigned)((Vf / bvol) * 2 * vgroups);
+  k_restrict_few<R, 8><<<grid, 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R, int RR>
+static void restrict_rr(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
+                        int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
+  const dim3 grid((Vf / bvol) * ((nrhs + RR - 1) / RR), 2);
+  const int vpw = (nvec + 7) / 8;
+  if (vpw == 1) k_restrict<R, RR, 1><<<grid, 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
+  else if (vpw == 2) k_restrict<R, RR, 2><<<grid, 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
+  else if (vpw == 3) k_restrict<R, RR, 3><<<grid, 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
+  else k_restrict<R, RR, 4><<<grid, 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
+  WCMG_LAUNCH_CHECK();
+}
+
 template <typename R>
 void launch_restrict(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
-                     int nrhs, bool fine, cudaStream_t st) {
-  const int Vc = Vf / bvol;
-  if (nrhs >= 4) {
-    k_restrict<R, 4, 4><<<dim3(Vc, (nrhs + 3) / 4), 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine);
-  } else {
-    k_restrict<R, 1, 8><<<dim3(Vc, nrhs), 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine);
-  }
-  WCMG_LAUNCH_CHECK();
+                     int nrhs, bool fine, cudaStream_t st, int face, const int* block) {
+  if (nvec > 32) throw Error(-1, "restrict supports nvec <= 32");
+  FaceSel fs;
+  fs.fd = face;
+  for (int k = 0; k < 4; ++k) fs.b[k] = block ? block[k] : 1;
+  if (face >= 0 && !block) throw Error(-1, "face restriction needs the aggregate extents");
+  if (sizeof(R) == 4 && nrhs >= 8) restrict_rr<R, 8>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else if (nrhs >= 4) restrict_rr<R, 4>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else restrict_few<R>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
 }
 
 template <typename R>
@@ -121,88 +269,111 @@ void launch_prolong(cplx<R>* out, const cplx<R>* coarse, const cplx<R>* vecs, in
                     int nrhs, bool fine, cudaStream_t st) {
   const int Vc = Vf / bvol, nb = 2 * nvec;
   if (nrhs >= 4) {
-    k_prolong<R, 4><<<dim3(Vc, (nrhs + 3) / 4), 256, 4 * nb * sizeof(cplx<R>), st>>>(out, coarse, vecs, Vf, nc, bvol,
-                                                                                   nvec, nrhs, fine);
+    k_prolong<R, 4><<<dim3(Vc * ((nrhs + 3) / 4)), 256, 4 * nb * sizeof(cplx<R>), st>>>(out, coarse, vecs, Vf, nc,
+                                                                                       bvol, nvec, nrhs, fine);
   } else {
-    k_prolong<R, 1><<<dim3(Vc, nrhs), 256, nb * sizeof(cplx<R>), st>>>(out, coarse, vecs, Vf, nc, bvol, nvec, nrhs,
-                                                                         fine);
+    k_prolong<R, 1><<<dim3(Vc * nrhs), 256, nb * sizeof(cplx<R>), st>>>(out, coarse, vecs, Vf, nc, bvol, nvec,
+                                                                           nrhs, fine);
   }
   WCMG_LAUNCH_CHECK();
 }
 
 // ---------------- block orthonormalisation (K6, FP64) ----------------
 // One CTA per (aggregate, chirality).  Column k of the panel is orthogonalised
-// against columns 0..k-1 by classical Gram-Schmidt applied twice (CGS2), then
-// normalised; in exact arithmetic this is the Q factor with positive real
-// diag(R).  Each thread keeps its panel elements of column k in registers.
-constexpr int ORTHO_MAXV = 32;
-constexpr int ORTHO_MAXE = 8;
-
+// against columns 0..k-1 by classical Gram-Schmidt; a second pass is taken when
+// the first one cancelled more than 1 - 1/sqrt(2) of the column's norm (the
+// "twice is enough" criterion of Kahan and Parlett), so the result is orthonormal
+// to FP64 rounding; then it is normalised.  In exact arithmetic this is the Q
+// factor with positive real diag(R).  Each thread keeps its MAXE panel elements
+// of column k in registers; the previous columns are re-read from L1/L2.
+template <int MAXV, int MAXE>
 __global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ vecs, int Vf, int nc, int bvol, int nvec,
                                                      bool fine, int* __restrict__ err) {
-  __shared__ double2 scratch[8 * ORTHO_MAXV];
-  __shared__ double2 red[ORTHO_MAXV];
-  __shared__ double dscratch[8];
-  __shared__ double dred[1];
+  __shared__ double2 scratch[8 * (MAXV + 1)];
+  __shared__ double2 red[MAXV + 1];
   const int blk = blockIdx.x, s = blockIdx.y;
   const int nelem = bvol * (nc >> 1);
   const long long fstride = (long long)Vf * nc;
-  long long addr[ORTHO_MAXE];
+  long long addr[MAXE];
 #pragma unroll
-  for (int q = 0; q < ORTHO_MAXE; ++q) {
+  for (int q = 0; q < MAXE; ++q) {
     const int e = threadIdx.x + q * blockDim.x;
     addr[q] = e < nelem ? elem_addr(fine, blk, e, s, Vf, nc, bvol) : -1;
   }
   for (int k = 0; k < nvec; ++k) {
-    double2 a[ORTHO_MAXE];
+    double2 a[MAXE];
 #pragma unroll
-    for (int q = 0; q < ORTHO_MAXE; ++q) a[q] = addr[q] >= 0 ? vecs[k * fstride + addr[q]] : make_double2(0, 0);
-    for (int pass = 0; pass < 2 && k > 0; ++pass) {
-      double2 part[ORTHO_MAXV];
+    for (int q = 0; q < MAXE; ++q) a[q] = addr[q] >= 0 ? vecs[k * fstride + addr[q]] : make_double2(0, 0);
+    double before2 = 0.0, after2 = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      // dots <q_i, a> for i < k and, in slot k, ||a||^2
+      double2 part[MAXV + 1];
 #pragma unroll
-      for (int i = 0; i < ORTHO_MAXV; ++i) part[i] = make_double2(0, 0);
+      for (int i = 0; i <= MAXV; ++i) part[i] = make_double2(0, 0);
 #pragma unroll
-      for (int i = 0; i < ORTHO_MAXV; ++i) {
-        if (i < k) {
+      for (int q = 0; q < MAXE; ++q) {
+        if (addr[q] < 0) continue;
 #pragma unroll
-          for (int q = 0; q < ORTHO_MAXE; ++q)
-            if (addr[q] >= 0) cjmac(part[i], vecs[i * fstride + addr[q]], a[q]);
-        }
+        for (int i = 0; i < MAXV; ++i)
+          if (i < k) cjmac(part[i], vecs[i * fstride + addr[q]], a[q]);
+        part[MAXV].x += cnorm2(a[q]);
       }
-      block_sum_many<double2>(part, k, scratch, red);
 #pragma unroll
-      for (int i = 0; i < ORTHO_MAXV; ++i) {
+      for (int i = 0; i < MAXV; ++i)
+        if (i == k) part[i] = part[MAXV];
+      block_sum_regs<double2, MAXV + 1>(part, k + 1, scratch, red);
+      if (pass == 0) before2 = red[k].x;
+#pragma unroll
+      for (int i = 0; i < MAXV; ++i) {
         if (i < k) {
           const double2 r = red[i];
 #pragma unroll
-          for (int q = 0; q < ORTHO_MAXE; ++q)
-            if (addr[q] >= 0) a[q] -= cmul(r, vecs[i * fstride + addr[q]]);
+          for (int q = 0; q < MAXE; ++q)
+            if (addr[q] >= 0) cnmac(a[q], r, vecs[i * fstride + addr[q]]);
         }
       }
       __syncthreads();
-    }
-    double n2 = 0;
+      double n2 = 0;
 #pragma unroll
-    for (int q = 0; q < ORTHO_MAXE; ++q) n2 += cnorm2(a[q]);
-    block_sum_many<double>(&n2, 1, dscratch, dred);
-    const double nrm = sqrt(dred[0]);
+      for (int q = 0; q < MAXE; ++q) n2 += cnorm2(a[q]);
+      const double2 t[1] = {make_double2(n2, 0)};
+      block_sum_regs<double2, 1>(t, 1, scratch, red);
+      after2 = red[0].x;
+      __syncthreads();
+      if (k == 0 || after2 >= 0.5 * before2) break;  // uniform over the block
+      before2 = after2;
+    }
+    const double nrm = sqrt(after2);
     if (!(nrm > 0.0) || !isfinite(nrm)) {
       if (threadIdx.x == 0) *err = 1;
     }
     const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
 #pragma unroll
-    for (int q = 0; q < ORTHO_MAXE; ++q)
+    for (int q = 0; q < MAXE; ++q)
       if (addr[q] >= 0) vecs[k * fstride + addr[q]] = inv * a[q];
     __syncthreads();
   }
 }
 
+template <int MAXV>
+static void block_ortho_v(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st) {
+  const int nelem = bvol * (nc / 2);
+  const dim3 grid(Vf / bvol, 2);
+  if (nelem <= 256 * 2) k_block_ortho<MAXV, 2><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  else if (nelem <= 256 * 4) k_block_ortho<MAXV, 4><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  else if (nelem <= 256 * 6) k_block_ortho<MAXV, 6><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  else k_block_ortho<MAXV, 8><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  WCMG_LAUNCH_CHECK();
+}
+
 void launch_block_ortho(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st) {
   const int nelem = bvol * (nc / 2);
-  if (nvec > ORTHO_MAXV) throw Error(-1, "block orthonormalisation supports nvec <= 32");
-  if (nelem > 256 * ORTHO_MAXE) throw Error(-1, "aggregate too large for block orthonormalisation");
-  k_block_ortho<<<dim3(Vf / bvol, 2), 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
-  WCMG_LAUNCH_CHECK();
+  if (nvec > 32) throw Error(-1, "block orthonormalisation supports nvec <= 32");
+  if (nelem > 256 * 8) throw Error(-1, "aggregate too large for block orthonormalisation");
+  if (nvec <= 8) block_ortho_v<8>(vecs, Vf, nc, bvol, nvec, fine, err, st);
+  else if (nvec <= 16) block_ortho_v<16>(vecs, Vf, nc, bvol, nvec, fine, err, st);
+  else if (nvec <= 24) block_ortho_v<24>(vecs, Vf, nc, bvol, nvec, fine, err, st);
+  else block_ortho_v<32>(vecs, Vf, nc, bvol, nvec, fine, err, st);
 }
 
 // ---------------- chirality-split columns of P ----------------
@@ -229,7 +400,7 @@ void launch_make_columns(cplx<R>* cols, const cplx<R>* vecs, int Vf, int nc, int
 
 #define WCMG_INST(R)                                                                                            \
   template void launch_restrict<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, int, int, int, int, int, bool,     \
-                                   cudaStream_t);                                                               \
+                                   cudaStream_t, int, const int*);                                              \
   template void launch_prolong<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, int, int, int, int, int, bool,      \
                                   cudaStream_t);                                                                \
   template void launch_make_columns<R>(cplx<R>*, const cplx<R>*, int, int, int, int, int, bool, cudaStream_t);

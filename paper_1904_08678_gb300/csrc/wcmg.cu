@@ -188,6 +188,7 @@ struct wcmg_ctx {
   DevBuf<double> partial_d;
   DevBuf<unsigned char> stage[3];
   DevBuf<int> errflag;
+  DevBuf<int> tma_err;       // nonzero after a bounded device-side wait gave up
   int* h_flags = nullptr;   // pinned host mirror of per-rhs flags
   double* h_vals = nullptr; // pinned host mirror of per-rhs values
   int hcap = 0;
@@ -308,7 +309,7 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
     if (!L.op64) throw Error(WCMG_ERR_ARG, "FP64 coarse apply needs FP64 links");
     KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 16.0 + 2.0 * nb * 16.0 * nrhs), flops,
           (launch_coarse_apply<double, double2>((double2*)out, (const double2*)in, L.L64.p, L.g.lg(), nb, nrhs,
-                                                mode, hopdir, c->st)));
+                                                mode, hopdir, c->st, c->tma_err.p)));
     return;
   }
   const int lp = c->p.coarse_link_prec;
@@ -316,11 +317,11 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
     if (lp == WCMG_BF16)
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
             (launch_coarse_apply<float, bf16c>((float2*)out, (const float2*)in, L.Lbf.p, L.g.lg(), nb, nrhs, mode,
-                                               hopdir, c->st)));
+                                               hopdir, c->st, c->tma_err.p)));
     else
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
             (launch_coarse_apply<float, f16c>((float2*)out, (const float2*)in, L.Lh.p, L.g.lg(), nb, nrhs, mode,
-                                              hopdir, c->st)));
+                                              hopdir, c->st, c->tma_err.p)));
     return;
   }
   if (!L.L32_valid) {
@@ -331,17 +332,20 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
   }
   KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 8.0 + 2.0 * nb * 8.0 * nrhs), flops,
         (launch_coarse_apply<float, float2>((float2*)out, (const float2*)in, L.L32.p, L.g.lg(), nb, nrhs, mode,
-                                            hopdir, c->st)));
+                                            hopdir, c->st, c->tma_err.p)));
 }
 
 template <typename R>
-static void restrict_op(wcmg_ctx* c, int l, cplx<R>* coarse, const cplx<R>* fine, int nrhs) {
+static void restrict_op(wcmg_ctx* c, int l, cplx<R>* coarse, const cplx<R>* fine, int nrhs, int face = -1) {
   Level& L = c->L[l];
   if (!L.have_P) throw Error(WCMG_ERR_STATE, "prolongator of level not built");
   const double s = sizeof(cplx<R>);
-  KPROF(c, WCMG_K_RESTRICT, (double)L.n() * s * (L.nvec + nrhs) + (double)L.g.V / L.g.bvol * 2 * L.nvec * s * nrhs,
-        (double)L.n() * 8.0 * L.nvec * nrhs,
-        launch_restrict<R>(coarse, fine, Prec<R>::vecs(c, L), L.g.V, L.nc, L.g.bvol, L.nvec, nrhs, L.fine, c->st));
+  const double frac = face < 0 ? 1.0 : 1.0 / L.g.b[face >> 1];  // share of the sites read
+  KPROF(c, WCMG_K_RESTRICT,
+        frac * (double)L.n() * s * (L.nvec + nrhs) + (double)L.g.V / L.g.bvol * 2 * L.nvec * s * nrhs,
+        frac * (double)L.n() * 8.0 * L.nvec * nrhs,
+        launch_restrict<R>(coarse, fine, Prec<R>::vecs(c, L), L.g.V, L.nc, L.g.bvol, L.nvec, nrhs, L.fine, c->st,
+                           face, L.g.b));
 }
 template <typename R>
 static void prolong_op(wcmg_ctx* c, int l, cplx<R>* fine, const cplx<R>* coarse, int nrhs) {
@@ -551,7 +555,7 @@ static void coarsen(wcmg_ctx* c, int l) {
       const int mode = dm == 0 ? ST_BLOCK_INTERIOR : ST_FACE_HOP;
       const int hop = dm == 0 ? 0 : dm - 1;
       apply_op<R>(c, l, T, cols, ncols, mode, hop);
-      restrict_op<R>(c, l, res, T, ncols);
+      restrict_op<R>(c, l, res, T, ncols, dm == 0 ? -1 : hop);
       KPROF(c, WCMG_K_COARSEN, (double)Vc * nb * ncols * 2.0 * sizeof(cplx<R>), 0.0,
             (launch_scatter_links<R, cplx<R>>(links, res, Vc, nb, dm == 0 ? 0 : dm, b0, ncols, c->st)));
     }
@@ -579,7 +583,9 @@ static void build_P(wcmg_ctx* c, int l) {
   launch_convert<R, double>(L.v64.p, Prec<R>::raw(L).p, n, c->st);
   WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
   const double V = L.g.V;
-  KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0 * L.nvec, 2.0 * 2.0 * 8.0 * n * L.nvec / 2.0,
+  // algorithmic work: one Gram-Schmidt pass, nvec (nvec - 1) complex MAC per panel row
+  // (dots + updates); a second pass, when the cancellation test asks for it, is extra.
+  KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0, 8.0 * n * (L.nvec - 1),
         launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
   (void)V;
   const int* e = read_ints(c, c->errflag.p, 1);
@@ -761,6 +767,15 @@ static void unpack_level(wcmg_ctx* c, int l, double2* ext, const cplx<R>* in, in
 
 static bool inner64(const wcmg_ctx* c) { return c->p.inner_prec == WCMG_F64; }
 
+// A bounded device-side wait that gave up leaves a nonzero word: report it.
+static void check_device_waits(wcmg_ctx* c) {
+  const int* e = read_ints(c, c->tma_err.p, 1);
+  if (e[0]) {
+    WCMG_CUDA(cudaMemsetAsync(c->tma_err.p, 0, sizeof(int), c->st));
+    throw Error(WCMG_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  }
+}
+
 static void kstat_delta(wcmg_kstat* out, const wcmg_kstat* now, const wcmg_kstat* before) {
   for (int i = 0; i < WCMG_NKCLASS; ++i) {
     out[i].launches = now[i].launches - before[i].launches;
@@ -908,6 +923,8 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
     }
     ensure_partials(c);
     c->errflag.ensure((size_t)max_rhs_all(c) + 1);
+    c->tma_err.ensure(1);
+    WCMG_CUDA(cudaMemset(c->tma_err.p, 0, sizeof(int)));
     c->prof.mask = p->profile;
   } catch (const Error& e) {
     int code = e.code;
@@ -978,7 +995,6 @@ int wcmg_apply_D(wcmg_ctx* c, const void* in, void* out, int nrhs, int prec, int
   else if (prec == WCMG_F32) apply_D_ext<float>(c, i, o, nrhs);
   else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
   out_finish(c, out, o, bytes, where);
-  c->prof.flush();
   API_END(c)
 }
 
@@ -1023,7 +1039,6 @@ int wcmg_get_nullvecs(wcmg_ctx* c, int level, void* vecs, int where, void* strea
   double2* o = out_dev(c, vecs, bytes, where, 1);
   unpack_level<double>(c, level, o, L.v64.p, L.nvec);
   out_finish(c, vecs, o, bytes, where);
-  c->prof.flush();
   API_END(c)
 }
 
@@ -1122,7 +1137,6 @@ int wcmg_restrict(wcmg_ctx* c, int level, const void* fine, void* coarse, int nr
   else if (prec == WCMG_F32) transfer_ext<float>(c, level, i, o, nrhs, true);
   else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
   out_finish(c, coarse, o, bo, where);
-  c->prof.flush();
   API_END(c)
 }
 
@@ -1139,7 +1153,6 @@ int wcmg_prolong(wcmg_ctx* c, int level, const void* coarse, void* fine, int nrh
   else if (prec == WCMG_F32) transfer_ext<float>(c, level, i, o, nrhs, false);
   else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
   out_finish(c, fine, o, bo, where);
-  c->prof.flush();
   API_END(c)
 }
 
@@ -1168,7 +1181,6 @@ int wcmg_apply_coarse(wcmg_ctx* c, int level, const void* in, void* out, int nrh
   else if (prec == WCMG_F32) coarse_ext<float>(c, level, i, o, nrhs);
   else throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
   out_finish(c, out, o, bytes, where);
-  c->prof.flush();
   API_END(c)
 }
 
@@ -1188,6 +1200,7 @@ int wcmg_setup(wcmg_ctx* c, const void* init_vecs, int where, void* stream, wcmg
   const long long l0 = launch_counter();
   if (inner64(c)) setup_all<double>(c, iv, st);
   else setup_all<float>(c, iv, st);
+  check_device_waits(c);
   c->prof.flush();
   if (st) {
     kstat_delta(st->k, c->prof.k, k0);
@@ -1219,7 +1232,6 @@ int wcmg_mg_cycle(wcmg_ctx* c, const void* r, void* e, int nrhs, int where, void
     unpack_level<float>(c, 0, o, b, nrhs);
   }
   out_finish(c, e, o, bytes, where);
-  c->prof.flush();
   API_END(c)
 }
 
@@ -1259,7 +1271,6 @@ int wcmg_krylov(wcmg_ctx* c, int level, int kind, const void* b, void* x, int nr
                        : krylov_ext<float>(c, level, kind, i, o, nrhs, steps_or_restart, tol, maxiter);
   out_finish(c, x, o, bytes, where);
   if (iters_out) *iters_out = its;
-  c->prof.flush();
   API_END(c)
 }
 
@@ -1290,6 +1301,7 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   pack_level<double>(c, 0, b64, bi, nrhs);
   if (inner64(c)) solve_f64(c, x64, b64, nrhs, st);
   else solve_mixed(c, x64, b64, nrhs, st);
+  check_device_waits(c);
   st->true_residual = true_residual(c, x64, b64, nrhs);
   st->converged = st->true_residual <= c->p.outer_tol;
   unpack_level<double>(c, 0, xo, x64, nrhs);
