@@ -348,6 +348,8 @@ def run_gpu(args, rank, world, local):
                 "setup_refine_ms": round(s1.ms_setup_refine, 2), "solve_ms": round(s2.ms_solve, 2)}
         ctx64.close()
 
+    learned = None if args.no_learned else learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample()
@@ -367,6 +369,7 @@ def run_gpu(args, rank, world, local):
             "solves_per_s": round(sum_over_ranks(dist, args.steps, dev) / (ms * args.steps / 1e3), 3),
             "roofline": roofline, "coarse_stencil": {"in_solve": coarse_live, "isolated": coarse_iso},
             "e2e": {"value": round(e2e_ms / 1e3, 5), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "learned": learned,
             "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
             "clocks": clocks, "wall_s_timed": round(t_wall, 3), "fp64_inner": fp64, "cpu_baseline": cpu,
             "kernel_shares": {k: round(v[1] / (ms * args.steps), 4) for k, v in acc.items() if v[1] > 0},
@@ -377,6 +380,51 @@ def run_gpu(args, rank, world, local):
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush):
+    """Learned coarse correction on the same field: train the PTC network on pairs the
+    multigrid generates, then time setup + solve with the network replacing the coarse
+    correction (fallback ratio 0.9) and as a warm start of the coarsest GMRES."""
+    ctx = wcmg.Context(params(wcmg, cfg, "f32", args.links, profile=0))
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        flush.fill_(7)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    ctx.set_gauge(Ud, stream)
+    ctx.setup(ivd, stream)
+    tr, ms_train = timed(lambda: ctx.ptc_train(npairs=24, batch=4, steps=300, lr=1e-2, target_tol=1e-6, seed=5,
+                                                stream=stream))
+    out["train"] = {"pairs": 24, "steps": 300, "batch": 4, "loss_initial": round(tr.loss_initial, 4),
+                    "loss_final": round(tr.loss_final, 4), "ms": round(ms_train, 1),
+                    "ms_generate": round(tr.ms_generate, 1)}
+    for name, mode, fb in (("plain_mg", wcmg.COARSE_MG, 0.9), ("learned_replace", wcmg.COARSE_LEARNED, 0.9),
+                           ("learned_warmstart", wcmg.COARSE_WARMSTART, 0.9)):
+        ctx.set_coarse_mode(mode, fb)
+        x = torch.zeros_like(bd)
+
+        def run():
+            ctx.set_gauge(Ud, stream)
+            s1 = ctx.setup(ivd, stream)
+            return ctx.solve(bd, x, stream=stream)
+
+        run()  # warm
+        st, ms = timed(run)
+        out[name] = {"time_to_solution_s": round(ms / 1e3, 5), "outer_iterations": st.outer_iterations,
+                     "coarse_iterations": st.coarse_iterations, "solve_ms": round(st.ms_solve, 2),
+                     "true_residual": st.true_residual, "learned_cycles": st.learned_cycles,
+                     "fallback": st.learned_fallback}
+    ctx.close()
+    return out
 
 
 def measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg, reps=200):
@@ -474,6 +522,7 @@ def main(argv=None):
     ap.add_argument("--links", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

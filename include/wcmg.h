@@ -104,13 +104,15 @@ typedef struct wcmg_stats {
   double ms_setup_init;                 /* wall time of the phases (host clock around synced work) */
   double ms_setup_refine;
   double ms_solve;
+  int learned_fallback;                 /* 1 if a learned solve fell back to plain multigrid */
+  int learned_cycles;                   /* cycles that used the network */
   wcmg_kstat k[WCMG_NKCLASS];           /* index: wcmg_kclass */
 } wcmg_stats;
 
 typedef enum {
   WCMG_K_DSLASH = 0, WCMG_K_COARSE = 1, WCMG_K_RESTRICT = 2, WCMG_K_PROLONG = 3,
   WCMG_K_BLAS = 4, WCMG_K_ORTHO = 5, WCMG_K_COARSEN = 6, WCMG_K_CLOVER = 7,
-  WCMG_K_PACK = 8, WCMG_K_KRYLOV = 9, WCMG_K_DSLASH64 = 10, WCMG_K_OTHER = 11
+  WCMG_K_PACK = 8, WCMG_K_KRYLOV = 9, WCMG_K_DSLASH64 = 10, WCMG_K_PTC = 11
 } wcmg_kclass;
 
 typedef struct wcmg_ctx wcmg_ctx;
@@ -210,6 +212,57 @@ int wcmg_get_kstats(wcmg_ctx* ctx, wcmg_kstat* out);
 #define WCMG_NOALLOC_MAX_ELEMS 262144
 int wcmg_block_orthonormalise_noalloc(const void* vecs_in, void* vecs_out, const int dims[4], const int block[4],
                                       int nvec, void* stream);
+
+/* ---- Learned coarse correction (no counterpart in the paper) ----------------
+ * A gauge-equivariant parallel-transport convolution (PTC) network N maps a fine
+ * residual r to an approximation of the coarse-grid correction P D_c^-1 P^dag r
+ * of the multigrid cycle (Sec. 2.1 operators).  Layer:
+ *   out_i(x) = sum_j sum_h W_{ijh} (T_h in_j)(x),  h = 0 (identity),
+ *   1 + 2 mu: U_mu(x) f(x + mu),  2 + 2 mu: U_mu(x - mu)^dag f(x - mu),
+ * W_{ijh} complex 4x4 spin matrices; two linear layers 1 -> 12 -> 1 fields.
+ * Weights: complex128 [3456] = W1 [12][1][9][4][4] followed by W2 [1][12][9][4][4].
+ * The network runs in FP32 and needs the gauge field (wcmg_set_gauge). */
+#define WCMG_PTC_HIDDEN 12
+#define WCMG_PTC_NWEIGHTS 3456
+int wcmg_ptc_set_weights(wcmg_ctx* ctx, const void* W, int where, void* stream);
+int wcmg_ptc_get_weights(wcmg_ctx* ctx, void* W, int where, void* stream);
+/* out = N(in) for nrhs fine fields (external fine layout). */
+int wcmg_ptc_forward(wcmg_ctx* ctx, const void* in, void* out, int nrhs, int where, void* stream);
+/* Given gout = dL/d conj(N(in)) (external fine layout), gin = dL/d conj(in) and
+ * gW = dL/d conj(W) (complex128 [3456]) summed over the nrhs fields. */
+int wcmg_ptc_backward(wcmg_ctx* ctx, const void* in, const void* gout, void* gin, void* gW, int nrhs, int where,
+                      void* stream);
+
+typedef struct wcmg_train_opts {
+  int npairs;          /* training pairs generated by the multigrid (even split: Gaussian r and
+                          residuals r = b - D M_0(b) of one cycle on a Gaussian b) */
+  int batch;           /* fields per optimisation step */
+  int steps;           /* Adam steps */
+  double lr;           /* Adam learning rate */
+  double target_tol;   /* coarse solves of the targets e = P GMRES(P^dag r) to this tolerance */
+  uint64_t seed;       /* counter-based generator seed for the Gaussian fields */
+} wcmg_train_opts;
+typedef struct wcmg_train_stats {
+  double loss_initial; /* mean ||N(r) - e||^2 / ||e||^2 over the pairs before training */
+  double loss_final;   /* same after training */
+  double ms_generate;  /* wall time of the pair generation */
+  double ms_train;     /* wall time of the optimisation */
+} wcmg_train_stats;
+/* Generate training pairs with the current setup (wcmg_setup first; inner_prec
+ * F32) and fit the PTC weights with Adam on the loss ||N(r) - e||^2 / ||e||^2
+ * (Wirtinger gradients, the real gradient is twice their real/imaginary parts). */
+int wcmg_ptc_train(wcmg_ctx* ctx, const wcmg_train_opts* opts, wcmg_train_stats* st, void* stream);
+
+/* Coarse correction used by wcmg_solve's cycle (inner_prec F32 for the learned modes):
+ *   WCMG_COARSE_MG          plain multigrid (default)
+ *   WCMG_COARSE_WARMSTART   the coarsest GMRES starts from P^dag N(r) instead of 0
+ *   WCMG_COARSE_LEARNED     the top-level coarse correction is N(r) (no coarse solve);
+ *                           when an outer iteration reduces the residual estimate by
+ *                           less than the factor fallback_ratio the solve falls back to
+ *                           plain MG for the rest of the solve (fallback_ratio <= 0:
+ *                           never; 0.9 is the library's default). */
+typedef enum { WCMG_COARSE_MG = 0, WCMG_COARSE_WARMSTART = 1, WCMG_COARSE_LEARNED = 2 } wcmg_coarse_mode;
+int wcmg_set_coarse_mode(wcmg_ctx* ctx, int mode, double fallback_ratio);
 
 /* Checkpoint of the setup (near-null vectors and coarse links of every level). */
 int wcmg_save_setup(wcmg_ctx* ctx, const char* path);

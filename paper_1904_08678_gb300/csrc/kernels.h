@@ -136,3 +136,17 @@ void launch_gmres_start(const GmresState& s, const double* nrm2, double tol, int
 namespace wcmg {
 void launch_sqrt_inplace(double* x, int n, cudaStream_t st);
 }
+
+namespace wcmg {
+// ---- learned coarse correction: PTC network (ptc.cu), FP32 fields [12][V] ----
+void launch_ptc_forward(float2* out, const float2* in, const float2* W, const float2* U, const int* nbr, int V,
+                        int nin, int nout, int nrhs, cudaStream_t st);
+void launch_ptc_backward_data(float2* gin, const float2* gout, const float2* W, const float2* U, const int* nbr, int V,
+                              int nin, int nout, int nrhs, cudaStream_t st);
+long long ptc_wgrad_partial_size(int V, int nin, int nout, int nrhs);
+void launch_ptc_wgrad(float2* gW, float2* partial, const float2* gout, const float2* in, const float2* U,
+                      const int* nbr, int V, int nin, int nout, int nrhs, cudaStream_t st);
+void launch_ptc_adam(float2* w, const float2* g, float2* m, float2* v, int n, float lr, int t, cudaStream_t st);
+void launch_gaussian_field(float2* out, long long n, unsigned long long seed, unsigned long long stream,
+                           cudaStream_t st);
+}  // namespace wcmg

@@ -195,6 +195,16 @@ struct wcmg_ctx {
   Prof prof;
   cudaStream_t st = nullptr;
   long long coarse_its = 0;
+  // learned coarse correction (PTC network)
+  DevBuf<float2> ptcW, ptcG, ptcM, ptcV, ptcPartial;
+  DevBuf<double> ptcScale;
+  DevBuf<float2> ds_r, ds_e;
+  bool have_ptc = false;
+  int ptc_t = 0;
+  int coarse_mode = WCMG_COARSE_MG;
+  double fallback_ratio = 0.9;
+  bool learned_on = false, learned_fallback = false;
+  int learned_cycles = 0;
   ~wcmg_ctx() {
     if (h_flags) cudaFreeHost(h_flags);
     if (h_vals) cudaFreeHost(h_vals);
@@ -440,6 +450,11 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
     launch_gmres_start(S, L.sc.slot(1), tol, nrhs, L.sc.slot(2), c->st);
     launch_scale_dev<R>(Vb, r, L.sc.slot(2), 0, n, nrhs, c->st);
     int steps = 0;
+    std::vector<double> prev_res;
+    if (precond && l == 0 && c->learned_on) {
+      const double* rs = read_doubles(c, S.resid, nrhs);
+      prev_res.assign(rs, rs + nrhs);
+    }
     const int* act = read_ints(c, S.active, nrhs);
     bool any = false;
     for (int q = 0; q < nrhs; ++q) any |= act[q] != 0;
@@ -464,6 +479,21 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
       launch_scale_dev<R>(Vb + (long long)(j + 1) * bstride, w, L.sc.slot(3), 0, n, nrhs, c->st);
       ++steps;
       ++out.iterations;
+      if (precond && l == 0 && c->learned_on && c->coarse_mode == WCMG_COARSE_LEARNED) {
+        // plain multigrid judges the learned correction: fall back when an outer
+        // iteration reduces the residual estimate by less than fallback_ratio
+        const double* rs = read_doubles(c, S.resid, nrhs);
+        double worst = 0.0;
+        for (int q = 0; q < nrhs; ++q) {
+          const double prev = prev_res.size() == (size_t)nrhs ? prev_res[q] : 0.0;
+          if (prev > 0.0) worst = std::max(worst, rs[q] / prev);
+        }
+        prev_res.assign(rs, rs + nrhs);
+        if (c->fallback_ratio > 0.0 && worst > c->fallback_ratio) {
+          c->learned_on = false;
+          c->learned_fallback = true;
+        }
+      }
       act = read_ints(c, S.active, nrhs);
       any = false;
       for (int q = 0; q < nrhs; ++q) any |= act[q] != 0;
@@ -498,6 +528,56 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
   }
 }
 
+// ---------------- learned coarse correction (PTC network) ----------------
+constexpr int PTC_NW1 = WCMG_PTC_HIDDEN * 1 * 9 * 16;
+constexpr int PTC_NW2 = 1 * WCMG_PTC_HIDDEN * 9 * 16;
+
+static void ptc_layer_fwd(wcmg_ctx* c, float2* out, const float2* in, const float2* W, int nin, int nout, int nrhs) {
+  Level& L = c->L[0];
+  const double V = L.g.V;
+  KPROF(c, WCMG_K_PTC, V * 96.0 * (nin + nout) * nrhs + 8.0 * V * 72.0 * 4,
+        V * 8.0 * (double)nin * nout * 9 * (48 + 36) * nrhs,
+        launch_ptc_forward(out, in, W, c->gauge32.p, L.g.d_nbr.p, L.g.V, nin, nout, nrhs, c->st));
+}
+
+// out = N(in), FP32, nrhs fields in the internal fine layout
+static void ptc_forward(wcmg_ctx* c, float2* out, const float2* in, int nrhs) {
+  if (!c->have_ptc) throw Error(WCMG_ERR_STATE, "PTC weights not set");
+  if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+  float2* hid = ws<float>(c->L[0], "ptc_hid", (long long)WCMG_PTC_HIDDEN * nrhs);
+  ptc_layer_fwd(c, hid, in, c->ptcW.p, 1, WCMG_PTC_HIDDEN, nrhs);
+  ptc_layer_fwd(c, out, hid, c->ptcW.p + PTC_NW1, WCMG_PTC_HIDDEN, 1, nrhs);
+}
+
+// Gradients dL/d conj(W) into ptcG (summed over the fields) and, if gin is not
+// null, dL/d conj(in), given gout = dL/d conj(N(in)).
+static void ptc_backward(wcmg_ctx* c, const float2* in, const float2* gout, float2* gin, int nrhs) {
+  Level& L = c->L[0];
+  const int V = L.g.V, H = WCMG_PTC_HIDDEN;
+  float2* hid = ws<float>(L, "ptc_hid", (long long)H * nrhs);
+  float2* ghid = ws<float>(L, "ptc_ghid", (long long)H * nrhs);
+  ptc_layer_fwd(c, hid, in, c->ptcW.p, 1, H, nrhs);
+  c->ptcPartial.ensure((size_t)std::max(ptc_wgrad_partial_size(V, H, 1, nrhs), ptc_wgrad_partial_size(V, 1, H, nrhs)));
+  const double flops = (double)V * 8.0 * H * 9 * (48 + 36) * nrhs;
+  KPROF(c, WCMG_K_PTC, (double)V * 96.0 * (H + 1) * nrhs, flops,
+        launch_ptc_wgrad(c->ptcG.p + PTC_NW1, c->ptcPartial.p, gout, hid, c->gauge32.p, L.g.d_nbr.p, V, H, 1, nrhs,
+                         c->st));
+  KPROF(c, WCMG_K_PTC, (double)V * 96.0 * (H + 1) * nrhs, flops,
+        launch_ptc_backward_data(ghid, gout, c->ptcW.p + PTC_NW1, c->gauge32.p, L.g.d_nbr.p, V, H, 1, nrhs, c->st));
+  KPROF(c, WCMG_K_PTC, (double)V * 96.0 * (H + 1) * nrhs, flops,
+        launch_ptc_wgrad(c->ptcG.p, c->ptcPartial.p, ghid, in, c->gauge32.p, L.g.d_nbr.p, V, 1, H, nrhs, c->st));
+  if (gin)
+    KPROF(c, WCMG_K_PTC, (double)V * 96.0 * (H + 1) * nrhs, flops,
+          launch_ptc_backward_data(gin, ghid, c->ptcW.p, c->gauge32.p, L.g.d_nbr.p, V, 1, H, nrhs, c->st));
+}
+
+static void ptc_alloc(wcmg_ctx* c) {
+  c->ptcW.ensure(WCMG_PTC_NWEIGHTS);
+  c->ptcG.ensure(WCMG_PTC_NWEIGHTS);
+  c->ptcM.ensure(WCMG_PTC_NWEIGHTS);
+  c->ptcV.ensure(WCMG_PTC_NWEIGHTS);
+}
+
 // ---------------- multigrid cycle ----------------
 // M_l(r): e = P_l CoarseSolve_{l+1}(P_l^dag r); e += MR_k(D_l; r - D_l e).
 // CoarseSolve is GMRES at the coarsest level and one cycle of level l+1 between.
@@ -506,17 +586,33 @@ static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
   Level& L = c->L[l];
   Level& C = c->L[l + 1];
   const long long n = L.n();
-  cplx<R>* rc = ws<R>(C, "cyc_rc", nrhs);
-  cplx<R>* ec = ws<R>(C, "cyc_ec", nrhs);
-  restrict_op<R>(c, l, rc, r, nrhs);
-  if (l + 1 == c->p.n_levels - 1) {
-    KrylovOut k = fgmres<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter, true,
-                            false, false);
-    c->coarse_its += k.iterations;
+  const bool learned = sizeof(R) == 4 && l == 0 && c->learned_on;
+  if (learned && c->coarse_mode == WCMG_COARSE_LEARNED) {
+    // learned coarse correction in place of P CoarseSolve(P^dag r)
+    ptc_forward(c, (float2*)e, (const float2*)r, nrhs);
+    ++c->learned_cycles;
   } else {
-    cycle<R>(c, l + 1, ec, rc, nrhs);
+    cplx<R>* rc = ws<R>(C, "cyc_rc", nrhs);
+    cplx<R>* ec = ws<R>(C, "cyc_ec", nrhs);
+    restrict_op<R>(c, l, rc, r, nrhs);
+    if (l + 1 == c->p.n_levels - 1) {
+      bool x0 = false;
+      if (learned && c->coarse_mode == WCMG_COARSE_WARMSTART) {
+        // initial guess of the coarsest GMRES: P^dag N(r)
+        cplx<R>* t = ws<R>(L, "cyc_ptc", nrhs);
+        ptc_forward(c, (float2*)t, (const float2*)r, nrhs);
+        restrict_op<R>(c, l, ec, t, nrhs);
+        ++c->learned_cycles;
+        x0 = true;
+      }
+      KrylovOut k = fgmres<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter,
+                              !x0, false, false);
+      c->coarse_its += k.iterations;
+    } else {
+      cycle<R>(c, l + 1, ec, rc, nrhs);
+    }
+    prolong_op<R>(c, l, e, ec, nrhs);
   }
-  prolong_op<R>(c, l, e, ec, nrhs);
   cplx<R>* t = ws<R>(L, "cyc_t", nrhs);
   cplx<R>* s = ws<R>(L, "cyc_s", nrhs);
   apply_op<R>(c, l, t, e, nrhs);
@@ -728,6 +824,122 @@ static double true_residual(wcmg_ctx* c, const double2* x, const double2* b, int
   double worst = 0;
   for (int q = 0; q < nrhs; ++q) worst = std::max(worst, h[q] > 0 ? std::sqrt(rn[q] / h[q]) : 0.0);
   return worst;
+}
+
+// ---------------- training of the learned coarse correction ----------------
+// Pairs (r, e = P GMRES(D_c; P^dag r)) are generated with the current hierarchy
+// in FP32 batches: half Gaussian r, half residuals r = b - D M_0(b) of one
+// multigrid cycle on a Gaussian b (the kind of vectors FGMRES feeds its
+// preconditioner); each r is normalised.  The loss is the mean over pairs of
+// ||N(r) - e||^2 / ||e||^2; Adam steps over contiguous minibatches.
+static double ptc_eval(wcmg_ctx* c, int npairs, int chunk) {
+  Level& L = c->L[0];
+  const long long n = L.n();
+  float2* out = ws<float>(L, "ptc_out", chunk);
+  double total = 0.0;
+  for (int p0 = 0; p0 < npairs; p0 += chunk) {
+    const int k = std::min(chunk, npairs - p0);
+    ptc_forward(c, out, c->ds_r.p + p0 * n, k);
+    launch_axpby<float>(out, -1.0, c->ds_e.p + p0 * n, 1.0, n, k, c->st);  // out = N(r) - e
+    norm2_op<float>(c, L.sc.slot(7), out, n, k);
+    norm2_op<float>(c, L.sc.slot(6), c->ds_e.p + p0 * n, n, k);
+    std::vector<double> d2(k);
+    const double* h = read_doubles(c, L.sc.slot(7), k);
+    for (int q = 0; q < k; ++q) d2[q] = h[q];
+    h = read_doubles(c, L.sc.slot(6), k);
+    for (int q = 0; q < k; ++q) total += d2[q] / h[q];
+  }
+  return total / npairs;
+}
+
+static void ptc_train(wcmg_ctx* c, const wcmg_train_opts* o, wcmg_train_stats* st) {
+  if (c->p.inner_prec != WCMG_F32) throw Error(WCMG_ERR_ARG, "training needs inner_prec F32");
+  for (int l = 0; l + 1 < c->p.n_levels; ++l)
+    if (!c->L[l].have_P || !c->L[l + 1].have_op) throw Error(WCMG_ERR_STATE, "setup not done");
+  const int np = o->npairs, B = o->batch;
+  const int chunk = max_rhs_all(c);
+  if (np < 1 || B < 1 || B > chunk || o->steps < 0) throw Error(WCMG_ERR_ARG, "npairs/batch/steps out of range");
+  Level& L = c->L[0];
+  Level& C1 = c->L[1];
+  const long long n = L.n();
+  L.sc.ensure(chunk, std::max(c->p.outer_restart, c->p.coarse_restart));
+  ptc_alloc(c);
+  if (!c->have_ptc) {  // small random start (counter-based generator), the scale keeps N(r) ~ 0.05 r
+    launch_gaussian_field(c->ptcW.p, WCMG_PTC_NWEIGHTS, o->seed, 977, c->st);
+    launch_axpby<float>(c->ptcW.p, 0.0, c->ptcW.p, 0.02, WCMG_PTC_NWEIGHTS, 1, c->st);
+    c->have_ptc = true;
+  }
+  WCMG_CUDA(cudaMemsetAsync(c->ptcM.p, 0, sizeof(float2) * WCMG_PTC_NWEIGHTS, c->st));
+  WCMG_CUDA(cudaMemsetAsync(c->ptcV.p, 0, sizeof(float2) * WCMG_PTC_NWEIGHTS, c->st));
+  c->ptc_t = 0;
+  auto t0 = std::chrono::steady_clock::now();
+  c->ds_r.ensure((size_t)np * n);
+  c->ds_e.ensure((size_t)np * n);
+  const bool saved_on = c->learned_on;
+  c->learned_on = false;
+  for (int p0 = 0; p0 < np; p0 += chunk) {
+    const int k = std::min(chunk, np - p0);
+    float2* r = c->ds_r.p + p0 * n;
+    float2* e = c->ds_e.p + p0 * n;
+    launch_gaussian_field(r, (long long)k * n, o->seed, 1 + p0, c->st);
+    const int nh = k / 2;  // the second half becomes residuals after one cycle
+    if (nh > 0) {
+      float2* b = r + (k - nh) * n;
+      float2* x = ws<float>(L, "ptc_x", nh);
+      float2* t = ws<float>(L, "ptc_t", nh);
+      cycle<float>(c, 0, x, b, nh);
+      apply_op<float>(c, 0, t, x, nh);
+      launch_axpby<float>(b, -1.0, t, 1.0, n, nh, c->st);  // b <- b - D M(b)
+    }
+    norm2_op<float>(c, L.sc.slot(7), r, n, k);
+    launch_scale_dev<float>(r, r, L.sc.slot(7), 1, n, k, c->st);
+    float2* rc = ws<float>(C1, "ptc_rc", k);
+    float2* ec = ws<float>(C1, "ptc_ec", k);
+    restrict_op<float>(c, 0, rc, r, k);
+    if (c->p.n_levels == 2) {
+      fgmres<float>(c, 1, ec, rc, k, c->p.coarse_restart, o->target_tol, 2000, true, false, false);
+    } else {
+      cycle<float>(c, 1, ec, rc, k);  // deeper hierarchies: one coarse cycle as the target
+    }
+    prolong_op<float>(c, 0, e, ec, k);
+  }
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  auto t1 = std::chrono::steady_clock::now();
+  st->loss_initial = ptc_eval(c, np, chunk);
+  // per-pair gradient scale 1 / (||e||^2 B)
+  std::vector<double> e2(np);
+  for (int p0 = 0; p0 < np; p0 += chunk) {
+    const int k = std::min(chunk, np - p0);
+    norm2_op<float>(c, L.sc.slot(6), c->ds_e.p + p0 * n, n, k);
+    const double* h = read_doubles(c, L.sc.slot(6), k);
+    for (int q = 0; q < k; ++q) e2[p0 + q] = h[q];
+  }
+  c->ptcScale.ensure(np);
+  {
+    std::vector<double> sc(np);
+    for (int q = 0; q < np; ++q) sc[q] = 1.0 / (e2[q] * B);
+    WCMG_CUDA(cudaMemcpyAsync(c->ptcScale.p, sc.data(), sizeof(double) * np, cudaMemcpyHostToDevice, c->st));
+  }
+  float2* out = ws<float>(L, "ptc_out", chunk);
+  for (int step = 0; step < o->steps; ++step) {
+    const int p0 = (int)(((long long)step * B) % np);
+    const int k = std::min(B, np - p0);
+    const float2* rb = c->ds_r.p + p0 * n;
+    ptc_forward(c, out, rb, k);
+    launch_axpby<float>(out, -1.0, c->ds_e.p + p0 * n, 1.0, n, k, c->st);       // N(r) - e
+    launch_scale_dev<float>(out, out, c->ptcScale.p + p0, 0, n, k, c->st);      // dL/d conj(N)
+    ptc_backward(c, rb, out, nullptr, k);
+    ++c->ptc_t;
+    KPROF(c, WCMG_K_PTC, 5.0 * WCMG_PTC_NWEIGHTS * 8, 0.0,
+          launch_ptc_adam(c->ptcW.p, c->ptcG.p, c->ptcM.p, c->ptcV.p, WCMG_PTC_NWEIGHTS, (float)o->lr, c->ptc_t,
+                          c->st));
+  }
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  auto t2 = std::chrono::steady_clock::now();
+  st->loss_final = ptc_eval(c, np, chunk);
+  st->ms_generate = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  st->ms_train = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  c->learned_on = saved_on;
 }
 
 // ---------------- external I/O ----------------
@@ -1292,6 +1504,13 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   c->coarse_its = 0;
   const long long l0 = launch_counter();
   auto t0 = std::chrono::steady_clock::now();
+  if (c->coarse_mode != WCMG_COARSE_MG) {
+    if (!c->have_ptc) throw Error(WCMG_ERR_STATE, "learned coarse mode needs PTC weights");
+    if (inner64(c)) throw Error(WCMG_ERR_ARG, "learned coarse modes need inner_prec F32");
+  }
+  c->learned_on = c->coarse_mode != WCMG_COARSE_MG;
+  c->learned_fallback = false;
+  c->learned_cycles = 0;
   Level& L = c->L[0];
   const size_t bytes = (size_t)nrhs * L.n() * 16;
   const double2* bi = in_dev(c, b, bytes, where, 0);
@@ -1313,6 +1532,9 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   kstat_delta(st->k, c->prof.k, k0);
   st->coarse_iterations = c->coarse_its;
   st->kernel_launches = launch_counter() - l0;
+  st->learned_cycles = c->learned_cycles;
+  st->learned_fallback = c->learned_fallback ? 1 : 0;
+  c->learned_on = false;
   if (!st->converged) {
     c->err = "outer solver reached outer_maxiter";
     return WCMG_ERR_NOT_CONVERGED;
@@ -1333,6 +1555,89 @@ int wcmg_get_kstats(wcmg_ctx* c, wcmg_kstat* out) {
   if (!out) throw Error(WCMG_ERR_ARG, "out");
   c->prof.flush();
   std::memcpy(out, c->prof.k, sizeof(c->prof.k));
+  API_END(c)
+}
+
+int wcmg_ptc_set_weights(wcmg_ctx* c, const void* W, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  const double2* w = in_dev(c, W, sizeof(double2) * WCMG_PTC_NWEIGHTS, where, 0);
+  ptc_alloc(c);
+  launch_convert<double, float>(c->ptcW.p, w, WCMG_PTC_NWEIGHTS, c->st);
+  c->have_ptc = true;
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  API_END(c)
+}
+
+int wcmg_ptc_get_weights(wcmg_ctx* c, void* W, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!c->have_ptc) throw Error(WCMG_ERR_STATE, "PTC weights not set");
+  const size_t bytes = sizeof(double2) * WCMG_PTC_NWEIGHTS;
+  double2* o = out_dev(c, W, bytes, where, 1);
+  launch_convert<float, double>(o, c->ptcW.p, WCMG_PTC_NWEIGHTS, c->st);
+  out_finish(c, W, o, bytes, where);
+  API_END(c)
+}
+
+int wcmg_ptc_forward(wcmg_ctx* c, const void* in, void* out, int nrhs, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_rhs(c, nrhs);
+  Level& L = c->L[0];
+  const size_t bytes = (size_t)nrhs * L.n() * 16;
+  const double2* i = in_dev(c, in, bytes, where, 0);
+  double2* o = out_dev(c, out, bytes, where, 1);
+  float2* a = ws<float>(L, "io_a", nrhs);
+  float2* b = ws<float>(L, "io_b", nrhs);
+  pack_level<float>(c, 0, a, i, nrhs);
+  ptc_forward(c, b, a, nrhs);
+  unpack_level<float>(c, 0, o, b, nrhs);
+  out_finish(c, out, o, bytes, where);
+  API_END(c)
+}
+
+int wcmg_ptc_backward(wcmg_ctx* c, const void* in, const void* gout, void* gin, void* gW, int nrhs, int where,
+                      void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_rhs(c, nrhs);
+  if (!c->have_ptc) throw Error(WCMG_ERR_STATE, "PTC weights not set");
+  Level& L = c->L[0];
+  const size_t bytes = (size_t)nrhs * L.n() * 16, wbytes = sizeof(double2) * WCMG_PTC_NWEIGHTS;
+  const double2* i = in_dev(c, in, bytes, where, 0);
+  const double2* g = in_dev(c, gout, bytes, where, 1);
+  float2* a = ws<float>(L, "io_a", nrhs);
+  float2* b = ws<float>(L, "io_b", nrhs);
+  float2* d = ws<float>(L, "io_c", nrhs);
+  pack_level<float>(c, 0, a, i, nrhs);
+  pack_level<float>(c, 0, b, g, nrhs);
+  ptc_backward(c, a, b, d, nrhs);
+  double2* go = out_dev(c, gin, bytes, where, 2);
+  unpack_level<float>(c, 0, go, d, nrhs);
+  out_finish(c, gin, go, bytes, where);
+  double2* wo = (where == WCMG_DEVICE) ? (double2*)gW : (double2*)c->stage[1].ensure(wbytes);
+  launch_convert<float, double>(wo, c->ptcG.p, WCMG_PTC_NWEIGHTS, c->st);
+  out_finish(c, gW, wo, wbytes, where);
+  API_END(c)
+}
+
+int wcmg_ptc_train(wcmg_ctx* c, const wcmg_train_opts* opts, wcmg_train_stats* st, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!opts || !st) throw Error(WCMG_ERR_ARG, "opts and st are required");
+  std::memset(st, 0, sizeof(*st));
+  ptc_train(c, opts, st);
+  check_device_waits(c);
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_set_coarse_mode(wcmg_ctx* c, int mode, double fallback_ratio) {
+  API_BEGIN(c)
+  if (mode < WCMG_COARSE_MG || mode > WCMG_COARSE_LEARNED) throw Error(WCMG_ERR_ARG, "coarse mode");
+  c->coarse_mode = mode;
+  c->fallback_ratio = fallback_ratio;
   API_END(c)
 }
 

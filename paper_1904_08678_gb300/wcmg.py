@@ -32,7 +32,9 @@ OK, ERR_ARG, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_NAN, ERR_TIMEOUT, ERR_O
 F64, F32, BF16, F16 = 0, 1, 2, 3
 HOST, DEVICE = 0, 1
 KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen", "clover", "pack", "krylov",
-          "dslash64", "other"]
+          "dslash64", "ptc"]
+PTC_HIDDEN, PTC_NWEIGHTS = 12, 3456
+COARSE_MG, COARSE_WARMSTART, COARSE_LEARNED = 0, 1, 2
 
 
 class wcmg_params(ctypes.Structure):
@@ -75,12 +77,24 @@ class wcmg_stats(ctypes.Structure):
         ("ms_setup_init", ctypes.c_double),
         ("ms_setup_refine", ctypes.c_double),
         ("ms_solve", ctypes.c_double),
+        ("learned_fallback", ctypes.c_int),
+        ("learned_cycles", ctypes.c_int),
         ("k", wcmg_kstat * NKCLASS),
     ]
 
     def kernels(self):
         return {KCLASS[i]: dict(launches=self.k[i].launches, ms=self.k[i].ms, bytes=self.k[i].bytes,
                                 flops=self.k[i].flops) for i in range(NKCLASS) if self.k[i].launches}
+
+
+class wcmg_train_opts(ctypes.Structure):
+    _fields_ = [("npairs", ctypes.c_int), ("batch", ctypes.c_int), ("steps", ctypes.c_int), ("lr", ctypes.c_double),
+                ("target_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class wcmg_train_stats(ctypes.Structure):
+    _fields_ = [("loss_initial", ctypes.c_double), ("loss_final", ctypes.c_double),
+                ("ms_generate", ctypes.c_double), ("ms_train", ctypes.c_double)]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -108,6 +122,12 @@ _SIGS = {
     "wcmg_set_profile": ([_PCTX, _i], _i),
     "wcmg_get_kstats": ([_PCTX, ctypes.POINTER(wcmg_kstat)], _i),
     "wcmg_block_orthonormalise_noalloc": ([_vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp], _i),
+    "wcmg_ptc_set_weights": ([_PCTX, _vp, _i, _vp], _i),
+    "wcmg_ptc_get_weights": ([_PCTX, _vp, _i, _vp], _i),
+    "wcmg_ptc_forward": ([_PCTX, _vp, _vp, _i, _i, _vp], _i),
+    "wcmg_ptc_backward": ([_PCTX, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
+    "wcmg_ptc_train": ([_PCTX, ctypes.POINTER(wcmg_train_opts), ctypes.POINTER(wcmg_train_stats), _vp], _i),
+    "wcmg_set_coarse_mode": ([_PCTX, _i, _d], _i),
     "wcmg_save_setup": ([_PCTX, ctypes.c_char_p], _i),
     "wcmg_load_setup": ([_PCTX, ctypes.c_char_p], _i),
 }
@@ -286,6 +306,37 @@ class Context:
         self._check(wcmg_get_kstats(self.h, arr))
         return {KCLASS[i]: dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes, flops=arr[i].flops)
                 for i in range(NKCLASS)}
+
+    def ptc_set_weights(self, W, stream=None):
+        p, w = _buf(W)
+        return self._check(wcmg_ptc_set_weights(self.h, p, w, _stream(stream)))
+
+    def ptc_get_weights(self, W, stream=None):
+        p, w = _buf(W, True)
+        return self._check(wcmg_ptc_get_weights(self.h, p, w, _stream(stream)))
+
+    def ptc_forward(self, inp, out, nrhs=1, stream=None):
+        pi, wi = _buf(inp)
+        po, wo = _buf(out, True)
+        assert wi == wo
+        return self._check(wcmg_ptc_forward(self.h, pi, po, nrhs, wi, _stream(stream)))
+
+    def ptc_backward(self, inp, gout, gin, gW, nrhs=1, stream=None):
+        pi, wi = _buf(inp)
+        pg, wg = _buf(gout)
+        pgi, wgi = _buf(gin, True)
+        pw, ww = _buf(gW, True)
+        assert wi == wg == wgi == ww
+        return self._check(wcmg_ptc_backward(self.h, pi, pg, pgi, pw, nrhs, wi, _stream(stream)))
+
+    def ptc_train(self, npairs=32, batch=4, steps=100, lr=1e-3, target_tol=1e-6, seed=1, stream=None):
+        o = wcmg_train_opts(npairs, batch, steps, lr, target_tol, seed)
+        st = wcmg_train_stats()
+        self._check(wcmg_ptc_train(self.h, ctypes.byref(o), ctypes.byref(st), _stream(stream)))
+        return st
+
+    def set_coarse_mode(self, mode, fallback_ratio=0.9):
+        return self._check(wcmg_set_coarse_mode(self.h, mode, fallback_ratio))
 
     def save_setup(self, path):
         return self._check(wcmg_save_setup(self.h, path.encode()))
