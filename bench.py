@@ -45,7 +45,7 @@ ORACLE_SAMPLE_DIMS = (8, 8, 8, 8)
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
 # for the kernel sources it was taken on (sha256 prefix of csrc/*.cu, *.cuh, *.h).
-NCU_TRAFFIC = {}  # {"<class>": {"src": "<hash>", "bytes_per_launch": B, "profile": "profiles/<file>"}}
+NCU_TRAFFIC = {"ortho": {"src": "484a4b5165c88129", "bytes_per_launch": 1185395712, "profile": "profiles/k_block_ortho_config2.md"}}
 
 KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen", "clover", "pack", "krylov",
           "dslash64", "other"]
