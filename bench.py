@@ -37,8 +37,22 @@ WORKLOAD = dict(
              "Nvec 24 (nbasis 48), 3 initial + 2 refinement sweeps, MR(4) smoother, GMRES(20) coarse to 0.05, "
              "FGMRES(20) to 1e-10, 1 Gaussian rhs",
     dims=(16, 16, 16, 32), eps=0.25, m0=-0.2, csw=1.0, blocks=[(4, 4, 4, 4)], nvec=[24],
-    init_sweeps=3, refine_sweeps=2, gauge_seed=1002, source_seed=0,
+    init_sweeps=3, refine_sweeps=2, gauge_seed=1002, source_seed=0, nrhs=1,
 )
+# Other configurations, measured with --workload (the default line is the one above).
+WORKLOADS = {
+    "c2": WORKLOAD,
+    "c3": dict(workload="wilson-clover 3-level MG, 32^3x64, eps 0.2, m0 -0.25, csw 1.0, blocks 4^4 -> 8^3x16 "
+                        "-> 2^4 -> 4^3x8, Nvec 24 / 32 (nbasis 48 / 64), 3 initial + 2 refinement sweeps, "
+                        "FGMRES(20) to 1e-10, 1 Gaussian rhs",
+               dims=(32, 32, 32, 64), eps=0.2, m0=-0.25, csw=1.0, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)],
+               nvec=[24, 32], init_sweeps=3, refine_sweeps=2, gauge_seed=1003, source_seed=0, nrhs=1),
+    "c4": dict(workload="wilson-clover 3-level MG, 24^3x48, eps 0.25, m0 -0.2, csw 1.0, blocks 4^4 -> 6^3x12 "
+                        "-> 2^4 -> 3^3x6, Nvec 24 / 24 (nbasis 48), 3 initial + 2 refinement sweeps, "
+                        "FGMRES(20) to 1e-10, NRHS Gaussian rhs solved together",
+               dims=(24, 24, 24, 48), eps=0.25, m0=-0.2, csw=1.0, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)],
+               nvec=[24, 24], init_sweeps=3, refine_sweeps=2, gauge_seed=1004, source_seed=0, nrhs=12),
+}
 # Reduced-volume sample of the same workload for the CPU oracle (same blocks,
 # Nvec and parameters; time scaled by the volume ratio).
 ORACLE_SAMPLE_DIMS = (8, 8, 8, 8)
@@ -181,19 +195,31 @@ class L2Flush:
 
 
 # ---------------------------------------------------------------- inputs
+def level_dims(cfg):
+    out = [tuple(cfg["dims"])]
+    for b in cfg["blocks"]:
+        out.append(tuple(L // x for L, x in zip(out[-1], b)))
+    return out
+
+
 def make_inputs(cfg):
     from paper_1904_08678_gb300 import inputs
     dims = cfg["dims"]
     U = inputs.random_gauge(dims, cfg["eps"], cfg["gauge_seed"])
-    iv = inputs.setup_vectors(dims, 12, cfg["nvec"][0], 0, cfg["gauge_seed"])
-    b = inputs.source(dims, cfg["source_seed"])
+    ld = level_dims(cfg)
+    ivs, nc = [], 12
+    for l, nv in enumerate(cfg["nvec"]):
+        ivs.append(inputs.setup_vectors(ld[l], nc, nv, l, cfg["gauge_seed"]).ravel())
+        nc = 2 * nv
+    iv = np.concatenate(ivs) if len(ivs) > 1 else ivs[0]
+    b = inputs.source(dims, cfg["source_seed"], nrhs=cfg.get("nrhs", 1))
     return U, iv, b
 
 
 def params(wcmg, cfg, inner, links, profile=0):
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
-                            n_levels=len(cfg["blocks"]) + 1, max_rhs=1, profile=profile)
+                            n_levels=len(cfg["blocks"]) + 1, max_rhs=cfg.get("nrhs", 1), profile=profile)
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -217,7 +243,10 @@ def run_gpu(args, rank, world, local):
     dist = dist_init(world, "nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    cfg = WORKLOAD
+    cfg = dict(WORKLOADS[args.workload])
+    if args.nrhs:
+        cfg["nrhs"] = args.nrhs
+    nrhs = cfg.get("nrhs", 1)
     U, iv, b = make_inputs(cfg)
     Ud = torch.from_numpy(U).to(dev)
     ivd = torch.from_numpy(iv).to(dev)
@@ -229,7 +258,7 @@ def run_gpu(args, rank, world, local):
     def step(x, U_, iv_, b_):
         ctx.set_gauge(U_, stream)
         s1 = ctx.setup(iv_, stream)
-        s2 = ctx.solve(b_, x, stream=stream)
+        s2 = ctx.solve(b_, x, nrhs=nrhs, stream=stream)
         return s1, s2
 
     # warm-up, all kernel classes timed: find the dominant class
@@ -327,7 +356,7 @@ def run_gpu(args, rank, world, local):
 
     # plain FP64 GPU multigrid on the same field, source and setup parameters (one step)
     fp64 = None
-    if args.inner != "f64" and not args.no_fp64_compare:
+    if args.inner != "f64" and not args.no_fp64_compare and args.workload == "c2":
         ctx64 = wcmg.Context(params(wcmg, cfg, "f64", "f32", profile=0))
         x64 = torch.zeros_like(bd)
         ctx64.set_gauge(Ud, stream)
@@ -348,10 +377,10 @@ def run_gpu(args, rank, world, local):
                 "setup_refine_ms": round(s1.ms_setup_refine, 2), "solve_ms": round(s2.ms_solve, 2)}
         ctx64.close()
 
-    learned = None if args.no_learned else learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush)
+    learned = None if (args.no_learned or args.workload != "c2") else learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "c2":
         cpu = oracle_sample()
 
     if rank == 0:
@@ -361,7 +390,8 @@ def run_gpu(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.inner == "f32" else "f64", "data": "synthetic",
-            "config": {"workload": cfg["workload"], "dims": list(cfg["dims"]), "inner_prec": args.inner,
+            "config": {"workload": cfg["workload"].replace("NRHS", str(nrhs)), "dims": list(cfg["dims"]),
+                       "nrhs": nrhs, "inner_prec": args.inner,
                        "coarse_links": args.links if args.inner == "f32" else "f64",
                        "l2": "flushed between steps (256 MiB write + 256 MiB read)", "parallelism": f"replicas x{world}",
                        "gauge": "U = exp(i eps X), X = sum_a xi_a lambda_a, seed 1002"},
@@ -523,6 +553,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--nrhs", type=int, default=0, help="override the workload's number of right-hand sides")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

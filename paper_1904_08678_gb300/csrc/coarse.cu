@@ -10,6 +10,7 @@
 // with masked gathers, gives the block-interior and single-face parts that the
 // Galerkin construction (CoarsenOperator) of the next level needs.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -142,6 +143,159 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
   }
 }
 
+// Multi-rhs coarse apply on the 5th-generation tensor cores (tcgen05, BF16
+// operands, FP32 accumulation in TMEM).  Per coarse site x the nine blocks form
+// Y = M(x) Phi(x), M: nb x 9 nb complex, Phi: 9 nb x N complex.  Real embedding
+// along K (k' = 2 k + 0 for the real, + 1 for the imaginary part):
+//   A[a][2k] = Re M[a][k],  A[a][2k+1] = -Im M[a][k]       (rows a < nb)
+//   A[nb+a][2k] = Im M[a][k], A[nb+a][2k+1] = Re M[a][k]
+//   B[n][2k] = Re Phi[k][n], B[n][2k+1] = Im Phi[k][n]
+// so D[a][n] = Re Y[a][n], D[nb+a][n] = Im Y[a][n]; M_mma = 128 (rows 2 nb .. 127
+// zero).  One CTA (4 warps) per (site, tile of <= 64 rhs).  K is walked in chunks
+// of 64: the chunk is read from global memory into registers one step ahead,
+// converted and stored into one of two shared-memory stages in the no-swizzle
+// K-major core-matrix layout, and one thread issues four K = 16 MMAs and commits
+// them to the stage's mbarrier.  Every wait is bounded; a timeout sets *err = 3,
+// frees the TMEM and ends the CTA.
+constexpr int MMA_M = 128, MMA_KC = 64, MMA_LBO = 128, MMA_SBO = (MMA_KC / 8) * 128;
+constexpr int MMA_AE = 16, MMA_BE = 16;  // per-thread staging: nb <= 64, rhs tile <= 64
+
+__device__ __forceinline__ int mma_off(int row, int k) {
+  return (row >> 3) * MMA_SBO + (k >> 3) * MMA_LBO + (row & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+template <typename L>
+__global__ void __launch_bounds__(128) k_coarse_apply_mma(float2* __restrict__ out, const float2* __restrict__ in,
+                                                          const L* __restrict__ links, const int* __restrict__ nbr,
+                                                          int Vc, int nb, int ld, int nrhs, int ntile, int tmem_cols,
+                                                          int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int nsite[9];
+  const int a_bytes = MMA_M * MMA_KC * 2, stage_bytes = a_bytes + ntile * MMA_KC * 2;
+  const int site = blockIdx.x, r0 = blockIdx.y * ntile;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Kc = 9 * nb, nchunks = (2 * Kc + MMA_KC - 1) / MMA_KC;
+  const int nvalid = min(ntile, nrhs - r0);
+  for (int i = tid; i < 2 * stage_bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  if (tid < 9) nsite[tid] = tid == 0 ? site : nbr[(tid - 1) * Vc + site];
+  if (warp == 0) tmem_alloc(&tmem_base, tmem_cols);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = umma_idesc_bf16(MMA_M, ntile);
+  const L* lsite = links + (long long)site * nb * ld;
+  float2 ra[MMA_AE], rb[MMA_BE];
+  auto load_chunk = [&](int c) {
+    const int kc0 = c * (MMA_KC / 2);
+#pragma unroll
+    for (int q = 0; q < MMA_AE; ++q) {
+      const int e = tid + 128 * q;
+      float2 v = make_float2(0.f, 0.f);
+      if (e < nb * (MMA_KC / 2)) {
+        const int a = e >> 5, k = kc0 + (e & 31);
+        if (k < Kc) v = link_load<L, float>(lsite[(long long)a * ld + k]);
+      }
+      ra[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < MMA_BE; ++q) {
+      const int e = tid + 128 * q;
+      float2 v = make_float2(0.f, 0.f);
+      if (e < ntile * (MMA_KC / 2)) {
+        const int n = e >> 5, k = kc0 + (e & 31);
+        if (n < nvalid && k < Kc) {
+          const int d = k / nb, cc = k - d * nb;
+          v = in[((long long)(r0 + n) * Vc + nsite[d]) * nb + cc];
+        }
+      }
+      rb[q] = v;
+    }
+  };
+  auto store_chunk = [&](int s) {
+    unsigned char* A = smem + s * stage_bytes;
+    unsigned char* B = A + a_bytes;
+#pragma unroll
+    for (int q = 0; q < MMA_AE; ++q) {
+      const int e = tid + 128 * q;
+      if (e < nb * (MMA_KC / 2)) {
+        const int a = e >> 5, kk = 2 * (e & 31);
+        *reinterpret_cast<uint32_t*>(A + mma_off(a, kk)) = pack_bf16x2(ra[q].x, -ra[q].y);
+        *reinterpret_cast<uint32_t*>(A + mma_off(nb + a, kk)) = pack_bf16x2(ra[q].y, ra[q].x);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MMA_BE; ++q) {
+      const int e = tid + 128 * q;
+      if (e < ntile * (MMA_KC / 2)) {
+        const int n = e >> 5, kk = 2 * (e & 31);
+        *reinterpret_cast<uint32_t*>(B + mma_off(n, kk)) = pack_bf16x2(rb[q].x, rb[q].y);
+      }
+    }
+  };
+  bool ok = true;
+  load_chunk(0);
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c & 1;
+    if (c >= 2) {  // the MMAs of chunk c - 2 read this stage
+      const int good = mbar_wait_bounded(&bar[s], (uint32_t)(((c - 2) >> 1) & 1)) ? 1 : 0;
+      if (!__syncthreads_and(good)) { ok = false; break; }
+    }
+    store_chunk(s);
+    if (c + 1 < nchunks) load_chunk(c + 1);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(smem + s * stage_bytes), b0 = a0 + a_bytes;
+#pragma unroll
+      for (int q = 0; q < MMA_KC / 16; ++q)
+        umma_bf16(tmem, umma_desc(a0 + q * 2 * MMA_LBO, MMA_LBO, MMA_SBO),
+                  umma_desc(b0 + q * 2 * MMA_LBO, MMA_LBO, MMA_SBO), idesc, (c > 0 || q > 0) ? 1u : 0u);
+      umma_commit(&bar[s]);
+    }
+  }
+  if (ok) {
+    const int cl = nchunks - 1;
+    const int good = mbar_wait_bounded(&bar[cl & 1], (uint32_t)((cl >> 1) & 1)) ? 1 : 0;
+    ok = __syncthreads_and(good) != 0;
+  }
+  if (ok) {
+    tc_fence_after();
+    const int m = 32 * warp + lane;
+    float* o = reinterpret_cast<float*>(out);
+    for (int j = 0; j < ntile / 16; ++j) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * j, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = 16 * j + i;
+        if (n < nvalid && m < 2 * nb) {
+          const int a = m < nb ? m : m - nb;
+          o[2 * (((long long)(r0 + n) * Vc + site) * nb + a) + (m < nb ? 0 : 1)] = v[i];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 3);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
 template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
 
 template <typename R, typename L, int RR>
@@ -190,10 +344,35 @@ static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const
   WCMG_LAUNCH_CHECK();
 }
 
+template <typename L>
+static void coarse_apply_mma(float2* out, const float2* in, const L* links, const LevelGeom& g, int nb, int nrhs,
+                             int* err, cudaStream_t st) {
+  const int ld = links_ld(nb);
+  const int ntile = std::min(64, (nrhs + 15) / 16 * 16);
+  const int tmem_cols = ntile <= 32 ? 32 : 64;
+  const size_t smem = 2 * ((size_t)MMA_M * MMA_KC * 2 + (size_t)ntile * MMA_KC * 2);
+  auto kern = k_coarse_apply_mma<L>;
+  WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<dim3(g.V, (nrhs + ntile - 1) / ntile), 128, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, nrhs, ntile,
+                                                                  tmem_cols, err);
+  WCMG_LAUNCH_CHECK();
+}
+
+// tensor-core path: BF16 coarse links, full stencil, several rhs, nbasis <= 64
+template <typename R, typename L>
+static bool use_mma(int nb, int nrhs, int mode, const int* err) {
+  return std::is_same<L, bf16c>::value && mode == ST_FULL && nrhs >= 8 && nb <= 64 && err != nullptr;
+}
+
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
                          int mode, int hopdir, cudaStream_t st, int* err) {
-  (void)err;
+  if constexpr (std::is_same<L, bf16c>::value) {
+    if (use_mma<R, L>(nb, nrhs, mode, err)) {
+      coarse_apply_mma<L>((float2*)out, (const float2*)in, links, g, nb, nrhs, err, st);
+      return;
+    }
+  }
   if (nrhs == 1 && mode == ST_FULL) coarse_apply1<R, L>(out, in, links, g, nb, st);
   else if (nrhs == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, st);
   else if (nrhs <= 4 || sizeof(R) == 8) coarse_apply_rr<R, L, 4>(out, in, links, g, nb, nrhs, mode, hopdir, st);

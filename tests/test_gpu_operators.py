@@ -186,3 +186,46 @@ def test_coarsen_second_level_matches_oracle(lib):
     D1 = coarsen(D, Aggregation(dims, b0, fields(raw0, dims, 12)))
     D2 = coarsen(D1, Aggregation(cd1, b1, fields(raw1, cd1, 2 * nv[0])))
     assert rel(host(A2), D2.A.reshape(9, -1, nb2, nb2)) < 1e-12
+
+
+def test_tensor_core_coarse_apply_exact_on_bf16_representable_data(lib):
+    """Multi-rhs coarse apply on tcgen05 (BF16 operands, FP32 accumulation): with
+    small-integer links and vectors every product and partial sum is exact, so the
+    result must equal the FP64 oracle exactly."""
+    dims, block, nvec = (8, 8, 8, 8), (2, 2, 2, 2), 24
+    cd = coarse_dims(dims, block)
+    Vc, nb = int(np.prod(cd)), 2 * nvec
+    rng = np.random.default_rng(71)
+    A = (rng.integers(-3, 4, size=(9, Vc, nb, nb)) + 1j * rng.integers(-3, 4, size=(9, Vc, nb, nb))).astype(complex)
+    p = lib.default_params(dims=dims, blocks=[block], nvec=[nvec], max_rhs=70, inner_prec=lib.F32,
+                           coarse_link_prec=lib.BF16)
+    ctx = lib.Context(p)
+    ctx.set_coarse_links(1, dev(A))
+    op = CoarseOperator(np.stack([to_grid(A[d], cd) for d in range(9)]), cd)
+    for nrhs in (8, 16, 37, 70):
+        phi = (rng.integers(-2, 3, size=(nrhs, Vc, nb)) + 1j * rng.integers(-2, 3, size=(nrhs, Vc, nb))).astype(complex)
+        out = dev(np.zeros_like(phi))
+        ctx.apply_coarse(1, dev(phi), out, nrhs=nrhs, prec=lib.F32)
+        got = host(out)
+        for r, f in enumerate(fields(phi, cd, nb)):
+            assert np.array_equal(got[r], op(f).reshape(Vc, nb)), (nrhs, r)
+
+
+@pytest.mark.parametrize("nvec", [8, 24, 32])
+def test_tensor_core_coarse_apply_matches_oracle(lib, nvec):
+    """Random data: BF16 rounding of links and vectors (unit roundoff 2^-8) bounds the error."""
+    dims, block = (8, 8, 8, 8), (2, 2, 2, 2)
+    cd = coarse_dims(dims, block)
+    Vc, nb = int(np.prod(cd)), 2 * nvec
+    A = random_links(72, Vc, nb)
+    p = lib.default_params(dims=dims, blocks=[block], nvec=[nvec], max_rhs=20, inner_prec=lib.F32,
+                           coarse_link_prec=lib.BF16)
+    ctx = lib.Context(p)
+    ctx.set_coarse_links(1, dev(A))
+    op = CoarseOperator(np.stack([to_grid(A[d], cd) for d in range(9)]), cd)
+    phi = inputs.complex_gaussian(73, 0, (20, Vc, nb))
+    out = dev(np.zeros_like(phi))
+    ctx.apply_coarse(1, dev(phi), out, nrhs=20, prec=lib.F32)
+    got = host(out)
+    for r, f in enumerate(fields(phi, cd, nb)):
+        assert rel(got[r], op(f).reshape(Vc, nb)) < 2e-2
