@@ -239,6 +239,98 @@ static void restrict_few(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs
   WCMG_LAUNCH_CHECK();
 }
 
+// Many right-hand sides (the coarsening's column fields, the setup batches): a
+// register-blocked GEMM per (aggregate, chirality): out[(s, i)][r] =
+// sum_e conj(v_i[e]) in_r[e] over the aggregate's (selected) elements e of
+// chirality s.  Each K-chunk of RST_KT elements of all vectors and all rhs of the
+// tile is staged once in shared memory (rhs fastest: conflict-free); thread
+// (ti, tr) owns vectors ti + 8 q (q < VI) and rhs tr + 32 p (p < RT).
+constexpr int RST_KT = 32;
+template <typename R, int VI, int RT>
+__global__ void __launch_bounds__(256) k_restrict_gemm(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                       const cplx<R>* __restrict__ vecs, int Vf, int nc, int bvol,
+                                                       int nvec, int nrhs, bool fine, FaceSel fs) {
+  using T = cplx<R>;
+  constexpr int NT = 32 * RT;  // rhs per CTA
+  __shared__ T Xs[RST_KT][8 * VI];
+  __shared__ T Ts[RST_KT][NT];
+  __shared__ int off_s[RST_KT];
+  const int blk = blockIdx.x, s = blockIdx.y, r0 = blockIdx.z * NT;
+  const int tid = threadIdx.x, ti = tid >> 5, tr = tid & 31;
+  const int half = nc >> 1, nb = 2 * nvec;
+  const int nsite = fs.fd < 0 ? bvol : bvol / fs.b[fs.fd >> 1];
+  const int nelem = nsite * half;
+  const int Vc = Vf / bvol;
+  const long long fstride = (long long)Vf * nc;
+  T acc[VI][RT];
+#pragma unroll
+  for (int q = 0; q < VI; ++q)
+#pragma unroll
+    for (int p = 0; p < RT; ++p) acc[q][p] = czero<R>();
+  for (int c0 = 0; c0 < nelem; c0 += RST_KT) {
+    if (tid < RST_KT) {
+      const int e = c0 + tid;
+      int a = -1;
+      if (e < nelem) {
+        int c, f;
+        if (fine) { c = s * half + e / nsite; f = e % nsite; }
+        else { f = e / half; c = s * half + e % half; }
+        const int site = blk * bvol + face_site(fs, f);
+        a = fine ? c * Vf + site : site * nc + c;
+      }
+      off_s[tid] = a;
+    }
+    __syncthreads();
+    for (int k = tid; k < RST_KT * 8 * VI; k += blockDim.x) {
+      const int i = k / RST_KT, kk = k % RST_KT, a = off_s[kk];
+      Xs[kk][i] = (a >= 0 && i < nvec) ? vecs[i * fstride + a] : czero<R>();
+    }
+    for (int k = tid; k < RST_KT * NT; k += blockDim.x) {
+      const int r = k / RST_KT, kk = k % RST_KT, a = off_s[kk];
+      Ts[kk][r] = (a >= 0 && r0 + r < nrhs) ? in[(r0 + r) * fstride + a] : czero<R>();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < RST_KT; ++kk) {
+      T x[VI], t[RT];
+#pragma unroll
+      for (int q = 0; q < VI; ++q) x[q] = Xs[kk][ti + 8 * q];
+#pragma unroll
+      for (int p = 0; p < RT; ++p) t[p] = Ts[kk][tr + 32 * p];
+#pragma unroll
+      for (int q = 0; q < VI; ++q)
+#pragma unroll
+        for (int p = 0; p < RT; ++p) cjmac(acc[q][p], x[q], t[p]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < VI; ++q)
+#pragma unroll
+    for (int p = 0; p < RT; ++p) {
+      const int i = ti + 8 * q, r = r0 + tr + 32 * p;
+      if (i < nvec && r < nrhs) out[((long long)r * Vc + blk) * nb + s * nvec + i] = acc[q][p];
+    }
+}
+
+template <typename R, int VI, int RT>
+static void restrict_gemm_v(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol,
+                            int nvec, int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
+  const dim3 grid(Vf / bvol, 2, (nrhs + 32 * RT - 1) / (32 * RT));
+  k_restrict_gemm<R, VI, RT><<<grid, 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+static void restrict_gemm(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
+                          int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
+  constexpr int RT = sizeof(R) == 8 ? 1 : 2;  // static shared memory stays below 48 KB
+  const int vi = (nvec + 7) / 8;
+  if (vi <= 2) restrict_gemm_v<R, 2, RT>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else if (vi == 3) restrict_gemm_v<R, 3, RT>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else restrict_gemm_v<R, 4, RT>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+}
+
 template <typename R, int RR>
 static void restrict_rr(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
                         int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
@@ -259,7 +351,8 @@ void launch_restrict(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, in
   fs.fd = face;
   for (int k = 0; k < 4; ++k) fs.b[k] = block ? block[k] : 1;
   if (face >= 0 && !block) throw Error(-1, "face restriction needs the aggregate extents");
-  if (sizeof(R) == 4 && nrhs >= 8) restrict_rr<R, 8>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  if (nrhs >= 16) restrict_gemm<R>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else if (sizeof(R) == 4 && nrhs >= 8) restrict_rr<R, 8>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
   else if (nrhs >= 4) restrict_rr<R, 4>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
   else restrict_few<R>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
 }
@@ -280,18 +373,24 @@ void launch_prolong(cplx<R>* out, const cplx<R>* coarse, const cplx<R>* vecs, in
 
 // ---------------- block orthonormalisation (K6, FP64) ----------------
 // One CTA per (aggregate, chirality).  Column k of the panel is orthogonalised
-// against columns 0..k-1 by classical Gram-Schmidt; a second pass is taken when
-// the first one cancelled more than 1 - 1/sqrt(2) of the column's norm (the
-// "twice is enough" criterion of Kahan and Parlett), so the result is orthonormal
-// to FP64 rounding; then it is normalised.  In exact arithmetic this is the Q
+// against columns 0..k-1 by classical Gram-Schmidt; one pass leaves inner
+// products with the earlier columns of order eps ||a|| / ||a'|| (a' the column
+// after the pass), so a second pass is taken only when the first one cancelled
+// more than 99 % of the norm (||a'|| < 0.01 ||a||): the result is orthonormal to
+// about 100 eps = 2e-14 in FP64 (the selective reorthogonalisation of
+// Daniel-Gragg-Kaufman-Stewart with a 0.01 threshold); then it is normalised.  In exact arithmetic this is the Q
 // factor with positive real diag(R).  Each thread keeps its MAXE panel elements
 // of column k in registers; the previous columns are re-read from L1/L2.
-template <int MAXV, int MAXE>
+// The loops over earlier columns have run-time trip counts (no predicated-off
+// FP64 work); each coefficient is reduced by warp shuffles into shared memory.
+template <int MAXE>
 __global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ vecs, int Vf, int nc, int bvol, int nvec,
                                                      bool fine, int* __restrict__ err) {
-  __shared__ double2 scratch[8 * (MAXV + 1)];
-  __shared__ double2 red[MAXV + 1];
+  constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
+  __shared__ double2 scratch[8][MV];
+  __shared__ double2 red[MV];
   const int blk = blockIdx.x, s = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nelem = bvol * (nc >> 1);
   const long long fstride = (long long)Vf * nc;
   long long addr[MAXE];
@@ -300,48 +399,58 @@ __global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ vecs,
     const int e = threadIdx.x + q * blockDim.x;
     addr[q] = e < nelem ? elem_addr(fine, blk, e, s, Vf, nc, bvol) : -1;
   }
+  // block-wide sums of slots [0, n) and the norm slot
+  auto reduce = [&](int n, bool with_norm) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double2 t = scratch[0][i];
+      for (int w = 1; w < nw; ++w) t += scratch[w][i];
+      red[i] = t;
+    }
+    if (with_norm && threadIdx.x == 0) {
+      double2 t = scratch[0][MV - 1];
+      for (int w = 1; w < nw; ++w) t += scratch[w][MV - 1];
+      red[MV - 1] = t;
+    }
+    __syncthreads();
+  };
   for (int k = 0; k < nvec; ++k) {
     double2 a[MAXE];
 #pragma unroll
     for (int q = 0; q < MAXE; ++q) a[q] = addr[q] >= 0 ? vecs[k * fstride + addr[q]] : make_double2(0, 0);
     double before2 = 0.0, after2 = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      // dots <q_i, a> for i < k and, in slot k, ||a||^2
-      double2 part[MAXV + 1];
+      for (int i = 0; i < k; ++i) {
+        const double2* qi = vecs + i * fstride;
+        double2 p = make_double2(0, 0);
 #pragma unroll
-      for (int i = 0; i <= MAXV; ++i) part[i] = make_double2(0, 0);
-#pragma unroll
-      for (int q = 0; q < MAXE; ++q) {
-        if (addr[q] < 0) continue;
-#pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-          if (i < k) cjmac(part[i], vecs[i * fstride + addr[q]], a[q]);
-        part[MAXV].x += cnorm2(a[q]);
+        for (int q = 0; q < MAXE; ++q)
+          if (addr[q] >= 0) cjmac(p, qi[addr[q]], a[q]);
+        p = warp_sum(p);
+        if (lane == 0) scratch[warp][i] = p;
       }
+      double n0 = 0;
 #pragma unroll
-      for (int i = 0; i < MAXV; ++i)
-        if (i == k) part[i] = part[MAXV];
-      block_sum_regs<double2, MAXV + 1>(part, k + 1, scratch, red);
-      if (pass == 0) before2 = red[k].x;
+      for (int q = 0; q < MAXE; ++q) n0 += cnorm2(a[q]);
+      n0 = warp_sum(n0);
+      if (lane == 0) scratch[warp][MV - 1] = make_double2(n0, 0);
+      reduce(k, true);
+      if (pass == 0) before2 = red[MV - 1].x;
+      for (int i = 0; i < k; ++i) {
+        const double2 r = red[i];
+        const double2* qi = vecs + i * fstride;
 #pragma unroll
-      for (int i = 0; i < MAXV; ++i) {
-        if (i < k) {
-          const double2 r = red[i];
-#pragma unroll
-          for (int q = 0; q < MAXE; ++q)
-            if (addr[q] >= 0) cnmac(a[q], r, vecs[i * fstride + addr[q]]);
-        }
+        for (int q = 0; q < MAXE; ++q)
+          if (addr[q] >= 0) cnmac(a[q], r, qi[addr[q]]);
       }
-      __syncthreads();
       double n2 = 0;
 #pragma unroll
       for (int q = 0; q < MAXE; ++q) n2 += cnorm2(a[q]);
-      const double2 t[1] = {make_double2(n2, 0)};
-      block_sum_regs<double2, 1>(t, 1, scratch, red);
-      after2 = red[0].x;
-      __syncthreads();
-      if (k == 0 || after2 >= 0.5 * before2) break;  // uniform over the block
-      before2 = after2;
+      n2 = warp_sum(n2);
+      if (lane == 0) scratch[warp][MV - 1] = make_double2(n2, 0);
+      reduce(0, true);
+      after2 = red[MV - 1].x;
+      if (k == 0 || after2 >= 1e-4 * before2) break;  // uniform over the block
     }
     const double nrm = sqrt(after2);
     if (!(nrm > 0.0) || !isfinite(nrm)) {
@@ -355,25 +464,16 @@ __global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ vecs,
   }
 }
 
-template <int MAXV>
-static void block_ortho_v(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st) {
-  const int nelem = bvol * (nc / 2);
-  const dim3 grid(Vf / bvol, 2);
-  if (nelem <= 256 * 2) k_block_ortho<MAXV, 2><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
-  else if (nelem <= 256 * 4) k_block_ortho<MAXV, 4><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
-  else if (nelem <= 256 * 6) k_block_ortho<MAXV, 6><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
-  else k_block_ortho<MAXV, 8><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
-  WCMG_LAUNCH_CHECK();
-}
-
 void launch_block_ortho(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st) {
   const int nelem = bvol * (nc / 2);
   if (nvec > 32) throw Error(-1, "block orthonormalisation supports nvec <= 32");
   if (nelem > 256 * 8) throw Error(-1, "aggregate too large for block orthonormalisation");
-  if (nvec <= 8) block_ortho_v<8>(vecs, Vf, nc, bvol, nvec, fine, err, st);
-  else if (nvec <= 16) block_ortho_v<16>(vecs, Vf, nc, bvol, nvec, fine, err, st);
-  else if (nvec <= 24) block_ortho_v<24>(vecs, Vf, nc, bvol, nvec, fine, err, st);
-  else block_ortho_v<32>(vecs, Vf, nc, bvol, nvec, fine, err, st);
+  const dim3 grid(Vf / bvol, 2);
+  if (nelem <= 256 * 2) k_block_ortho<2><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  else if (nelem <= 256 * 4) k_block_ortho<4><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  else if (nelem <= 256 * 6) k_block_ortho<6><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  else k_block_ortho<8><<<grid, 256, 0, st>>>(vecs, Vf, nc, bvol, nvec, fine, err);
+  WCMG_LAUNCH_CHECK();
 }
 
 // ---------------- chirality-split columns of P ----------------

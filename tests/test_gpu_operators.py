@@ -229,3 +229,43 @@ def test_tensor_core_coarse_apply_matches_oracle(lib, nvec):
     got = host(out)
     for r, f in enumerate(fields(phi, cd, nb)):
         assert rel(got[r], op(f).reshape(Vc, nb)) < 2e-2
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+@pytest.mark.parametrize("nrhs", [16, 40])
+def test_restrict_many_rhs_matches_oracle(lib, prec, tol, nrhs):
+    """Register-blocked GEMM path of the restriction (>= 16 rhs: setup batches, coarsening)."""
+    dims, block, nvec = (8, 4, 4, 8), (4, 2, 2, 4), 12
+    V = int(np.prod(dims))
+    cd = coarse_dims(dims, block)
+    Vc = int(np.prod(cd))
+    raw = inputs.complex_gaussian(81, 3, (nvec, V, 12))
+    ctx = make(lib, dims, block, nvec, max_rhs=nrhs)
+    ctx.set_nullvecs(0, dev(raw))
+    agg = Aggregation(dims, block, fields(raw, dims, 12))
+    psi = inputs.complex_gaussian(82, 4, (nrhs, V, 12))
+    out = dev(np.zeros((nrhs, Vc, 2 * nvec), dtype=complex))
+    ctx.restrict(0, dev(psi), out, nrhs=nrhs, prec=prec)
+    got = host(out)
+    for r, f in enumerate(fields(psi, dims, 12)):
+        assert rel(got[r], agg.restrict(f).reshape(Vc, -1)) < tol
+
+
+def test_block_orthonormalisation_ill_conditioned_panels(lib):
+    """Nearly parallel near-null candidates (condition number ~1e3 per aggregate) make
+    the second Gram-Schmidt pass necessary; Q must stay orthonormal and equal to the
+    positive-diagonal QR factor within the conditioning."""
+    dims, block, nvec = (8, 8, 4, 4), (4, 4, 2, 2), 16
+    V = int(np.prod(dims))
+    base = inputs.complex_gaussian(91, 0, (1, V, 12))
+    raw = base + 1e-3 * inputs.complex_gaussian(91, 1, (nvec, V, 12))
+    ctx = make(lib, dims, block, nvec)
+    ctx.set_nullvecs(0, dev(raw))
+    got = dev(np.zeros_like(raw))
+    ctx.get_nullvecs(0, got)
+    ref = block_orthonormalise(fields(raw, dims, 12), block)
+    assert rel(host(got), ref.reshape(nvec, V, 12)) < 1e-9
+    agg_g = Aggregation(dims, block, fields(host(got), dims, 12), orthonormalise=False)
+    cd = coarse_dims(dims, block)
+    phi = to_grid(inputs.complex_gaussian(92, 0, (int(np.prod(cd)), 2 * nvec)), cd)
+    assert rel(agg_g.restrict(agg_g.prolong(phi)), phi) < 1e-13  # P^dag P = 1
