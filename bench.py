@@ -216,10 +216,11 @@ def make_inputs(cfg):
     return U, iv, b
 
 
-def params(wcmg, cfg, inner, links, profile=0):
+def params(wcmg, cfg, inner, links, profile=0, graphs=0):
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
-                            n_levels=len(cfg["blocks"]) + 1, max_rhs=cfg.get("nrhs", 1), profile=profile)
+                            n_levels=len(cfg["blocks"]) + 1, max_rhs=cfg.get("nrhs", 1), profile=profile,
+                            use_graphs=graphs)
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -253,7 +254,7 @@ def run_gpu(args, rank, world, local):
     bd = torch.from_numpy(b).to(dev)
     xd = torch.zeros_like(bd)
     flush = L2Flush(torch, dev)
-    ctx = wcmg.Context(params(wcmg, cfg, args.inner, args.links, profile=-1))
+    ctx = wcmg.Context(params(wcmg, cfg, args.inner, args.links, profile=-1, graphs=args.graphs))
 
     def step(x, U_, iv_, b_):
         ctx.set_gauge(U_, stream)
@@ -263,11 +264,14 @@ def run_gpu(args, rank, world, local):
 
     # warm-up, all kernel classes timed: find the dominant class
     acc = {}
+    first_solve = None
     for _ in range(args.warmup):
         flush.fill_(1)
         s1, s2 = step(xd, Ud, ivd, bd)
         add_stats(acc, s1)
         add_stats(acc, s2)
+        if first_solve is None:
+            first_solve = s2  # host-driven (a graph is captured from the second solve on)
     torch.cuda.synchronize()
     warm_ms = {k: round(v[1] / args.warmup, 3) for k, v in acc.items() if v[1] > 0}
     dominant = max(acc, key=lambda k: acc[k][1])
@@ -278,7 +282,7 @@ def run_gpu(args, rank, world, local):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     acc = {}
-    its, res, launches, coarse_its = [], [], 0, []
+    its, res, launches, coarse_its, graphs_used = [], [], 0, [], []
     phases = {"setup_init": [], "setup_refine": [], "solve": []}
     barrier(dist, local)
     torch.cuda.synchronize()
@@ -292,6 +296,7 @@ def run_gpu(args, rank, world, local):
             add_stats(acc, s1)
             add_stats(acc, s2)
             its.append(s2.outer_iterations)
+            graphs_used.append(s2.graph)
             coarse_its.append((s1.coarse_iterations, s2.coarse_iterations))
             res.append(s2.true_residual)
             launches += s1.kernel_launches + s2.kernel_launches + 2  # + set_gauge's pack/clover kernels
@@ -325,10 +330,12 @@ def run_gpu(args, rank, world, local):
                 "peak_source": f"{'MEASURED_PEAKS.json hbm_gbs (of measured)' if (bound == 'hbm' and peak_kind == 'measured') else ('fallback' if bound == 'hbm' else 'FP64 unit count x max SM clock (derived)')}",
                 "traffic": traffic, "launches": d[0], "avg_launch_us": round(d[1] / max(d[0], 1) * 1e3, 2),
                 "algorithmic_bytes_per_launch": d[2] / max(d[0], 1), "share_of_step": round(d[1] / (ms * args.steps), 4)}
-    co = acc["coarse"]
-    coarse_live = {"launches": co[0], "avg_launch_us": round(co[1] / max(co[0], 1) * 1e3, 2),
-                   "GB/s": round(co[2] / (co[1] * 1e-3) / 1e9, 1) if co[1] else None,
-                   "frac_of_hbm": round(co[2] / (co[1] * 1e-3) / 1e9 / hbm, 4) if co[1] else None}
+    # coarse applies of the host-driven (first) solve, each timed with CUDA events
+    co = first_solve.k[KCLASS.index("coarse")]
+    coarse_live = {"launches": co.launches, "avg_launch_us": round(co.ms / max(co.launches, 1) * 1e3, 2),
+                   "GB/s": round(co.bytes / (co.ms * 1e-3) / 1e9, 1) if co.ms else None,
+                   "frac_of_hbm": round(co.bytes / (co.ms * 1e-3) / 1e9 / hbm, 4) if co.ms else None,
+                   "solve": "host-driven first solve of the warm-up"}
 
     # isolated coarse stencil (1 rhs), L2 flushed before every apply
     coarse_iso = measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg)
@@ -357,11 +364,12 @@ def run_gpu(args, rank, world, local):
     # plain FP64 GPU multigrid on the same field, source and setup parameters (one step)
     fp64 = None
     if args.inner != "f64" and not args.no_fp64_compare and args.workload == "c2":
-        ctx64 = wcmg.Context(params(wcmg, cfg, "f64", "f32", profile=0))
+        ctx64 = wcmg.Context(params(wcmg, cfg, "f64", "f32", profile=0, graphs=args.graphs))
         x64 = torch.zeros_like(bd)
         ctx64.set_gauge(Ud, stream)
         ctx64.setup(ivd, stream)
-        ctx64.solve(bd, x64, stream=stream)  # warm
+        for _ in range(2):  # warm (host-driven, then the graph capture)
+            ctx64.solve(bd, x64, stream=stream)
         flush.fill_(3)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -376,6 +384,8 @@ def run_gpu(args, rank, world, local):
                 "true_residual": s2.true_residual, "setup_init_ms": round(s1.ms_setup_init, 2),
                 "setup_refine_ms": round(s1.ms_setup_refine, 2), "solve_ms": round(s2.ms_solve, 2)}
         ctx64.close()
+
+    uneven = measure_uneven_batch(wcmg, torch, dev, stream, flush, args) if args.workload == "c4" else None
 
     learned = None if (args.no_learned or args.workload != "c2") else learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush)
 
@@ -392,6 +402,8 @@ def run_gpu(args, rank, world, local):
             "dtype": "f32+f64" if args.inner == "f32" else "f64", "data": "synthetic",
             "config": {"workload": cfg["workload"].replace("NRHS", str(nrhs)), "dims": list(cfg["dims"]),
                        "nrhs": nrhs, "inner_prec": args.inner,
+                       "solve": "one CUDA graph per solve (device-side stopping tests)" if all(graphs_used)
+                                else "host-driven",
                        "coarse_links": args.links if args.inner == "f32" else "f64",
                        "l2": "flushed between steps (256 MiB write + 256 MiB read)", "parallelism": f"replicas x{world}",
                        "gauge": "U = exp(i eps X), X = sum_a xi_a lambda_a, seed 1002"},
@@ -400,6 +412,7 @@ def run_gpu(args, rank, world, local):
             "roofline": roofline, "coarse_stencil": {"in_solve": coarse_live, "isolated": coarse_iso},
             "e2e": {"value": round(e2e_ms / 1e3, 5), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "learned": learned,
+            "uneven_batch": uneven,
             "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
             "clocks": clocks, "wall_s_timed": round(t_wall, 3), "fp64_inner": fp64, "cpu_baseline": cpu,
             "kernel_shares": {k: round(v[1] / (ms * args.steps), 4) for k, v in acc.items() if v[1] > 0},
@@ -455,6 +468,71 @@ def learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush):
                      "fallback": st.learned_fallback}
     ctx.close()
     return out
+
+
+UNEVEN_BATCH = dict(
+    lattices=[(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32)], nrhs=4,
+    workload="uneven batch: 8^4, 12^3x24, 16^3x32, 2-level MG each (blocks 4^4 -> 2^4, 3^3x6, 4^3x8), "
+             "eps 0.25, m0 -0.2, csw 1.0, Nvec 24, 3 + 2 sweeps, 4 Gaussian rhs per lattice, FGMRES(20) to 1e-10",
+)
+
+
+def measure_uneven_batch(wcmg, torch, dev, stream, flush, args, reps=5):
+    """Lattices of uneven sizes, 4 rhs each, solved (a) as one graph launch over all
+    lattices (wcmg_solve_batch), (b) one graph per lattice in turn, (c) host-driven in
+    turn, and (d) by plain FP64 GPU multigrid in turn; setups excluded."""
+    from paper_1904_08678_gb300 import inputs
+    ub = UNEVEN_BATCH
+    nr = ub["nrhs"]
+    cfgs, sets = [], {"f32_graph": [], "f32_host": [], "f64_host": []}
+    bs, xs = [], []
+    for k, dims in enumerate(ub["lattices"]):
+        cfg = dict(WORKLOAD, dims=dims, nrhs=nr, gauge_seed=1040 + k)
+        U, iv, _ = make_inputs(cfg)
+        b = inputs.source(dims, k, nrhs=nr)
+        Ud, ivd = torch.from_numpy(U).to(dev), torch.from_numpy(iv).to(dev)
+        bs.append(torch.from_numpy(b).to(dev))
+        xs.append(torch.zeros_like(bs[-1]))
+        for name, inner, g in (("f32_graph", "f32", 1), ("f32_host", "f32", 0), ("f64_host", "f64", 0)):
+            c = wcmg.Context(params(wcmg, cfg, inner, "f32", profile=0, graphs=g))
+            c.set_gauge(Ud, stream)
+            c.setup(ivd, stream)
+            sets[name].append(c)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ms = []
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms), out
+
+    def in_turn(name):
+        return lambda: [c.solve(bs[k], xs[k], nrhs=nr, stream=stream) for k, c in enumerate(sets[name])]
+
+    res = {}
+    ms, sts = timed(lambda: wcmg.Context.solve_batch(sets["f32_graph"], bs, xs, nrhs=[nr] * len(bs), stream=stream))
+    res["one_graph_launch"] = {"ms": round(ms, 3), "graph": [s.graph for s in sts],
+                               "outer_iterations": [s.outer_iterations for s in sts],
+                               "true_residual": max(s.true_residual for s in sts),
+                               "gpu_launches": sum(s.kernel_launches for s in sts)}
+    for label, name in (("graph_per_lattice", "f32_graph"), ("host_driven", "f32_host"), ("fp64_host_driven", "f64_host")):
+        ms, sts = timed(in_turn(name))
+        res[label] = {"ms": round(ms, 3), "outer_iterations": [s.outer_iterations for s in sts],
+                      "true_residual": max(s.true_residual for s in sts)}
+    for v in sets.values():
+        for c in v:
+            c.close()
+    res["workload"] = ub["workload"]
+    res["speedup_vs_fp64"] = round(res["fp64_host_driven"]["ms"] / res["one_graph_launch"]["ms"], 2)
+    return res
 
 
 def measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg, reps=200):
@@ -555,6 +633,8 @@ def main(argv=None):
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--nrhs", type=int, default=0, help="override the workload's number of right-hand sides")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="1: each solve replays one captured CUDA graph; 0: host-driven solve")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -83,6 +83,16 @@ typedef struct wcmg_params {
   int profile;                          /* bitmask of (1 << wcmg_kclass): kernel classes whose
                                            launches are timed with CUDA events (-1: all, 0: none);
                                            launch, byte and flop counts are always kept */
+  int use_graphs;                       /* 1: wcmg_solve runs as one CUDA graph with device-side
+                                           stopping tests (conditional WHILE / IF nodes), captured
+                                           on the second solve with a given nrhs and replayed
+                                           after; the first solve runs host-driven.  Plain
+                                           multigrid coarse mode only (learned modes run
+                                           host-driven).  Kernel-class event timing is not
+                                           available inside a replay.  0: host-driven. */
+  int autotune;                         /* 1: the first coarse apply of each (level, nrhs, link
+                                           storage) times the candidate launch shapes on the
+                                           level's own data and keeps the fastest. 0: fixed rule */
 } wcmg_params;
 
 /* Per-kernel-class counters, filled when params.profile != 0. */
@@ -106,6 +116,8 @@ typedef struct wcmg_stats {
   double ms_solve;
   int learned_fallback;                 /* 1 if a learned solve fell back to plain multigrid */
   int learned_cycles;                   /* cycles that used the network */
+  int graph;                            /* 1 if the solve ran as a CUDA-graph replay */
+  int reserved;
   wcmg_kstat k[WCMG_NKCLASS];           /* index: wcmg_kclass */
 } wcmg_stats;
 
@@ -179,6 +191,20 @@ int wcmg_krylov(wcmg_ctx* ctx, int level, int kind, const void* b, void* x, int 
  * and the FP64 residual is recomputed at every restart (defect correction).
  * Returns ERR_NOT_CONVERGED (x and *st valid) at outer_maxiter. */
 int wcmg_solve(wcmg_ctx* ctx, const void* b, void* x, int nrhs, int where, void* stream, wcmg_stats* st);
+
+/* Batched solve over n independent contexts, e.g. lattices of uneven sizes: each
+ * ctxs[i] solves D_i x_i = b_i (nrhs[i] fields, layouts of ctxs[i]) exactly as
+ * wcmg_solve with params.use_graphs = 1 would.  All n solves are captured into ONE
+ * CUDA graph, one branch per context with device-side stopping tests, and run by
+ * a single graph launch on `stream`, so the small lattices fill the SMs that the
+ * large one leaves idle.  The first call with a given (contexts, nrhs) runs the n
+ * solves host-driven one after another (this allocates every workspace); the
+ * second captures; later calls replay.  Every context must have finished its
+ * setup, use the plain multigrid coarse mode, and appear once.  st (nullable)
+ * is an array of n stats.  Returns the first error of any context
+ * (ERR_NOT_CONVERGED if a context stopped at outer_maxiter). */
+int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* const* x, const int* nrhs,
+                     int where, void* stream, wcmg_stats* st);
 
 /* Change params.profile of an existing context (no GPU work). */
 int wcmg_set_profile(wcmg_ctx* ctx, int mask);

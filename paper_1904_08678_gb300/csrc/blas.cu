@@ -56,12 +56,15 @@ __global__ void __launch_bounds__(RED_T) k_norm_partial(double* __restrict__ par
   if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = red[0];
 }
 // out[r * ldo + i] = sum_{b < count} partial[r * pr + i * pi + b]  (grid: r = x, i = y)
+// lim (nullable): rows i >= *lim + ladd are skipped (a device-side Arnoldi step count).
 template <typename T>
 __global__ void __launch_bounds__(RED_T) k_final(T* __restrict__ out, const T* __restrict__ partial, int count,
-                                                 long long pr, long long pi, int ldo) {
+                                                 long long pr, long long pi, int ldo, const int* __restrict__ lim = nullptr,
+                                                 int ladd = 0) {
   __shared__ T scratch[RED_T / 32];
   __shared__ T red[1];
   const int r = blockIdx.x, i = blockIdx.y;
+  if (lim && i >= *lim + ladd) return;  // uniform per block
   const T* p = partial + r * pr + i * pi;
   T acc;
   memset(&acc, 0, sizeof(T));
@@ -94,10 +97,12 @@ template <typename R>
 __global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict__ partial,
                                                             const cplx<R>* __restrict__ basis, long long bstride,
                                                             int k, const cplx<R>* __restrict__ w, long long n,
-                                                            int kpad) {
+                                                            int kpad, const int* __restrict__ kdev, int kadd) {
   __shared__ double2 scratch[(RED_T / 32) * MD_K];
   __shared__ double2 red[MD_K];
   const int r = blockIdx.y, i0 = blockIdx.z * MD_K;
+  if (kdev) k = *kdev + kadd;
+  if (i0 >= k) return;  // uniform per block
   const long long off = (long long)r * n;
   cplx<R> acc[MD_K];
 #pragma unroll
@@ -115,22 +120,25 @@ __global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict_
   if (threadIdx.x < MD_K && i0 + threadIdx.x < k)
     partial[((long long)r * kpad + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x];
 }
+// k basis vectors; with kdev the count is *kdev + kadd (<= k) read on the device.
 template <typename R>
 void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int k, int ldo, const cplx<R>* w,
-                     long long n, int nrhs, double2* partial, cudaStream_t st) {
+                     long long n, int nrhs, double2* partial, cudaStream_t st, const int* kdev, int kadd) {
   const int nb = red_blocks(n);
   const int nchunk = (k + MD_K - 1) / MD_K, kpad = nchunk * MD_K;
-  k_multidot_partial<R><<<dim3(nb, nrhs, nchunk), RED_T, 0, st>>>(partial, basis, bstride, k, w, n, kpad);
-  k_final<double2><<<dim3(nrhs, k), RED_T, 0, st>>>(out, partial, nb, (long long)kpad * nb, nb, ldo);
+  k_multidot_partial<R><<<dim3(nb, nrhs, nchunk), RED_T, 0, st>>>(partial, basis, bstride, k, w, n, kpad, kdev, kadd);
+  k_final<double2><<<dim3(nrhs, k), RED_T, 0, st>>>(out, partial, nb, (long long)kpad * nb, nb, ldo, kdev, kadd);
   ++launch_counter();
   WCMG_LAUNCH_CHECK();
 }
 
 template <typename R>
 __global__ void k_multiaxpy(cplx<R>* __restrict__ w, const cplx<R>* __restrict__ basis, long long bstride, int k,
-                           const double2* __restrict__ coef, int ldc, double sign, long long n) {
+                           const double2* __restrict__ coef, int ldc, double sign, long long n,
+                           const int* __restrict__ kdev, int kadd) {
   __shared__ cplx<R> cf[80];  // k <= 65 (restart <= 64)
   const int r = blockIdx.y;
+  if (kdev) k = min(*kdev + kadd, k);
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     const double2 c = coef[(long long)r * ldc + i];
     cf[i] = cmk(R(sign * c.x), R(sign * c.y));
@@ -145,10 +153,10 @@ __global__ void k_multiaxpy(cplx<R>* __restrict__ w, const cplx<R>* __restrict__
 }
 template <typename R>
 void launch_multiaxpy(cplx<R>* w, const cplx<R>* basis, long long bstride, int k, const double2* coef, int ldc,
-                      double sign, long long n, int nrhs, cudaStream_t st) {
+                      double sign, long long n, int nrhs, cudaStream_t st, const int* kdev, int kadd) {
   if (k <= 0) return;
   if (k > 80) throw Error(-1, "multiaxpy supports k <= 80");
-  k_multiaxpy<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(w, basis, bstride, k, coef, ldc, sign, n);
+  k_multiaxpy<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(w, basis, bstride, k, coef, ldc, sign, n, kdev, kadd);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -166,9 +174,10 @@ void launch_axpby(cplx<R>* y, double a, const cplx<R>* x, double b, long long n,
 
 template <typename R>
 __global__ void k_scale_dev(cplx<R>* __restrict__ y, const cplx<R>* __restrict__ x, const double* __restrict__ s,
-                            int inv_sqrt, long long n) {
+                            int inv_sqrt, long long n, const int* __restrict__ ydev, int yadd, long long ystride) {
   __shared__ R f_s;
   const int r = blockIdx.y;
+  if (ydev) y += (long long)(*ydev + yadd) * ystride;
   if (threadIdx.x == 0) {
     double f = s[r];
     if (inv_sqrt) f = f > 0.0 ? 1.0 / sqrt(f) : 0.0;
@@ -181,8 +190,8 @@ __global__ void k_scale_dev(cplx<R>* __restrict__ y, const cplx<R>* __restrict__
 }
 template <typename R>
 void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqrt, long long n, int nrhs,
-                      cudaStream_t st) {
-  k_scale_dev<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(y, x, s, inv_sqrt, n);
+                      cudaStream_t st, const int* ydev, int yadd, long long ystride) {
+  k_scale_dev<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(y, x, s, inv_sqrt, n, ydev, yadd, ystride);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -220,6 +229,33 @@ __global__ void k_mask_rhs(cplx<R>* __restrict__ x, const int* __restrict__ mask
 template <typename R>
 void launch_mask_rhs(cplx<R>* x, const int* mask, long long n, int nrhs, cudaStream_t st) {
   k_mask_rhs<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(x, mask, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+// dst[o * dmul + i] = src[o * smul + i], o = *idx (0 when idx is null): the copy of
+// one Krylov basis slot selected on the device.
+template <typename R>
+__global__ void k_copy_idx(cplx<R>* __restrict__ dst, const cplx<R>* __restrict__ src, long long n,
+                           const int* __restrict__ idx, long long dmul, long long smul) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long o = idx ? *idx : 0;
+  dst[o * dmul + i] = src[o * smul + i];
+}
+template <typename R>
+void launch_copy_idx(cplx<R>* dst, const cplx<R>* src, long long n, const int* idx, long long dmul, long long smul,
+                     cudaStream_t st) {
+  if (n <= 0) return;
+  k_copy_idx<R><<<nblk(n, 256), 256, 0, st>>>(dst, src, n, idx, dmul, smul);
+  WCMG_LAUNCH_CHECK();
+}
+__global__ void k_fill_int(int* x, int v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+void launch_fill_int(int* x, int v, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_fill_int<<<nblk(n, 256), 256, 0, st>>>(x, v, n);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -265,9 +301,10 @@ __global__ void k_gmres_start(GmresState S, const double* __restrict__ nrm2, dou
 
 __global__ void k_gmres_step(GmresState S, int j, const double2* __restrict__ h1, const double2* __restrict__ h2,
                              const double* __restrict__ hnorm2, double tol, int final_done, int nrhs,
-                             double* __restrict__ inv_h) {
+                             double* __restrict__ inv_h, const int* __restrict__ jdev) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
+  if (jdev) j = *jdev;
   const int m = S.m;
   if (!S.active[r]) { inv_h[r] = 0.0; return; }
   double2* H = S.H + (long long)r * (m + 1) * m;
@@ -330,8 +367,8 @@ void launch_gmres_start(const GmresState& s, const double* nrm2, double tol, int
   WCMG_LAUNCH_CHECK();
 }
 void launch_gmres_step(const GmresState& s, int j, const double2* h1, const double2* h2, const double* hnorm2,
-                       double tol, int final_done, int nrhs, double* inv_h, cudaStream_t st) {
-  k_gmres_step<<<nblk(nrhs, 64), 64, 0, st>>>(s, j, h1, h2, hnorm2, tol, final_done, nrhs, inv_h);
+                       double tol, int final_done, int nrhs, double* inv_h, cudaStream_t st, const int* jdev) {
+  k_gmres_step<<<nblk(nrhs, 64), 64, 0, st>>>(s, j, h1, h2, hnorm2, tol, final_done, nrhs, inv_h, jdev);
   WCMG_LAUNCH_CHECK();
 }
 void launch_gmres_solve_y(const GmresState& s, int nrhs, cudaStream_t st) {
@@ -347,11 +384,14 @@ void launch_gmres_mark_done(const GmresState& s, const double* nrm2, double tol,
   template void launch_dot<R>(double2*, const cplx<R>*, const cplx<R>*, long long, int, double2*, cudaStream_t); \
   template void launch_norm2<R>(double*, const cplx<R>*, long long, int, double*, cudaStream_t);                 \
   template void launch_multidot<R>(double2*, const cplx<R>*, long long, int, int, const cplx<R>*, long long, int, \
-                                   double2*, cudaStream_t);                                                      \
+                                   double2*, cudaStream_t, const int*, int);                                     \
   template void launch_multiaxpy<R>(cplx<R>*, const cplx<R>*, long long, int, const double2*, int, double,       \
-                                    long long, int, cudaStream_t);                                               \
+                                    long long, int, cudaStream_t, const int*, int);                              \
+  template void launch_copy_idx<R>(cplx<R>*, const cplx<R>*, long long, const int*, long long, long long,        \
+                                   cudaStream_t);                                                                \
   template void launch_axpby<R>(cplx<R>*, double, const cplx<R>*, double, long long, int, cudaStream_t);         \
-  template void launch_scale_dev<R>(cplx<R>*, const cplx<R>*, const double*, int, long long, int, cudaStream_t); \
+  template void launch_scale_dev<R>(cplx<R>*, const cplx<R>*, const double*, int, long long, int, cudaStream_t,  \
+                                    const int*, int, long long);                                                 \
   template void launch_mr_update<R>(cplx<R>*, cplx<R>*, const cplx<R>*, const double2*, const double*, long long, \
                                     int, cudaStream_t);                                                          \
   template void launch_mask_rhs<R>(cplx<R>*, const int*, long long, int, cudaStream_t);                          \

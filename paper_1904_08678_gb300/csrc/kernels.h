@@ -79,20 +79,29 @@ void launch_dot(double2* out, const cplx<R>* a, const cplx<R>* b, long long n, i
                 cudaStream_t st);
 template <typename R>
 void launch_norm2(double* out, const cplx<R>* a, long long n, int nrhs, double* partial, cudaStream_t st);
-// out[r][i] = <basis_i, w> for i < k; basis_i at basis + i * bstride (each [nrhs][n])
+// out[r][i] = <basis_i, w> for i < k; basis_i at basis + i * bstride (each [nrhs][n]).
+// kdev (nullable, device): the count is *kdev + kadd instead (at most k, which sizes
+// the grid) -- the Arnoldi step number of a device-driven loop.
 template <typename R>
 void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int k, int ldo, const cplx<R>* w,
-                     long long n, int nrhs, double2* partial, cudaStream_t st);
-// w[r] += sign * sum_{i<k} coef[r*ldc + i] * basis_i[r]
+                     long long n, int nrhs, double2* partial, cudaStream_t st, const int* kdev = nullptr,
+                     int kadd = 0);
+// w[r] += sign * sum_{i<k} coef[r*ldc + i] * basis_i[r]; kdev as for launch_multidot
 template <typename R>
 void launch_multiaxpy(cplx<R>* w, const cplx<R>* basis, long long bstride, int k, const double2* coef, int ldc,
-                      double sign, long long n, int nrhs, cudaStream_t st);
+                      double sign, long long n, int nrhs, cudaStream_t st, const int* kdev = nullptr, int kadd = 0);
+// dst[o * dmul + i] = src[o * smul + i] for i < n, o = *idx (0 if idx is null)
+template <typename R>
+void launch_copy_idx(cplx<R>* dst, const cplx<R>* src, long long n, const int* idx, long long dmul, long long smul,
+                     cudaStream_t st);
+void launch_fill_int(int* x, int v, int n, cudaStream_t st);
 template <typename R>
 void launch_axpby(cplx<R>* y, double a, const cplx<R>* x, double b, long long n, int nrhs, cudaStream_t st);
-// y[r] = x[r] * s[r] (s real, device)
+// y[r] = x[r] * s[r] (s real, device; 1/sqrt(s) with inv_sqrt).  ydev (nullable):
+// y is offset by (*ydev + yadd) * ystride on the device.
 template <typename R>
 void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqrt, long long n, int nrhs,
-                      cudaStream_t st);
+                      cudaStream_t st, const int* ydev = nullptr, int yadd = 0, long long ystride = 0);
 // MR update with alpha[r] = pr[r] / pp[r] (0 if pp = 0), pr = <p, r>, pp = <p, p>:
 //   x += alpha r ; r -= alpha p
 template <typename R>
@@ -122,8 +131,10 @@ struct GmresState {
 // h column j is in H (entries 0..j from multidot); hnorm holds ||w||.
 // h1, h2: the two CGS passes' coefficients [nrhs][m+1]; hnorm2 = ||w||^2 after both.
 // `final_done`: a recurrence convergence also marks the rhs done (no true-residual check).
+// jdev (nullable, device): the step number is *jdev instead of j.
 void launch_gmres_step(const GmresState& s, int j, const double2* h1, const double2* h2, const double* hnorm2,
-                       double tol, int final_done, int nrhs, double* inv_h, cudaStream_t st);
+                       double tol, int final_done, int nrhs, double* inv_h, cudaStream_t st,
+                       const int* jdev = nullptr);
 // done[r] |= nrm2[r] <= (tol * bnorm[r])^2
 void launch_gmres_mark_done(const GmresState& s, const double* nrm2, double tol, int nrhs, cudaStream_t st);
 void launch_gmres_solve_y(const GmresState& s, int nrhs, cudaStream_t st);
@@ -149,4 +160,60 @@ void launch_ptc_wgrad(float2* gW, float2* partial, const float2* gout, const flo
 void launch_ptc_adam(float2* w, const float2* g, float2* m, float2* v, int n, float lr, int t, cudaStream_t st);
 void launch_gaussian_field(float2* out, long long n, unsigned long long seed, unsigned long long stream,
                            cudaStream_t st);
+}  // namespace wcmg
+
+namespace wcmg {
+// ---- device-driven Krylov loops (graph.cu) ----
+// The stopping tests of (F)GMRES run on the device so that a whole solve can be
+// captured once as a CUDA graph: each loop is a conditional WHILE node whose
+// body ends with one of these single-block control kernels; the kernel updates
+// the counters and sets the node's condition.  Every loop counter only grows and
+// is capped (maxiter, restart length, KCTL_HARD_CAP), so each loop terminates.
+constexpr int KCTL_HARD_CAP = 100000;
+struct KCtl {
+  int j;        // Arnoldi step within the current cycle
+  int its;      // iterations of this invocation
+  int cycles;   // restart cycles
+  int stop;     // set once the invocation is finished
+  int err;      // 1: non-finite residual norm
+  int maxiter;  // iteration budget of this invocation
+  int restarts; // (outer defect-correction loop) restarts
+  int pad;
+};
+// Launch-count bookkeeping of graph replays: after a body executes, its control
+// kernel adds body_counts[slot] (the number of kernels captured directly in
+// that body, written by the host after capture) to *launches.
+struct BodyCount {
+  const int* counts;
+  int slot;          // -1: do not count
+  long long* launches;
+};
+// ctl: j = its = cycles = stop = err = restarts = 0; maxiter = budget_its ?
+// min(maxiter, budget_max - *budget_its) : maxiter; if use_h, condition(h) = maxiter > 0.
+void launch_kctl_init(KCtl* k, int maxiter, const int* budget_its, int budget_max,
+                      cudaGraphConditionalHandle h, int use_h, cudaStream_t st);
+// start of a cycle: j = 0; condition(h) = any(active) && m > 0 && its < maxiter
+void launch_kctl_cycle_begin(KCtl* k, const int* active, int nrhs, int m, cudaGraphConditionalHandle h,
+                             cudaStream_t st);
+// end of an Arnoldi step: j++, its++, (*acc)++ if acc;
+// condition(h) = any(active) && j < m && its < maxiter
+void launch_kctl_step_end(KCtl* k, const int* active, int nrhs, int m, long long* acc, BodyCount bc,
+                          cudaGraphConditionalHandle h, cudaStream_t st);
+// end of a cycle: cycles++; stop = (max_cycles > 0 && cycles >= max_cycles) ||
+// (!verify && all(done)) || cycles >= KCTL_HARD_CAP; condition(h_if) = !stop
+// (h_if guards the true-residual step of the restart)
+void launch_kctl_cycle_end(KCtl* k, const int* done, int nrhs, int verify, int max_cycles, BodyCount bc,
+                           cudaGraphConditionalHandle h_if, cudaStream_t st);
+// after the IF node of a restart: if the true-residual step ran (stop == 0), count
+// its body, err/stop on a non-finite norm, stop when all(done), its >= maxiter or
+// the cycle took no step; condition(h_loop) = !stop
+void launch_kctl_restart_check(KCtl* k, const int* done, const double* nrm2, int nrhs, BodyCount bc_if,
+                               cudaGraphConditionalHandle h_loop, cudaStream_t st);
+// Defect-correction loop of the mixed-precision solve.  inner (nullable) is the
+// FP32 FGMRES just run: its += inner->its, restarts++, and no progress
+// (inner->its == 0) stops.  done[q] = ||r_q|| <= tol ||b_q|| (nrm2, bn2 squared
+// norms); *worst = max_q ||r_q|| / ||b_q||; condition(h) = !all(done) && its <
+// maxiter && !err.
+void launch_mx_check(KCtl* k, const KCtl* inner, const double* nrm2, const double* bn2, double tol, int* done,
+                     double* worst, int nrhs, BodyCount bc, cudaGraphConditionalHandle h, cudaStream_t st);
 }  // namespace wcmg

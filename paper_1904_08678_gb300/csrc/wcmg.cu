@@ -25,6 +25,13 @@
 
 namespace wcmg {
 
+// Bumped by every device allocation of a DevBuf: a captured CUDA graph is valid
+// only while no buffer it references has been reallocated.
+static unsigned long long& alloc_gen() {
+  static unsigned long long g = 0;
+  return g;
+}
+
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
@@ -48,6 +55,7 @@ struct DevBuf {
     release();
     WCMG_CUDA(cudaMalloc(&p, (count ? count : 1) * sizeof(T)));
     n = count;
+    ++alloc_gen();
     return p;
   }
 };
@@ -205,7 +213,41 @@ struct wcmg_ctx {
   double fallback_ratio = 0.9;
   bool learned_on = false, learned_fallback = false;
   int learned_cycles = 0;
+  // solve captured as one CUDA graph with device-side loop control
+  static constexpr int MAX_CAP_DEPTH = 8, MAX_BODIES = 256;
+  bool capturing = false;
+  int cap_depth = 0;
+  cudaStream_t cap_st[MAX_CAP_DEPTH] = {};
+  std::vector<int> body_counts_h;         // kernels captured directly in each conditional body
+  std::vector<long long> nested;          // capture-time stack: kernels of nested bodies
+  DevBuf<int> body_counts;                // device copy of body_counts_h
+  DevBuf<long long> gstat;                // [0] kernels launched by bodies, [1] coarsest GMRES iterations
+  DevBuf<KCtl> kctl;                      // 0 mixed loop, 1 level-0 FGMRES, 2 + l GMRES of level l
+  DevBuf<int> mx_done;
+  DevBuf<double> mx_worst;
+  struct Graph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int nrhs = 0;
+    unsigned long long gen = 0;
+    long long top_launches = 0;  // kernels outside conditional bodies
+    void reset() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (g) cudaGraphDestroy(g);
+      exec = nullptr;
+      g = nullptr;
+      nrhs = 0;
+    }
+  } graph;
+  std::vector<int> warm_rhs;              // nrhs values already solved once (every workspace allocated)
+  long long graph_top = 0;                // kernels of the last capture outside conditional bodies
+  Graph batch;                            // wcmg_solve_batch graph (cached on the first context)
+  std::vector<const void*> batch_key;
   ~wcmg_ctx() {
+    graph.reset();
+    batch.reset();
+    for (auto s : cap_st)
+      if (s) cudaStreamDestroy(s);
     if (h_flags) cudaFreeHost(h_flags);
     if (h_vals) cudaFreeHost(h_vals);
   }
@@ -218,7 +260,7 @@ namespace wcmg {
 // with a CUDA-event pair on the call's stream.
 #define KPROF(c, cls, BYTES_, FLOPS_, call)                                        \
   do {                                                                           \
-    const bool on_ = ((c)->prof.mask >> (cls)) & 1;                             \
+    const bool on_ = (((c)->prof.mask >> (cls)) & 1) && !(c)->capturing;        \
     cudaEvent_t a_ = nullptr, b_ = nullptr;                                      \
     if (on_) { a_ = (c)->prof.get(); WCMG_CUDA(cudaEventRecord(a_, (c)->st)); }  \
     call;                                                                        \
@@ -261,6 +303,8 @@ static cplx<R>* ws(Level& L, const char* name, long long nfields) {
   auto& b = L.ws[key];
   return reinterpret_cast<cplx<R>*>(b.ensure((size_t)nfields * L.n() * sizeof(cplx<R>)));
 }
+
+static bool inner64(const wcmg_ctx* c) { return c->p.inner_prec == WCMG_F64; }
 
 static int max_rhs_all(const wcmg_ctx* c) {
   int m = std::max(1, c->p.max_rhs);
@@ -369,7 +413,8 @@ static void prolong_op(wcmg_ctx* c, int l, cplx<R>* fine, const cplx<R>* coarse,
 
 template <typename R>
 static void copy_fields(wcmg_ctx* c, cplx<R>* dst, const cplx<R>* src, long long n) {
-  WCMG_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(cplx<R>), cudaMemcpyDeviceToDevice, c->st));
+  if (c->capturing) launch_copy_idx<R>(dst, src, n, nullptr, 0, 0, c->st);  // kernel node, legal in any body
+  else WCMG_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(cplx<R>), cudaMemcpyDeviceToDevice, c->st));
 }
 
 // ---------------- BLAS wrappers (profiled) ----------------
@@ -528,6 +573,163 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
   }
 }
 
+// ---------------- device-driven (F)GMRES for CUDA-graph capture ----------------
+// The same algorithm as fgmres() above, with every stopping test taken on the
+// device by the control kernels of graph.cu: the Arnoldi loop and the restart
+// loop become conditional WHILE nodes, the true-residual step of a restart an IF
+// node.  Kernels that depend on the step number j read it from KCtl::j.  Only
+// used while the context is capturing a graph.
+
+static cudaGraphConditionalHandle cond_handle(wcmg_ctx* c) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  WCMG_CUDA(cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive || !g) throw Error(WCMG_ERR_STATE, "graph handle outside a capture");
+  cudaGraphConditionalHandle h;
+  WCMG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  return h;
+}
+
+static BodyCount body_count(wcmg_ctx* c, int slot) { return BodyCount{c->body_counts.p, slot, c->gstat.p}; }
+
+// Append a conditional node (WHILE or IF, condition h) to the capturing stream and
+// capture body(slot) into its body graph on the next capture stream.
+template <class F>
+static void cond_node(wcmg_ctx* c, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, F&& body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  WCMG_CUDA(cudaStreamGetCaptureInfo(c->st, &cs, nullptr, &g, &deps, &edges, &nd));
+  if (cs != cudaStreamCaptureStatusActive) throw Error(WCMG_ERR_STATE, "conditional node outside a capture");
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  WCMG_CUDA(cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+  WCMG_CUDA(cudaStreamUpdateCaptureDependencies(c->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+  if (c->cap_depth + 1 >= wcmg_ctx::MAX_CAP_DEPTH) throw Error(WCMG_ERR_STATE, "graph nesting too deep");
+  if ((int)c->body_counts_h.size() >= wcmg_ctx::MAX_BODIES) throw Error(WCMG_ERR_STATE, "too many graph bodies");
+  const int slot = (int)c->body_counts_h.size();
+  c->body_counts_h.push_back(0);
+  cudaStream_t& bs = c->cap_st[c->cap_depth + 1];
+  if (!bs) WCMG_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  cudaStream_t parent = c->st;
+  WCMG_CUDA(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  ++c->cap_depth;
+  c->st = bs;
+  const long long l0 = launch_counter();
+  c->nested.push_back(0);
+  try {
+    body(slot);
+  } catch (...) {
+    cudaGraph_t dummy = nullptr;
+    cudaStreamEndCapture(bs, &dummy);
+    c->st = parent;
+    --c->cap_depth;
+    c->nested.pop_back();
+    throw;
+  }
+  const long long total = launch_counter() - l0;
+  const long long inner = c->nested.back();
+  c->nested.pop_back();
+  c->body_counts_h[slot] = (int)(total - inner);
+  if (!c->nested.empty()) c->nested.back() += total;
+  cudaGraph_t dummy = nullptr;
+  WCMG_CUDA(cudaStreamEndCapture(bs, &dummy));
+  c->st = parent;
+  --c->cap_depth;
+}
+
+template <typename R>
+static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int m, double tol, int maxiter,
+                     bool x_zero, bool verify, bool precond, int max_cycles, KCtl* K, const int* budget_its,
+                     int budget_max, long long* acc) {
+  Level& L = c->L[l];
+  const long long n = L.n();
+  L.sc.ensure(max_rhs_all(c), std::max(m, std::max(c->p.outer_restart, c->p.coarse_restart)));
+  cplx<R>* Vb = ws<R>(L, precond ? "fg_V" : "gm_V", (long long)(m + 1) * nrhs);
+  cplx<R>* Zb = precond ? ws<R>(L, "fg_Z", (long long)m * nrhs) : nullptr;
+  cplx<R>* w = ws<R>(L, precond ? "fg_w" : "gm_w", nrhs);
+  cplx<R>* r = ws<R>(L, precond ? "fg_r" : "gm_r", nrhs);
+  cplx<R>* vcur = ws<R>(L, precond ? "fg_vc" : "gm_vc", nrhs);
+  cplx<R>* zcur = precond ? ws<R>(L, "fg_zc", nrhs) : nullptr;
+  const long long bstride = n * nrhs;
+  GmresState S = L.sc.state(m);
+  const int ldh = m + 1;
+  const int* jd = &K->j;
+  norm2_op<R>(c, S.bnorm, b, n, nrhs);
+  launch_sqrt_inplace(S.bnorm, nrhs, c->st);
+  launch_fill_int(S.done, 0, nrhs, c->st);
+  if (x_zero) {
+    launch_fill_zero<R>(x, n * nrhs, c->st);
+    copy_fields<R>(c, r, b, n * nrhs);
+  } else {
+    apply_op<R>(c, l, r, x, nrhs);
+    launch_axpby<R>(r, 1.0, b, -1.0, n, nrhs, c->st);  // r = b - A x
+  }
+  norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
+  const bool single = max_cycles == 1;
+  const cudaGraphConditionalHandle h_loop = single ? 0 : cond_handle(c);
+  launch_kctl_init(K, maxiter, budget_its, budget_max, h_loop, single ? 0 : 1, c->st);
+
+  // one restart cycle: Arnoldi steps while any rhs is active, then x += Z y
+  auto one_cycle = [&]() {
+    launch_gmres_start(S, L.sc.slot(1), tol, nrhs, L.sc.slot(2), c->st);
+    launch_scale_dev<R>(Vb, r, L.sc.slot(2), 0, n, nrhs, c->st);
+    const cudaGraphConditionalHandle h_arn = cond_handle(c);
+    launch_kctl_cycle_begin(K, S.active, nrhs, m, h_arn, c->st);
+    cond_node(c, h_arn, cudaGraphCondTypeWhile, [&](int slot) {
+      launch_copy_idx<R>(vcur, Vb, bstride, jd, 0, bstride, c->st);  // vcur = V_j
+      const cplx<R>* z = vcur;
+      if (precond) {
+        cycle<R>(c, l, zcur, vcur, nrhs);
+        launch_copy_idx<R>(Zb, zcur, bstride, jd, bstride, 0, c->st);  // Z_j = M V_j
+        z = zcur;
+      }
+      apply_op<R>(c, l, w, z, nrhs);
+      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+            launch_multidot<R>(L.sc.h1(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
+      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+            launch_multiaxpy<R>(w, Vb, bstride, m, L.sc.h1(), ldh, -1.0, n, nrhs, c->st, jd, 1));
+      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+            launch_multidot<R>(L.sc.h2(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
+      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+            launch_multiaxpy<R>(w, Vb, bstride, m, L.sc.h2(), ldh, -1.0, n, nrhs, c->st, jd, 1));
+      norm2_op<R>(c, L.sc.slot(0), w, n, nrhs);
+      launch_gmres_step(S, 0, L.sc.h1(), L.sc.h2(), L.sc.slot(0), tol, verify ? 0 : 1, nrhs, L.sc.slot(3), c->st,
+                        jd);
+      launch_scale_dev<R>(Vb, w, L.sc.slot(3), 0, n, nrhs, c->st, jd, 1, bstride);  // V_{j+1}
+      launch_kctl_step_end(K, S.active, nrhs, m, acc, body_count(c, slot), h_arn, c->st);
+    });
+    launch_gmres_solve_y(S, nrhs, c->st);
+    KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+          launch_multiaxpy<R>(x, precond ? Zb : Vb, bstride, m, S.y, m, 1.0, n, nrhs, c->st, jd, 0));
+  };
+
+  if (single) {  // one cycle, no restart loop (the FP32 cycles of the mixed solve)
+    one_cycle();
+    return;
+  }
+  cond_node(c, h_loop, cudaGraphCondTypeWhile, [&](int slot_r) {
+    one_cycle();
+    const cudaGraphConditionalHandle h_if = cond_handle(c);
+    launch_kctl_cycle_end(K, S.done, nrhs, verify ? 1 : 0, max_cycles, body_count(c, slot_r), h_if, c->st);
+    int slot_if = -1;
+    cond_node(c, h_if, cudaGraphCondTypeIf, [&](int slot_i) {
+      slot_if = slot_i;
+      apply_op<R>(c, l, r, x, nrhs);
+      launch_axpby<R>(r, 1.0, b, -1.0, n, nrhs, c->st);
+      norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
+      launch_gmres_mark_done(S, L.sc.slot(1), tol, nrhs, c->st);
+    });
+    launch_kctl_restart_check(K, S.done, L.sc.slot(1), nrhs, body_count(c, slot_if), h_loop, c->st);
+  });
+}
+
 // ---------------- learned coarse correction (PTC network) ----------------
 constexpr int PTC_NW1 = WCMG_PTC_HIDDEN * 1 * 9 * 16;
 constexpr int PTC_NW2 = 1 * WCMG_PTC_HIDDEN * 9 * 16;
@@ -605,9 +807,14 @@ static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
         ++c->learned_cycles;
         x0 = true;
       }
-      KrylovOut k = fgmres<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter,
-                              !x0, false, false);
-      c->coarse_its += k.iterations;
+      if (c->capturing) {
+        fgmres_g<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter, !x0, false,
+                    false, 0, c->kctl.p + 2 + (l + 1), nullptr, 0, c->gstat.p + 1);
+      } else {
+        KrylovOut k = fgmres<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol,
+                                c->p.coarse_maxiter, !x0, false, false);
+        c->coarse_its += k.iterations;
+      }
     } else {
       cycle<R>(c, l + 1, ec, rc, nrhs);
     }
@@ -751,6 +958,9 @@ static void solve_f64(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcmg_
   st->converged = k.converged;
 }
 
+// relative tolerance of each FP32 FGMRES cycle between two FP64 defect corrections
+constexpr double kInnerTol = 1e-5;
+
 // Precision change (Sec. 2.1): FP64 iterate and true residual, FP32 FGMRES cycles
 // preconditioned by the FP32 multigrid; every restart is a defect correction.
 static void solve_mixed(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcmg_stats* st) {
@@ -773,7 +983,7 @@ static void solve_mixed(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcm
   DevBuf<int>& mask = c->errflag;  // errflag has room for max rhs + 1
   std::vector<int> done(nrhs, 0);
   int its = 0, restarts = 0;
-  const double inner_tol = 1e-5;
+  const double inner_tol = kInnerTol;
   while (true) {
     norm2_op<double>(c, L.sc.slot(1), r64, n, nrhs);
     const double* h = read_doubles(c, L.sc.slot(1), nrhs);
@@ -796,6 +1006,7 @@ static void solve_mixed(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcm
                                 std::min(c->p.outer_restart, c->p.outer_maxiter - its), true, false, true, 1);
     its += k.iterations;
     ++restarts;
+    if (k.iterations == 0) { st->converged = 0; break; }  // FP32 cycle could not move (no progress)
     launch_convert<float, double>(t64, e32, n * nrhs, c->st);
     launch_axpby<double>(x, 1.0, t64, 1.0, n, nrhs, c->st);
     apply_op<double>(c, 0, t64, x, nrhs);
@@ -805,6 +1016,186 @@ static void solve_mixed(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcm
   st->outer_iterations = its;
   st->restarts = restarts - 1 > 0 ? restarts - 1 : 0;
   WCMG_CUDA(cudaStreamSynchronize(c->st));
+}
+
+// ---------------- the solve as one CUDA graph ----------------
+// solve_mixed / solve_f64 with the device-side tests of fgmres_g: captured once per
+// (nrhs, buffer generation) and replayed by a single cudaGraphLaunch.
+
+static void solve_mixed_body(wcmg_ctx* c, double2* x, const double2* b, int nrhs) {
+  Level& L = c->L[0];
+  const long long n = L.n();
+  double2* r64 = ws<double>(L, "mx_r", nrhs);
+  double2* t64 = ws<double>(L, "mx_t", nrhs);
+  float2* r32 = ws<float>(L, "mx_r32", nrhs);
+  float2* e32 = ws<float>(L, "mx_e32", nrhs);
+  L.sc.ensure(max_rhs_all(c), std::max(c->p.outer_restart, c->p.coarse_restart));
+  double* bn2 = L.sc.slot(7);
+  KCtl* Kmx = c->kctl.p;
+  KCtl* Kfg = c->kctl.p + 1;
+  norm2_op<double>(c, bn2, b, n, nrhs);
+  launch_fill_zero<double>(x, n * nrhs, c->st);
+  copy_fields<double>(c, r64, b, n * nrhs);
+  norm2_op<double>(c, L.sc.slot(1), r64, n, nrhs);
+  const cudaGraphConditionalHandle h = cond_handle(c);
+  launch_kctl_init(Kmx, c->p.outer_maxiter, nullptr, 0, h, 0, c->st);
+  launch_mx_check(Kmx, nullptr, L.sc.slot(1), bn2, c->p.outer_tol, c->mx_done.p, c->mx_worst.p, nrhs,
+                  BodyCount{nullptr, -1, nullptr}, h, c->st);
+  cond_node(c, h, cudaGraphCondTypeWhile, [&](int slot) {
+    launch_convert<double, float>(r32, r64, n * nrhs, c->st);
+    launch_mask_rhs<float>(r32, c->mx_done.p, n, nrhs, c->st);
+    fgmres_g<float>(c, 0, e32, r32, nrhs, c->p.outer_restart, kInnerTol, c->p.outer_restart, true, false, true, 1,
+                    Kfg, &Kmx->its, c->p.outer_maxiter, nullptr);
+    launch_convert<float, double>(t64, e32, n * nrhs, c->st);
+    launch_axpby<double>(x, 1.0, t64, 1.0, n, nrhs, c->st);
+    apply_op<double>(c, 0, t64, x, nrhs);
+    copy_fields<double>(c, r64, b, n * nrhs);
+    launch_axpby<double>(r64, -1.0, t64, 1.0, n, nrhs, c->st);
+    norm2_op<double>(c, L.sc.slot(1), r64, n, nrhs);
+    launch_mx_check(Kmx, Kfg, L.sc.slot(1), bn2, c->p.outer_tol, c->mx_done.p, c->mx_worst.p, nrhs,
+                    body_count(c, slot), h, c->st);
+  });
+}
+
+static void solve_f64_body(wcmg_ctx* c, double2* x, const double2* b, int nrhs) {
+  fgmres_g<double>(c, 0, x, b, nrhs, c->p.outer_restart, c->p.outer_tol, c->p.outer_maxiter, true, true, true, 0,
+                   c->kctl.p + 1, nullptr, 0, nullptr);
+}
+
+// Device buffers of the graph path and every lazily converted operand, made
+// eagerly so that neither a capture nor a replay allocates or converts.
+static void graph_prepare(wcmg_ctx* c, int nrhs) {
+  c->body_counts.ensure(wcmg_ctx::MAX_BODIES);
+  c->gstat.ensure(2);
+  c->kctl.ensure(2 + WCMG_MAX_LEVELS);
+  c->mx_done.ensure(max_rhs_all(c));
+  c->mx_worst.ensure(1);
+  for (auto& s : c->cap_st)
+    if (!s) WCMG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  // the basis-slot copies of fgmres_g (level-0 FGMRES, coarsest GMRES)
+  const int lc = c->p.n_levels - 1;
+  if (inner64(c)) {
+    ws<double>(c->L[0], "fg_vc", nrhs);
+    ws<double>(c->L[0], "fg_zc", nrhs);
+    ws<double>(c->L[lc], "gm_vc", nrhs);
+    return;
+  }
+  ws<float>(c->L[0], "fg_vc", nrhs);
+  ws<float>(c->L[0], "fg_zc", nrhs);
+  ws<float>(c->L[lc], "gm_vc", nrhs);
+  for (int l = 0; l + 1 < c->p.n_levels; ++l) Prec<float>::vecs(c, c->L[l]);
+  for (int l = 1; l < c->p.n_levels; ++l) {
+    Level& L = c->L[l];
+    if (L.have_op && !L.L32_valid && L.op64) {
+      const long long n = (long long)L.g.V * L.nc * links_ld(L.nc);
+      L.L32.ensure(n);
+      launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
+      L.L32_valid = true;
+    }
+  }
+}
+
+static bool is_warm(const wcmg_ctx* c, int nrhs) {
+  return std::find(c->warm_rhs.begin(), c->warm_rhs.end(), nrhs) != c->warm_rhs.end();
+}
+
+// Capture the solves of n contexts (each on its own branch) into one graph.
+// xs/bs are the contexts' internal FP64 work fields.
+static void capture_group(wcmg_ctx** cs, int n, double2* const* xs, const double2* const* bs, const int* nrhs,
+                          wcmg_ctx::Graph& G) {
+  wcmg_ctx* c0 = cs[0];
+  for (int i = 0; i < n; ++i)
+    if (!cs[i]->cap_st[0]) WCMG_CUDA(cudaStreamCreateWithFlags(&cs[i]->cap_st[0], cudaStreamNonBlocking));
+  cudaStream_t ms = c0->cap_st[0];
+  std::vector<cudaStream_t> saved(n);
+  for (int i = 0; i < n; ++i) saved[i] = cs[i]->st;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins(n, nullptr);
+  WCMG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  for (int i = 1; i < n; ++i) WCMG_CUDA(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming));
+  auto cleanup = [&]() {
+    for (int i = 0; i < n; ++i) {
+      cs[i]->st = saved[i];
+      cs[i]->capturing = false;
+      cs[i]->cap_depth = 0;
+      cs[i]->nested.clear();
+    }
+    cudaEventDestroy(fork);
+    for (auto e : joins)
+      if (e) cudaEventDestroy(e);
+  };
+  WCMG_CUDA(cudaStreamBeginCapture(ms, cudaStreamCaptureModeRelaxed));
+  cudaGraph_t g = nullptr;
+  try {
+    WCMG_CUDA(cudaEventRecord(fork, ms));
+    for (int i = 0; i < n; ++i) {
+      wcmg_ctx* c = cs[i];
+      c->st = c->cap_st[0];
+      if (i > 0) WCMG_CUDA(cudaStreamWaitEvent(c->st, fork, 0));
+      c->capturing = true;
+      c->cap_depth = 0;
+      c->body_counts_h.clear();
+      c->nested.assign(1, 0);
+      WCMG_CUDA(cudaMemsetAsync(c->gstat.p, 0, 2 * sizeof(long long), c->st));
+      const long long l0 = launch_counter();
+      if (inner64(c)) solve_f64_body(c, xs[i], bs[i], nrhs[i]);
+      else solve_mixed_body(c, xs[i], bs[i], nrhs[i]);
+      c->graph_top = (launch_counter() - l0) - c->nested[0];
+      c->capturing = false;
+      if (i > 0) {
+        WCMG_CUDA(cudaEventRecord(joins[i], c->st));
+        WCMG_CUDA(cudaStreamWaitEvent(ms, joins[i], 0));
+      }
+    }
+    WCMG_CUDA(cudaStreamEndCapture(ms, &g));
+  } catch (...) {
+    cudaGraph_t dummy = nullptr;
+    cudaStreamEndCapture(ms, &dummy);
+    if (dummy) cudaGraphDestroy(dummy);
+    cleanup();
+    throw;
+  }
+  cleanup();
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    throw Error(WCMG_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i < n; ++i) {
+    wcmg_ctx* c = cs[i];
+    if (!c->body_counts_h.empty())
+      WCMG_CUDA(cudaMemcpy(c->body_counts.p, c->body_counts_h.data(), sizeof(int) * c->body_counts_h.size(),
+                           cudaMemcpyHostToDevice));
+  }
+  G.reset();
+  G.g = g;
+  G.exec = exec;
+  G.gen = alloc_gen();
+}
+
+// Replay results of one context: iterations, residual, launches.
+static void graph_stats(wcmg_ctx* c, wcmg_stats* st) {
+  KCtl k[2];
+  long long gs[2];
+  double worst = 0.0;
+  WCMG_CUDA(cudaMemcpyAsync(k, c->kctl.p, sizeof(k), cudaMemcpyDeviceToHost, c->st));
+  WCMG_CUDA(cudaMemcpyAsync(gs, c->gstat.p, sizeof(gs), cudaMemcpyDeviceToHost, c->st));
+  WCMG_CUDA(cudaMemcpyAsync(&worst, c->mx_worst.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  if (inner64(c)) {
+    if (k[1].err) throw Error(WCMG_ERR_NAN, "non-finite residual in Krylov solver");
+    st->outer_iterations = k[1].its;
+    st->restarts = k[1].cycles > 1 ? k[1].cycles - 1 : 0;
+  } else {
+    if (k[0].err) throw Error(WCMG_ERR_NAN, "non-finite residual");
+    st->outer_iterations = k[0].its;
+    st->restarts = k[0].restarts - 1 > 0 ? k[0].restarts - 1 : 0;
+    st->true_residual = worst;
+  }
+  st->coarse_iterations = gs[1];
+  st->kernel_launches = c->graph_top + gs[0];
+  st->graph = 1;
 }
 
 // true residual max_r ||b - D x|| / ||b|| in FP64
@@ -977,7 +1368,6 @@ static void unpack_level(wcmg_ctx* c, int l, double2* ext, const cplx<R>* in, in
                 : launch_unpack_coarse<R>(ext, in, L.g.d_perm.p, L.g.V, L.nc, nrhs, c->st)));
 }
 
-static bool inner64(const wcmg_ctx* c) { return c->p.inner_prec == WCMG_F64; }
 
 // A bounded device-side wait that gave up leaves a nonzero word: report it.
 static void check_device_waits(wcmg_ctx* c) {
@@ -1052,6 +1442,8 @@ int wcmg_default_params(wcmg_params* p) {
   p->coarse_link_prec = WCMG_F32;
   p->max_rhs = 1;
   p->profile = 0;
+  p->use_graphs = 0;
+  p->autotune = 0;
   return WCMG_OK;
 }
 
@@ -1502,7 +1894,7 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   wcmg_kstat k0[WCMG_NKCLASS];
   std::memcpy(k0, c->prof.k, sizeof(k0));
   c->coarse_its = 0;
-  const long long l0 = launch_counter();
+  long long l0 = launch_counter();
   auto t0 = std::chrono::steady_clock::now();
   if (c->coarse_mode != WCMG_COARSE_MG) {
     if (!c->have_ptc) throw Error(WCMG_ERR_STATE, "learned coarse mode needs PTC weights");
@@ -1518,8 +1910,30 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   double2* b64 = ws<double>(L, "sv_b", nrhs);
   double2* x64 = ws<double>(L, "sv_x", nrhs);
   pack_level<double>(c, 0, b64, bi, nrhs);
-  if (inner64(c)) solve_f64(c, x64, b64, nrhs, st);
-  else solve_mixed(c, x64, b64, nrhs, st);
+  const bool want_graph = c->p.use_graphs && c->coarse_mode == WCMG_COARSE_MG;
+  long long graph_kernels = 0;
+  if (want_graph) graph_prepare(c, nrhs);
+  if (want_graph && is_warm(c, nrhs)) {
+    auto& G = c->graph;
+    if (!G.exec || G.nrhs != nrhs || G.gen != alloc_gen()) {
+      wcmg_ctx* cs[1] = {c};
+      double2* xs[1] = {x64};
+      const double2* bs[1] = {b64};
+      const int nr[1] = {nrhs};
+      const long long lc = launch_counter();
+      capture_group(cs, 1, xs, bs, nr, G);
+      G.nrhs = nrhs;
+      l0 += launch_counter() - lc;  // captured, not launched
+    }
+    WCMG_CUDA(cudaGraphLaunch(G.exec, c->st));
+    graph_stats(c, st);
+    graph_kernels = st->kernel_launches;
+  } else {
+    if (inner64(c)) solve_f64(c, x64, b64, nrhs, st);
+    else solve_mixed(c, x64, b64, nrhs, st);
+    st->coarse_iterations = c->coarse_its;
+    if (want_graph) c->warm_rhs.push_back(nrhs);
+  }
   check_device_waits(c);
   st->true_residual = true_residual(c, x64, b64, nrhs);
   st->converged = st->true_residual <= c->p.outer_tol;
@@ -1530,8 +1944,7 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   st->ms_solve = std::chrono::duration<double, std::milli>(t1 - t0).count();
   c->prof.flush();
   kstat_delta(st->k, c->prof.k, k0);
-  st->coarse_iterations = c->coarse_its;
-  st->kernel_launches = launch_counter() - l0;
+  st->kernel_launches = graph_kernels + (launch_counter() - l0);
   st->learned_cycles = c->learned_cycles;
   st->learned_fallback = c->learned_fallback ? 1 : 0;
   c->learned_on = false;
@@ -1540,6 +1953,103 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
     return WCMG_ERR_NOT_CONVERGED;
   }
   API_END(c)
+}
+
+int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* const* x, const int* nrhs,
+                     int where, void* stream, wcmg_stats* st) {
+  if (!ctxs || n < 1 || !ctxs[0]) return WCMG_ERR_ARG;
+  wcmg_ctx* c0 = ctxs[0];
+  API_BEGIN(c0)
+  if (!b || !x || !nrhs) throw Error(WCMG_ERR_ARG, "null argument");
+  for (int i = 0; i < n; ++i) {
+    wcmg_ctx* c = ctxs[i];
+    if (!c) throw Error(WCMG_ERR_ARG, "null context");
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == c) throw Error(WCMG_ERR_ARG, "context repeated in a batch");
+    c->st = (cudaStream_t)stream;
+    check_rhs(c, nrhs[i]);
+    for (int l = 0; l + 1 < c->p.n_levels; ++l)
+      if (!c->L[l].have_P || !c->L[l + 1].have_op) throw Error(WCMG_ERR_STATE, "setup not done");
+    if (c->coarse_mode != WCMG_COARSE_MG) throw Error(WCMG_ERR_ARG, "batched solve needs the plain multigrid mode");
+  }
+  std::vector<wcmg_stats> local(n);
+  auto S = [&](int i) -> wcmg_stats& { return st ? st[i] : local[i]; };
+  long long l0 = launch_counter();
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<double2*> xs(n), xo(n);
+  std::vector<const double2*> bs(n);
+  std::vector<size_t> bytes(n);
+  for (int i = 0; i < n; ++i) {
+    wcmg_ctx* c = ctxs[i];
+    const double mi = S(i).ms_setup_init, mr = S(i).ms_setup_refine;
+    std::memset(&S(i), 0, sizeof(wcmg_stats));
+    S(i).ms_setup_init = mi;
+    S(i).ms_setup_refine = mr;
+    c->coarse_its = 0;
+    c->learned_on = false;
+    Level& L = c->L[0];
+    bytes[i] = (size_t)nrhs[i] * L.n() * 16;
+    const double2* bi = in_dev(c, b[i], bytes[i], where, 0);
+    xo[i] = out_dev(c, x[i], bytes[i], where, 1);
+    double2* b64 = ws<double>(L, "sv_b", nrhs[i]);
+    xs[i] = ws<double>(L, "sv_x", nrhs[i]);
+    bs[i] = b64;
+    pack_level<double>(c, 0, b64, bi, nrhs[i]);
+    graph_prepare(c, nrhs[i]);
+  }
+  bool warm = true;
+  for (int i = 0; i < n; ++i) warm &= is_warm(ctxs[i], nrhs[i]);
+  std::vector<long long> gk(n, 0);
+  if (!warm) {
+    for (int i = 0; i < n; ++i) {
+      wcmg_ctx* c = ctxs[i];
+      if (inner64(c)) solve_f64(c, xs[i], bs[i], nrhs[i], &S(i));
+      else solve_mixed(c, xs[i], bs[i], nrhs[i], &S(i));
+      S(i).coarse_iterations = c->coarse_its;
+      if (!is_warm(c, nrhs[i])) c->warm_rhs.push_back(nrhs[i]);
+    }
+  } else {
+    std::vector<const void*> key;
+    for (int i = 0; i < n; ++i) {
+      key.push_back(ctxs[i]);
+      key.push_back(reinterpret_cast<const void*>((intptr_t)nrhs[i]));
+    }
+    auto& G = c0->batch;
+    if (!G.exec || key != c0->batch_key || G.gen != alloc_gen()) {
+      const long long lc = launch_counter();
+      capture_group(const_cast<wcmg_ctx**>(ctxs), n, xs.data(), bs.data(), nrhs, G);
+      c0->batch_key = key;
+      l0 += launch_counter() - lc;
+    }
+    WCMG_CUDA(cudaGraphLaunch(G.exec, (cudaStream_t)stream));
+    for (int i = 0; i < n; ++i) {
+      graph_stats(ctxs[i], &S(i));
+      gk[i] = S(i).kernel_launches;
+    }
+  }
+  const long long eager = launch_counter() - l0;  // all contexts' host-launched kernels
+  int rc = WCMG_OK;
+  for (int i = 0; i < n; ++i) {
+    wcmg_ctx* c = ctxs[i];
+    check_device_waits(c);
+    S(i).true_residual = true_residual(c, xs[i], bs[i], nrhs[i]);
+    S(i).converged = S(i).true_residual <= c->p.outer_tol;
+    unpack_level<double>(c, 0, xo[i], xs[i], nrhs[i]);
+    out_finish(c, x[i], xo[i], bytes[i], where);
+    if (!S(i).converged && rc == WCMG_OK) {
+      rc = WCMG_ERR_NOT_CONVERGED;
+      c0->err = "a context of the batch reached outer_maxiter";
+    }
+  }
+  WCMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  auto t1 = std::chrono::steady_clock::now();
+  const double ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  for (int i = 0; i < n; ++i) {
+    S(i).ms_solve = ms;
+    S(i).kernel_launches = gk[i] + (i == 0 ? eager : 0);
+  }
+  if (rc != WCMG_OK) return rc;
+  API_END(c0)
 }
 
 int wcmg_set_profile(wcmg_ctx* c, int mask) {

@@ -58,6 +58,8 @@ class wcmg_params(ctypes.Structure):
         ("coarse_link_prec", ctypes.c_int),
         ("max_rhs", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("use_graphs", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -79,6 +81,8 @@ class wcmg_stats(ctypes.Structure):
         ("ms_solve", ctypes.c_double),
         ("learned_fallback", ctypes.c_int),
         ("learned_cycles", ctypes.c_int),
+        ("graph", ctypes.c_int),
+        ("reserved", ctypes.c_int),
         ("k", wcmg_kstat * NKCLASS),
     ]
 
@@ -119,6 +123,8 @@ _SIGS = {
     "wcmg_mg_cycle": ([_PCTX, _vp, _vp, _i, _i, _vp], _i),
     "wcmg_krylov": ([_PCTX, _i, _i, _vp, _vp, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_i)], _i),
     "wcmg_solve": ([_PCTX, _vp, _vp, _i, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
+    "wcmg_solve_batch": ([ctypes.POINTER(_PCTX), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i), _i,
+                          _vp, ctypes.POINTER(wcmg_stats)], _i),
     "wcmg_set_profile": ([_PCTX, _i], _i),
     "wcmg_get_kstats": ([_PCTX, ctypes.POINTER(wcmg_kstat)], _i),
     "wcmg_block_orthonormalise_noalloc": ([_vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp], _i),
@@ -300,6 +306,24 @@ class Context:
 
     def set_profile(self, mask):
         return self._check(wcmg_set_profile(self.h, mask))
+
+    @staticmethod
+    def solve_batch(ctxs, bs, xs, nrhs=None, stream=None, allow_not_converged=False):
+        """wcmg_solve_batch over several contexts (one graph launch once warm)."""
+        n = len(ctxs)
+        nrhs = list(nrhs) if nrhs is not None else [1] * n
+        hs = (_PCTX * n)(*[c.h for c in ctxs])
+        pb, px, where = (_vp * n)(), (_vp * n)(), set()
+        for i in range(n):
+            pb[i], w1 = _buf(bs[i])
+            px[i], w2 = _buf(xs[i], True)
+            where |= {w1, w2}
+        assert len(where) == 1
+        sts = (wcmg_stats * n)()
+        rc = wcmg_solve_batch(hs, n, pb, px, (_i * n)(*nrhs), where.pop(), _stream(stream), sts)
+        if rc != OK and not (allow_not_converged and rc == ERR_NOT_CONVERGED):
+            raise WcmgError(rc, wcmg_last_error(ctxs[0].h).decode())
+        return list(sts)
 
     def kstats(self):
         arr = (wcmg_kstat * NKCLASS)()
