@@ -216,11 +216,11 @@ def make_inputs(cfg):
     return U, iv, b
 
 
-def params(wcmg, cfg, inner, links, profile=0, graphs=0):
+def params(wcmg, cfg, inner, links, profile=0, graphs=0, autotune=1):
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
                             n_levels=len(cfg["blocks"]) + 1, max_rhs=cfg.get("nrhs", 1), profile=profile,
-                            use_graphs=graphs)
+                            use_graphs=graphs, autotune=autotune)
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -254,7 +254,8 @@ def run_gpu(args, rank, world, local):
     bd = torch.from_numpy(b).to(dev)
     xd = torch.zeros_like(bd)
     flush = L2Flush(torch, dev)
-    ctx = wcmg.Context(params(wcmg, cfg, args.inner, args.links, profile=-1, graphs=args.graphs))
+    ctx = wcmg.Context(params(wcmg, cfg, args.inner, args.links, profile=-1, graphs=args.graphs,
+                              autotune=args.autotune))
 
     def step(x, U_, iv_, b_):
         ctx.set_gauge(U_, stream)
@@ -287,6 +288,8 @@ def run_gpu(args, rank, world, local):
     barrier(dist, local)
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
+    if args.ncu_region:
+        torch.cuda.profiler.start()  # ncu --profile-from-start off: profile the timed steps only
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
@@ -304,6 +307,8 @@ def run_gpu(args, rank, world, local):
             phases["setup_refine"].append(s1.ms_setup_refine)
             phases["solve"].append(s2.ms_solve)
         torch.cuda.synchronize()
+    if args.ncu_region:
+        torch.cuda.profiler.stop()
     t_wall = time.perf_counter() - t_wall
     barrier(dist, local)
     step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
@@ -336,6 +341,17 @@ def run_gpu(args, rank, world, local):
                    "GB/s": round(co.bytes / (co.ms * 1e-3) / 1e9, 1) if co.ms else None,
                    "frac_of_hbm": round(co.bytes / (co.ms * 1e-3) / 1e9 / hbm, 4) if co.ms else None,
                    "solve": "host-driven first solve of the warm-up"}
+
+    # launch shapes of the coarse applies (autotuned on first use, else the fixed rule)
+    tiles = {}
+    pr = wcmg.F64 if args.inner == "f64" else wcmg.F32
+    for lev in range(1, len(cfg["blocks"]) + 1):
+        for nr in sorted({1, nrhs, *cfg["nvec"]}):
+            try:
+                t = ctx.get_coarse_tile(lev, nr, pr)
+            except wcmg.WcmgError:
+                continue
+            tiles[f"level{lev}_rhs{nr}"] = {k: (round(v, 2) if isinstance(v, float) else v) for k, v in t.items()}
 
     # isolated coarse stencil (1 rhs), L2 flushed before every apply
     coarse_iso = measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg)
@@ -413,6 +429,7 @@ def run_gpu(args, rank, world, local):
             "e2e": {"value": round(e2e_ms / 1e3, 5), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "learned": learned,
             "uneven_batch": uneven,
+            "coarse_tiles": tiles,
             "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
             "clocks": clocks, "wall_s_timed": round(t_wall, 3), "fp64_inner": fp64, "cpu_baseline": cpu,
             "kernel_shares": {k: round(v[1] / (ms * args.steps), 4) for k, v in acc.items() if v[1] > 0},
@@ -635,6 +652,10 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=0, help="override the workload's number of right-hand sides")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="1: each solve replays one captured CUDA graph; 0: host-driven solve")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="1: coarse-apply launch shapes picked by the autotuner; 0: fixed rule")
+    ap.add_argument("--ncu-region", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

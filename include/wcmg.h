@@ -206,6 +206,38 @@ int wcmg_solve(wcmg_ctx* ctx, const void* b, void* x, int nrhs, int where, void*
 int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* const* x, const int* nrhs,
                      int where, void* stream, wcmg_stats* st);
 
+/* Launch shape of the nine-point coarse apply (K4 / K4m).  Fixed rule: one rhs ->
+ * the one-rhs kernel (kind 0); several rhs -> the rhs-tile kernel (kind 1); BF16
+ * links with >= 8 rhs -> the tcgen05 tensor-core kernel (kind 2). */
+typedef struct wcmg_tile {
+  int kind;             /* 0 one-rhs kernel, 1 rhs-tile SIMT kernel, 2 tensor-core kernel, -1 none */
+  int rhs_per_cta;      /* kind 1: 1, 4 or 8 rhs per CTA */
+  int parts;            /* kinds 0, 1: CTAs sharing one coarse site's rows (kind 1: 0 = automatic) */
+  int threads;          /* kind 0: threads per CTA (64 .. 512, multiple of 32) */
+  int ntile;            /* kind 2: rhs per MMA N tile (16, 32, 48 or 64) */
+  int source;           /* 0 fixed rule, 1 autotuner, 2 wcmg_set_coarse_tile */
+  int candidates;       /* shapes the autotuner timed (fixed rule included) */
+  int reserved;
+  double us;            /* autotuner: time per apply of the chosen shape (back-to-back applies) */
+  double us_default;    /* autotuner: time per apply of the fixed rule */
+} wcmg_tile;
+
+/* The tile the next full coarse apply of `level` with nrhs rhs at `prec` will use
+ * (prec F64: FP64 links; F32: FP32 vectors on the level's params.coarse_link_prec
+ * storage).  No GPU work.  ERR_STATE before the level's coarse operator exists. */
+int wcmg_get_coarse_tile(wcmg_ctx* ctx, int level, int nrhs, int prec, wcmg_tile* out);
+
+/* Run the autotuner now for (level, nrhs, prec): every candidate shape is timed
+ * with CUDA events on the level's own links (10 back-to-back applies after 2
+ * warm-up applies, on `stream`) and the fastest is kept for later applies.
+ * Synchronises `stream`. */
+int wcmg_tune_coarse(wcmg_ctx* ctx, int level, int nrhs, int prec, void* stream, wcmg_tile* out);
+
+/* Force a tile for (level, nrhs, prec); t->kind = -1 clears it (back to the
+ * fixed rule, or the autotuner when params.autotune = 1).  ERR_ARG if the shape
+ * is not valid for the level (e.g. kind 2 without BF16 links). */
+int wcmg_set_coarse_tile(wcmg_ctx* ctx, int level, int nrhs, int prec, const wcmg_tile* t);
+
 /* Change params.profile of an existing context (no GPU work). */
 int wcmg_set_profile(wcmg_ctx* ctx, int mask);
 /* Per-kernel-class counters accumulated over the context's lifetime

@@ -300,7 +300,7 @@ template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
 
 template <typename R, typename L, int RR>
 static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
-                            int mode, int hopdir, cudaStream_t st) {
+                            int mode, int hopdir, int parts, cudaStream_t st) {
   constexpr int VEC = VecOf<L>::v;
   const int ld = links_ld(nb);
   BlockInfoC bi;
@@ -309,11 +309,13 @@ static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, con
   const size_t smem = (size_t)RR * ld * sizeof(cplx<R>);
   auto kern = k_coarse_apply<R, L, RR, VEC>;
   if (smem > 48 * 1024) WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // enough CTAs to fill every SM several times over: split the rows of a site
-  int parts = 1;
-  const long long want = 6LL * 152;
   const long long ncta_y = (nrhs + RR - 1) / RR;
-  while (parts < nb / 4 && (long long)g.V * parts * ncta_y < want) parts *= 2;
+  if (parts <= 0) {
+    // enough CTAs to fill every SM several times over: split the rows of a site
+    parts = 1;
+    const long long want = 6LL * 152;
+    while (parts < nb / 4 && (long long)g.V * parts * ncta_y < want) parts *= 2;
+  }
   const int rpc = (nb + parts - 1) / parts;
   const int rpw = (rpc + 15) / 16;  // rows per warp, at most 16 warps
   const int threads = std::max(64, 32 * ((rpc + rpw - 1) / rpw));
@@ -323,18 +325,15 @@ static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, con
 }
 
 template <typename R, typename L>
-static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb,
-                          cudaStream_t st) {
+static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int parts,
+                          int threads, cudaStream_t st) {
   constexpr int VEC = VecOf<L>::v;
   const int ld = links_ld(nb);
   const int nk = (ld + 32 * VEC - 1) / (32 * VEC);
-  // one site per CTA, 16 warps; split a site only when there are too few sites
-  int parts = 1;
-  while (parts < 4 && (long long)g.V * parts < 2LL * 152) parts *= 2;
   const size_t smem = (size_t)ld * sizeof(cplx<R>);
   const unsigned grid = (unsigned)(g.V * parts);
 #define WCMG_C1(NKV) \
-  k_coarse_apply1<R, L, VEC, NKV><<<grid, 512, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, parts)
+  k_coarse_apply1<R, L, VEC, NKV><<<grid, threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, parts)
   if (nk <= 4) WCMG_C1(4);
   else if (nk <= 8) WCMG_C1(8);
   else if (nk <= 12) WCMG_C1(12);
@@ -346,9 +345,8 @@ static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const
 
 template <typename L>
 static void coarse_apply_mma(float2* out, const float2* in, const L* links, const LevelGeom& g, int nb, int nrhs,
-                             int* err, cudaStream_t st) {
+                             int ntile, int* err, cudaStream_t st) {
   const int ld = links_ld(nb);
-  const int ntile = std::min(64, (nrhs + 15) / 16 * 16);
   const int tmem_cols = ntile <= 32 ? 32 : 64;
   const size_t smem = 2 * ((size_t)MMA_M * MMA_KC * 2 + (size_t)ntile * MMA_KC * 2);
   auto kern = k_coarse_apply_mma<L>;
@@ -358,25 +356,78 @@ static void coarse_apply_mma(float2* out, const float2* in, const L* links, cons
   WCMG_LAUNCH_CHECK();
 }
 
-// tensor-core path: BF16 coarse links, full stencil, several rhs, nbasis <= 64
-template <typename R, typename L>
-static bool use_mma(int nb, int nrhs, int mode, const int* err) {
-  return std::is_same<L, bf16c>::value && mode == ST_FULL && nrhs >= 8 && nb <= 64 && err != nullptr;
+// The fixed launch rule (used unless a tile is given):
+//  - BF16 links, full stencil, >= 8 rhs, nbasis <= 64: tensor cores, N tile = rhs rounded to 16 (<= 64);
+//  - one rhs, full stencil: the one-rhs kernel, 512 threads, a site split in up to 4
+//    CTAs while there are fewer than 2 CTAs per SM;
+//  - otherwise the rhs-tile kernel, 4 rhs per CTA (FP64 or <= 4 rhs) else 8, rows split
+//    until about 6 CTAs per SM.
+CoarseTile coarse_default_tile(int nb, int nrhs, int mode, int Vc, int link_kind) {
+  CoarseTile t;
+  if (link_kind == 2 && mode == ST_FULL && nrhs >= 8 && nb <= 64) {
+    t.kind = 2;
+    t.ntile = std::min(64, (nrhs + 15) / 16 * 16);
+    return t;
+  }
+  if (nrhs == 1 && mode == ST_FULL) {
+    t.kind = 0;
+    t.rr = 1;
+    t.parts = 1;
+    while (t.parts < 4 && (long long)Vc * t.parts < 2LL * 152) t.parts *= 2;
+    t.threads = 512;
+    return t;
+  }
+  t.kind = 1;
+  t.rr = nrhs == 1 ? 1 : (nrhs <= 4 || link_kind == 0) ? 4 : 8;
+  t.parts = 0;  // automatic
+  return t;
+}
+
+template <typename L> struct LinkKind;
+template <> struct LinkKind<double2> { static constexpr int v = 0; };
+template <> struct LinkKind<float2> { static constexpr int v = 1; };
+template <> struct LinkKind<bf16c> { static constexpr int v = 2; };
+template <> struct LinkKind<f16c> { static constexpr int v = 3; };
+
+bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link_kind) {
+  switch (t.kind) {
+    case 0:
+      return nrhs == 1 && mode == ST_FULL && t.parts >= 1 && t.parts <= nb && t.threads >= 64 && t.threads <= 512 &&
+             t.threads % 32 == 0;
+    case 1:
+      return (t.rr == 1 || t.rr == 4 || t.rr == 8) && t.parts >= 0 && t.parts <= nb;
+    case 2:
+      return link_kind == 2 && mode == ST_FULL && nb <= 64 &&
+             (t.ntile == 16 || t.ntile == 32 || t.ntile == 48 || t.ntile == 64);
+    default:
+      return false;
+  }
 }
 
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
-                         int mode, int hopdir, cudaStream_t st, int* err) {
-  if constexpr (std::is_same<L, bf16c>::value) {
-    if (use_mma<R, L>(nb, nrhs, mode, err)) {
-      coarse_apply_mma<L>((float2*)out, (const float2*)in, links, g, nb, nrhs, err, st);
+                         int mode, int hopdir, cudaStream_t st, int* err, const CoarseTile* tile) {
+  constexpr int lk = LinkKind<L>::v;
+  CoarseTile t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
+  if (tile && tile->kind >= 0) {
+    if (!coarse_tile_valid(*tile, nb, nrhs, mode, lk)) throw Error(-1, "coarse apply: invalid launch tile");
+    t = *tile;
+  }
+  if (t.kind == 2 && !err) t = coarse_default_tile(nb, nrhs, mode, g.V, lk == 2 ? 1 : lk);
+  if (t.kind == 2) {
+    if constexpr (std::is_same<L, bf16c>::value) {
+      coarse_apply_mma<L>((float2*)out, (const float2*)in, links, g, nb, nrhs, t.ntile, err, st);
       return;
     }
+    throw Error(-1, "coarse apply: tensor-core tile needs BF16 links");
   }
-  if (nrhs == 1 && mode == ST_FULL) coarse_apply1<R, L>(out, in, links, g, nb, st);
-  else if (nrhs == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, st);
-  else if (nrhs <= 4 || sizeof(R) == 8) coarse_apply_rr<R, L, 4>(out, in, links, g, nb, nrhs, mode, hopdir, st);
-  else coarse_apply_rr<R, L, 8>(out, in, links, g, nb, nrhs, mode, hopdir, st);
+  if (t.kind == 0) {
+    coarse_apply1<R, L>(out, in, links, g, nb, t.parts, t.threads, st);
+    return;
+  }
+  if (t.rr == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, t.parts, st);
+  else if (t.rr == 4) coarse_apply_rr<R, L, 4>(out, in, links, g, nb, nrhs, mode, hopdir, t.parts, st);
+  else coarse_apply_rr<R, L, 8>(out, in, links, g, nb, nrhs, mode, hopdir, t.parts, st);
 }
 
 // ---------------- link packing / assembly ----------------
@@ -482,13 +533,13 @@ void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int 
 }
 
 template void launch_coarse_apply<double, double2>(double2*, const double2*, const double2*, const LevelGeom&, int,
-                                                   int, int, int, cudaStream_t, int*);
+                                                   int, int, int, cudaStream_t, int*, const CoarseTile*);
 template void launch_coarse_apply<float, float2>(float2*, const float2*, const float2*, const LevelGeom&, int, int,
-                                                 int, int, cudaStream_t, int*);
+                                                 int, int, cudaStream_t, int*, const CoarseTile*);
 template void launch_coarse_apply<float, bf16c>(float2*, const float2*, const bf16c*, const LevelGeom&, int, int, int,
-                                                int, cudaStream_t, int*);
+                                                int, cudaStream_t, int*, const CoarseTile*);
 template void launch_coarse_apply<float, f16c>(float2*, const float2*, const f16c*, const LevelGeom&, int, int, int,
-                                               int, cudaStream_t, int*);
+                                               int, cudaStream_t, int*, const CoarseTile*);
 #define WCMG_INST_L(L)                                                                                   \
   template void launch_pack_links<L>(L*, const double2*, const int*, int, int, cudaStream_t);           \
   template void launch_unpack_links<L>(double2*, const L*, const int*, int, int, cudaStream_t);

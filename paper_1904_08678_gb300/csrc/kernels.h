@@ -60,11 +60,23 @@ template <typename R>
 void launch_pack_coarse(cplx<R>* out, const double2* ext, const int* perm, int V, int nc, int nrhs, cudaStream_t st);
 template <typename R>
 void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int V, int nc, int nrhs, cudaStream_t st);
-// err (device int, may be null): receives 2 if a bounded wait of the TMA path
-// gave up; a null err selects the plain load path.
+// Launch shape of the coarse apply.  kind 0: one-rhs kernel (parts CTAs per
+// site, threads per CTA); kind 1: rhs-tile kernel (rr rhs per CTA, parts CTAs
+// per site, 0 = automatic); kind 2: tcgen05 tensor-core kernel (BF16 links, N
+// tile ntile).  kind -1: the fixed rule of coarse_default_tile.
+struct CoarseTile {
+  int kind = -1, rr = 0, parts = 0, threads = 0, ntile = 0;
+};
+// link_kind: 0 FP64, 1 FP32, 2 BF16, 3 FP16 link storage
+CoarseTile coarse_default_tile(int nb, int nrhs, int mode, int Vc, int link_kind);
+bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link_kind);
+// err (device int, may be null): receives 3 if a bounded wait of the tensor-core
+// path gave up; a null err keeps the SIMT kernels.  tile (nullable): launch shape
+// (validated; an invalid tile throws).
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
-                         int mode, int hopdir, cudaStream_t st, int* err = nullptr);
+                         int mode, int hopdir, cudaStream_t st, int* err = nullptr,
+                         const CoarseTile* tile = nullptr);
 // links[x][a][d*nb + b0 + j] = res[j][x][a] for j < ncols (res: restrict output of the column fields)
 template <typename R, typename L>
 void launch_scatter_links(L* links, const cplx<R>* res, int Vc, int nb, int d, int b0, int ncols, cudaStream_t st);

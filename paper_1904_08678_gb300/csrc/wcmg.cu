@@ -25,9 +25,10 @@
 
 namespace wcmg {
 
-// Bumped by every device allocation of a DevBuf: a captured CUDA graph is valid
-// only while no buffer it references has been reallocated.
-static unsigned long long& alloc_gen() {
+// Bumped by every device allocation of a DevBuf and by every change of a coarse
+// launch tile: a captured CUDA graph is valid only while no buffer it references
+// has been reallocated and every launch shape it baked in still holds.
+static unsigned long long& graph_epoch() {
   static unsigned long long g = 0;
   return g;
 }
@@ -55,7 +56,7 @@ struct DevBuf {
     release();
     WCMG_CUDA(cudaMalloc(&p, (count ? count : 1) * sizeof(T)));
     n = count;
-    ++alloc_gen();
+    ++graph_epoch();
     return p;
   }
 };
@@ -143,6 +144,14 @@ struct Level {
   bool L32_valid = false, low_valid = false;
   LevelScalars sc;
   std::map<std::string, DevBuf<unsigned char>> ws;
+  // coarse-apply launch shape per (nrhs, link storage): tuned or forced
+  struct TileInfo {
+    CoarseTile t;
+    int source = 0;  // 1 autotuned, 2 set by the caller
+    int candidates = 0;
+    double us = 0.0, us_default = 0.0;
+  };
+  std::map<std::pair<int, int>, TileInfo> tiles;
   long long n() const { return (long long)g.V * nc; }
 };
 
@@ -342,6 +351,93 @@ template <> struct Prec<float> {
 
 static double sz(int prec) { return prec == WCMG_F64 ? 16.0 : prec == WCMG_F32 ? 8.0 : 4.0; }
 
+// ---------------- coarse-apply autotuner ----------------
+// Candidate launch shapes of the full nine-point coarse apply (K4 / K4m).
+static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
+  std::vector<CoarseTile> v;
+  auto add = [&](int kind, int rr, int parts, int threads, int ntile) {
+    CoarseTile t;
+    t.kind = kind; t.rr = rr; t.parts = parts; t.threads = threads; t.ntile = ntile;
+    if (coarse_tile_valid(t, nb, nrhs, ST_FULL, lk)) v.push_back(t);
+  };
+  if (nrhs == 1) {
+    for (int th : {256, 512})
+      for (int p : {1, 2, 4, 8}) add(0, 1, p, th, 0);
+    for (int p : {1, 2, 4, 8, 16}) add(1, 1, p, 0, 0);
+    return v;
+  }
+  for (int rr : {1, 4, 8})
+    if (rr <= nrhs || rr == 4)
+      for (int p : {0, 1, 2, 4, 8, 16}) add(1, rr, p, 0, 0);
+  if (lk == 2)
+    for (int nt : {16, 32, 48, 64})
+      if (nt <= (nrhs + 15) / 16 * 16) add(2, 0, 0, 0, nt);
+  return v;
+}
+
+// Time every candidate on the level's own links (back-to-back applies, as in a
+// Krylov loop) and keep the fastest; the fixed rule is timed too.
+template <typename R, typename Lt>
+static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs, int lk) {
+  Level& L = c->L[l];
+  const int nb = L.nc;
+  cplx<R>* in = ws<R>(L, "tune_in", nrhs);
+  cplx<R>* out = ws<R>(L, "tune_out", nrhs);
+  launch_fill_zero<R>(in, L.n() * nrhs, c->st);
+  cudaEvent_t e0, e1;
+  WCMG_CUDA(cudaEventCreate(&e0));
+  WCMG_CUDA(cudaEventCreate(&e1));
+  const int reps = 10;
+  auto time_one = [&](const CoarseTile* t) -> double {
+    for (int i = 0; i < 2; ++i)
+      launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
+    WCMG_CUDA(cudaEventRecord(e0, c->st));
+    for (int i = 0; i < reps; ++i)
+      launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
+    WCMG_CUDA(cudaEventRecord(e1, c->st));
+    WCMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    WCMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return 1e3 * ms / reps;
+  };
+  Level::TileInfo ti;
+  ti.t = coarse_default_tile(nb, nrhs, ST_FULL, L.g.V, lk);
+  try {
+    ti.us_default = ti.us = time_one(nullptr);
+    const auto cands = coarse_candidates(nb, nrhs, lk);
+    for (const auto& cand : cands) {
+      const double us = time_one(&cand);
+      if (us < ti.us) {
+        ti.us = us;
+        ti.t = cand;
+      }
+    }
+    ti.candidates = (int)cands.size() + 1;
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ti.source = 1;
+  return ti;
+}
+
+// Launch shape for the full coarse apply of level l with nrhs rhs: a tile set by
+// the caller or found by the autotuner (params.autotune, tuned on first use and
+// never while a graph is being captured); nullptr selects the fixed rule.
+template <typename R, typename Lt>
+static const CoarseTile* coarse_tile(wcmg_ctx* c, int l, const Lt* links, int nrhs, int lk) {
+  Level& L = c->L[l];
+  auto it = L.tiles.find({nrhs, lk});
+  if (it != L.tiles.end()) return &it->second.t;
+  if (!c->p.autotune || c->capturing) return nullptr;
+  Level::TileInfo ti = tune_coarse<R, Lt>(c, l, links, nrhs, lk);
+  ++graph_epoch();
+  return &(L.tiles[{nrhs, lk}] = ti).t;
+}
+
 // ---------------- operators ----------------
 template <typename R>
 static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nrhs, int mode = ST_FULL,
@@ -361,21 +457,25 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
   const double flops = Vc * 8.0 * 9.0 * nb2 * nrhs;
   if (sizeof(R) == 8) {
     if (!L.op64) throw Error(WCMG_ERR_ARG, "FP64 coarse apply needs FP64 links");
+    const CoarseTile* t = mode == ST_FULL ? coarse_tile<double, double2>(c, l, L.L64.p, nrhs, 0) : nullptr;
     KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 16.0 + 2.0 * nb * 16.0 * nrhs), flops,
           (launch_coarse_apply<double, double2>((double2*)out, (const double2*)in, L.L64.p, L.g.lg(), nb, nrhs,
-                                                mode, hopdir, c->st, c->tma_err.p)));
+                                                mode, hopdir, c->st, c->tma_err.p, t)));
     return;
   }
   const int lp = c->p.coarse_link_prec;
   if (mode == ST_FULL && L.low_valid && (lp == WCMG_BF16 || lp == WCMG_F16)) {
-    if (lp == WCMG_BF16)
+    if (lp == WCMG_BF16) {
+      const CoarseTile* t = coarse_tile<float, bf16c>(c, l, L.Lbf.p, nrhs, 2);
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
             (launch_coarse_apply<float, bf16c>((float2*)out, (const float2*)in, L.Lbf.p, L.g.lg(), nb, nrhs, mode,
-                                               hopdir, c->st, c->tma_err.p)));
-    else
+                                               hopdir, c->st, c->tma_err.p, t)));
+    } else {
+      const CoarseTile* t = coarse_tile<float, f16c>(c, l, L.Lh.p, nrhs, 3);
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
             (launch_coarse_apply<float, f16c>((float2*)out, (const float2*)in, L.Lh.p, L.g.lg(), nb, nrhs, mode,
-                                              hopdir, c->st, c->tma_err.p)));
+                                              hopdir, c->st, c->tma_err.p, t)));
+    }
     return;
   }
   if (!L.L32_valid) {
@@ -384,9 +484,10 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
     launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
     L.L32_valid = true;
   }
+  const CoarseTile* t = mode == ST_FULL ? coarse_tile<float, float2>(c, l, L.L32.p, nrhs, 1) : nullptr;
   KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 8.0 + 2.0 * nb * 8.0 * nrhs), flops,
         (launch_coarse_apply<float, float2>((float2*)out, (const float2*)in, L.L32.p, L.g.lg(), nb, nrhs, mode,
-                                            hopdir, c->st, c->tma_err.p)));
+                                            hopdir, c->st, c->tma_err.p, t)));
 }
 
 template <typename R>
@@ -1171,7 +1272,7 @@ static void capture_group(wcmg_ctx** cs, int n, double2* const* xs, const double
   G.reset();
   G.g = g;
   G.exec = exec;
-  G.gen = alloc_gen();
+  G.gen = graph_epoch();
 }
 
 // Replay results of one context: iterations, residual, launches.
@@ -1463,6 +1564,8 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
     if (p->smoother_steps < 0 || p->coarse_restart < 1 || p->outer_restart < 1 || p->coarse_restart > 64 ||
         p->outer_restart > 64 || p->max_rhs < 1 || p->max_rhs > 1024)
       throw Error(WCMG_ERR_ARG, "solver parameters out of range");
+    if ((p->use_graphs != 0 && p->use_graphs != 1) || (p->autotune != 0 && p->autotune != 1))
+      throw Error(WCMG_ERR_ARG, "use_graphs and autotune must be 0 or 1");
     c->L.resize(nl);
     int dims[4];
     for (int k = 0; k < 4; ++k) dims[k] = p->dims[k];
@@ -1915,7 +2018,7 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   if (want_graph) graph_prepare(c, nrhs);
   if (want_graph && is_warm(c, nrhs)) {
     auto& G = c->graph;
-    if (!G.exec || G.nrhs != nrhs || G.gen != alloc_gen()) {
+    if (!G.exec || G.nrhs != nrhs || G.gen != graph_epoch()) {
       wcmg_ctx* cs[1] = {c};
       double2* xs[1] = {x64};
       const double2* bs[1] = {b64};
@@ -2015,7 +2118,7 @@ int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* c
       key.push_back(reinterpret_cast<const void*>((intptr_t)nrhs[i]));
     }
     auto& G = c0->batch;
-    if (!G.exec || key != c0->batch_key || G.gen != alloc_gen()) {
+    if (!G.exec || key != c0->batch_key || G.gen != graph_epoch()) {
       const long long lc = launch_counter();
       capture_group(const_cast<wcmg_ctx**>(ctxs), n, xs.data(), bs.data(), nrhs, G);
       c0->batch_key = key;
@@ -2050,6 +2153,102 @@ int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* c
   }
   if (rc != WCMG_OK) return rc;
   API_END(c0)
+}
+
+// ---- coarse-apply tiles ----
+extern "C++" {
+// link storage kind of the full coarse apply of level l at `prec` (0 FP64, 1 FP32, 2 BF16, 3 FP16)
+static int link_kind_for(wcmg_ctx* c, int l, int prec) {
+  Level& L = c->L[l];
+  if (!L.have_op) throw Error(WCMG_ERR_STATE, "coarse operator of level not built");
+  if (prec == WCMG_F64) {
+    if (!L.op64) throw Error(WCMG_ERR_ARG, "FP64 coarse apply needs FP64 links");
+    return 0;
+  }
+  if (prec != WCMG_F32) throw Error(WCMG_ERR_ARG, "prec must be F64 or F32");
+  const int lp = c->p.coarse_link_prec;
+  if (L.low_valid && lp == WCMG_BF16) return 2;
+  if (L.low_valid && lp == WCMG_F16) return 3;
+  return 1;
+}
+static void tile_out(const Level::TileInfo& ti, wcmg_tile* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->kind = ti.t.kind;
+  o->rhs_per_cta = ti.t.rr;
+  o->parts = ti.t.parts;
+  o->threads = ti.t.threads;
+  o->ntile = ti.t.ntile;
+  o->source = ti.source;
+  o->candidates = ti.candidates;
+  o->us = ti.us;
+  o->us_default = ti.us_default;
+}
+}  // extern "C++"
+
+int wcmg_get_coarse_tile(wcmg_ctx* c, int level, int nrhs, int prec, wcmg_tile* out) {
+  API_BEGIN(c)
+  check_level(c, level, 1, c->p.n_levels - 1);
+  check_rhs(c, nrhs);
+  if (!out) throw Error(WCMG_ERR_ARG, "out");
+  Level& L = c->L[level];
+  const int lk = link_kind_for(c, level, prec);
+  auto it = L.tiles.find({nrhs, lk});
+  Level::TileInfo ti;
+  if (it != L.tiles.end()) ti = it->second;
+  else ti.t = coarse_default_tile(L.nc, nrhs, ST_FULL, L.g.V, lk);
+  tile_out(ti, out);
+  API_END(c)
+}
+
+int wcmg_tune_coarse(wcmg_ctx* c, int level, int nrhs, int prec, void* stream, wcmg_tile* out) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  check_level(c, level, 1, c->p.n_levels - 1);
+  check_rhs(c, nrhs);
+  Level& L = c->L[level];
+  const int lk = link_kind_for(c, level, prec);
+  Level::TileInfo ti;
+  if (lk == 0) ti = tune_coarse<double, double2>(c, level, L.L64.p, nrhs, 0);
+  else if (lk == 2) ti = tune_coarse<float, bf16c>(c, level, L.Lbf.p, nrhs, 2);
+  else if (lk == 3) ti = tune_coarse<float, f16c>(c, level, L.Lh.p, nrhs, 3);
+  else {
+    if (!L.L32_valid) {
+      const long long n = (long long)L.g.V * L.nc * links_ld(L.nc);
+      L.L32.ensure(n);
+      launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
+      L.L32_valid = true;
+    }
+    ti = tune_coarse<float, float2>(c, level, L.L32.p, nrhs, 1);
+  }
+  L.tiles[{nrhs, lk}] = ti;
+  ++graph_epoch();
+  check_device_waits(c);
+  if (out) tile_out(ti, out);
+  API_END(c)
+}
+
+int wcmg_set_coarse_tile(wcmg_ctx* c, int level, int nrhs, int prec, const wcmg_tile* t) {
+  API_BEGIN(c)
+  check_level(c, level, 1, c->p.n_levels - 1);
+  check_rhs(c, nrhs);
+  if (!t) throw Error(WCMG_ERR_ARG, "tile");
+  Level& L = c->L[level];
+  const int lk = link_kind_for(c, level, prec);
+  if (t->kind < 0) {
+    L.tiles.erase({nrhs, lk});
+  } else {
+    Level::TileInfo ti;
+    ti.t.kind = t->kind;
+    ti.t.rr = t->rhs_per_cta;
+    ti.t.parts = t->parts;
+    ti.t.threads = t->threads;
+    ti.t.ntile = t->ntile;
+    if (!coarse_tile_valid(ti.t, L.nc, nrhs, ST_FULL, lk)) throw Error(WCMG_ERR_ARG, "tile not valid for this level");
+    ti.source = 2;
+    L.tiles[{nrhs, lk}] = ti;
+  }
+  ++graph_epoch();
+  API_END(c)
 }
 
 int wcmg_set_profile(wcmg_ctx* c, int mask) {

@@ -91,6 +91,16 @@ class wcmg_stats(ctypes.Structure):
                                 flops=self.k[i].flops) for i in range(NKCLASS) if self.k[i].launches}
 
 
+class wcmg_tile(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rhs_per_cta", ctypes.c_int), ("parts", ctypes.c_int),
+                ("threads", ctypes.c_int), ("ntile", ctypes.c_int), ("source", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("reserved", ctypes.c_int), ("us", ctypes.c_double),
+                ("us_default", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class wcmg_train_opts(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int), ("batch", ctypes.c_int), ("steps", ctypes.c_int), ("lr", ctypes.c_double),
                 ("target_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
@@ -126,6 +136,9 @@ _SIGS = {
     "wcmg_solve_batch": ([ctypes.POINTER(_PCTX), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i), _i,
                           _vp, ctypes.POINTER(wcmg_stats)], _i),
     "wcmg_set_profile": ([_PCTX, _i], _i),
+    "wcmg_get_coarse_tile": ([_PCTX, _i, _i, _i, ctypes.POINTER(wcmg_tile)], _i),
+    "wcmg_tune_coarse": ([_PCTX, _i, _i, _i, _vp, ctypes.POINTER(wcmg_tile)], _i),
+    "wcmg_set_coarse_tile": ([_PCTX, _i, _i, _i, ctypes.POINTER(wcmg_tile)], _i),
     "wcmg_get_kstats": ([_PCTX, ctypes.POINTER(wcmg_kstat)], _i),
     "wcmg_block_orthonormalise_noalloc": ([_vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp], _i),
     "wcmg_ptc_set_weights": ([_PCTX, _vp, _i, _vp], _i),
@@ -306,6 +319,20 @@ class Context:
 
     def set_profile(self, mask):
         return self._check(wcmg_set_profile(self.h, mask))
+
+    def get_coarse_tile(self, level, nrhs=1, prec=F32):
+        t = wcmg_tile()
+        self._check(wcmg_get_coarse_tile(self.h, level, nrhs, prec, ctypes.byref(t)))
+        return t.as_dict()
+
+    def tune_coarse(self, level, nrhs=1, prec=F32, stream=None):
+        t = wcmg_tile()
+        self._check(wcmg_tune_coarse(self.h, level, nrhs, prec, _stream(stream), ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_coarse_tile(self, level, nrhs=1, prec=F32, kind=-1, rhs_per_cta=0, parts=0, threads=0, ntile=0):
+        t = wcmg_tile(kind=kind, rhs_per_cta=rhs_per_cta, parts=parts, threads=threads, ntile=ntile)
+        return self._check(wcmg_set_coarse_tile(self.h, level, nrhs, prec, ctypes.byref(t)))
 
     @staticmethod
     def solve_batch(ctxs, bs, xs, nrhs=None, stream=None, allow_not_converged=False):

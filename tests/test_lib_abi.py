@@ -27,3 +27,26 @@ def test_invalid_params_rejected_without_gpu_work():
     assert wcmg.wcmg_create(ctypes.byref(p), ctypes.byref(h)) == wcmg.ERR_ARG
     p = wcmg.default_params(n_levels=7)
     assert wcmg.wcmg_create(ctypes.byref(p), ctypes.byref(h)) == wcmg.ERR_ARG
+
+
+def test_graph_and_autotune_params_validated_without_gpu_work():
+    wcmg = pytest.importorskip("paper_1904_08678_gb300.wcmg")
+    p = wcmg.default_params()
+    assert p.use_graphs == 0 and p.autotune == 0 and p.profile == 0 and p.max_rhs == 1
+    h = ctypes.c_void_p()
+    for field in ("use_graphs", "autotune"):
+        q = wcmg.default_params(**{field: 2})
+        assert wcmg.wcmg_create(ctypes.byref(q), ctypes.byref(h)) == wcmg.ERR_ARG
+
+
+def test_batch_solve_rejects_empty_batch_without_gpu_work():
+    wcmg = pytest.importorskip("paper_1904_08678_gb300.wcmg")
+    assert wcmg.wcmg_solve_batch(None, 0, None, None, None, wcmg.DEVICE, None, None) == wcmg.ERR_ARG
+
+
+def test_tile_and_stats_structs_match_header_sizes():
+    """wcmg_tile: 8 ints + 2 doubles; wcmg_stats ends with the kernel-class array."""
+    wcmg = pytest.importorskip("paper_1904_08678_gb300.wcmg")
+    assert ctypes.sizeof(wcmg.wcmg_tile) == 8 * 4 + 2 * 8
+    assert wcmg.wcmg_stats.k.offset % 8 == 0
+    assert ctypes.sizeof(wcmg.wcmg_stats) == wcmg.wcmg_stats.k.offset + wcmg.NKCLASS * ctypes.sizeof(wcmg.wcmg_kstat)
