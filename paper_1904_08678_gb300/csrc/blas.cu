@@ -4,13 +4,22 @@
 // loops issue no host round trip except their stopping tests.
 // Reductions are two-stage with fixed block counts and fixed summation trees:
 // results are bitwise reproducible run to run.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace wcmg {
 
 constexpr int RED_T = 256;
-static inline int red_blocks(long long n) {
-  long long b = (n + 8 * RED_T - 1) / (8 * RED_T);
+// Blocks along the vector of a two-stage reduction: about 8 elements per thread
+// for long vectors, but never fewer CTAs (over all `others` = rhs x chunks) than
+// ~4 per SM while every thread still has an element: short coarse vectors are
+// spread over the GPU instead of a dozen CTAs.  At most 608 (partial buffers).
+static inline int red_blocks(long long n, long long others = 1) {
+  const long long per8 = (n + 8 * RED_T - 1) / (8 * RED_T);
+  const long long per1 = (n + RED_T - 1) / RED_T;
+  const long long want = (4 * 152 + others - 1) / others;
+  long long b = std::min(std::max(per8, want), per1);
   return (int)(b < 1 ? 1 : (b > 608 ? 608 : b));
 }
 
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(RED_T) k_final(T* __restrict__ out, const T* _
 template <typename R>
 void launch_dot(double2* out, const cplx<R>* a, const cplx<R>* b, long long n, int nrhs, double2* partial,
                 cudaStream_t st) {
-  const int nb = red_blocks(n);
+  const int nb = red_blocks(n, nrhs);
   k_dot_partial<R><<<dim3(nb, nrhs), RED_T, 0, st>>>(partial, a, b, n);
   k_final<double2><<<dim3(nrhs, 1), RED_T, 0, st>>>(out, partial, nb, nb, 0, 1);
   ++launch_counter();
@@ -84,7 +93,7 @@ void launch_dot(double2* out, const cplx<R>* a, const cplx<R>* b, long long n, i
 }
 template <typename R>
 void launch_norm2(double* out, const cplx<R>* a, long long n, int nrhs, double* partial, cudaStream_t st) {
-  const int nb = red_blocks(n);
+  const int nb = red_blocks(n, nrhs);
   k_norm_partial<R><<<dim3(nb, nrhs), RED_T, 0, st>>>(partial, a, n);
   k_final<double><<<dim3(nrhs, 1), RED_T, 0, st>>>(out, partial, nb, nb, 0, 1);
   ++launch_counter();
@@ -124,8 +133,8 @@ __global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict_
 template <typename R>
 void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int k, int ldo, const cplx<R>* w,
                      long long n, int nrhs, double2* partial, cudaStream_t st, const int* kdev, int kadd) {
-  const int nb = red_blocks(n);
   const int nchunk = (k + MD_K - 1) / MD_K, kpad = nchunk * MD_K;
+  const int nb = red_blocks(n, nrhs);  // independent of k: a captured graph sums in the same order
   k_multidot_partial<R><<<dim3(nb, nrhs, nchunk), RED_T, 0, st>>>(partial, basis, bstride, k, w, n, kpad, kdev, kadd);
   k_final<double2><<<dim3(nrhs, k), RED_T, 0, st>>>(out, partial, nb, (long long)kpad * nb, nb, ldo, kdev, kadd);
   ++launch_counter();

@@ -99,6 +99,45 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ double2 warp_sum(double2 v) { return make_double2(warp_sum(v.x), warp_sum(v.y)); }
 __device__ __forceinline__ float2 warp_sum(float2 v) { return make_float2(warp_sum(v.x), warp_sum(v.y)); }
 
+__device__ __forceinline__ double2 shfl_xor2(double2 v, int o) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+// Warp sums of 8 values at once by a transposing butterfly: at each of the first
+// three exchange steps (lane distance 16, 8, 4) a lane keeps half of its values
+// and adds its partner's copy of that half, so 8 values cost 7 + 2 additions per
+// lane instead of 8 x 5.  On return v[0] of lane l holds the full warp sum of
+// value 4 b4 + 2 b3 + b2 (b_i: bit i of l); lanes with (l & 3) == 0 hold distinct
+// values.
+__device__ __forceinline__ void warp_sum8_transposed(double2 (&v)[8], int lane) {
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const double2 send = up ? v[j] : v[j + 4];
+      const double2 keep = up ? v[j + 4] : v[j];
+      v[j] = keep + shfl_xor2(send, 16);
+    }
+  }
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double2 send = up ? v[j] : v[j + 2];
+      const double2 keep = up ? v[j + 2] : v[j];
+      v[j] = keep + shfl_xor2(send, 8);
+    }
+  }
+  {
+    const bool up = lane & 4;
+    const double2 send = up ? v[0] : v[1];
+    const double2 keep = up ? v[1] : v[0];
+    v[0] = keep + shfl_xor2(send, 4);
+  }
+  v[0] += shfl_xor2(v[0], 2);
+  v[0] += shfl_xor2(v[0], 1);
+}
+
 // Sum `n` complex values held per thread across the whole block; result for value k
 // is left in red[k] (shared, size >= n).  scratch must hold (blockDim/32) * n values.
 template <typename T>

@@ -265,81 +265,91 @@ __device__ __forceinline__ void applyBdag(T (&out)[2][3], const T (&v)[2][3]) {
   }
 }
 
-template <typename R, int MU, bool FWD>
-__device__ __forceinline__ void hop(cplx<R> (&acc)[12], const cplx<R>* __restrict__ in, const cplx<R>* __restrict__ U,
-                                    int V, int s, int y) {
+// One hop of the stencil for NR right-hand sides at once: the link (U_mu(x) forward,
+// U_mu(x - mu)^dag backward) is loaded once and applied to every rhs's
+// projected half spinor.
+template <typename R, int MU, bool FWD, int NR>
+__device__ __forceinline__ void hop(cplx<R> (&acc)[NR][12], const cplx<R>* __restrict__ in, long long rstride,
+                                    const cplx<R>* __restrict__ U, int V, int s, int y) {
   using T = cplx<R>;
-  T pu[2][3], pl[2][3];
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      pu[sp][c] = in[(long long)(3 * sp + c) * V + y];
-      pl[sp][c] = in[(long long)(6 + 3 * sp + c) * V + y];
-    }
-  T Bpl[2][3], h[2][3];
-  applyB<MU>(Bpl, pl);
-#pragma unroll
-  for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) h[sp][c] = FWD ? pu[sp][c] - Bpl[sp][c] : pu[sp][c] + Bpl[sp][c];
   const int ls = FWD ? s : y;  // link U_mu(x) forward, U_mu(x - mu) backward
   T u[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) u[k] = U[((long long)MU * 9 + k) * V + ls];
-  T w[2][3];
 #pragma unroll
-  for (int sp = 0; sp < 2; ++sp)
+  for (int q = 0; q < NR; ++q) {
+    const cplx<R>* iq = in + q * rstride;
+    T pu[2][3], pl[2][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      T t = czero<R>();
+    for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if (FWD) cmac(t, u[3 * a + b], h[sp][b]);
-        else cjmac(t, u[3 * b + a], h[sp][b]);
+      for (int c = 0; c < 3; ++c) {
+        pu[sp][c] = iq[(long long)(3 * sp + c) * V + y];
+        pl[sp][c] = iq[(long long)(6 + 3 * sp + c) * V + y];
       }
-      w[sp][a] = t;
-    }
-  T Bw[2][3];
-  applyBdag<MU>(Bw, w);
+    T Bpl[2][3], h[2][3];
+    applyB<MU>(Bpl, pl);
 #pragma unroll
-  for (int sp = 0; sp < 2; ++sp)
+    for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      acc[3 * sp + c] += w[sp][c];
-      if (FWD) acc[6 + 3 * sp + c] -= Bw[sp][c];
-      else acc[6 + 3 * sp + c] += Bw[sp][c];
-    }
+      for (int c = 0; c < 3; ++c) h[sp][c] = FWD ? pu[sp][c] - Bpl[sp][c] : pu[sp][c] + Bpl[sp][c];
+    T w[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T t = czero<R>();
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          if (FWD) cmac(t, u[3 * a + b], h[sp][b]);
+          else cjmac(t, u[3 * b + a], h[sp][b]);
+        }
+        w[sp][a] = t;
+      }
+    T Bw[2][3];
+    applyBdag<MU>(Bw, w);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[q][3 * sp + c] += w[sp][c];
+        if (FWD) acc[q][6 + 3 * sp + c] -= Bw[sp][c];
+        else acc[q][6 + 3 * sp + c] += Bw[sp][c];
+      }
+  }
 }
 
-template <typename R>
-__device__ __forceinline__ void clover_apply(cplx<R> (&out)[12], const cplx<R>* __restrict__ clov,
-                                             const cplx<R>* __restrict__ in, int V, int s) {
+// acc_q = C(x) psi_q - acc_q / 2 for the components of chirality half h (NR rhs;
+// each clover entry is loaded once); p holds psi_q's six components of half h.
+template <typename R, int NR>
+__device__ __forceinline__ void clover_half(cplx<R> (&acc)[NR][12], const cplx<R>* __restrict__ clov,
+                                            const cplx<R> (&p)[NR][6], int h, int V, int s) {
   using T = cplx<R>;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    T p[6];
+  for (int q = 0; q < NR; ++q)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) p[i] = in[(long long)(6 * h + i) * V + s];
-    T y[6];
+    for (int i = 0; i < 6; ++i) acc[q][6 * h + i] = R(-0.5) * acc[q][6 * h + i];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      T d = clov[(long long)(18 * h + k) * V + s];
-      y[2 * k] = d.x * p[2 * k];
-      y[2 * k + 1] = d.y * p[2 * k + 1];
+  for (int k = 0; k < 3; ++k) {
+    const T d = clov[(long long)(18 * h + k) * V + s];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      acc[q][6 * h + 2 * k] += d.x * p[q][2 * k];
+      acc[q][6 * h + 2 * k + 1] += d.y * p[q][2 * k + 1];
     }
-    int o = 3;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = i + 1; j < 6; ++j) {
-        T c = clov[(long long)(18 * h + o++) * V + s];
-        cmac(y[i], c, p[j]);
-        cjmac(y[j], c, p[i]);
-      }
-#pragma unroll
-    for (int i = 0; i < 6; ++i) out[6 * h + i] = y[i];
   }
+  int o = 3;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      const T c = clov[(long long)(18 * h + o++) * V + s];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        cmac(acc[q][6 * h + i], c, p[q][j]);
+        cjmac(acc[q][6 * h + j], c, p[q][i]);
+      }
+    }
 }
 
 struct BlockInfo { int b[4]; int bvol; };
@@ -355,48 +365,113 @@ __device__ __forceinline__ bool on_face(const BlockInfo& bi, int s, int d) {
   return (d & 1) ? (l[mu] == 0) : (l[mu] == bi.b[mu] - 1);
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 1) k_dslash(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
-                                                const cplx<R>* __restrict__ U, const cplx<R>* __restrict__ clov,
-                                                const int* __restrict__ nbr, int V, BlockInfo bi, int hopdir,
-                                                int nrhs) {
+// MR epilogue (DOTS): the CTA also sums <out, in> = sum conj(out) in and <out, out>
+// over its sites (FP32/FP64 per thread, FP64 across the CTA) into one partial per
+// (rhs, CTA): the minimal-residual step p = D r, alpha = <p, r>/<p, p> then needs
+// no extra pass over p and r.
+template <typename R, int MODE, bool DOTS, int NR>
+__global__ void __launch_bounds__(128, (sizeof(R) == 4 && NR == 1) ? 6 : (sizeof(R) == 4 ? 4 : 1))
+    k_dslash(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in, const cplx<R>* __restrict__ U,
+             const cplx<R>* __restrict__ clov, const int* __restrict__ nbr, int V, BlockInfo bi, int hopdir, int nrhs,
+             double2* __restrict__ pr_part, double* __restrict__ pp_part) {
   using T = cplx<R>;
-  // right-hand side fastest in the grid: the CTAs running together cover the same
-  // sites for every rhs, so links and clover are fetched from HBM once
-  const int rhs = blockIdx.x % nrhs;
-  const int s = (blockIdx.x / nrhs) * blockDim.x + threadIdx.x;
-  if (s >= V) return;
+  // rhs groups fastest in the grid: the CTAs running together cover the same sites
+  // for every rhs, so links and clover are fetched from HBM once
+  const int ngrp = (nrhs + NR - 1) / NR;
+  const int grp = blockIdx.x % ngrp;
+  const int r0 = grp * NR;
+  const int nq = min(NR, nrhs - r0);  // rhs of this thread (the last group may be short)
+  const int s = (blockIdx.x / ngrp) * blockDim.x + threadIdx.x;
+  const bool valid = s < V;
+  if (!DOTS && !valid) return;
   // single-face mode: sites off the face are never read by the face restriction
   if (MODE == ST_FACE_HOP && !on_face(bi, s, hopdir)) return;
-  const long long off = (long long)rhs * 12 * V;
-  in += off;
-  out += off;
-  T acc[12];
+  const long long rstride = 12LL * V;
+  // a short last group re-reads its last rhs (nothing of it is stored)
+  const long long off = (long long)r0 * rstride;
+  const cplx<R>* inr = in + off;
+  const long long rs = nq > 1 ? rstride : 0;
+  R dr[NR], di[NR], nn[NR];
 #pragma unroll
-  for (int c = 0; c < 12; ++c) acc[c] = czero<R>();
-  auto use = [&](int d) -> bool {
-    if (MODE == ST_FULL) return true;
-    if (MODE == ST_BLOCK_INTERIOR) return !on_face(bi, s, d);
-    return d == hopdir && on_face(bi, s, d);
-  };
-#define WCMG_HOP(MU)                                                               \
-  if (use(2 * MU)) hop<R, MU, true>(acc, in, U, V, s, nbr[(2 * MU) * V + s]);       \
-  if (use(2 * MU + 1)) hop<R, MU, false>(acc, in, U, V, s, nbr[(2 * MU + 1) * V + s]);
-  WCMG_HOP(0)
-  WCMG_HOP(1)
-  WCMG_HOP(2)
-  WCMG_HOP(3)
+  for (int q = 0; q < NR; ++q) dr[q] = di[q] = nn[q] = 0;
+  if (valid) {
+    T acc[NR][12];
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int c = 0; c < 12; ++c) acc[q][c] = czero<R>();
+    auto use = [&](int d) -> bool {
+      if (MODE == ST_FULL) return true;
+      if (MODE == ST_BLOCK_INTERIOR) return !on_face(bi, s, d);
+      return d == hopdir && on_face(bi, s, d);
+    };
+#define WCMG_HOP(MU)                                                                             \
+  if (use(2 * MU)) hop<R, MU, true, NR>(acc, inr, rs, U, V, s, nbr[(2 * MU) * V + s]);            \
+  if (use(2 * MU + 1)) hop<R, MU, false, NR>(acc, inr, rs, U, V, s, nbr[(2 * MU + 1) * V + s]);
+    WCMG_HOP(0)
+    WCMG_HOP(1)
+    WCMG_HOP(2)
+    WCMG_HOP(3)
 #undef WCMG_HOP
-  T res[12];
-  if (MODE != ST_FACE_HOP) {
-    clover_apply<R>(res, clov, in, V, s);
-  } else {
+    // epilogue per chirality half: clover term, store, MR reductions
 #pragma unroll
-    for (int c = 0; c < 12; ++c) res[c] = czero<R>();
+    for (int h = 0; h < 2; ++h) {
+      if (MODE != ST_FACE_HOP) {
+        T p[NR][6];
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+#pragma unroll
+          for (int i = 0; i < 6; ++i) p[q][i] = inr[q * rs + (long long)(6 * h + i) * V + s];
+        clover_half<R, NR>(acc, clov, p, h, V, s);
+        if (DOTS) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q)
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+              const T o = acc[q][6 * h + i];
+              dr[q] += o.x * p[q][i].x + o.y * p[q][i].y;
+              di[q] += o.x * p[q][i].y - o.y * p[q][i].x;
+              nn[q] += o.x * o.x + o.y * o.y;
+            }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+#pragma unroll
+          for (int i = 0; i < 6; ++i) acc[q][6 * h + i] = R(-0.5) * acc[q][6 * h + i];
+      }
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (q < nq) {
+          cplx<R>* oq = out + off + q * rstride;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) oq[(long long)(6 * h + i) * V + s] = acc[q][6 * h + i];
+        }
+    }
   }
+  if (DOTS) {
+    __shared__ double scratch[(128 / 32) * 3 * NR];
+    __shared__ double red[3 * NR];
+    double v[3 * NR];
 #pragma unroll
-  for (int c = 0; c < 12; ++c) out[(long long)c * V + s] = res[c] + R(-0.5) * acc[c];
+    for (int q = 0; q < NR; ++q) {
+      v[3 * q] = dr[q];
+      v[3 * q + 1] = di[q];
+      v[3 * q + 2] = nn[q];
+    }
+    block_sum_regs<double, 3 * NR>(v, 3 * NR, scratch, red);
+    if (threadIdx.x < nq) {
+      const int q = threadIdx.x;
+      const int nsb = gridDim.x / ngrp, sb = blockIdx.x / ngrp;
+      pr_part[(long long)(r0 + q) * nsb + sb] = make_double2(red[3 * q], red[3 * q + 1]);
+      pp_part[(long long)(r0 + q) * nsb + sb] = red[3 * q + 2];
+    }
+  }
 }
+
+// rhs per thread: 2 for FP32 with several rhs, else 1
+template <typename R>
+static int dslash_nr(int nrhs) { return (sizeof(R) == 4 && nrhs > 1) ? 2 : 1; }
 
 template <typename R>
 void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
@@ -404,11 +479,73 @@ void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const 
   BlockInfo bi;
   for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
   bi.bvol = g.bvol;
-  const dim3 grid((unsigned)(nblk(g.V, 128) * (long long)nrhs));
-  if (mode == ST_FULL) k_dslash<R, ST_FULL><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs);
-  else if (mode == ST_BLOCK_INTERIOR)
-    k_dslash<R, ST_BLOCK_INTERIOR><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs);
-  else k_dslash<R, ST_FACE_HOP><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs);
+  const int nr = dslash_nr<R>(nrhs);
+  const dim3 grid((unsigned)(nblk(g.V, 128) * (long long)((nrhs + nr - 1) / nr)));
+#define WCMG_DS(MODE, NR) \
+  k_dslash<R, MODE, false, NR><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs, nullptr, nullptr)
+  if constexpr (sizeof(R) == 4) {
+    if (nr == 2) {
+      if (mode == ST_FULL) WCMG_DS(ST_FULL, 2);
+      else if (mode == ST_BLOCK_INTERIOR) WCMG_DS(ST_BLOCK_INTERIOR, 2);
+      else WCMG_DS(ST_FACE_HOP, 2);
+      WCMG_LAUNCH_CHECK();
+      return;
+    }
+  }
+  {
+    if (mode == ST_FULL) WCMG_DS(ST_FULL, 1);
+    else if (mode == ST_BLOCK_INTERIOR) WCMG_DS(ST_BLOCK_INTERIOR, 1);
+    else WCMG_DS(ST_FACE_HOP, 1);
+  }
+#undef WCMG_DS
+  WCMG_LAUNCH_CHECK();
+}
+
+// pr[r] = sum_b pr_part[r][b], pp[r] = sum_b pp_part[r][b] (fixed tree)
+__global__ void __launch_bounds__(256) k_mr_final(double2* __restrict__ pr, double* __restrict__ pp,
+                                                  const double2* __restrict__ pr_part,
+                                                  const double* __restrict__ pp_part, int nsb) {
+  __shared__ double scratch[(256 / 32) * 3];
+  __shared__ double red[3];
+  const int r = blockIdx.x;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nsb; b += 256) {
+    const double2 a = pr_part[(long long)r * nsb + b];
+    v[0] += a.x;
+    v[1] += a.y;
+    v[2] += pp_part[(long long)r * nsb + b];
+  }
+  block_sum_regs<double, 3>(v, 3, scratch, red);
+  if (threadIdx.x == 0) {
+    pr[r] = make_double2(red[0], red[1]);
+    pp[r] = red[2];
+  }
+}
+
+int dslash_partials(int V) { return (int)nblk(V, 128); }
+
+template <typename R>
+void launch_dslash_mr(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
+                      int nrhs, double2* pr, double* pp, double2* pr_part, double* pp_part, cudaStream_t st) {
+  BlockInfo bi;
+  for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
+  bi.bvol = g.bvol;
+  const int nsb = dslash_partials(g.V);
+  const int nr = dslash_nr<R>(nrhs);
+  const unsigned grid = (unsigned)((long long)nsb * ((nrhs + nr - 1) / nr));
+  bool done = false;
+  if constexpr (sizeof(R) == 4) {
+    if (nr == 2) {
+      k_dslash<R, ST_FULL, true, 2><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, 0, nrhs, pr_part,
+                                                           pp_part);
+      done = true;
+    }
+  }
+  if (!done)
+    k_dslash<R, ST_FULL, true, 1><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, 0, nrhs, pr_part,
+                                                         pp_part);
+  WCMG_LAUNCH_CHECK();
+  k_mr_final<<<nrhs, 256, 0, st>>>(pr, pp, pr_part, pp_part, nsb);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -417,7 +554,9 @@ void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const 
   template void launch_unpack_fine<R>(double2*, const cplx<R>*, const int*, int, int, cudaStream_t);          \
   template void launch_pack_gauge<R>(cplx<R>*, const double2*, const int*, int, cudaStream_t);                \
   template void launch_dslash<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
-                                 int, int, int, cudaStream_t);
+                                 int, int, int, cudaStream_t);                                               \
+  template void launch_dslash_mr<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
+                                    int, double2*, double*, double2*, double*, cudaStream_t);
 WCMG_INST(double)
 WCMG_INST(float)
 #undef WCMG_INST

@@ -29,6 +29,13 @@ void launch_clover_expand(double2* ext, const double2* clov, const int* perm, in
 template <typename R>
 void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
                    int nrhs, int mode, int hopdir, cudaStream_t st);
+// out = D in (full stencil) and, per rhs r, pr[r] = <out_r, in_r> = sum conj(out) in,
+// pp[r] = <out_r, out_r> (the minimal-residual step's two reductions, fused into the
+// stencil).  pr_part / pp_part: scratch of nrhs * dslash_partials(V) entries.
+int dslash_partials(int V);
+template <typename R>
+void launch_dslash_mr(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
+                      int nrhs, double2* pr, double* pp, double2* pr_part, double* pp_part, cudaStream_t st);
 
 // ---- transfers (transfer.cu) ----
 // `fine` selects the component-major fine layout [ncomp][V]; otherwise fields are

@@ -244,19 +244,21 @@ static void restrict_few(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs
 // sum_e conj(v_i[e]) in_r[e] over the aggregate's (selected) elements e of
 // chirality s.  Each K-chunk of RST_KT elements of all vectors and all rhs of the
 // tile is staged once in shared memory (rhs fastest: conflict-free); thread
-// (ti, tr) owns vectors ti + 8 q (q < VI) and rhs tr + 32 p (p < RT).
+// (ti, tr) of the 8 x TR threads owns vectors ti + 8 q (q < VI) and rhs tr + TR p
+// (p < RT): VI x RT complex accumulators per thread, VI + RT shared loads per
+// element for VI x RT complex MACs.
 constexpr int RST_KT = 32;
-template <typename R, int VI, int RT>
-__global__ void __launch_bounds__(256) k_restrict_gemm(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
-                                                       const cplx<R>* __restrict__ vecs, int Vf, int nc, int bvol,
-                                                       int nvec, int nrhs, bool fine, FaceSel fs) {
+template <typename R, int VI, int RT, int TR>
+__global__ void __launch_bounds__(8 * TR) k_restrict_gemm(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                          const cplx<R>* __restrict__ vecs, int Vf, int nc, int bvol,
+                                                          int nvec, int nrhs, bool fine, FaceSel fs) {
   using T = cplx<R>;
-  constexpr int NT = 32 * RT;  // rhs per CTA
+  constexpr int NT = TR * RT;  // rhs per CTA
   __shared__ T Xs[RST_KT][8 * VI];
   __shared__ T Ts[RST_KT][NT];
   __shared__ int off_s[RST_KT];
   const int blk = blockIdx.x, s = blockIdx.y, r0 = blockIdx.z * NT;
-  const int tid = threadIdx.x, ti = tid >> 5, tr = tid & 31;
+  const int tid = threadIdx.x, ti = tid / TR, tr = tid % TR;
   const int half = nc >> 1, nb = 2 * nvec;
   const int nsite = fs.fd < 0 ? bvol : bvol / fs.b[fs.fd >> 1];
   const int nelem = nsite * half;
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(256) k_restrict_gemm(cplx<R>* __restrict__ out
 #pragma unroll
       for (int q = 0; q < VI; ++q) x[q] = Xs[kk][ti + 8 * q];
 #pragma unroll
-      for (int p = 0; p < RT; ++p) t[p] = Ts[kk][tr + 32 * p];
+      for (int p = 0; p < RT; ++p) t[p] = Ts[kk][tr + TR * p];
 #pragma unroll
       for (int q = 0; q < VI; ++q)
 #pragma unroll
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(256) k_restrict_gemm(cplx<R>* __restrict__ out
   for (int q = 0; q < VI; ++q)
 #pragma unroll
     for (int p = 0; p < RT; ++p) {
-      const int i = ti + 8 * q, r = r0 + tr + 32 * p;
+      const int i = ti + 8 * q, r = r0 + tr + TR * p;
       if (i < nvec && r < nrhs) out[((long long)r * Vc + blk) * nb + s * nvec + i] = acc[q][p];
     }
 }
@@ -316,19 +318,27 @@ __global__ void __launch_bounds__(256) k_restrict_gemm(cplx<R>* __restrict__ out
 template <typename R, int VI, int RT>
 static void restrict_gemm_v(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol,
                             int nvec, int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
-  const dim3 grid(Vf / bvol, 2, (nrhs + 32 * RT - 1) / (32 * RT));
-  k_restrict_gemm<R, VI, RT><<<grid, 256, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
+  constexpr int TR = 16;
+  const dim3 grid(Vf / bvol, 2, (nrhs + TR * RT - 1) / (TR * RT));
+  k_restrict_gemm<R, VI, RT, TR><<<grid, 8 * TR, 0, st>>>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs);
   WCMG_LAUNCH_CHECK();
+}
+
+template <typename R, int VI>
+static void restrict_gemm_vi(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol,
+                             int nvec, int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
+  // rhs per CTA 16 x RT: 32 (<= 32 rhs), 48 (more; the 48 column fields of nbasis 48)
+  if (nrhs <= 32) restrict_gemm_v<R, VI, 2>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else restrict_gemm_v<R, VI, 3>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
 }
 
 template <typename R>
 static void restrict_gemm(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs, int Vf, int nc, int bvol, int nvec,
                           int nrhs, bool fine, const FaceSel& fs, cudaStream_t st) {
-  constexpr int RT = sizeof(R) == 8 ? 1 : 2;  // static shared memory stays below 48 KB
   const int vi = (nvec + 7) / 8;
-  if (vi <= 2) restrict_gemm_v<R, 2, RT>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
-  else if (vi == 3) restrict_gemm_v<R, 3, RT>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
-  else restrict_gemm_v<R, 4, RT>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  if (vi <= 2) restrict_gemm_vi<R, 2>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else if (vi == 3) restrict_gemm_vi<R, 3>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
+  else restrict_gemm_vi<R, 4>(coarse, in, vecs, Vf, nc, bvol, nvec, nrhs, fine, fs, st);
 }
 
 template <typename R, int RR>
@@ -384,7 +394,7 @@ void launch_prolong(cplx<R>* out, const cplx<R>* coarse, const cplx<R>* vecs, in
 // The loops over earlier columns have run-time trip counts (no predicated-off
 // FP64 work); each coefficient is reduced by warp shuffles into shared memory.
 template <int MAXE>
-__global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ vecs, int Vf, int nc, int bvol, int nvec,
+__global__ void __launch_bounds__(256, 2) k_block_ortho(double2* __restrict__ vecs, int Vf, int nc, int bvol, int nvec,
                                                      bool fine, int* __restrict__ err) {
   constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
   __shared__ double2 scratch[8][MV];
@@ -420,14 +430,22 @@ __global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ vecs,
     for (int q = 0; q < MAXE; ++q) a[q] = addr[q] >= 0 ? vecs[k * fstride + addr[q]] : make_double2(0, 0);
     double before2 = 0.0, after2 = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int i = 0; i < k; ++i) {
-        const double2* qi = vecs + i * fstride;
-        double2 p = make_double2(0, 0);
+      // projections <q_i, a> for i < k, eight at a time (one transposing warp reduction)
+      for (int i0 = 0; i0 < k; i0 += 8) {
+        double2 p[8];
 #pragma unroll
-        for (int q = 0; q < MAXE; ++q)
-          if (addr[q] >= 0) cjmac(p, qi[addr[q]], a[q]);
-        p = warp_sum(p);
-        if (lane == 0) scratch[warp][i] = p;
+        for (int g = 0; g < 8; ++g) {
+          p[g] = make_double2(0, 0);
+          if (i0 + g < k) {
+            const double2* qi = vecs + (i0 + g) * fstride;
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q)
+              if (addr[q] >= 0) cjmac(p[g], qi[addr[q]], a[q]);
+          }
+        }
+        warp_sum8_transposed(p, lane);
+        const int g = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if ((lane & 3) == 0 && i0 + g < k) scratch[warp][i0 + g] = p[0];
       }
       double n0 = 0;
 #pragma unroll

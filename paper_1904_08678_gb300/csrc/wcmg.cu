@@ -203,6 +203,8 @@ struct wcmg_ctx {
   bool have_gauge = false;
   DevBuf<double2> partial;
   DevBuf<double> partial_d;
+  DevBuf<double2> mr_pr;   // per-CTA partials of the fused MR Dslash
+  DevBuf<double> mr_pp;
   DevBuf<unsigned char> stage[3];
   DevBuf<int> errflag;
   DevBuf<int> tma_err;       // nonzero after a bounded device-side wait gave up
@@ -543,9 +545,22 @@ static void mr(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int s
   copy_fields<R>(c, r, b, n * nrhs);
   launch_fill_zero<R>(x, n * nrhs, c->st);
   for (int k = 0; k < steps; ++k) {
-    apply_op<R>(c, l, p, r, nrhs);
-    dot_op<R>(c, L.sc.pr(), p, r, n, nrhs);
-    norm2_op<R>(c, L.sc.slot(4), p, n, nrhs);
+    if (l == 0) {
+      // fine level: the two reductions come out of the Dslash epilogue
+      if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+      const long long np = (long long)max_rhs_all(c) * dslash_partials(L.g.V);
+      c->mr_pr.ensure(np);
+      c->mr_pp.ensure(np);
+      const double V = L.g.V, s = sizeof(cplx<R>);
+      const int cls = sizeof(R) == 8 ? WCMG_K_DSLASH64 : WCMG_K_DSLASH;
+      KPROF(c, cls, V * s * (24.0 * nrhs + 72.0), V * (1872.0 + 16.0) * nrhs,
+            launch_dslash_mr<R>(p, r, Prec<R>::gauge(c), Prec<R>::clover(c), L.g.lg(), nrhs, L.sc.pr(),
+                                L.sc.slot(4), c->mr_pr.p, c->mr_pp.p, c->st));
+    } else {
+      apply_op<R>(c, l, p, r, nrhs);
+      dot_op<R>(c, L.sc.pr(), p, r, n, nrhs);
+      norm2_op<R>(c, L.sc.slot(4), p, n, nrhs);
+    }
     KPROF(c, WCMG_K_BLAS, 5.0 * n * nrhs * sizeof(cplx<R>), 16.0 * n * nrhs,
           launch_mr_update<R>(x, r, p, L.sc.pr(), L.sc.slot(4), n, nrhs, c->st));
   }

@@ -36,6 +36,19 @@ def test_mr_matches_oracle(lib):
         assert rel(got[r], mr(D, f, 4).reshape(V, 12)) < 1e-12
 
 
+@pytest.mark.parametrize("nrhs", [1, 3, 4])
+def test_mr_fp32_fused_reductions_match_oracle(lib, nrhs):
+    """FP32 MR: <p, r> and <p, p> come out of the Dslash epilogue (two rhs per thread)."""
+    ctx, D = config1_ctx(lib, prec=1, max_rhs=4)
+    V = 256
+    b = inputs.complex_gaussian(25, nrhs, (nrhs, V, 12))
+    x = dev(np.zeros_like(b))
+    ctx.krylov(0, 0, dev(b), x, nrhs=nrhs, steps_or_restart=4)
+    got = host(x)
+    for r, f in enumerate(fields(b, DIMS, 12)):
+        assert rel(got[r], mr(D, f, 4).reshape(V, 12)) < 1e-5
+
+
 def test_gmres_fixed_iterations_matches_oracle(lib):
     ctx, D = config1_ctx(lib, max_rhs=2)
     V = 256
