@@ -52,6 +52,18 @@ WORKLOADS = {
                         "FGMRES(20) to 1e-10, NRHS Gaussian rhs solved together",
                dims=(24, 24, 24, 48), eps=0.25, m0=-0.2, csw=1.0, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)],
                nvec=[24, 24], init_sweeps=3, refine_sweeps=2, gauge_seed=1004, source_seed=0, nrhs=12),
+    "c5": dict(workload="learned coarse correction: PTC network trained on 16^3x32 (eps 0.25, m0 -0.2) on pairs "
+                        "the multigrid generates (fresh pools, POOLS x 48 pairs), deployed unchanged on 32^3x64 (eps "
+                        "0.25, m0 -0.2, blocks 4^4 -> 8^3x16, Nvec 24, 3 + 2 sweeps) in place of the coarse "
+                        "correction, plain MG as fallback (ratio 0.9), FGMRES(20) to 1e-10, 1 Gaussian rhs",
+               dims=(32, 32, 32, 64), eps=0.25, m0=-0.2, csw=1.0, blocks=[(4, 4, 4, 4)], nvec=[24], init_sweeps=3,
+               refine_sweeps=2, gauge_seed=1005, source_seed=0, nrhs=1, learned_from="c2",
+               train=dict(npairs=48, batch=4, refresh=8, lr=1e-2, target_tol=1e-6, seed=5)),
+    "table2": dict(workload="Table-2-shaped sweep: 16^4, eps 0.25, m0 -0.25, csw 1.0, blocks 4^4 -> 4^4, Nvec 20 "
+                            "(nbasis 40), GMRES(4) smoother, 3 initial sweeps, 0..10 refinement sweeps, FGMRES(20) "
+                            "to 1e-10, 1 Gaussian rhs",
+                   dims=(16, 16, 16, 16), eps=0.25, m0=-0.25, csw=1.0, blocks=[(4, 4, 4, 4)], nvec=[20],
+                   init_sweeps=3, refine_sweeps=0, gauge_seed=1006, source_seed=0, nrhs=1, smoother="gmres"),
 }
 # Reduced-volume sample of the same workload for the CPU oracle (same blocks,
 # Nvec and parameters; time scaled by the volume ratio).
@@ -220,7 +232,8 @@ def params(wcmg, cfg, inner, links, profile=0, graphs=0, autotune=1):
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
                             n_levels=len(cfg["blocks"]) + 1, max_rhs=cfg.get("nrhs", 1), profile=profile,
-                            use_graphs=graphs, autotune=autotune)
+                            use_graphs=graphs, autotune=autotune,
+                            smoother={"mr": wcmg.SMOOTHER_MR, "gmres": wcmg.SMOOTHER_GMRES}[cfg.get("smoother", "mr")])
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -262,6 +275,12 @@ def run_gpu(args, rank, world, local):
         s1 = ctx.setup(iv_, stream)
         s2 = ctx.solve(b_, x, nrhs=nrhs, stream=stream)
         return s1, s2
+
+    trained = None
+    if cfg.get("learned_from"):
+        trained = train_network(wcmg, torch, dev, stream, cfg, args)
+        ctx.ptc_set_weights(trained.pop("weights"), stream)
+        ctx.set_coarse_mode(wcmg.COARSE_LEARNED, 0.9)
 
     # warm-up, all kernel classes timed: find the dominant class
     acc = {}
@@ -402,6 +421,11 @@ def run_gpu(args, rank, world, local):
         ctx64.close()
 
     uneven = measure_uneven_batch(wcmg, torch, dev, stream, flush, args) if args.workload == "c4" else None
+    per_level = precision_per_level(ctx, wcmg, torch, dev, cfg, args, stream) if args.workload == "c3" else None
+    if trained is not None:
+        trained["deployed"] = deployed_comparison(ctx, wcmg, torch, stream, flush, step, xd, Ud, ivd, bd)
+        trained["deployed"]["fp64_plain_mg"] = fp64_reference(wcmg, torch, stream, flush, cfg, Ud, ivd, bd,
+                                                              args.graphs)
 
     learned = None if (args.no_learned or args.workload != "c2") else learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush)
 
@@ -427,8 +451,9 @@ def run_gpu(args, rank, world, local):
             "solves_per_s": round(sum_over_ranks(dist, args.steps, dev) / (ms * args.steps / 1e3), 3),
             "roofline": roofline, "coarse_stencil": {"in_solve": coarse_live, "isolated": coarse_iso},
             "e2e": {"value": round(e2e_ms / 1e3, 5), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "learned": learned,
+            "learned": learned if trained is None else trained,
             "uneven_batch": uneven,
+            "precision_per_level": per_level,
             "coarse_tiles": tiles,
             "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
             "clocks": clocks, "wall_s_timed": round(t_wall, 3), "fp64_inner": fp64, "cpu_baseline": cpu,
@@ -484,6 +509,125 @@ def learned_variant(wcmg, torch, cfg, args, Ud, ivd, bd, stream, flush):
                      "true_residual": st.true_residual, "learned_cycles": st.learned_cycles,
                      "fallback": st.learned_fallback}
     ctx.close()
+    return out
+
+
+def train_network(wcmg, torch, dev, stream, cfg, args):
+    """Train the PTC network on the workload named by cfg["learned_from"] (pairs from its
+    own multigrid, fresh pools every `refresh` steps) and return its weights."""
+    src = dict(WORKLOADS[cfg["learned_from"]])
+    tr = dict(cfg["train"])
+    pools = args.pools
+    U, iv, _ = make_inputs(src)
+    c = wcmg.Context(params(wcmg, src, "f32", "f32", profile=0))
+    c.set_gauge(torch.from_numpy(U).to(dev), stream)
+    c.setup(torch.from_numpy(iv).to(dev), stream)
+    steps = pools * tr["refresh"]
+    t0 = time.perf_counter()
+    st = c.ptc_train(npairs=tr["npairs"], batch=tr["batch"], steps=steps, lr=tr["lr"], target_tol=tr["target_tol"],
+                     seed=tr["seed"], refresh=tr["refresh"], stream=stream)
+    wall = time.perf_counter() - t0
+    W = torch.zeros(3456, dtype=torch.complex128, device=dev)
+    c.ptc_get_weights(W, stream)
+    c.close()
+    return {"weights": W, "trained_on": src["workload"], "pairs_total": st.pairs_total, "steps": steps,
+            "batch": tr["batch"], "loss_initial": round(st.loss_initial, 4), "loss_final": round(st.loss_final, 4),
+            "loss_heldout": round(st.loss_heldout, 4), "ms_generate": round(st.ms_generate, 1),
+            "ms_train": round(st.ms_train, 1), "wall_s": round(wall, 2)}
+
+
+def deployed_comparison(ctx, wcmg, torch, stream, flush, step, xd, Ud, ivd, bd, reps=3):
+    """The deployed network against plain MG (and as a warm start) on the same field."""
+    out = {}
+    for name, mode in (("learned_replace", wcmg.COARSE_LEARNED), ("learned_warmstart", wcmg.COARSE_WARMSTART),
+                       ("plain_mg", wcmg.COARSE_MG)):
+        ctx.set_coarse_mode(mode, 0.9)
+        step(xd, Ud, ivd, bd)
+        step(xd, Ud, ivd, bd)  # warm (and, for plain MG, the graph capture)
+        ms = []
+        for i in range(reps):
+            flush.fill_(i)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s1, s2 = step(xd, Ud, ivd, bd)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[name] = {"time_to_solution_s": round(statistics.median(ms) / 1e3, 5), "outer_iterations": s2.outer_iterations,
+                     "coarse_iterations": s2.coarse_iterations, "solve_ms": round(s2.ms_solve, 2),
+                     "true_residual": s2.true_residual, "learned_cycles": s2.learned_cycles,
+                     "fallback": s2.learned_fallback, "graph": s2.graph}
+    ctx.set_coarse_mode(wcmg.COARSE_LEARNED, 0.9)
+    return out
+
+
+def fp64_reference(wcmg, torch, stream, flush, cfg, Ud, ivd, bd, graphs=1):
+    """Plain FP64 GPU multigrid (same field, source and setup parameters): one timed step."""
+    c = wcmg.Context(params(wcmg, cfg, "f64", "f32", profile=0, graphs=graphs))
+    x = torch.zeros_like(bd)
+    c.set_gauge(Ud, stream)
+    c.setup(ivd, stream)
+    for _ in range(2):  # warm (host-driven, then the graph capture)
+        c.solve(bd, x, stream=stream)
+    flush.fill_(3)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    c.set_gauge(Ud, stream)
+    s1 = c.setup(ivd, stream)
+    s2 = c.solve(bd, x, stream=stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    c.close()
+    return {"time_to_solution_s": round(f0.elapsed_time(f1) / 1e3, 4), "outer_iterations": s2.outer_iterations,
+            "true_residual": s2.true_residual, "setup_init_ms": round(s1.ms_setup_init, 2),
+            "setup_refine_ms": round(s1.ms_setup_refine, 2), "solve_ms": round(s2.ms_solve, 2)}
+
+
+def precision_per_level(ctx, wcmg, torch, dev, cfg, args, stream):
+    """Error of each level's FP32 transfers and of the coarse apply in FP32 / BF16 / FP16
+    link storage, each against the FP64 apply of the same operator (the level's links as
+    this setup built them, applied by an FP64 context), on a Gaussian vector."""
+    from paper_1904_08678_gb300 import inputs
+    ld = level_dims(cfg)
+    nl = len(cfg["blocks"]) + 1
+    out = {}
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    refs = {}
+    for lp in ("f32", "bf16", "f16", "f64"):
+        refs[lp] = wcmg.Context(params(wcmg, cfg, "f64" if lp == "f64" else "f32", "f32" if lp == "f64" else lp,
+                                       profile=0, autotune=0))
+    for l in range(1, nl):
+        Vc = int(np.prod(ld[l]))
+        nb = 2 * cfg["nvec"][l - 1]
+        A = torch.zeros((9, Vc, nb, nb), dtype=torch.complex128, device=dev)
+        ctx.get_coarse_links(l, A, stream)
+        x = torch.from_numpy(inputs.complex_gaussian(77, l, (1, Vc, nb))).to(dev)
+        y = {}
+        for lp, c in refs.items():
+            c.set_coarse_links(l, A, stream)
+            y[lp] = torch.zeros_like(x)
+            c.apply_coarse(l, x, y[lp], nrhs=1, prec=wcmg.F64 if lp == "f64" else wcmg.F32, stream=stream)
+        Vf = int(np.prod(ld[l - 1]))
+        nf = 12 if l == 1 else 2 * cfg["nvec"][l - 2]
+        f = torch.from_numpy(inputs.complex_gaussian(78, l, (1, Vf, nf))).to(dev)
+        r64, r32 = torch.zeros_like(x), torch.zeros_like(x)
+        ctx.restrict(l - 1, f, r64, prec=wcmg.F64, stream=stream)
+        ctx.restrict(l - 1, f, r32, prec=wcmg.F32, stream=stream)
+        p64, p32 = torch.zeros_like(f), torch.zeros_like(f)
+        ctx.prolong(l - 1, x, p64, prec=wcmg.F64, stream=stream)
+        ctx.prolong(l - 1, x, p32, prec=wcmg.F32, stream=stream)
+        out[f"level{l}"] = {"coarse_apply_f32": rel(y["f32"], y["f64"]), "coarse_apply_bf16": rel(y["bf16"], y["f64"]),
+                            "coarse_apply_f16": rel(y["f16"], y["f64"]), "restrict_f32": rel(r32, r64),
+                            "prolong_f32": rel(p32, p64), "sites": Vc, "nbasis": nb}
+    for c in refs.values():
+        c.close()
+    out["note"] = ("relative error ||y - y64|| / ||y64|| of one application on a Gaussian vector; y64 = the FP64 "
+                   "apply of the same (FP32-built) coarse links and FP64 near-null vectors")
     return out
 
 
@@ -637,6 +781,56 @@ def run_reference(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_table2(args, rank, world, local):
+    """Setup-vs-solve trade-off of Table 2 on the synthetic 16^4 field: for 0..10
+    refinement sweeps, the initial-setup, iterative-setup and solve times and the outer
+    iterations (the paper's columns), each the median of 3 steps after 2 warm-up steps."""
+    import torch
+    from paper_1904_08678_gb300 import wcmg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = L2Flush(torch, dev)
+    cfg = dict(WORKLOADS["table2"])
+    U, iv, b = make_inputs(cfg)
+    Ud, ivd, bd = (torch.from_numpy(a).to(dev) for a in (U, iv, b))
+    xd = torch.zeros_like(bd)
+    rows = []
+    with ClockSampler(local) as clk:
+        for sweeps in range(11):
+            c = dict(cfg, refine_sweeps=sweeps)
+            ctx = wcmg.Context(params(wcmg, c, args.inner, args.links, graphs=args.graphs))
+            res = []
+            for i in range(5):
+                flush.fill_(i)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.set_gauge(Ud, stream)
+                s1 = ctx.setup(ivd, stream)
+                s2 = ctx.solve(bd, xd, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res.append((e0.elapsed_time(e1), s1, s2))
+            res = res[2:]
+            med = lambda f: round(statistics.median(f(r) for r in res), 2)
+            rows.append({"setup_iter": sweeps, "outer_iterations": res[-1][2].outer_iterations,
+                         "initial_setup_ms": med(lambda r: r[1].ms_setup_init),
+                         "iterative_setup_ms": med(lambda r: r[1].ms_setup_refine),
+                         "solve_ms": med(lambda r: r[2].ms_solve), "total_ms": med(lambda r: r[0]),
+                         "true_residual": max(r[2].true_residual for r in res)})
+            ctx.close()
+    best = min(rows, key=lambda r: r["total_ms"])
+    line = {"metric": "time_to_solution_1e-10", "value": round(best["total_ms"] / 1e3, 5), "unit": "s",
+            "n_gpus": 1, "steps": 3, "warmup": 2, "ms_per_step": best["total_ms"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.inner == "f32" else "f64",
+            "data": "synthetic", "config": {"workload": cfg["workload"], "best_setup_iter": best["setup_iter"],
+                                            "inner_prec": args.inner},
+            "table2": rows, "clocks": clk.summary(), "roofline": None,
+            "note": "a parameter sweep; per-kernel rooflines are in the 16^3x32 line"}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -654,6 +848,8 @@ def main(argv=None):
                     help="1: each solve replays one captured CUDA graph; 0: host-driven solve")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1: coarse-apply launch shapes picked by the autotuner; 0: fixed rule")
+    ap.add_argument("--pools", type=int, default=417,
+                    help="c5: training pools of 48 fresh pairs (417 pools = 20016 pairs)")
     ap.add_argument("--ncu-region", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)
@@ -662,6 +858,8 @@ def main(argv=None):
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "table2":
+        run_table2(args, rank, world, local)
     else:
         run_gpu(args, rank, world, local)
 

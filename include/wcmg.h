@@ -93,7 +93,13 @@ typedef struct wcmg_params {
   int autotune;                         /* 1: the first coarse apply of each (level, nrhs, link
                                            storage) times the candidate launch shapes on the
                                            level's own data and keeps the fastest. 0: fixed rule */
+  int smoother;                         /* WCMG_SMOOTHER_MR: MR(smoother_steps) (Sec. 2.1);
+                                           WCMG_SMOOTHER_GMRES: GMRES with smoother_steps steps,
+                                           zero guess, no restart (Sec. 4 comparison runs).  The
+                                           same smoother serves the cycle and the setup sweeps. */
 } wcmg_params;
+
+typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1 } wcmg_smoother;
 
 /* Per-kernel-class counters, filled when params.profile != 0. */
 #define WCMG_NKCLASS 12
@@ -160,6 +166,8 @@ int wcmg_get_nullvecs(wcmg_ctx* ctx, int level, void* vecs, int where, void* str
 /* Sec. 2.1 CoarsenOperator: D_{level+1} = P_level^dag D_level P_level as the
  * nine-block stencil (Sec. 4: 9 stencil points).  Needs P_level and D_level. */
 int wcmg_coarsen(wcmg_ctx* ctx, int level, void* stream);
+/* Read the coarse links of `level` (external coarse-link layout, FP64): the most
+ * precise copy the context holds (FP64, else FP32, else the BF16/FP16 storage). */
 int wcmg_get_coarse_links(wcmg_ctx* ctx, int level, void* A, int where, void* stream);
 int wcmg_set_coarse_links(wcmg_ctx* ctx, int level, const void* A, int where, void* stream);
 
@@ -292,19 +300,23 @@ int wcmg_ptc_backward(wcmg_ctx* ctx, const void* in, const void* gout, void* gin
                       void* stream);
 
 typedef struct wcmg_train_opts {
-  int npairs;          /* training pairs generated by the multigrid (even split: Gaussian r and
-                          residuals r = b - D M_0(b) of one cycle on a Gaussian b) */
+  int npairs;          /* training pairs held at a time (even split: Gaussian r and residuals
+                          r = b - D M_0(b) of one cycle on a Gaussian b) */
   int batch;           /* fields per optimisation step */
   int steps;           /* Adam steps */
+  int refresh;         /* > 0: a fresh pool of npairs pairs is generated every `refresh` steps
+                          (pairs seen = npairs x pools); 0: one pool */
   double lr;           /* Adam learning rate */
   double target_tol;   /* coarse solves of the targets e = P GMRES(P^dag r) to this tolerance */
   uint64_t seed;       /* counter-based generator seed for the Gaussian fields */
 } wcmg_train_opts;
 typedef struct wcmg_train_stats {
-  double loss_initial; /* mean ||N(r) - e||^2 / ||e||^2 over the pairs before training */
-  double loss_final;   /* same after training */
+  double loss_initial; /* mean ||N(r) - e||^2 / ||e||^2 over the first pool before training */
+  double loss_final;   /* same over the last training pool after training */
   double ms_generate;  /* wall time of the pair generation */
   double ms_train;     /* wall time of the optimisation */
+  double loss_heldout; /* after training, over a fresh pool never trained on */
+  long long pairs_total; /* distinct pairs generated for training */
 } wcmg_train_stats;
 /* Generate training pairs with the current setup (wcmg_setup first; inner_prec
  * F32) and fit the PTC weights with Adam on the loss ||N(r) - e||^2 / ||e||^2

@@ -6,14 +6,17 @@ Sec. 2.1 describes the pieces but not the algorithmic parameters:
     near-null vectors, then builds the intergrid and coarse operators;
   * the iterative-refinement setup (from DDalphaAMG) then applies the whole MG
     preconditioner to the near-null vectors and rebuilds the operators;
-  * MR is the smoother, GMRES the coarsest solver, FGMRES the outer solver.
+  * MR is the smoother, GMRES the coarsest solver, FGMRES the outer solver;
+    the benchmark comparison of Sec. 4 (Table 1) runs GMRES as the smoother.
 
 Readings used here (each listed with the other readings of the paper):
-  cycle  M_l(r):  e = P_l CoarseSolve_{l+1}(P_l^dag r);  e += MR_k(D_l; r - D_l e);
+  cycle  M_l(r):  e = P_l CoarseSolve_{l+1}(P_l^dag r);  e += S_k(D_l; r - D_l e);
+         S_k is the smoother: MR_k, or GMRES with k steps (zero initial guess, no
+         restart, no tolerance), the same smoother in the setup sweeps;
          no pre-smoothing.  CoarseSolve is GMRES(m) with a relative tolerance at the
          coarsest level and one application of M_{l+1} (V-cycle) in between.
   initial setup on level l: for each sweep, for each i:
-         v_i <- MR_k(D_l; v_i) (zero initial guess), v_i <- v_i / ||v_i||;
+         v_i <- S_k(D_l; v_i) (zero initial guess), v_i <- v_i / ||v_i||;
          then P_l (block orthonormalisation) and D_{l+1} = P_l^dag D_l P_l; recurse
          with the level-(l+1) random vectors.
   iterative refinement: for each sweep: v_i <- M_0(v_i), v_i <- v_i/||v_i|| for all i
@@ -44,6 +47,7 @@ class MGParams:
     outer_restart: int = 20
     outer_tol: float = 1e-10
     outer_maxiter: int = 1000
+    smoother: str = "mr"                     # "mr" or "gmres"
 
 
 @dataclass
@@ -68,11 +72,20 @@ class Multigrid:
         return len(self.p.blocks) + 1
 
     # ---------------- setup ----------------
+    def smooth(self, op, b):
+        """S_k(op; b) from a zero initial guess."""
+        k = self.p.smoother_steps
+        if self.p.smoother == "mr":
+            return mr(op, b, k)
+        if self.p.smoother == "gmres":
+            return gmres(op, b, restart=k, tol=0.0, maxiter=k)[0]
+        raise ValueError(self.p.smoother)
+
     def _smooth_sweep(self, l):
         lev = self.levels[l]
         out = []
         for v in lev.vecs:
-            x = mr(lev.op, v, self.p.smoother_steps)
+            x = self.smooth(lev.op, v)
             out.append(x / norm(x))
         lev.vecs = out
 
@@ -118,7 +131,7 @@ class Multigrid:
     def cycle(self, l, r):
         lev = self.levels[l]
         e = lev.agg.prolong(self.coarse_solve(l + 1, lev.agg.restrict(r)))
-        return e + mr(lev.op, r - lev.op(e), self.p.smoother_steps)
+        return e + self.smooth(lev.op, r - lev.op(e))
 
     def solve(self, b, x0=None):
         return fgmres(self.levels[0].op, b, lambda v: self.cycle(0, v),

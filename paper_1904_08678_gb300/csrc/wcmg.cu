@@ -109,11 +109,17 @@ struct LevelScalars {
     cap_rhs = rhs;
     cap_m = m;
   }
-  double2* h1() { return c2.p; }
-  double2* h2() { return c2.p + (size_t)cap_rhs * (cap_m + 1); }
-  double2* pr() { return c2.p + (size_t)2 * cap_rhs * (cap_m + 1); }
-  double* slot(int k) { return d.p + (size_t)k * cap_rhs; }
+  // a host-side check: every accessor needs the buffers (never hand a kernel a null pointer)
+  void need() const {
+    if (!c2.p || !d.p || !H.p || !ints.p) throw Error(WCMG_ERR_STATE, "Krylov scalars used before allocation");
+  }
+  double2* h1() { need(); return c2.p; }
+  double2* h2() { need(); return c2.p + (size_t)cap_rhs * (cap_m + 1); }
+  double2* pr() { need(); return c2.p + (size_t)2 * cap_rhs * (cap_m + 1); }
+  double* slot(int k) { need(); return d.p + (size_t)k * cap_rhs; }
   GmresState state(int m) {
+    need();
+    if (m > cap_m) throw Error(WCMG_ERR_STATE, "Krylov scalars too small for the restart length");
     GmresState s;
     s.H = H.p; s.cs = cs.p; s.sn = sn.p; s.g = g.p; s.y = y.p;
     s.hnorm = slot(0); s.bnorm = slot(5); s.resid = slot(6);
@@ -143,6 +149,7 @@ struct Level {
   DevBuf<f16c> Lh;
   bool L32_valid = false, low_valid = false;
   LevelScalars sc;
+  LevelScalars sc_s;  // the GMRES smoother's own Krylov state (it runs inside the outer FGMRES)
   std::map<std::string, DevBuf<unsigned char>> ws;
   // coarse-apply launch shape per (nrhs, link storage): tuned or forced
   struct TileInfo {
@@ -233,7 +240,8 @@ struct wcmg_ctx {
   std::vector<long long> nested;          // capture-time stack: kernels of nested bodies
   DevBuf<int> body_counts;                // device copy of body_counts_h
   DevBuf<long long> gstat;                // [0] kernels launched by bodies, [1] coarsest GMRES iterations
-  DevBuf<KCtl> kctl;                      // 0 mixed loop, 1 level-0 FGMRES, 2 + l GMRES of level l
+  DevBuf<KCtl> kctl;                      // 0 mixed loop, 1 level-0 FGMRES, 2 + l coarsest GMRES,
+                                          // 2 + WCMG_MAX_LEVELS + l GMRES smoother of level l
   DevBuf<int> mx_done;
   DevBuf<double> mx_worst;
   struct Graph {
@@ -567,6 +575,7 @@ static void mr(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int s
 }
 
 template <typename R> static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs);
+template <typename R> static void smooth(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs);
 
 // ---------------- (F)GMRES ----------------
 struct KrylovOut {
@@ -582,17 +591,19 @@ struct KrylovOut {
 // b - A x decides at the end of a cycle.  max_cycles = 0: unlimited restarts.
 template <typename R>
 static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int m, double tol, int maxiter,
-                        bool x_zero, bool verify, bool precond, int max_cycles = 0) {
+                        bool x_zero, bool verify, bool precond, int max_cycles = 0,
+                        LevelScalars* scp = nullptr) {
   Level& L = c->L[l];
+  LevelScalars& SC = scp ? *scp : L.sc;
   const long long n = L.n();
   const int mr_ = max_rhs_all(c);
-  L.sc.ensure(mr_, std::max(m, std::max(c->p.outer_restart, c->p.coarse_restart)));
+  SC.ensure(mr_, std::max(m, std::max(c->p.outer_restart, c->p.coarse_restart)));
   cplx<R>* Vb = ws<R>(L, precond ? "fg_V" : "gm_V", (long long)(m + 1) * nrhs);
   cplx<R>* Zb = precond ? ws<R>(L, "fg_Z", (long long)m * nrhs) : nullptr;
   cplx<R>* w = ws<R>(L, precond ? "fg_w" : "gm_w", nrhs);
   cplx<R>* r = ws<R>(L, precond ? "fg_r" : "gm_r", nrhs);
   const long long bstride = n * nrhs;
-  GmresState S = L.sc.state(m);
+  GmresState S = SC.state(m);
   const int ldh = m + 1;
   norm2_op<R>(c, S.bnorm, b, n, nrhs);
   launch_sqrt_inplace(S.bnorm, nrhs, c->st);
@@ -606,10 +617,10 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
   }
   KrylovOut out;
   int cycles = 0;
-  norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
+  norm2_op<R>(c, SC.slot(1), r, n, nrhs);
   while (true) {
-    launch_gmres_start(S, L.sc.slot(1), tol, nrhs, L.sc.slot(2), c->st);
-    launch_scale_dev<R>(Vb, r, L.sc.slot(2), 0, n, nrhs, c->st);
+    launch_gmres_start(S, SC.slot(1), tol, nrhs, SC.slot(2), c->st);
+    launch_scale_dev<R>(Vb, r, SC.slot(2), 0, n, nrhs, c->st);
     int steps = 0;
     std::vector<double> prev_res;
     if (precond && l == 0 && c->learned_on) {
@@ -628,16 +639,16 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
       }
       apply_op<R>(c, l, w, z, nrhs);
       KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multidot<R>(L.sc.h1(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
+            launch_multidot<R>(SC.h1(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
       KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multiaxpy<R>(w, Vb, bstride, j + 1, L.sc.h1(), ldh, -1.0, n, nrhs, c->st));
+            launch_multiaxpy<R>(w, Vb, bstride, j + 1, SC.h1(), ldh, -1.0, n, nrhs, c->st));
       KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multidot<R>(L.sc.h2(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
+            launch_multidot<R>(SC.h2(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
       KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multiaxpy<R>(w, Vb, bstride, j + 1, L.sc.h2(), ldh, -1.0, n, nrhs, c->st));
-      norm2_op<R>(c, L.sc.slot(0), w, n, nrhs);
-      launch_gmres_step(S, j, L.sc.h1(), L.sc.h2(), L.sc.slot(0), tol, verify ? 0 : 1, nrhs, L.sc.slot(3), c->st);
-      launch_scale_dev<R>(Vb + (long long)(j + 1) * bstride, w, L.sc.slot(3), 0, n, nrhs, c->st);
+            launch_multiaxpy<R>(w, Vb, bstride, j + 1, SC.h2(), ldh, -1.0, n, nrhs, c->st));
+      norm2_op<R>(c, SC.slot(0), w, n, nrhs);
+      launch_gmres_step(S, j, SC.h1(), SC.h2(), SC.slot(0), tol, verify ? 0 : 1, nrhs, SC.slot(3), c->st);
+      launch_scale_dev<R>(Vb + (long long)(j + 1) * bstride, w, SC.slot(3), 0, n, nrhs, c->st);
       ++steps;
       ++out.iterations;
       if (precond && l == 0 && c->learned_on && c->coarse_mode == WCMG_COARSE_LEARNED) {
@@ -676,9 +687,9 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
     if (all && !verify) { out.converged = true; return out; }
     apply_op<R>(c, l, r, x, nrhs);
     launch_axpby<R>(r, 1.0, b, -1.0, n, nrhs, c->st);
-    norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
-    launch_gmres_mark_done(S, L.sc.slot(1), tol, nrhs, c->st);
-    const double* nr = read_doubles(c, L.sc.slot(1), nrhs);
+    norm2_op<R>(c, SC.slot(1), r, n, nrhs);
+    launch_gmres_mark_done(S, SC.slot(1), tol, nrhs, c->st);
+    const double* nr = read_doubles(c, SC.slot(1), nrhs);
     for (int q = 0; q < nrhs; ++q)
       if (!std::isfinite(nr[q])) throw Error(WCMG_ERR_NAN, "non-finite residual in Krylov solver");
     dn = read_ints(c, S.done, nrhs);
@@ -763,10 +774,11 @@ static void cond_node(wcmg_ctx* c, cudaGraphConditionalHandle h, cudaGraphCondit
 template <typename R>
 static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int m, double tol, int maxiter,
                      bool x_zero, bool verify, bool precond, int max_cycles, KCtl* K, const int* budget_its,
-                     int budget_max, long long* acc) {
+                     int budget_max, long long* acc, LevelScalars* scp = nullptr) {
   Level& L = c->L[l];
+  LevelScalars& SC = scp ? *scp : L.sc;
   const long long n = L.n();
-  L.sc.ensure(max_rhs_all(c), std::max(m, std::max(c->p.outer_restart, c->p.coarse_restart)));
+  SC.ensure(max_rhs_all(c), std::max(m, std::max(c->p.outer_restart, c->p.coarse_restart)));
   cplx<R>* Vb = ws<R>(L, precond ? "fg_V" : "gm_V", (long long)(m + 1) * nrhs);
   cplx<R>* Zb = precond ? ws<R>(L, "fg_Z", (long long)m * nrhs) : nullptr;
   cplx<R>* w = ws<R>(L, precond ? "fg_w" : "gm_w", nrhs);
@@ -774,7 +786,7 @@ static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs,
   cplx<R>* vcur = ws<R>(L, precond ? "fg_vc" : "gm_vc", nrhs);
   cplx<R>* zcur = precond ? ws<R>(L, "fg_zc", nrhs) : nullptr;
   const long long bstride = n * nrhs;
-  GmresState S = L.sc.state(m);
+  GmresState S = SC.state(m);
   const int ldh = m + 1;
   const int* jd = &K->j;
   norm2_op<R>(c, S.bnorm, b, n, nrhs);
@@ -787,15 +799,15 @@ static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs,
     apply_op<R>(c, l, r, x, nrhs);
     launch_axpby<R>(r, 1.0, b, -1.0, n, nrhs, c->st);  // r = b - A x
   }
-  norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
+  norm2_op<R>(c, SC.slot(1), r, n, nrhs);
   const bool single = max_cycles == 1;
   const cudaGraphConditionalHandle h_loop = single ? 0 : cond_handle(c);
   launch_kctl_init(K, maxiter, budget_its, budget_max, h_loop, single ? 0 : 1, c->st);
 
   // one restart cycle: Arnoldi steps while any rhs is active, then x += Z y
   auto one_cycle = [&]() {
-    launch_gmres_start(S, L.sc.slot(1), tol, nrhs, L.sc.slot(2), c->st);
-    launch_scale_dev<R>(Vb, r, L.sc.slot(2), 0, n, nrhs, c->st);
+    launch_gmres_start(S, SC.slot(1), tol, nrhs, SC.slot(2), c->st);
+    launch_scale_dev<R>(Vb, r, SC.slot(2), 0, n, nrhs, c->st);
     const cudaGraphConditionalHandle h_arn = cond_handle(c);
     launch_kctl_cycle_begin(K, S.active, nrhs, m, h_arn, c->st);
     cond_node(c, h_arn, cudaGraphCondTypeWhile, [&](int slot) {
@@ -808,17 +820,17 @@ static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs,
       }
       apply_op<R>(c, l, w, z, nrhs);
       KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multidot<R>(L.sc.h1(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
+            launch_multidot<R>(SC.h1(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
       KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multiaxpy<R>(w, Vb, bstride, m, L.sc.h1(), ldh, -1.0, n, nrhs, c->st, jd, 1));
+            launch_multiaxpy<R>(w, Vb, bstride, m, SC.h1(), ldh, -1.0, n, nrhs, c->st, jd, 1));
       KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multidot<R>(L.sc.h2(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
+            launch_multidot<R>(SC.h2(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
       KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multiaxpy<R>(w, Vb, bstride, m, L.sc.h2(), ldh, -1.0, n, nrhs, c->st, jd, 1));
-      norm2_op<R>(c, L.sc.slot(0), w, n, nrhs);
-      launch_gmres_step(S, 0, L.sc.h1(), L.sc.h2(), L.sc.slot(0), tol, verify ? 0 : 1, nrhs, L.sc.slot(3), c->st,
+            launch_multiaxpy<R>(w, Vb, bstride, m, SC.h2(), ldh, -1.0, n, nrhs, c->st, jd, 1));
+      norm2_op<R>(c, SC.slot(0), w, n, nrhs);
+      launch_gmres_step(S, 0, SC.h1(), SC.h2(), SC.slot(0), tol, verify ? 0 : 1, nrhs, SC.slot(3), c->st,
                         jd);
-      launch_scale_dev<R>(Vb, w, L.sc.slot(3), 0, n, nrhs, c->st, jd, 1, bstride);  // V_{j+1}
+      launch_scale_dev<R>(Vb, w, SC.slot(3), 0, n, nrhs, c->st, jd, 1, bstride);  // V_{j+1}
       launch_kctl_step_end(K, S.active, nrhs, m, acc, body_count(c, slot), h_arn, c->st);
     });
     launch_gmres_solve_y(S, nrhs, c->st);
@@ -839,11 +851,30 @@ static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs,
       slot_if = slot_i;
       apply_op<R>(c, l, r, x, nrhs);
       launch_axpby<R>(r, 1.0, b, -1.0, n, nrhs, c->st);
-      norm2_op<R>(c, L.sc.slot(1), r, n, nrhs);
-      launch_gmres_mark_done(S, L.sc.slot(1), tol, nrhs, c->st);
+      norm2_op<R>(c, SC.slot(1), r, n, nrhs);
+      launch_gmres_mark_done(S, SC.slot(1), tol, nrhs, c->st);
     });
-    launch_kctl_restart_check(K, S.done, L.sc.slot(1), nrhs, body_count(c, slot_if), h_loop, c->st);
+    launch_kctl_restart_check(K, S.done, SC.slot(1), nrhs, body_count(c, slot_if), h_loop, c->st);
   });
+}
+
+// ---------------- smoother ----------------
+// S_k(D_l; b) from a zero initial guess: MR(k), or GMRES with k steps (no restart,
+// no tolerance) on the level's own Krylov state, so that it can run inside the
+// outer FGMRES on the same level.
+template <typename R>
+static void smooth(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs) {
+  const int k = c->p.smoother_steps;
+  if (c->p.smoother == WCMG_SMOOTHER_MR || k == 0) {
+    mr<R>(c, l, x, b, nrhs, k);
+    return;
+  }
+  Level& L = c->L[l];
+  if (c->capturing)
+    fgmres_g<R>(c, l, x, b, nrhs, k, 0.0, k, true, false, false, 1, c->kctl.p + 2 + WCMG_MAX_LEVELS + l, nullptr, 0,
+                nullptr, &L.sc_s);
+  else
+    fgmres<R>(c, l, x, b, nrhs, k, 0.0, k, true, false, false, 1, &L.sc_s);
 }
 
 // ---------------- learned coarse correction (PTC network) ----------------
@@ -940,7 +971,7 @@ static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
   cplx<R>* s = ws<R>(L, "cyc_s", nrhs);
   apply_op<R>(c, l, t, e, nrhs);
   launch_axpby<R>(t, 1.0, r, -1.0, n, nrhs, c->st);  // t = r - D e
-  mr<R>(c, l, s, t, nrhs, c->p.smoother_steps);
+  smooth<R>(c, l, s, t, nrhs);
   launch_axpby<R>(e, 1.0, s, 1.0, n, nrhs, c->st);
 }
 
@@ -1019,7 +1050,7 @@ static void smooth_sweep(wcmg_ctx* c, int l) {
   const int nv = L.nvec;
   cplx<R>* raw = Prec<R>::raw(L).p;
   cplx<R>* x = ws<R>(L, "sw_x", nv);
-  mr<R>(c, l, x, raw, nv, c->p.smoother_steps);
+  smooth<R>(c, l, x, raw, nv);
   norm2_op<R>(c, L.sc.slot(7), x, L.n(), nv);
   launch_scale_dev<R>(raw, x, L.sc.slot(7), 1, L.n(), nv, c->st);
 }
@@ -1183,22 +1214,25 @@ static void solve_f64_body(wcmg_ctx* c, double2* x, const double2* b, int nrhs) 
 static void graph_prepare(wcmg_ctx* c, int nrhs) {
   c->body_counts.ensure(wcmg_ctx::MAX_BODIES);
   c->gstat.ensure(2);
-  c->kctl.ensure(2 + WCMG_MAX_LEVELS);
+  c->kctl.ensure(2 + 2 * WCMG_MAX_LEVELS);
   c->mx_done.ensure(max_rhs_all(c));
   c->mx_worst.ensure(1);
   for (auto& s : c->cap_st)
     if (!s) WCMG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  // the basis-slot copies of fgmres_g (level-0 FGMRES, coarsest GMRES)
+  // the basis-slot copies of fgmres_g (level-0 FGMRES, coarsest GMRES, GMRES smoothers)
   const int lc = c->p.n_levels - 1;
+  const bool gsm = c->p.smoother == WCMG_SMOOTHER_GMRES;
   if (inner64(c)) {
     ws<double>(c->L[0], "fg_vc", nrhs);
     ws<double>(c->L[0], "fg_zc", nrhs);
     ws<double>(c->L[lc], "gm_vc", nrhs);
+    for (int l = 0; gsm && l < lc; ++l) ws<double>(c->L[l], "gm_vc", nrhs);
     return;
   }
   ws<float>(c->L[0], "fg_vc", nrhs);
   ws<float>(c->L[0], "fg_zc", nrhs);
   ws<float>(c->L[lc], "gm_vc", nrhs);
+  for (int l = 0; gsm && l < lc; ++l) ws<float>(c->L[l], "gm_vc", nrhs);
   for (int l = 0; l + 1 < c->p.n_levels; ++l) Prec<float>::vecs(c, c->L[l]);
   for (int l = 1; l < c->p.n_levels; ++l) {
     Level& L = c->L[l];
@@ -1365,7 +1399,8 @@ static void ptc_train(wcmg_ctx* c, const wcmg_train_opts* o, wcmg_train_stats* s
     if (!c->L[l].have_P || !c->L[l + 1].have_op) throw Error(WCMG_ERR_STATE, "setup not done");
   const int np = o->npairs, B = o->batch;
   const int chunk = max_rhs_all(c);
-  if (np < 1 || B < 1 || B > chunk || o->steps < 0) throw Error(WCMG_ERR_ARG, "npairs/batch/steps out of range");
+  if (np < 1 || B < 1 || B > chunk || o->steps < 0 || o->refresh < 0)
+    throw Error(WCMG_ERR_ARG, "npairs/batch/steps/refresh out of range");
   Level& L = c->L[0];
   Level& C1 = c->L[1];
   const long long n = L.n();
@@ -1379,57 +1414,69 @@ static void ptc_train(wcmg_ctx* c, const wcmg_train_opts* o, wcmg_train_stats* s
   WCMG_CUDA(cudaMemsetAsync(c->ptcM.p, 0, sizeof(float2) * WCMG_PTC_NWEIGHTS, c->st));
   WCMG_CUDA(cudaMemsetAsync(c->ptcV.p, 0, sizeof(float2) * WCMG_PTC_NWEIGHTS, c->st));
   c->ptc_t = 0;
-  auto t0 = std::chrono::steady_clock::now();
   c->ds_r.ensure((size_t)np * n);
   c->ds_e.ensure((size_t)np * n);
+  c->ptcScale.ensure(np);
   const bool saved_on = c->learned_on;
   c->learned_on = false;
-  for (int p0 = 0; p0 < np; p0 += chunk) {
-    const int k = std::min(chunk, np - p0);
-    float2* r = c->ds_r.p + p0 * n;
-    float2* e = c->ds_e.p + p0 * n;
-    launch_gaussian_field(r, (long long)k * n, o->seed, 1 + p0, c->st);
-    const int nh = k / 2;  // the second half becomes residuals after one cycle
-    if (nh > 0) {
-      float2* b = r + (k - nh) * n;
-      float2* x = ws<float>(L, "ptc_x", nh);
-      float2* t = ws<float>(L, "ptc_t", nh);
-      cycle<float>(c, 0, x, b, nh);
-      apply_op<float>(c, 0, t, x, nh);
-      launch_axpby<float>(b, -1.0, t, 1.0, n, nh, c->st);  // b <- b - D M(b)
+  double ms_gen = 0.0;
+  long long pools = 0;
+  // a pool of np pairs from generator stream `pool` (every pool draws fresh fields)
+  auto generate = [&](long long pool) {
+    WCMG_CUDA(cudaStreamSynchronize(c->st));  // queued training steps count as training time
+    auto g0 = std::chrono::steady_clock::now();
+    for (int p0 = 0; p0 < np; p0 += chunk) {
+      const int k = std::min(chunk, np - p0);
+      float2* r = c->ds_r.p + p0 * n;
+      float2* e = c->ds_e.p + p0 * n;
+      launch_gaussian_field(r, (long long)k * n, o->seed, 1 + p0 + (unsigned long long)pool * 1000003ULL, c->st);
+      const int nh = k / 2;  // the second half becomes residuals after one cycle
+      if (nh > 0) {
+        float2* b = r + (k - nh) * n;
+        float2* x = ws<float>(L, "ptc_x", nh);
+        float2* t = ws<float>(L, "ptc_t", nh);
+        cycle<float>(c, 0, x, b, nh);
+        apply_op<float>(c, 0, t, x, nh);
+        launch_axpby<float>(b, -1.0, t, 1.0, n, nh, c->st);  // b <- b - D M(b)
+      }
+      norm2_op<float>(c, L.sc.slot(7), r, n, k);
+      launch_scale_dev<float>(r, r, L.sc.slot(7), 1, n, k, c->st);
+      float2* rc = ws<float>(C1, "ptc_rc", k);
+      float2* ec = ws<float>(C1, "ptc_ec", k);
+      restrict_op<float>(c, 0, rc, r, k);
+      if (c->p.n_levels == 2) {
+        fgmres<float>(c, 1, ec, rc, k, c->p.coarse_restart, o->target_tol, 2000, true, false, false);
+      } else {
+        cycle<float>(c, 1, ec, rc, k);  // deeper hierarchies: one coarse cycle as the target
+      }
+      prolong_op<float>(c, 0, e, ec, k);
     }
-    norm2_op<float>(c, L.sc.slot(7), r, n, k);
-    launch_scale_dev<float>(r, r, L.sc.slot(7), 1, n, k, c->st);
-    float2* rc = ws<float>(C1, "ptc_rc", k);
-    float2* ec = ws<float>(C1, "ptc_ec", k);
-    restrict_op<float>(c, 0, rc, r, k);
-    if (c->p.n_levels == 2) {
-      fgmres<float>(c, 1, ec, rc, k, c->p.coarse_restart, o->target_tol, 2000, true, false, false);
-    } else {
-      cycle<float>(c, 1, ec, rc, k);  // deeper hierarchies: one coarse cycle as the target
-    }
-    prolong_op<float>(c, 0, e, ec, k);
-  }
-  WCMG_CUDA(cudaStreamSynchronize(c->st));
-  auto t1 = std::chrono::steady_clock::now();
-  st->loss_initial = ptc_eval(c, np, chunk);
-  // per-pair gradient scale 1 / (||e||^2 B)
-  std::vector<double> e2(np);
-  for (int p0 = 0; p0 < np; p0 += chunk) {
-    const int k = std::min(chunk, np - p0);
-    norm2_op<float>(c, L.sc.slot(6), c->ds_e.p + p0 * n, n, k);
-    const double* h = read_doubles(c, L.sc.slot(6), k);
-    for (int q = 0; q < k; ++q) e2[p0 + q] = h[q];
-  }
-  c->ptcScale.ensure(np);
-  {
+    // per-pair gradient scale 1 / (||e||^2 B)
     std::vector<double> sc(np);
-    for (int q = 0; q < np; ++q) sc[q] = 1.0 / (e2[q] * B);
+    for (int p0 = 0; p0 < np; p0 += chunk) {
+      const int k = std::min(chunk, np - p0);
+      norm2_op<float>(c, L.sc.slot(6), c->ds_e.p + p0 * n, n, k);
+      const double* h = read_doubles(c, L.sc.slot(6), k);
+      for (int q = 0; q < k; ++q) sc[p0 + q] = 1.0 / (h[q] * B);
+    }
     WCMG_CUDA(cudaMemcpyAsync(c->ptcScale.p, sc.data(), sizeof(double) * np, cudaMemcpyHostToDevice, c->st));
-  }
+    WCMG_CUDA(cudaStreamSynchronize(c->st));
+    ms_gen += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g0).count();
+    ++pools;
+  };
+  generate(0);
+  st->loss_initial = ptc_eval(c, np, chunk);
+  auto t1 = std::chrono::steady_clock::now();
+  const double gen_before = ms_gen;
   float2* out = ws<float>(L, "ptc_out", chunk);
+  int pool_step = 0;
   for (int step = 0; step < o->steps; ++step) {
-    const int p0 = (int)(((long long)step * B) % np);
+    if (o->refresh > 0 && step > 0 && step % o->refresh == 0) {
+      generate(pools);
+      pool_step = 0;
+    }
+    const int p0 = (int)(((long long)pool_step * B) % np);
+    ++pool_step;
     const int k = std::min(B, np - p0);
     const float2* rb = c->ds_r.p + p0 * n;
     ptc_forward(c, out, rb, k);
@@ -1443,9 +1490,13 @@ static void ptc_train(wcmg_ctx* c, const wcmg_train_opts* o, wcmg_train_stats* s
   }
   WCMG_CUDA(cudaStreamSynchronize(c->st));
   auto t2 = std::chrono::steady_clock::now();
+  const double gen_in_loop = ms_gen - gen_before;
   st->loss_final = ptc_eval(c, np, chunk);
-  st->ms_generate = std::chrono::duration<double, std::milli>(t1 - t0).count();
-  st->ms_train = std::chrono::duration<double, std::milli>(t2 - t1).count();
+  st->pairs_total = pools * (long long)np;
+  generate(pools);  // held out: never trained on
+  st->loss_heldout = ptc_eval(c, np, chunk);
+  st->ms_generate = ms_gen;
+  st->ms_train = std::chrono::duration<double, std::milli>(t2 - t1).count() - gen_in_loop;
   c->learned_on = saved_on;
 }
 
@@ -1560,6 +1611,7 @@ int wcmg_default_params(wcmg_params* p) {
   p->profile = 0;
   p->use_graphs = 0;
   p->autotune = 0;
+  p->smoother = WCMG_SMOOTHER_MR;
   return WCMG_OK;
 }
 
@@ -1581,6 +1633,10 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       throw Error(WCMG_ERR_ARG, "solver parameters out of range");
     if ((p->use_graphs != 0 && p->use_graphs != 1) || (p->autotune != 0 && p->autotune != 1))
       throw Error(WCMG_ERR_ARG, "use_graphs and autotune must be 0 or 1");
+    if (p->smoother != WCMG_SMOOTHER_MR && p->smoother != WCMG_SMOOTHER_GMRES)
+      throw Error(WCMG_ERR_ARG, "smoother must be WCMG_SMOOTHER_MR or WCMG_SMOOTHER_GMRES");
+    if (p->smoother == WCMG_SMOOTHER_GMRES && p->smoother_steps > 64)
+      throw Error(WCMG_ERR_ARG, "GMRES smoother: at most 64 steps");
     c->L.resize(nl);
     int dims[4];
     for (int k = 0; k < 4; ++k) dims[k] = p->dims[k];
@@ -1644,6 +1700,7 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       WCMG_CUDA(cudaMemcpy(G.d_nbr.p, G.nbr.data(), sizeof(int) * 8 * G.V, cudaMemcpyHostToDevice));
     }
     ensure_partials(c);
+    for (auto& L : c->L) L.sc.ensure(max_rhs_all(c), std::max(c->p.outer_restart, c->p.coarse_restart));
     c->errflag.ensure((size_t)max_rhs_all(c) + 1);
     c->tma_err.ensure(1);
     WCMG_CUDA(cudaMemset(c->tma_err.p, 0, sizeof(int)));
@@ -1785,6 +1842,7 @@ int wcmg_get_coarse_links(wcmg_ctx* c, int level, void* A, int where, void* stre
   const size_t bytes = (size_t)9 * L.g.V * nb * nb * 16;
   double2* o = out_dev(c, A, bytes, where, 1);
   if (L.op64) launch_unpack_links<double2>(o, L.L64.p, L.g.d_perm.p, L.g.V, nb, c->st);
+  else if (L.L32_valid) launch_unpack_links<float2>(o, L.L32.p, L.g.d_perm.p, L.g.V, nb, c->st);
   else if (L.low_valid && c->p.coarse_link_prec == WCMG_BF16)
     launch_unpack_links<bf16c>(o, L.Lbf.p, L.g.d_perm.p, L.g.V, nb, c->st);
   else if (L.low_valid && c->p.coarse_link_prec == WCMG_F16)

@@ -35,6 +35,7 @@ KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen",
           "dslash64", "ptc"]
 PTC_HIDDEN, PTC_NWEIGHTS = 12, 3456
 COARSE_MG, COARSE_WARMSTART, COARSE_LEARNED = 0, 1, 2
+SMOOTHER_MR, SMOOTHER_GMRES = 0, 1
 
 
 class wcmg_params(ctypes.Structure):
@@ -60,6 +61,7 @@ class wcmg_params(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("smoother", ctypes.c_int),
     ]
 
 
@@ -102,13 +104,14 @@ class wcmg_tile(ctypes.Structure):
 
 
 class wcmg_train_opts(ctypes.Structure):
-    _fields_ = [("npairs", ctypes.c_int), ("batch", ctypes.c_int), ("steps", ctypes.c_int), ("lr", ctypes.c_double),
-                ("target_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+    _fields_ = [("npairs", ctypes.c_int), ("batch", ctypes.c_int), ("steps", ctypes.c_int), ("refresh", ctypes.c_int),
+                ("lr", ctypes.c_double), ("target_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class wcmg_train_stats(ctypes.Structure):
     _fields_ = [("loss_initial", ctypes.c_double), ("loss_final", ctypes.c_double),
-                ("ms_generate", ctypes.c_double), ("ms_train", ctypes.c_double)]
+                ("ms_generate", ctypes.c_double), ("ms_train", ctypes.c_double),
+                ("loss_heldout", ctypes.c_double), ("pairs_total", ctypes.c_longlong)]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -380,8 +383,9 @@ class Context:
         assert wi == wg == wgi == ww
         return self._check(wcmg_ptc_backward(self.h, pi, pg, pgi, pw, nrhs, wi, _stream(stream)))
 
-    def ptc_train(self, npairs=32, batch=4, steps=100, lr=1e-3, target_tol=1e-6, seed=1, stream=None):
-        o = wcmg_train_opts(npairs, batch, steps, lr, target_tol, seed)
+    def ptc_train(self, npairs=32, batch=4, steps=100, lr=1e-3, target_tol=1e-6, seed=1, refresh=0, stream=None):
+        o = wcmg_train_opts(npairs=npairs, batch=batch, steps=steps, refresh=refresh, lr=lr, target_tol=target_tol,
+                            seed=seed)
         st = wcmg_train_stats()
         self._check(wcmg_ptc_train(self.h, ctypes.byref(o), ctypes.byref(st), _stream(stream)))
         return st

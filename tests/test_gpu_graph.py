@@ -27,11 +27,11 @@ def make_ctx(lib, dims, block, nvec, prec, seed, eps=0.3, m0=-0.1, setup=True, *
     return ctx, U, iv
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32_inner"])
-def test_graph_replay_matches_host_driven(lib, prec):
+@pytest.mark.parametrize("prec,smoother", [(0, 0), (1, 0), (1, 1)], ids=["f64", "f32_inner", "f32_gmres_smoother"])
+def test_graph_replay_matches_host_driven(lib, prec, smoother):
     dims, block = (8, 8, 8, 8), (2, 2, 2, 2)
-    ref, U, iv = make_ctx(lib, dims, block, 6, prec, 1021)
-    ctx, _, _ = make_ctx(lib, dims, block, 6, prec, 1021, use_graphs=1)
+    ref, U, iv = make_ctx(lib, dims, block, 6, prec, 1021, smoother=smoother)
+    ctx, _, _ = make_ctx(lib, dims, block, 6, prec, 1021, use_graphs=1, smoother=smoother)
     b = inputs.source(dims, 0)
     xe = dev(np.zeros_like(b))
     se = ref.solve(dev(b), xe)

@@ -105,3 +105,32 @@ def test_learned_mode_without_weights_is_state_error(lib):
     with pytest.raises(lib.WcmgError) as e:
         ctx.solve(dev(b), dev(np.zeros_like(b)))
     assert e.value.code == lib.ERR_STATE
+
+
+def test_training_on_fresh_pools_generalises_and_transfers_to_a_larger_lattice(lib):
+    """Pools of pairs are regenerated during training; the held-out loss (a pool never
+    trained on) stays below the zero network's 1.  The weights act per site and hop,
+    so a network trained on 8^3 x 16 deploys unchanged on 8^3 x 32 (another gauge
+    field): there it must still beat the cycle without coarse correction."""
+    ctx = setup_small(lib)
+    st = ctx.ptc_train(npairs=12, batch=4, steps=240, lr=1e-2, target_tol=1e-6, seed=7, refresh=30)
+    assert st.pairs_total == 12 * 8
+    assert st.loss_heldout < 0.97 and st.loss_final < 0.97
+    W = dev(np.zeros(3456, dtype=complex))
+    ctx.ptc_get_weights(W)
+    ctx.close()
+    big = (8, 8, 8, 32)
+    p = lib.default_params(dims=big, blocks=[(4, 4, 4, 4)], nvec=[24], m0=-0.2, csw=1.0, inner_prec=lib.F32,
+                           setup_refine_sweeps=2, max_rhs=24)
+    out = {}
+    for name, w in (("zero", dev(np.zeros(3456, dtype=complex))), ("trained", W)):
+        c2 = lib.Context(p)
+        c2.set_gauge(dev(inputs.random_gauge(big, 0.25, 3020)))
+        c2.setup(dev(inputs.setup_vectors(big, 12, 24, 0, 3020)))
+        c2.ptc_set_weights(w)
+        c2.set_coarse_mode(lib.COARSE_LEARNED, 0.0)
+        b = inputs.source(big, 0)
+        out[name] = c2.solve(dev(b), dev(np.zeros_like(b)))
+        c2.close()
+    assert out["trained"].converged and out["trained"].true_residual <= 1e-10
+    assert out["trained"].outer_iterations < out["zero"].outer_iterations

@@ -193,3 +193,26 @@ def test_not_converged_reported(lib):
     b = inputs.source(DIMS, 0)
     st = ctx.solve(dev(b), dev(np.zeros_like(b)), allow_not_converged=True)
     assert not st.converged and st.outer_iterations == 2
+
+
+def test_gmres_smoother_setup_cycle_and_solve_match_oracle(lib):
+    """GMRES(4) as the smoother (zero guess, no restart) in the setup sweeps and the cycle."""
+    ctx, D = config1_ctx(lib, smoother=lib.SMOOTHER_GMRES, setup_refine_sweeps=1)
+    iv = inputs.setup_vectors(DIMS, 12, NVEC, 0, 1001)
+    ctx.setup(dev(iv))
+    mg = oracle_mg(D, iv, smoother="gmres", refine_sweeps=1)
+    V = 256
+    P = dev(np.zeros((NVEC, V, 12), dtype=complex))
+    ctx.get_nullvecs(0, P)
+    assert rel(host(P), mg.levels[0].agg.v.reshape(NVEC, V, 12)) < 1e-9
+    r = inputs.complex_gaussian(26, 0, (1, V, 12))
+    e = dev(np.zeros_like(r))
+    ctx.mg_cycle(dev(r), e)
+    assert rel(host(e)[0], mg.cycle(0, fields(r, DIMS, 12)[0]).reshape(V, 12)) < 1e-9
+    b = inputs.source(DIMS, 0)
+    x = dev(np.zeros_like(b))
+    st = ctx.solve(dev(b), x)
+    xo, info = mg.solve(fields(b, DIMS, 12)[0])
+    assert st.converged and st.true_residual <= 1e-10
+    assert rel(host(x)[0].reshape(V, 12), xo.reshape(V, 12)) < 1e-8
+    assert abs(st.outer_iterations - info.iterations) <= 1

@@ -74,3 +74,33 @@ def test_refinement_reduces_iterations():
         assert info.converged
         its.append(info.iterations)
     assert its[1] < its[0]
+
+
+def test_gmres_smoother_never_leaves_a_larger_residual_than_mr():
+    """MR(k) and GMRES(k) from a zero guess both stay in the Krylov space K_k(D, r);
+    GMRES(k) minimises ||r - D x|| over all of it, so its smoothed residual is never
+    larger than MR's (and differs from it: a dropped term in either shows here)."""
+    dims, D, b = config1()
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 8, 0, 1001)]]
+    for k in (1, 2, 4, 6):
+        res = {}
+        for sm in ("mr", "gmres"):
+            mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[8], smoother_steps=k, smoother=sm), iv,
+                           build=False)
+            x = mg.smooth(D, b)
+            res[sm] = np.linalg.norm((b - D(x)).ravel())
+        assert res["gmres"] <= res["mr"] * (1 + 1e-12)
+        if k == 1:
+            assert abs(res["gmres"] - res["mr"]) <= 1e-12 * res["mr"]  # one step: the same minimiser
+        else:
+            assert res["gmres"] < res["mr"] * (1 - 1e-6)
+
+
+def test_gmres_smoother_solve_converges_to_the_dense_solution():
+    dims, D, b = config1()
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 8, 0, 1001)]]
+    mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[8], smoother="gmres"), iv)
+    x, info = mg.solve(b)
+    assert info.converged and info.true_residual <= 1e-10
+    x_ref, _ = gmres(D, b, restart=60, tol=1e-13, maxiter=5000, verify=True)
+    assert rel(x, x_ref) < 1e-8
