@@ -46,9 +46,11 @@ __global__ void __launch_bounds__(RED_T) k_dot_partial(double2* __restrict__ par
   cplx<R> acc = czero<R>();
   for (long long i = blockIdx.x * (long long)RED_T + threadIdx.x; i < n; i += (long long)gridDim.x * RED_T)
     cjmac(acc, a[i], b[i]);
-  double2 v = to_c64(acc);
-  block_sum_many<double2>(&v, 1, scratch, red);
-  if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = red[0];
+  const R v[2] = {acc.x, acc.y};
+  double* sd = reinterpret_cast<double*>(scratch);
+  double* rd = reinterpret_cast<double*>(red);
+  block_sum_mixed<R, 2>(v, sd, rd);
+  if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = make_double2(rd[0], rd[1]);
 }
 template <typename R>
 __global__ void __launch_bounds__(RED_T) k_norm_partial(double* __restrict__ partial, const cplx<R>* __restrict__ a,
@@ -60,8 +62,8 @@ __global__ void __launch_bounds__(RED_T) k_norm_partial(double* __restrict__ par
   R acc = 0;
   for (long long i = blockIdx.x * (long long)RED_T + threadIdx.x; i < n; i += (long long)gridDim.x * RED_T)
     acc += cnorm2(a[i]);
-  double v = acc;
-  block_sum_many<double>(&v, 1, scratch, red);
+  const R v[1] = {acc};
+  block_sum_mixed<R, 1>(v, scratch, red);
   if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = red[0];
 }
 // out[r * ldo + i] = sum_{b < count} partial[r * pr + i * pi + b]  (grid: r = x, i = y)
@@ -108,7 +110,6 @@ __global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict_
                                                             int k, const cplx<R>* __restrict__ w, long long n,
                                                             int kpad, const int* __restrict__ kdev, int kadd) {
   __shared__ double2 scratch[(RED_T / 32) * MD_K];
-  __shared__ double2 red[MD_K];
   const int r = blockIdx.y, i0 = blockIdx.z * MD_K;
   if (kdev) k = *kdev + kadd;
   if (i0 >= k) return;  // uniform per block
@@ -122,12 +123,18 @@ __global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict_
     for (int q = 0; q < MD_K; ++q)
       if (i0 + q < k) cjmac(acc[q], basis[(i0 + q) * bstride + off + e], x);
   }
-  double2 v[MD_K];
-#pragma unroll
-  for (int q = 0; q < MD_K; ++q) v[q] = to_c64(acc[q]);
-  block_sum_many<double2>(v, MD_K, scratch, red);
-  if (threadIdx.x < MD_K && i0 + threadIdx.x < k)
-    partial[((long long)r * kpad + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = red[threadIdx.x];
+  // warp sums in the working precision (one transposing butterfly for the 8 values),
+  // then FP64 across the warps of the CTA and across CTAs
+  static_assert(MD_K == 8, "transposing warp reduction of 8 values");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum8_transposed(acc, lane);
+  if ((lane & 3) == 0) scratch[warp * MD_K + warp_sum8_index(lane)] = to_c64(acc[0]);
+  __syncthreads();
+  if (threadIdx.x < MD_K && i0 + threadIdx.x < k) {
+    double2 t = scratch[threadIdx.x];
+    for (int w = 1; w < RED_T / 32; ++w) t += scratch[w * MD_K + threadIdx.x];
+    partial[((long long)r * kpad + i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
 }
 // k basis vectors; with kdev the count is *kdev + kadd (<= k) read on the device.
 template <typename R>

@@ -102,6 +102,9 @@ __device__ __forceinline__ float2 warp_sum(float2 v) { return make_float2(warp_s
 __device__ __forceinline__ double2 shfl_xor2(double2 v, int o) {
   return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
 
 // Warp sums of 8 values at once by a transposing butterfly: at each of the first
 // three exchange steps (lane distance 16, 8, 4) a lane keeps half of its values
@@ -109,13 +112,14 @@ __device__ __forceinline__ double2 shfl_xor2(double2 v, int o) {
 // lane instead of 8 x 5.  On return v[0] of lane l holds the full warp sum of
 // value 4 b4 + 2 b3 + b2 (b_i: bit i of l); lanes with (l & 3) == 0 hold distinct
 // values.
-__device__ __forceinline__ void warp_sum8_transposed(double2 (&v)[8], int lane) {
+template <typename T>
+__device__ __forceinline__ void warp_sum8_transposed(T (&v)[8], int lane) {
   {
     const bool up = lane & 16;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const double2 send = up ? v[j] : v[j + 4];
-      const double2 keep = up ? v[j + 4] : v[j];
+      const T send = up ? v[j] : v[j + 4];
+      const T keep = up ? v[j + 4] : v[j];
       v[j] = keep + shfl_xor2(send, 16);
     }
   }
@@ -123,19 +127,43 @@ __device__ __forceinline__ void warp_sum8_transposed(double2 (&v)[8], int lane) 
     const bool up = lane & 8;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      const double2 send = up ? v[j] : v[j + 2];
-      const double2 keep = up ? v[j + 2] : v[j];
+      const T send = up ? v[j] : v[j + 2];
+      const T keep = up ? v[j + 2] : v[j];
       v[j] = keep + shfl_xor2(send, 8);
     }
   }
   {
     const bool up = lane & 4;
-    const double2 send = up ? v[0] : v[1];
-    const double2 keep = up ? v[1] : v[0];
+    const T send = up ? v[0] : v[1];
+    const T keep = up ? v[1] : v[0];
     v[0] = keep + shfl_xor2(send, 4);
   }
   v[0] += shfl_xor2(v[0], 2);
   v[0] += shfl_xor2(v[0], 1);
+}
+// index of the value that lane l holds after warp_sum8_transposed
+__device__ __forceinline__ int warp_sum8_index(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// Block sums of N real values: warp sums in the working precision R (FP32 shuffles
+// and adds are cheap; FP64 adds run at 1/64 of the FP32 rate on this part), then
+// FP64 across the warps.  Result k in red[k]; scratch holds (blockDim/32) * N.
+template <typename R, int N>
+__device__ __forceinline__ void block_sum_mixed(const R (&vals)[N], double* scratch, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const R s = warp_sum(vals[k]);
+    if (lane == 0) scratch[warp * N + k] = (double)s;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double t = scratch[threadIdx.x];
+    for (int w = 1; w < nw; ++w) t += scratch[w * N + threadIdx.x];
+    red[threadIdx.x] = t;
+  }
+  __syncthreads();
 }
 
 // Sum `n` complex values held per thread across the whole block; result for value k

@@ -452,14 +452,14 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && NR == 1) ? 6 : (sizeof
   if (DOTS) {
     __shared__ double scratch[(128 / 32) * 3 * NR];
     __shared__ double red[3 * NR];
-    double v[3 * NR];
+    R v[3 * NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
       v[3 * q] = dr[q];
       v[3 * q + 1] = di[q];
       v[3 * q + 2] = nn[q];
     }
-    block_sum_regs<double, 3 * NR>(v, 3 * NR, scratch, red);
+    block_sum_mixed<R, 3 * NR>(v, scratch, red);
     if (threadIdx.x < nq) {
       const int q = threadIdx.x;
       const int nsb = gridDim.x / ngrp, sb = blockIdx.x / ngrp;
@@ -498,6 +498,154 @@ void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const 
     else WCMG_DS(ST_FACE_HOP, 1);
   }
 #undef WCMG_DS
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---- chirality pairs for CoarsenOperator (K5) ----
+// For each near-null vector v_i the Galerkin construction needs the masked stencil
+// applied to both chirality projections: out[i] = D_mode(Pi_+ v_i),
+// out[nv + i] = D_mode(Pi_- v_i).  Pi_+ v keeps spin 0, 1 and Pi_- v spin 2, 3
+// (chiral basis), so one load of v's neighbour spinor serves both: the projected
+// half spinor of Pi_+ v is its upper half, that of Pi_- v is -/+ B of its lower
+// half.  The clover term is chirality-diagonal: C Pi_+ v = C_upper acting on the
+// upper half only.
+template <typename R, int MU, bool FWD>
+__device__ __forceinline__ void hop_chiral(cplx<R> (&ap)[12], cplx<R> (&am)[12], const cplx<R>* __restrict__ in,
+                                           const cplx<R>* __restrict__ U, int V, int s, int y) {
+  using T = cplx<R>;
+  const int ls = FWD ? s : y;
+  T u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = U[((long long)MU * 9 + k) * V + ls];
+  T hp[2][3], pl[2][3];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      hp[sp][c] = in[(long long)(3 * sp + c) * V + y];
+      pl[sp][c] = in[(long long)(6 + 3 * sp + c) * V + y];
+    }
+  T hm[2][3];
+  applyB<MU>(hm, pl);
+  if (FWD) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) hm[sp][c] = -hm[sp][c];
+  }
+  T wp[2][3], wm[2][3];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T tp = czero<R>(), tm = czero<R>();
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (FWD) {
+          cmac(tp, u[3 * a + b], hp[sp][b]);
+          cmac(tm, u[3 * a + b], hm[sp][b]);
+        } else {
+          cjmac(tp, u[3 * b + a], hp[sp][b]);
+          cjmac(tm, u[3 * b + a], hm[sp][b]);
+        }
+      }
+      wp[sp][a] = tp;
+      wm[sp][a] = tm;
+    }
+  T Bp[2][3], Bm[2][3];
+  applyBdag<MU>(Bp, wp);
+  applyBdag<MU>(Bm, wm);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ap[3 * sp + c] += wp[sp][c];
+      am[3 * sp + c] += wm[sp][c];
+      if (FWD) {
+        ap[6 + 3 * sp + c] -= Bp[sp][c];
+        am[6 + 3 * sp + c] -= Bm[sp][c];
+      } else {
+        ap[6 + 3 * sp + c] += Bp[sp][c];
+        am[6 + 3 * sp + c] += Bm[sp][c];
+      }
+    }
+}
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1)
+    k_dslash_chiral(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in, const cplx<R>* __restrict__ U,
+                    const cplx<R>* __restrict__ clov, const int* __restrict__ nbr, int V, BlockInfo bi, int hopdir,
+                    int nv) {
+  using T = cplx<R>;
+  const int i = blockIdx.x % nv;  // vector fastest: the CTAs running together share links and clover
+  const int s = (blockIdx.x / nv) * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  if (MODE == ST_FACE_HOP && !on_face(bi, s, hopdir)) return;
+  const long long rstride = 12LL * V;
+  const cplx<R>* vi = in + (long long)i * rstride;
+  T ap[12], am[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) ap[c] = am[c] = czero<R>();
+  auto use = [&](int d) -> bool {
+    if (MODE == ST_BLOCK_INTERIOR) return !on_face(bi, s, d);
+    return d == hopdir && on_face(bi, s, d);
+  };
+#define WCMG_HOPC(MU)                                                                       \
+  if (use(2 * MU)) hop_chiral<R, MU, true>(ap, am, vi, U, V, s, nbr[(2 * MU) * V + s]);      \
+  if (use(2 * MU + 1)) hop_chiral<R, MU, false>(ap, am, vi, U, V, s, nbr[(2 * MU + 1) * V + s]);
+  WCMG_HOPC(0)
+  WCMG_HOPC(1)
+  WCMG_HOPC(2)
+  WCMG_HOPC(3)
+#undef WCMG_HOPC
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    ap[c] = R(-0.5) * ap[c];
+    am[c] = R(-0.5) * am[c];
+  }
+  if (MODE != ST_FACE_HOP) {
+    // C Pi_+ v: upper 6x6 block on the upper half; C Pi_- v: lower block on the lower half
+    T p[1][6];
+    T accp[1][12], accm[1][12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      accp[0][c] = R(-2.0) * ap[c];  // clover_half computes C p - acc / 2 on its half
+      accm[0][c] = R(-2.0) * am[c];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[0][k] = vi[(long long)k * V + s];
+    clover_half<R, 1>(accp, clov, p, 0, V, s);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[0][k] = vi[(long long)(6 + k) * V + s];
+    clover_half<R, 1>(accm, clov, p, 1, V, s);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      ap[k] = accp[0][k];
+      am[6 + k] = accm[0][6 + k];
+    }
+  }
+  T* op = out + (long long)i * rstride;
+  T* om = out + (long long)(nv + i) * rstride;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    op[(long long)c * V + s] = ap[c];
+    om[(long long)c * V + s] = am[c];
+  }
+}
+
+template <typename R>
+void launch_dslash_chiral(cplx<R>* out, const cplx<R>* vecs, const cplx<R>* gauge, const cplx<R>* clov,
+                          const LevelGeom& g, int nv, int mode, int hopdir, cudaStream_t st) {
+  BlockInfo bi;
+  for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
+  bi.bvol = g.bvol;
+  const dim3 grid((unsigned)(nblk(g.V, 128) * (long long)nv));
+  if (mode == ST_BLOCK_INTERIOR)
+    k_dslash_chiral<R, ST_BLOCK_INTERIOR><<<grid, 128, 0, st>>>(out, vecs, gauge, clov, g.nbr, g.V, bi, hopdir, nv);
+  else if (mode == ST_FACE_HOP)
+    k_dslash_chiral<R, ST_FACE_HOP><<<grid, 128, 0, st>>>(out, vecs, gauge, clov, g.nbr, g.V, bi, hopdir, nv);
+  else
+    throw Error(-1, "chirality-pair stencil: block-interior or face mode only");
   WCMG_LAUNCH_CHECK();
 }
 
@@ -556,7 +704,9 @@ void launch_dslash_mr(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, con
   template void launch_dslash<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
                                  int, int, int, cudaStream_t);                                               \
   template void launch_dslash_mr<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
-                                    int, double2*, double*, double2*, double*, cudaStream_t);
+                                    int, double2*, double*, double2*, double*, cudaStream_t);                  \
+  template void launch_dslash_chiral<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*,              \
+                                        const LevelGeom&, int, int, int, cudaStream_t);
 WCMG_INST(double)
 WCMG_INST(float)
 #undef WCMG_INST

@@ -33,6 +33,11 @@ void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const 
 // pp[r] = <out_r, out_r> (the minimal-residual step's two reductions, fused into the
 // stencil).  pr_part / pp_part: scratch of nrhs * dslash_partials(V) entries.
 int dslash_partials(int V);
+// Masked stencil (ST_BLOCK_INTERIOR or ST_FACE_HOP) of both chirality projections of
+// nv vectors: out[i] = D_mode(Pi_+ v_i), out[nv + i] = D_mode(Pi_- v_i) (CoarsenOperator).
+template <typename R>
+void launch_dslash_chiral(cplx<R>* out, const cplx<R>* vecs, const cplx<R>* gauge, const cplx<R>* clov,
+                          const LevelGeom& g, int nv, int mode, int hopdir, cudaStream_t st);
 template <typename R>
 void launch_dslash_mr(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
                       int nrhs, double2* pr, double* pp, double2* pr_part, double* pp_part, cudaStream_t st);

@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256, 2) k_block_ortho(double2* __restrict__ ve
           }
         }
         warp_sum8_transposed(p, lane);
-        const int g = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        const int g = warp_sum8_index(lane);
         if ((lane & 3) == 0 && i0 + g < k) scratch[warp][i0 + g] = p[0];
       }
       double n0 = 0;

@@ -994,10 +994,36 @@ static void coarsen(wcmg_ctx* c, int l) {
   }
   WCMG_CUDA(cudaMemsetAsync(links, 0, (size_t)nl * sizeof(cplx<R>), c->st));
   const int chunk = std::min(nb, 48);
-  cplx<R>* cols = ws<R>(F, "co_cols", chunk);
   cplx<R>* T = ws<R>(F, "co_T", chunk);
   cplx<R>* res = ws<R>(C, "co_res", chunk);
-  for (int b0 = 0; b0 < nb; b0 += chunk) {
+  if (F.fine) {
+    // fine level: both chirality columns of each vector from one stencil pass
+    if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+    const int vchunk = chunk / 2;
+    const cplx<R>* vecs = Prec<R>::vecs(c, F);
+    const double V = F.g.V, s = sizeof(cplx<R>);
+    for (int i0 = 0; i0 < F.nvec; i0 += vchunk) {
+      const int nv = std::min(vchunk, F.nvec - i0);
+      for (int dm = 0; dm < 9; ++dm) {
+        const int mode = dm == 0 ? ST_BLOCK_INTERIOR : ST_FACE_HOP;
+        const int hop = dm == 0 ? 0 : dm - 1;
+        const double frac = dm == 0 ? 1.0 : 1.0 / F.g.b[hop >> 1];
+        KPROF(c, sizeof(R) == 8 ? WCMG_K_DSLASH64 : WCMG_K_DSLASH, frac * V * s * (36.0 * nv + 72.0),
+              frac * V * 1872.0 * 2 * nv,
+              launch_dslash_chiral<R>(T, vecs + (long long)i0 * F.n(), Prec<R>::gauge(c), Prec<R>::clover(c),
+                                      F.g.lg(), nv, mode, hop, c->st));
+        restrict_op<R>(c, l, res, T, 2 * nv, dm == 0 ? -1 : hop);
+        const long long half = (long long)nv * Vc * nb;
+        KPROF(c, WCMG_K_COARSEN, (double)Vc * nb * nv * 4.0 * sizeof(cplx<R>), 0.0,
+              (launch_scatter_links<R, cplx<R>>(links, res, Vc, nb, dm == 0 ? 0 : dm, i0, nv, c->st)));
+        KPROF(c, WCMG_K_COARSEN, 0.0, 0.0,
+              (launch_scatter_links<R, cplx<R>>(links, res + half, Vc, nb, dm == 0 ? 0 : dm, F.nvec + i0, nv,
+                                                c->st)));
+      }
+    }
+  }
+  cplx<R>* cols = F.fine ? nullptr : ws<R>(F, "co_cols", chunk);
+  for (int b0 = 0; !F.fine && b0 < nb; b0 += chunk) {
     const int ncols = std::min(chunk, nb - b0);
     KPROF(c, WCMG_K_COARSEN, 2.0 * F.n() * ncols * sizeof(cplx<R>), 0.0,
           launch_make_columns<R>(cols, Prec<R>::vecs(c, F), F.g.V, F.nc, F.nvec, b0, ncols, F.fine, c->st));
