@@ -6,6 +6,8 @@
 // results are bitwise reproducible run to run.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace wcmg {
@@ -315,22 +317,19 @@ __global__ void k_gmres_start(GmresState S, const double* __restrict__ nrm2, dou
   inv_beta[r] = go ? 1.0 / beta : 0.0;
 }
 
-__global__ void k_gmres_step(GmresState S, int j, const double2* __restrict__ h1, const double2* __restrict__ h2,
-                             const double* __restrict__ hnorm2, double tol, int final_done, int nrhs,
-                             double* __restrict__ inv_h, const int* __restrict__ jdev) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
-  if (jdev) j = *jdev;
+// Column j of the Hessenberg matrix of rhs r: h_col[0..j] (both CGS passes summed)
+// and ||w||^2; the earlier rotations, a new complex Givens rotation and the
+// recurrence residual; returns 1 / ||w|| (0 if ||w|| = 0).
+__device__ double gmres_column(GmresState S, int r, int j, const double2* hcol, double hn2, double tol,
+                               int final_done) {
   const int m = S.m;
-  if (!S.active[r]) { inv_h[r] = 0.0; return; }
   double2* H = S.H + (long long)r * (m + 1) * m;
   double* cs = S.cs + (long long)r * m;
   double2* sn = S.sn + (long long)r * m;
   double2* g = S.g + (long long)r * (m + 1);
-  for (int i = 0; i <= j; ++i) H[i * m + j] = h1[(long long)r * (m + 1) + i] + h2[(long long)r * (m + 1) + i];
-  const double h = sqrt(hnorm2[r]);
+  for (int i = 0; i <= j; ++i) H[i * m + j] = hcol[i];
+  const double h = sqrt(hn2);
   H[(j + 1) * m + j] = make_double2(h, 0);
-  inv_h[r] = h > 0.0 ? 1.0 / h : 0.0;
   for (int i = 0; i < j; ++i) {
     const double2 a = H[i * m + j], b = H[(i + 1) * m + j];
     H[i * m + j] = cs[i] * a + cmul(sn[i], b);
@@ -351,7 +350,203 @@ __global__ void k_gmres_step(GmresState S, int j, const double2* __restrict__ h1
     S.active[r] = 0;
     if (final_done) S.done[r] = 1;
   }
+  return h > 0.0 ? 1.0 / h : 0.0;
 }
+
+__global__ void k_gmres_step(GmresState S, int j, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                             const double* __restrict__ hnorm2, double tol, int final_done, int nrhs,
+                             double* __restrict__ inv_h, const int* __restrict__ jdev) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  if (jdev) j = *jdev;
+  const int m = S.m;
+  if (!S.active[r]) { inv_h[r] = 0.0; return; }
+  double2 hcol[65];
+  for (int i = 0; i <= j; ++i) hcol[i] = h1[(long long)r * (m + 1) + i] + h2[(long long)r * (m + 1) + i];
+  inv_h[r] = gmres_column(S, r, j, hcol, hnorm2[r], tol, final_done);
+}
+
+// ---- fused Arnoldi step for short vectors (one rhs) ----
+// Everything of one (F)GMRES Arnoldi step after the operator application, for
+// vectors short enough that a single thread-block cluster streams them from L2:
+// both classical Gram-Schmidt passes h1 = V^dag w, w -= V h1, h2 = V^dag w,
+// w -= V h2, the norm ||w||^2, the Givens update of Hessenberg column j and
+// V_{j+1} = w / ||w||.  CTA c of the C-CTA cluster owns a contiguous range of the
+// vector; its partial sums (warp sums in the working precision, FP64 across
+// warps) are exchanged through distributed shared memory, and every CTA adds the C
+// partials in the same order, so all CTAs hold identical coefficients.  One
+// launch replaces ten (three two-stage reductions, two updates, Givens, scaling).
+constexpr int AC_T = 256, AC_MAXK = 65;
+
+template <typename R>
+__device__ __forceinline__ void ac_reduce8(cplx<R> (&acc)[8], double2* __restrict__ scr, double2* __restrict__ out,
+                                           int i0, int k) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum8_transposed(acc, lane);
+  if ((lane & 3) == 0) scr[warp * 8 + warp_sum8_index(lane)] = to_c64(acc[0]);
+  __syncthreads();
+  if (threadIdx.x < 8 && i0 + threadIdx.x < k) {
+    double2 t = scr[threadIdx.x];
+    for (int w = 1; w < AC_T / 32; ++w) t += scr[w * 8 + threadIdx.x];
+    out[i0 + threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(AC_T) k_arnoldi_cluster(cplx<R>* __restrict__ Vb, long long bstride,
+                                                          cplx<R>* __restrict__ w, long long n, GmresState S, int j,
+                                                          const int* __restrict__ jdev, double tol, int final_done) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+  __shared__ double2 pA[AC_MAXK], pB[AC_MAXK];  // this CTA's partial sums (read by the whole cluster)
+  __shared__ double pN;
+  __shared__ double2 h1s[AC_MAXK], hcol[AC_MAXK];
+  __shared__ double2 scr[(AC_T / 32) * 8];
+  __shared__ double dscr[AC_T / 32];
+  if (jdev) j = *jdev;
+  const int k = j + 1;
+  const bool act = S.active[0] != 0;  // before this step (CTA 0 may change it below)
+  const long long per = (n + C - 1) / C;
+  const long long e0 = (long long)crank * per, e1 = e0 + per < n ? e0 + per : n;
+  // pass 1: <V_i, w>
+  for (int i0 = 0; i0 < k; i0 += 8) {
+    cplx<R> acc[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) acc[g] = czero<R>();
+    for (long long e = e0 + threadIdx.x; e < e1; e += AC_T) {
+      const cplx<R> x = w[e];
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (i0 + g < k) cjmac(acc[g], Vb[(i0 + g) * bstride + e], x);
+    }
+    ac_reduce8<R>(acc, scr, pA, i0, k);
+  }
+  cl.sync();
+  for (int i = threadIdx.x; i < k; i += AC_T) {
+    double2 t = make_double2(0, 0);
+    for (int c = 0; c < C; ++c) t += cl.map_shared_rank(pA, c)[i];
+    h1s[i] = t;
+  }
+  __syncthreads();
+  // w -= V h1, then pass 2: <V_i, w>  (each thread revisits only its own elements)
+  for (long long e = e0 + threadIdx.x; e < e1; e += AC_T) {
+    cplx<R> x = w[e];
+    for (int i = 0; i < k; ++i) {
+      const double2 h = h1s[i];
+      cnmac(x, cmk(R(h.x), R(h.y)), Vb[i * bstride + e]);
+    }
+    w[e] = x;
+  }
+  for (int i0 = 0; i0 < k; i0 += 8) {
+    cplx<R> acc[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) acc[g] = czero<R>();
+    for (long long e = e0 + threadIdx.x; e < e1; e += AC_T) {
+      const cplx<R> x = w[e];
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (i0 + g < k) cjmac(acc[g], Vb[(i0 + g) * bstride + e], x);
+    }
+    ac_reduce8<R>(acc, scr, pB, i0, k);
+  }
+  cl.sync();
+  for (int i = threadIdx.x; i < k; i += AC_T) {
+    double2 t = make_double2(0, 0);
+    for (int c = 0; c < C; ++c) t += cl.map_shared_rank(pB, c)[i];
+    hcol[i] = h1s[i] + t;
+    h1s[i] = t;  // h2
+  }
+  __syncthreads();
+  // w -= V h2 and ||w||^2
+  R nn = 0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += AC_T) {
+    cplx<R> x = w[e];
+    for (int i = 0; i < k; ++i) {
+      const double2 h = h1s[i];
+      cnmac(x, cmk(R(h.x), R(h.y)), Vb[i * bstride + e]);
+    }
+    w[e] = x;
+    nn += cnorm2(x);
+  }
+  {
+    const R v[1] = {nn};
+    double red[1];
+    block_sum_mixed<R, 1>(v, dscr, red);
+    if (threadIdx.x == 0) pN = red[0];
+  }
+  cl.sync();
+  double hn2 = 0.0;
+  for (int c = 0; c < C; ++c) hn2 += *cl.map_shared_rank(&pN, c);
+  // V_{j+1} = w / ||w|| and, on one thread, the Givens update of column j
+  const double h = sqrt(hn2);
+  const R inv = (R)(act && h > 0.0 ? 1.0 / h : 0.0);
+  cplx<R>* vn = Vb + (long long)(j + 1) * bstride;
+  for (long long e = e0 + threadIdx.x; e < e1; e += AC_T) vn[e] = inv * w[e];
+  if (crank == 0 && threadIdx.x == 0 && act) gmres_column(S, 0, j, hcol, hn2, tol, final_done);
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+static int arnoldi_cluster_size() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  cached = 0;
+  for (int C : {16, 8}) {
+    auto kern = k_arnoldi_cluster<float>;
+    if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(AC_T);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0) {
+      cached = C;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return cached;
+}
+
+bool arnoldi_fused_ok(long long n, int nrhs, int m) {
+  return nrhs == 1 && m + 1 <= AC_MAXK && n <= (1LL << 20) && arnoldi_cluster_size() > 0;
+}
+
+template <typename R>
+void launch_arnoldi_fused(cplx<R>* Vb, long long bstride, cplx<R>* w, long long n, const GmresState& S, int j,
+                          const int* jdev, double tol, int final_done, cudaStream_t st) {
+  const int C = arnoldi_cluster_size();
+  if (C <= 0) throw Error(-1, "no thread-block cluster available for the fused Arnoldi step");
+  auto kern = k_arnoldi_cluster<R>;
+  if (C > 8) WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(AC_T);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  WCMG_CUDA(cudaLaunchKernelEx(&cfg, kern, Vb, bstride, w, n, S, j, jdev, tol, final_done));
+  WCMG_LAUNCH_CHECK();
+}
+template void launch_arnoldi_fused<float>(float2*, long long, float2*, long long, const GmresState&, int, const int*,
+                                          double, int, cudaStream_t);
+template void launch_arnoldi_fused<double>(double2*, long long, double2*, long long, const GmresState&, int,
+                                           const int*, double, int, cudaStream_t);
 
 __global__ void k_gmres_solve_y(GmresState S, int nrhs) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;

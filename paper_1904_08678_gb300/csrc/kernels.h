@@ -155,6 +155,14 @@ struct GmresState {
 // h column j is in H (entries 0..j from multidot); hnorm holds ||w||.
 // h1, h2: the two CGS passes' coefficients [nrhs][m+1]; hnorm2 = ||w||^2 after both.
 // `final_done`: a recurrence convergence also marks the rhs done (no true-residual check).
+// One fused Arnoldi step after the operator application, for one short rhs
+// (n <= 2^20, restart <= 64): CGS2 projections of w against V_0..V_j, the norm,
+// the Givens update of Hessenberg column j and V_{j+1} = w / ||w||, in one launch
+// of a thread-block cluster (16 CTAs, else 8).  jdev (nullable): step on the device.
+bool arnoldi_fused_ok(long long n, int nrhs, int m);
+template <typename R>
+void launch_arnoldi_fused(cplx<R>* Vb, long long bstride, cplx<R>* w, long long n, const GmresState& S, int j,
+                          const int* jdev, double tol, int final_done, cudaStream_t st);
 // jdev (nullable, device): the step number is *jdev instead of j.
 void launch_gmres_step(const GmresState& s, int j, const double2* h1, const double2* h2, const double* hnorm2,
                        double tol, int final_done, int nrhs, double* inv_h, cudaStream_t st,

@@ -638,17 +638,22 @@ static KrylovOut fgmres(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nr
         cycle<R>(c, l, z, vj, nrhs);
       }
       apply_op<R>(c, l, w, z, nrhs);
-      KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multidot<R>(SC.h1(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
-      KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multiaxpy<R>(w, Vb, bstride, j + 1, SC.h1(), ldh, -1.0, n, nrhs, c->st));
-      KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multidot<R>(SC.h2(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
-      KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
-            launch_multiaxpy<R>(w, Vb, bstride, j + 1, SC.h2(), ldh, -1.0, n, nrhs, c->st));
-      norm2_op<R>(c, SC.slot(0), w, n, nrhs);
-      launch_gmres_step(S, j, SC.h1(), SC.h2(), SC.slot(0), tol, verify ? 0 : 1, nrhs, SC.slot(3), c->st);
-      launch_scale_dev<R>(Vb + (long long)(j + 1) * bstride, w, SC.slot(3), 0, n, nrhs, c->st);
+      if (arnoldi_fused_ok(n, nrhs, m)) {
+        KPROF(c, WCMG_K_KRYLOV, (4.0 * (j + 1) + 6.0) * n * sizeof(cplx<R>), 32.0 * (j + 1) * n,
+              launch_arnoldi_fused<R>(Vb, bstride, w, n, S, j, nullptr, tol, verify ? 0 : 1, c->st));
+      } else {
+        KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+              launch_multidot<R>(SC.h1(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
+        KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+              launch_multiaxpy<R>(w, Vb, bstride, j + 1, SC.h1(), ldh, -1.0, n, nrhs, c->st));
+        KPROF(c, WCMG_K_KRYLOV, (double)(j + 2) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+              launch_multidot<R>(SC.h2(), Vb, bstride, j + 1, ldh, w, n, nrhs, c->partial.p, c->st));
+        KPROF(c, WCMG_K_KRYLOV, (double)(j + 3) * n * nrhs * sizeof(cplx<R>), 8.0 * (j + 1) * n * nrhs,
+              launch_multiaxpy<R>(w, Vb, bstride, j + 1, SC.h2(), ldh, -1.0, n, nrhs, c->st));
+        norm2_op<R>(c, SC.slot(0), w, n, nrhs);
+        launch_gmres_step(S, j, SC.h1(), SC.h2(), SC.slot(0), tol, verify ? 0 : 1, nrhs, SC.slot(3), c->st);
+        launch_scale_dev<R>(Vb + (long long)(j + 1) * bstride, w, SC.slot(3), 0, n, nrhs, c->st);
+      }
       ++steps;
       ++out.iterations;
       if (precond && l == 0 && c->learned_on && c->coarse_mode == WCMG_COARSE_LEARNED) {
@@ -819,18 +824,23 @@ static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs,
         z = zcur;
       }
       apply_op<R>(c, l, w, z, nrhs);
-      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multidot<R>(SC.h1(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
-      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multiaxpy<R>(w, Vb, bstride, m, SC.h1(), ldh, -1.0, n, nrhs, c->st, jd, 1));
-      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multidot<R>(SC.h2(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
-      KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
-            launch_multiaxpy<R>(w, Vb, bstride, m, SC.h2(), ldh, -1.0, n, nrhs, c->st, jd, 1));
-      norm2_op<R>(c, SC.slot(0), w, n, nrhs);
-      launch_gmres_step(S, 0, SC.h1(), SC.h2(), SC.slot(0), tol, verify ? 0 : 1, nrhs, SC.slot(3), c->st,
-                        jd);
-      launch_scale_dev<R>(Vb, w, SC.slot(3), 0, n, nrhs, c->st, jd, 1, bstride);  // V_{j+1}
+      if (arnoldi_fused_ok(n, nrhs, m)) {
+        KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+              launch_arnoldi_fused<R>(Vb, bstride, w, n, S, 0, jd, tol, verify ? 0 : 1, c->st));
+      } else {
+        KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+              launch_multidot<R>(SC.h1(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
+        KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+              launch_multiaxpy<R>(w, Vb, bstride, m, SC.h1(), ldh, -1.0, n, nrhs, c->st, jd, 1));
+        KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+              launch_multidot<R>(SC.h2(), Vb, bstride, m, ldh, w, n, nrhs, c->partial.p, c->st, jd, 1));
+        KPROF(c, WCMG_K_KRYLOV, 0.0, 0.0,
+              launch_multiaxpy<R>(w, Vb, bstride, m, SC.h2(), ldh, -1.0, n, nrhs, c->st, jd, 1));
+        norm2_op<R>(c, SC.slot(0), w, n, nrhs);
+        launch_gmres_step(S, 0, SC.h1(), SC.h2(), SC.slot(0), tol, verify ? 0 : 1, nrhs, SC.slot(3), c->st,
+                          jd);
+        launch_scale_dev<R>(Vb, w, SC.slot(3), 0, n, nrhs, c->st, jd, 1, bstride);  // V_{j+1}
+      }
       launch_kctl_step_end(K, S.active, nrhs, m, acc, body_count(c, slot), h_arn, c->st);
     });
     launch_gmres_solve_y(S, nrhs, c->st);
