@@ -243,7 +243,8 @@ def params(wcmg, cfg, inner, links, profile=0, graphs=0, autotune=1):
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
                             n_levels=len(cfg["blocks"]) + 1, max_rhs=cfg.get("nrhs", 1), profile=profile,
                             use_graphs=graphs, autotune=autotune,
-                            smoother={"mr": wcmg.SMOOTHER_MR, "gmres": wcmg.SMOOTHER_GMRES}[cfg.get("smoother", "mr")])
+                            smoother={"mr": wcmg.SMOOTHER_MR, "gmres": wcmg.SMOOTHER_GMRES}[cfg.get("smoother", "mr")],
+                            kcycle=int(cfg.get("kcycle", 0)))
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -270,6 +271,9 @@ def run_gpu(args, rank, world, local):
     cfg = dict(WORKLOADS[args.workload])
     if args.nrhs:
         cfg["nrhs"] = args.nrhs
+    if args.kcycle:
+        cfg["kcycle"] = 1
+        cfg["workload"] = cfg["workload"] + ", K-cycle (FGMRES(5) to 0.1 on the intermediate levels)"
     nrhs = cfg.get("nrhs", 1)
     U, iv, b = make_inputs(cfg)
     Ud = torch.from_numpy(U).to(dev)
@@ -858,6 +862,7 @@ def main(argv=None):
                     help="1: each solve replays one captured CUDA graph; 0: host-driven solve")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1: coarse-apply launch shapes picked by the autotuner; 0: fixed rule")
+    ap.add_argument("--kcycle", action="store_true", help="K-cycle on the intermediate levels (3-level workloads)")
     ap.add_argument("--pools", type=int, default=417,
                     help="c5: training pools of 48 fresh pairs (417 pools = 20016 pairs)")
     ap.add_argument("--ncu-region", action="store_true",

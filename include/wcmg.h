@@ -97,6 +97,12 @@ typedef struct wcmg_params {
                                            WCMG_SMOOTHER_GMRES: GMRES with smoother_steps steps,
                                            zero guess, no restart (Sec. 4 comparison runs).  The
                                            same smoother serves the cycle and the setup sweeps. */
+  int kcycle;                           /* 0: V-cycle (one cycle of an intermediate level as its
+                                           coarse solve); 1: K-cycle: FGMRES(kcycle_steps) to
+                                           kcycle_tol, right-preconditioned by the level's cycle,
+                                           on every level between the finest and the coarsest */
+  int kcycle_steps;                     /* 1 .. 64 */
+  double kcycle_tol;                    /* relative residual of the intermediate FGMRES */
 } wcmg_params;
 
 typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1 } wcmg_smoother;

@@ -13,6 +13,9 @@ Readings used here (each listed with the other readings of the paper):
   cycle  M_l(r):  e = P_l CoarseSolve_{l+1}(P_l^dag r);  e += S_k(D_l; r - D_l e);
          S_k is the smoother: MR_k, or GMRES with k steps (zero initial guess, no
          restart, no tolerance), the same smoother in the setup sweeps;
+         on an intermediate level (neither finest nor coarsest) CoarseSolve is one
+         cycle of that level (V-cycle) or, with kcycle, FGMRES(kcycle_steps) to
+         kcycle_tol right-preconditioned by that level's cycle (K-cycle);
          no pre-smoothing.  CoarseSolve is GMRES(m) with a relative tolerance at the
          coarsest level and one application of M_{l+1} (V-cycle) in between.
   initial setup on level l: for each sweep, for each i:
@@ -48,6 +51,9 @@ class MGParams:
     outer_tol: float = 1e-10
     outer_maxiter: int = 1000
     smoother: str = "mr"                     # "mr" or "gmres"
+    kcycle: bool = False                     # intermediate levels: FGMRES around the cycle
+    kcycle_steps: int = 5
+    kcycle_tol: float = 0.1
 
 
 @dataclass
@@ -121,10 +127,15 @@ class Multigrid:
 
     # ---------------- solve ----------------
     def coarse_solve(self, l, r):
-        """Solve on level l (l >= 1): GMRES at the coarsest level, else one cycle."""
+        """Solve on level l (l >= 1): GMRES at the coarsest level, else one cycle
+        (V-cycle) or a short FGMRES preconditioned by the cycle (K-cycle)."""
         if l == self.nlevels - 1:
             x, _ = gmres(self.levels[l].op, r, restart=self.p.coarse_restart,
                          tol=self.p.coarse_tol, maxiter=self.p.coarse_maxiter)
+            return x
+        if self.p.kcycle:
+            x, _ = fgmres(self.levels[l].op, r, lambda v: self.cycle(l, v), restart=self.p.kcycle_steps,
+                          tol=self.p.kcycle_tol, maxiter=self.p.kcycle_steps)
             return x
         return self.cycle(l, r)
 

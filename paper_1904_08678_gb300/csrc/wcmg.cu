@@ -972,6 +972,14 @@ static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
                                 c->p.coarse_maxiter, !x0, false, false);
         c->coarse_its += k.iterations;
       }
+    } else if (c->p.kcycle) {
+      // K-cycle: a short FGMRES on the intermediate level, preconditioned by its cycle
+      const int ks = c->p.kcycle_steps;
+      if (c->capturing)
+        fgmres_g<R>(c, l + 1, ec, rc, nrhs, ks, c->p.kcycle_tol, ks, true, false, true, 1, c->kctl.p + 2 + (l + 1),
+                    nullptr, 0, nullptr);
+      else
+        fgmres<R>(c, l + 1, ec, rc, nrhs, ks, c->p.kcycle_tol, ks, true, false, true, 1);
     } else {
       cycle<R>(c, l + 1, ec, rc, nrhs);
     }
@@ -1263,12 +1271,20 @@ static void graph_prepare(wcmg_ctx* c, int nrhs) {
     ws<double>(c->L[0], "fg_zc", nrhs);
     ws<double>(c->L[lc], "gm_vc", nrhs);
     for (int l = 0; gsm && l < lc; ++l) ws<double>(c->L[l], "gm_vc", nrhs);
+    for (int l = 1; c->p.kcycle && l < lc; ++l) {
+      ws<double>(c->L[l], "fg_vc", nrhs);
+      ws<double>(c->L[l], "fg_zc", nrhs);
+    }
     return;
   }
   ws<float>(c->L[0], "fg_vc", nrhs);
   ws<float>(c->L[0], "fg_zc", nrhs);
   ws<float>(c->L[lc], "gm_vc", nrhs);
   for (int l = 0; gsm && l < lc; ++l) ws<float>(c->L[l], "gm_vc", nrhs);
+  for (int l = 1; c->p.kcycle && l < lc; ++l) {
+    ws<float>(c->L[l], "fg_vc", nrhs);
+    ws<float>(c->L[l], "fg_zc", nrhs);
+  }
   for (int l = 0; l + 1 < c->p.n_levels; ++l) Prec<float>::vecs(c, c->L[l]);
   for (int l = 1; l < c->p.n_levels; ++l) {
     Level& L = c->L[l];
@@ -1648,6 +1664,9 @@ int wcmg_default_params(wcmg_params* p) {
   p->use_graphs = 0;
   p->autotune = 0;
   p->smoother = WCMG_SMOOTHER_MR;
+  p->kcycle = 0;
+  p->kcycle_steps = 5;
+  p->kcycle_tol = 0.1;
   return WCMG_OK;
 }
 
@@ -1673,6 +1692,8 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       throw Error(WCMG_ERR_ARG, "smoother must be WCMG_SMOOTHER_MR or WCMG_SMOOTHER_GMRES");
     if (p->smoother == WCMG_SMOOTHER_GMRES && p->smoother_steps > 64)
       throw Error(WCMG_ERR_ARG, "GMRES smoother: at most 64 steps");
+    if ((p->kcycle != 0 && p->kcycle != 1) || p->kcycle_steps < 1 || p->kcycle_steps > 64 || !(p->kcycle_tol >= 0.0))
+      throw Error(WCMG_ERR_ARG, "kcycle must be 0 or 1, kcycle_steps 1..64, kcycle_tol >= 0");
     c->L.resize(nl);
     int dims[4];
     for (int k = 0; k < 4; ++k) dims[k] = p->dims[k];

@@ -62,6 +62,9 @@ class wcmg_params(ctypes.Structure):
         ("use_graphs", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("smoother", ctypes.c_int),
+        ("kcycle", ctypes.c_int),
+        ("kcycle_steps", ctypes.c_int),
+        ("kcycle_tol", ctypes.c_double),
     ]
 
 

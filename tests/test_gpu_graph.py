@@ -56,10 +56,11 @@ def test_graph_replay_matches_host_driven(lib, prec, smoother):
         assert abs(runs[2][0].outer_iterations - info.iterations) <= 1
 
 
-def test_graph_replay_three_levels(lib):
+@pytest.mark.parametrize("kcycle", [0, 1], ids=["vcycle", "kcycle"])
+def test_graph_replay_three_levels(lib, kcycle):
     dims = (8, 8, 8, 8)
     kw = dict(dims=dims, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvec=[6, 4], n_levels=3, m0=-0.1, csw=1.0,
-              inner_prec=1, setup_refine_sweeps=1)
+              inner_prec=1, setup_refine_sweeps=1, kcycle=kcycle)
     U = inputs.random_gauge(dims, 0.3, 1003)
     iv = np.concatenate([inputs.setup_vectors(dims, 12, 6, 0, 1003).ravel(),
                          inputs.setup_vectors((4, 4, 4, 4), 12, 4, 1, 1003).ravel()])

@@ -216,3 +216,32 @@ def test_gmres_smoother_setup_cycle_and_solve_match_oracle(lib):
     assert st.converged and st.true_residual <= 1e-10
     assert rel(host(x)[0].reshape(V, 12), xo.reshape(V, 12)) < 1e-8
     assert abs(st.outer_iterations - info.iterations) <= 1
+
+
+@pytest.mark.parametrize("kcycle", [0, 1], ids=["vcycle", "kcycle"])
+def test_three_level_cycles_match_oracle(lib, kcycle):
+    """Three levels with the V-cycle (one cycle of level 1 as its coarse solve) and the
+    K-cycle (FGMRES(5) to 0.1 around the level-1 cycle): cycle output and solve vs the oracle."""
+    dims, b0, b1 = (8, 8, 8, 8), (2, 2, 2, 2), (2, 2, 2, 2)
+    p = lib.default_params(dims=dims, blocks=[b0, b1], nvec=[6, 4], n_levels=3, m0=-0.1, csw=1.0, kcycle=kcycle)
+    ctx = lib.Context(p)
+    U = inputs.random_gauge(dims, 0.3, 1003)
+    ctx.set_gauge(dev(U))
+    iv0 = inputs.setup_vectors(dims, 12, 6, 0, 1003)
+    iv1 = inputs.setup_vectors((4, 4, 4, 4), 12, 4, 1, 1003)
+    ctx.setup(dev(np.concatenate([iv0.ravel(), iv1.ravel()])))
+    D = WilsonClover(U, dims, -0.1, 1.0)
+    mg = Multigrid(D, MGParams(blocks=[b0, b1], nvecs=[6, 4], kcycle=bool(kcycle)),
+                   [fields(iv0, dims, 12), fields(iv1, (4, 4, 4, 4), 12)])
+    V = 4096
+    r = inputs.complex_gaussian(32, 0, (1, V, 12))
+    e = dev(np.zeros_like(r))
+    ctx.mg_cycle(dev(r), e)
+    assert rel(host(e)[0], mg.cycle(0, fields(r, dims, 12)[0]).reshape(V, 12)) < 1e-9
+    b = inputs.source(dims, 0)
+    x = dev(np.zeros_like(b))
+    st = ctx.solve(dev(b), x)
+    xo, info = mg.solve(fields(b, dims, 12)[0])
+    assert st.converged and st.true_residual <= 1e-10
+    assert rel(host(x)[0].reshape(V, 12), xo.reshape(V, 12)) < 1e-8
+    assert abs(st.outer_iterations - info.iterations) <= 1

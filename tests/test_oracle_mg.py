@@ -104,3 +104,42 @@ def test_gmres_smoother_solve_converges_to_the_dense_solution():
     assert info.converged and info.true_residual <= 1e-10
     x_ref, _ = gmres(D, b, restart=60, tol=1e-13, maxiter=5000, verify=True)
     assert rel(x, x_ref) < 1e-8
+
+
+def three_level_parts(kcycle, steps=5, tol=0.1):
+    dims = (8, 8, 8, 8)
+    U = inputs.random_gauge(dims, 0.3, 1003)
+    D = WilsonClover(U, dims, -0.1, 1.0)
+    iv0 = [to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 6, 0, 1003)]
+    iv1 = [to_grid(v, (4, 4, 4, 4)) for v in inputs.setup_vectors((4, 4, 4, 4), 12, 4, 1, 1003)]
+    p = MGParams(blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvecs=[6, 4], kcycle=kcycle, kcycle_steps=steps, kcycle_tol=tol)
+    return dims, D, iv0, iv1, Multigrid(D, p, [iv0, iv1])
+
+
+@pytest.mark.slow
+def test_kcycle_with_exact_inner_solve_is_the_two_level_cycle_with_exact_coarse_solve():
+    """With its FGMRES run to 1e-13 the K-cycle's intermediate solve is D_1^-1, so the
+    three-level K-cycle equals the two-level cycle (same P_0) whose coarse GMRES is
+    exact; the V-cycle (one cycle of level 1) does not."""
+    dims, D, iv0, iv1, mgk = three_level_parts(True, steps=120, tol=1e-13)
+    mg2 = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[6], coarse_restart=120, coarse_tol=1e-13,
+                                coarse_maxiter=3000), [iv0])
+    _, _, _, _, mgv = three_level_parts(False)
+    V = int(np.prod(dims))
+    r = to_grid(inputs.complex_gaussian(31, 0, (1, V, 12))[0], dims)
+    ek, e2, ev = mgk.cycle(0, r), mg2.cycle(0, r), mgv.cycle(0, r)
+    assert rel(ek, e2) < 1e-9
+    assert rel(ev, e2) > 1e4 * max(rel(ek, e2), 1e-16)  # one V-cycle is far from the exact coarse solve
+
+
+@pytest.mark.slow
+def test_kcycle_solve_needs_no_more_iterations_than_the_vcycle():
+    dims, D, iv0, iv1, mgk = three_level_parts(True)
+    _, _, _, _, mgv = three_level_parts(False)
+    V = int(np.prod(dims))
+    b = to_grid(inputs.source(dims, 0)[0].reshape(V, 12), dims)
+    xk, ik = mgk.solve(b)
+    xv, iv = mgv.solve(b)
+    assert ik.converged and iv.converged and ik.true_residual <= 1e-10
+    assert ik.iterations <= iv.iterations
+    assert rel(xk, xv) < 1e-8
