@@ -711,7 +711,9 @@ def measure_uneven_batch(wcmg, torch, dev, stream, flush, args, reps=5):
 
 
 def measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg, reps=200):
-    """K4 alone: 1 rhs on the workload's coarse operator, L2 flushed before each apply."""
+    """K4 alone: 1 rhs on the workload's coarse operator, L2 flushed before each apply;
+    once with the launch shape the autotuner chose for the solve (links partly
+    L2-resident) and once with the shape it picks for streamed links (cold mode)."""
     nb = 2 * cfg["nvec"][0]
     cd = [L // b for L, b in zip(cfg["dims"], cfg["blocks"][0])]
     Vc = int(np.prod(cd))
@@ -720,24 +722,38 @@ def measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg, reps
     out = torch.zeros_like(phi)
     ctx.set_profile(1 << KCLASS.index("coarse"))
     prec = wcmg.F32 if ctx.params.inner_prec == wcmg.F32 else wcmg.F64
-    for _ in range(5):
-        ctx.apply_coarse(1, phi, out, prec=prec, stream=stream)
-    k0 = ctx.kstats()["coarse"]
-    for _ in range(reps):
-        flush.fill_(5)
-        ctx.apply_coarse(1, phi, out, prec=prec, stream=stream)
-    torch.cuda.synchronize()
-    k1 = ctx.kstats()["coarse"]
-    n = k1["launches"] - k0["launches"]
-    kms = (k1["ms"] - k0["ms"]) / max(n, 1)
-    kbytes = (k1["bytes"] - k0["bytes"]) / max(n, 1)
     link_b = {"f32": 8, "bf16": 4, "f16": 4}[{wcmg.F32: "f32", wcmg.BF16: "bf16", wcmg.F16: "f16"}.get(
         ctx.params.coarse_link_prec, "f32")] if prec == wcmg.F32 else 16
     vec_b = 8 if prec == wcmg.F32 else 16
     algo = Vc * (9 * nb * nb * link_b + 2 * nb * vec_b)
-    return {"sites": Vc, "nbasis": nb, "link_bytes": link_b, "algorithmic_bytes": algo, "launches": n,
-            "kernel_us": round(kms * 1e3, 2), "GB/s": round(kbytes / (kms * 1e-3) / 1e9, 1),
-            "frac_of_hbm": round(kbytes / (kms * 1e-3) / 1e9 / hbm, 4), "l2": "flushed before every apply"}
+
+    def run():
+        for _ in range(5):
+            ctx.apply_coarse(1, phi, out, prec=prec, stream=stream)
+        k0 = ctx.kstats()["coarse"]
+        for _ in range(reps):
+            flush.fill_(5)
+            ctx.apply_coarse(1, phi, out, prec=prec, stream=stream)
+        torch.cuda.synchronize()
+        k1 = ctx.kstats()["coarse"]
+        n = k1["launches"] - k0["launches"]
+        kms = (k1["ms"] - k0["ms"]) / max(n, 1)
+        kbytes = (k1["bytes"] - k0["bytes"]) / max(n, 1)
+        t = ctx.get_coarse_tile(1, 1, prec)
+        return {"launches": n, "kernel_us": round(kms * 1e3, 2), "GB/s": round(kbytes / (kms * 1e-3) / 1e9, 1),
+                "frac_of_hbm": round(kbytes / (kms * 1e-3) / 1e9 / hbm, 4),
+                "tile": {k: t[k] for k in ("kind", "rhs_per_cta", "parts", "threads", "ntile")}}
+
+    warm = run()
+    saved = ctx.get_coarse_tile(1, 1, prec)
+    ctx.tune_coarse(1, 1, prec, cold=1, stream=stream)
+    cold = run()
+    ctx.set_coarse_tile(1, 1, prec, kind=saved["kind"], rhs_per_cta=saved["rhs_per_cta"], parts=saved["parts"],
+                        threads=saved["threads"], ntile=saved["ntile"])
+    best = cold if cold["kernel_us"] <= warm["kernel_us"] else warm
+    return {"sites": Vc, "nbasis": nb, "link_bytes": link_b, "algorithmic_bytes": algo, "l2": "flushed before every apply",
+            "kernel_us": best["kernel_us"], "GB/s": best["GB/s"], "frac_of_hbm": best["frac_of_hbm"],
+            "shape_tuned_for_solve": warm, "shape_tuned_for_streaming": cold}
 
 
 # ---------------------------------------------------------------- oracle

@@ -242,10 +242,12 @@ typedef struct wcmg_tile {
 int wcmg_get_coarse_tile(wcmg_ctx* ctx, int level, int nrhs, int prec, wcmg_tile* out);
 
 /* Run the autotuner now for (level, nrhs, prec): every candidate shape is timed
- * with CUDA events on the level's own links (10 back-to-back applies after 2
- * warm-up applies, on `stream`) and the fastest is kept for later applies.
- * Synchronises `stream`. */
-int wcmg_tune_coarse(wcmg_ctx* ctx, int level, int nrhs, int prec, void* stream, wcmg_tile* out);
+ * with CUDA events on the level's own links and the fastest is kept for later
+ * applies.  cold = 0: 10 back-to-back applies after 2 warm-up applies (links
+ * partly L2-resident, as inside a Krylov loop; the mode of params.autotune);
+ * cold = 1: the median of 9 single applies, each after a 256 MiB scratch write
+ * that evicts L2 (links streamed from HBM).  Synchronises `stream`. */
+int wcmg_tune_coarse(wcmg_ctx* ctx, int level, int nrhs, int prec, int cold, void* stream, wcmg_tile* out);
 
 /* Force a tile for (level, nrhs, prec); t->kind = -1 clears it (back to the
  * fixed rule, or the autotuner when params.autotune = 1).  ERR_ARG if the shape

@@ -210,6 +210,7 @@ struct wcmg_ctx {
   bool have_gauge = false;
   DevBuf<double2> partial;
   DevBuf<double> partial_d;
+  DevBuf<unsigned char> l2flush;  // scratch written to evict L2 (cold autotuning)
   DevBuf<double2> mr_pr;   // per-CTA partials of the fused MR Dslash
   DevBuf<double> mr_pp;
   DevBuf<unsigned char> stage[3];
@@ -387,13 +388,18 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
 
 // Time every candidate on the level's own links (back-to-back applies, as in a
 // Krylov loop) and keep the fastest; the fixed rule is timed too.
+// cold: the links start in HBM for every timed apply (L2 overwritten by a 256 MiB
+// scratch write before it; median of 9 single applies) -- the streaming case;
+// otherwise 10 back-to-back applies, as inside a Krylov loop.
 template <typename R, typename Lt>
-static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs, int lk) {
+static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs, int lk, bool cold = false) {
   Level& L = c->L[l];
   const int nb = L.nc;
   cplx<R>* in = ws<R>(L, "tune_in", nrhs);
   cplx<R>* out = ws<R>(L, "tune_out", nrhs);
   launch_fill_zero<R>(in, L.n() * nrhs, c->st);
+  const size_t flush_bytes = (size_t)256 << 20;
+  if (cold) c->l2flush.ensure(flush_bytes);
   cudaEvent_t e0, e1;
   WCMG_CUDA(cudaEventCreate(&e0));
   WCMG_CUDA(cudaEventCreate(&e1));
@@ -401,6 +407,19 @@ static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs
   auto time_one = [&](const CoarseTile* t) -> double {
     for (int i = 0; i < 2; ++i)
       launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
+    if (cold) {
+      std::vector<float> ms(9);
+      for (int i = 0; i < 9; ++i) {
+        WCMG_CUDA(cudaMemsetAsync(c->l2flush.p, i & 0xFF, flush_bytes, c->st));
+        WCMG_CUDA(cudaEventRecord(e0, c->st));
+        launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
+        WCMG_CUDA(cudaEventRecord(e1, c->st));
+        WCMG_CUDA(cudaEventSynchronize(e1));
+        WCMG_CUDA(cudaEventElapsedTime(&ms[i], e0, e1));
+      }
+      std::sort(ms.begin(), ms.end());
+      return 1e3 * ms[4];
+    }
     WCMG_CUDA(cudaEventRecord(e0, c->st));
     for (int i = 0; i < reps; ++i)
       launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
@@ -2330,17 +2349,18 @@ int wcmg_get_coarse_tile(wcmg_ctx* c, int level, int nrhs, int prec, wcmg_tile* 
   API_END(c)
 }
 
-int wcmg_tune_coarse(wcmg_ctx* c, int level, int nrhs, int prec, void* stream, wcmg_tile* out) {
+int wcmg_tune_coarse(wcmg_ctx* c, int level, int nrhs, int prec, int cold, void* stream, wcmg_tile* out) {
   API_BEGIN(c)
   c->st = (cudaStream_t)stream;
   check_level(c, level, 1, c->p.n_levels - 1);
   check_rhs(c, nrhs);
+  if (cold != 0 && cold != 1) throw Error(WCMG_ERR_ARG, "cold must be 0 or 1");
   Level& L = c->L[level];
   const int lk = link_kind_for(c, level, prec);
   Level::TileInfo ti;
-  if (lk == 0) ti = tune_coarse<double, double2>(c, level, L.L64.p, nrhs, 0);
-  else if (lk == 2) ti = tune_coarse<float, bf16c>(c, level, L.Lbf.p, nrhs, 2);
-  else if (lk == 3) ti = tune_coarse<float, f16c>(c, level, L.Lh.p, nrhs, 3);
+  if (lk == 0) ti = tune_coarse<double, double2>(c, level, L.L64.p, nrhs, 0, cold);
+  else if (lk == 2) ti = tune_coarse<float, bf16c>(c, level, L.Lbf.p, nrhs, 2, cold);
+  else if (lk == 3) ti = tune_coarse<float, f16c>(c, level, L.Lh.p, nrhs, 3, cold);
   else {
     if (!L.L32_valid) {
       const long long n = (long long)L.g.V * L.nc * links_ld(L.nc);
@@ -2348,7 +2368,7 @@ int wcmg_tune_coarse(wcmg_ctx* c, int level, int nrhs, int prec, void* stream, w
       launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
       L.L32_valid = true;
     }
-    ti = tune_coarse<float, float2>(c, level, L.L32.p, nrhs, 1);
+    ti = tune_coarse<float, float2>(c, level, L.L32.p, nrhs, 1, cold);
   }
   L.tiles[{nrhs, lk}] = ti;
   ++graph_epoch();

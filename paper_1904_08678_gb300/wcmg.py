@@ -143,7 +143,7 @@ _SIGS = {
                           _vp, ctypes.POINTER(wcmg_stats)], _i),
     "wcmg_set_profile": ([_PCTX, _i], _i),
     "wcmg_get_coarse_tile": ([_PCTX, _i, _i, _i, ctypes.POINTER(wcmg_tile)], _i),
-    "wcmg_tune_coarse": ([_PCTX, _i, _i, _i, _vp, ctypes.POINTER(wcmg_tile)], _i),
+    "wcmg_tune_coarse": ([_PCTX, _i, _i, _i, _i, _vp, ctypes.POINTER(wcmg_tile)], _i),
     "wcmg_set_coarse_tile": ([_PCTX, _i, _i, _i, ctypes.POINTER(wcmg_tile)], _i),
     "wcmg_get_kstats": ([_PCTX, ctypes.POINTER(wcmg_kstat)], _i),
     "wcmg_block_orthonormalise_noalloc": ([_vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp], _i),
@@ -331,9 +331,9 @@ class Context:
         self._check(wcmg_get_coarse_tile(self.h, level, nrhs, prec, ctypes.byref(t)))
         return t.as_dict()
 
-    def tune_coarse(self, level, nrhs=1, prec=F32, stream=None):
+    def tune_coarse(self, level, nrhs=1, prec=F32, cold=0, stream=None):
         t = wcmg_tile()
-        self._check(wcmg_tune_coarse(self.h, level, nrhs, prec, _stream(stream), ctypes.byref(t)))
+        self._check(wcmg_tune_coarse(self.h, level, nrhs, prec, cold, _stream(stream), ctypes.byref(t)))
         return t.as_dict()
 
     def set_coarse_tile(self, level, nrhs=1, prec=F32, kind=-1, rhs_per_cta=0, parts=0, threads=0, ntile=0):

@@ -120,3 +120,18 @@ def test_invalid_tiles_are_rejected(lib):
         with pytest.raises(lib.WcmgError) as e:
             ctx.set_coarse_tile(1, nrhs, lib.F32, **t)
         assert e.value.code == lib.ERR_ARG, t
+
+
+def test_autotuner_cold_mode_times_streamed_links(lib):
+    """cold = 1: every timed apply follows an L2-evicting scratch write; the choice is
+    still a valid shape that reproduces the oracle exactly."""
+    ctx, op, rng, cd, Vc, nb = ctx_with_int_links(lib, lib.F32, lib.F32, 8)
+    t = ctx.tune_coarse(1, 1, lib.F32, cold=1)
+    assert t["source"] == 1 and t["candidates"] > 5 and 0.0 < t["us"] <= t["us_default"]
+    phi = int_phi(rng, 1, Vc, nb)
+    out = dev(np.zeros_like(phi))
+    ctx.apply_coarse(1, dev(phi), out, nrhs=1, prec=lib.F32)
+    assert np.array_equal(host(out)[0], op(fields(phi, cd, nb)[0]).reshape(Vc, nb))
+    with pytest.raises(lib.WcmgError) as e:
+        ctx.tune_coarse(1, 1, lib.F32, cold=2)
+    assert e.value.code == lib.ERR_ARG
