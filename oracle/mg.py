@@ -11,8 +11,9 @@ Sec. 2.1 describes the pieces but not the algorithmic parameters:
 
 Readings used here (each listed with the other readings of the paper):
   cycle  M_l(r):  e = P_l CoarseSolve_{l+1}(P_l^dag r);  e += S_k(D_l; r - D_l e);
-         S_k is the smoother: MR_k, or GMRES with k steps (zero initial guess, no
-         restart, no tolerance), the same smoother in the setup sweeps;
+         S_k is the smoother: MR_k, GMRES with k steps (zero initial guess, no
+         restart, no tolerance), or SAP over the level's aggregates (sap.py), the
+         same smoother in the setup sweeps;
          on an intermediate level (neither finest nor coarsest) CoarseSolve is one
          cycle of that level (V-cycle) or, with kcycle, FGMRES(kcycle_steps) to
          kcycle_tol right-preconditioned by that level's cycle (K-cycle);
@@ -34,6 +35,7 @@ from typing import List, Sequence
 
 from .aggregation import Aggregation
 from .coarse import coarsen
+from .sap import sap
 from .solvers import fgmres, gmres, mr, norm
 
 
@@ -50,7 +52,8 @@ class MGParams:
     outer_restart: int = 20
     outer_tol: float = 1e-10
     outer_maxiter: int = 1000
-    smoother: str = "mr"                     # "mr" or "gmres"
+    smoother: str = "mr"                     # "mr", "gmres" or "sap"
+    sap_cycles: int = 1                      # SAP: cycles; smoother_steps = MR steps per block solve
     kcycle: bool = False                     # intermediate levels: FGMRES around the cycle
     kcycle_steps: int = 5
     kcycle_tol: float = 0.1
@@ -78,20 +81,22 @@ class Multigrid:
         return len(self.p.blocks) + 1
 
     # ---------------- setup ----------------
-    def smooth(self, op, b):
-        """S_k(op; b) from a zero initial guess."""
-        k = self.p.smoother_steps
+    def smooth(self, l, b):
+        """S_k(D_l; b) from a zero initial guess."""
+        op, k = self.levels[l].op, self.p.smoother_steps
         if self.p.smoother == "mr":
             return mr(op, b, k)
         if self.p.smoother == "gmres":
             return gmres(op, b, restart=k, tol=0.0, maxiter=k)[0]
+        if self.p.smoother == "sap":
+            return sap(op, self.levels[l].dims, self.p.blocks[l], b, k, self.p.sap_cycles)
         raise ValueError(self.p.smoother)
 
     def _smooth_sweep(self, l):
         lev = self.levels[l]
         out = []
         for v in lev.vecs:
-            x = self.smooth(lev.op, v)
+            x = self.smooth(l, v)
             out.append(x / norm(x))
         lev.vecs = out
 
@@ -142,7 +147,7 @@ class Multigrid:
     def cycle(self, l, r):
         lev = self.levels[l]
         e = lev.agg.prolong(self.coarse_solve(l + 1, lev.agg.restrict(r)))
-        return e + self.smooth(lev.op, r - lev.op(e))
+        return e + self.smooth(l, r - lev.op(e))
 
     def solve(self, b, x0=None):
         return fgmres(self.levels[0].op, b, lambda v: self.cycle(0, v),
