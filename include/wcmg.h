@@ -95,17 +95,26 @@ typedef struct wcmg_params {
                                            level's own data and keeps the fastest. 0: fixed rule */
   int smoother;                         /* WCMG_SMOOTHER_MR: MR(smoother_steps) (Sec. 2.1);
                                            WCMG_SMOOTHER_GMRES: GMRES with smoother_steps steps,
-                                           zero guess, no restart (Sec. 4 comparison runs).  The
-                                           same smoother serves the cycle and the setup sweeps. */
+                                           zero guess, no restart (Sec. 4 comparison runs);
+                                           WCMG_SMOOTHER_SAP: Schwarz alternating procedure
+                                           (Sec. 4): sap_cycles cycles of two colour passes over
+                                           the level's aggregates (coloured by the parity of their
+                                           coarse coordinates), each pass r = b - D x on the
+                                           blocks of one colour, then smoother_steps MR steps of
+                                           the block-local operator D_B (D without the hops that
+                                           leave a block) with one step length per block, added
+                                           to x.  The same smoother serves the cycle and the
+                                           setup sweeps. */
   int kcycle;                           /* 0: V-cycle (one cycle of an intermediate level as its
                                            coarse solve); 1: K-cycle: FGMRES(kcycle_steps) to
                                            kcycle_tol, right-preconditioned by the level's cycle,
                                            on every level between the finest and the coarsest */
   int kcycle_steps;                     /* 1 .. 64 */
   double kcycle_tol;                    /* relative residual of the intermediate FGMRES */
+  int sap_cycles;                       /* SAP smoother: cycles (1 .. 16) */
 } wcmg_params;
 
-typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1 } wcmg_smoother;
+typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1, WCMG_SMOOTHER_SAP = 2 } wcmg_smoother;
 
 /* Per-kernel-class counters, filled when params.profile != 0. */
 #define WCMG_NKCLASS 12
@@ -194,7 +203,9 @@ int wcmg_setup(wcmg_ctx* ctx, const void* init_vecs, int where, void* stream, wc
 int wcmg_mg_cycle(wcmg_ctx* ctx, const void* r, void* e, int nrhs, int where, void* stream);
 
 /* Krylov solve of D_level x = b at the inner precision: kind 0 = MR(steps,
- * zero guess), kind 1 = GMRES(restart) to tol (relative to ||b||) / maxiter.
+ * zero guess), kind 1 = GMRES(restart) to tol (relative to ||b||) / maxiter,
+ * kind 2 = the SAP smoother (params.sap_cycles cycles, `steps` block-local MR
+ * steps; level < n_levels - 1, whose aggregates are the Schwarz blocks).
  * iters_out (nullable) receives the iterations of the slowest rhs. */
 int wcmg_krylov(wcmg_ctx* ctx, int level, int kind, const void* b, void* x, int nrhs,
                 int steps_or_restart, double tol, int maxiter, int where, void* stream, int* iters_out);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libwcmg.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["fine.cu", "transfer.cu", "coarse.cu", "blas.cu", "wcmg.cu", "noalloc.cu", "ptc.cu", "graph.cu"]
+SOURCES = ["fine.cu", "transfer.cu", "coarse.cu", "blas.cu", "wcmg.cu", "noalloc.cu", "ptc.cu", "graph.cu", "sap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -137,6 +137,19 @@ void launch_mask_rhs(cplx<R>* x, const int* mask, long long n, int nrhs, cudaStr
 template <typename R>
 void launch_fill_zero(cplx<R>* x, long long n, cudaStream_t st);
 
+// ---- SAP smoother (sap.cu) ----
+// Blocks are the level's aggregates (block B = sites [B bvol, (B+1) bvol)); colour[B]
+// is 0 or 1.  fine: fields component-major [nc][V], else site-major [V][nc].
+// r = colour == c ? b - Dx : 0 per element (Dx null: b - 0)
+template <typename R>
+void launch_sap_residual(cplx<R>* r, const cplx<R>* b, const cplx<R>* Dx, const unsigned char* colour, int c, int V,
+                         int nc, int bvol, bool fine, int nrhs, cudaStream_t st);
+// One block-local MR step on the blocks of colour c (p = D_B r):
+//   alpha_B = <p, r>_B / <p, p>_B (0 if <p, p>_B = 0); x += alpha_B r; r -= alpha_B p
+template <typename R>
+void launch_sap_block_mr(cplx<R>* x, cplx<R>* r, const cplx<R>* p, const unsigned char* colour, int c, int V, int nc,
+                         int bvol, bool fine, int nrhs, cudaStream_t st);
+
 // Arnoldi/Givens bookkeeping for batched (F)GMRES, one thread per rhs.
 struct GmresState {
   double2* H;      // [nrhs][m+1][m]

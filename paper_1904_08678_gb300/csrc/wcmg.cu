@@ -150,6 +150,7 @@ struct Level {
   bool L32_valid = false, low_valid = false;
   LevelScalars sc;
   LevelScalars sc_s;  // the GMRES smoother's own Krylov state (it runs inside the outer FGMRES)
+  DevBuf<unsigned char> colour;  // SAP: colour (coarse-coordinate parity) of each aggregate
   std::map<std::string, DevBuf<unsigned char>> ws;
   // coarse-apply launch shape per (nrhs, link storage): tuned or forced
   struct TileInfo {
@@ -892,10 +893,17 @@ static void fgmres_g(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs,
 // no tolerance) on the level's own Krylov state, so that it can run inside the
 // outer FGMRES on the same level.
 template <typename R>
+static void sap(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int steps, int cycles);
+
+template <typename R>
 static void smooth(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs) {
   const int k = c->p.smoother_steps;
   if (c->p.smoother == WCMG_SMOOTHER_MR || k == 0) {
     mr<R>(c, l, x, b, nrhs, k);
+    return;
+  }
+  if (c->p.smoother == WCMG_SMOOTHER_SAP) {
+    sap<R>(c, l, x, b, nrhs, k, c->p.sap_cycles);
     return;
   }
   Level& L = c->L[l];
@@ -904,6 +912,36 @@ static void smooth(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs) {
                 nullptr, &L.sc_s);
   else
     fgmres<R>(c, l, x, b, nrhs, k, 0.0, k, true, false, false, 1, &L.sc_s);
+}
+
+// SAP (Sec. 4): from x = 0, `cycles` times, for colour c = 0 then 1:
+//   r = b - D x on the blocks of colour c (0 elsewhere);
+//   `steps` block-local MR steps on D_B (D without the hops leaving a block), one
+//   step length per block, the steps added to x.
+// D_B r vanishes outside the blocks of colour c (r does), so every step needs one
+// block-interior stencil and one fused block-reduction + update kernel.
+template <typename R>
+static void sap(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int steps, int cycles) {
+  Level& L = c->L[l];
+  if (!L.colour.p) throw Error(WCMG_ERR_STATE, "SAP needs the level's aggregates");
+  const long long n = L.n();
+  cplx<R>* r = ws<R>(L, "sap_r", nrhs);
+  cplx<R>* p = ws<R>(L, "sap_p", nrhs);
+  const double s = sizeof(cplx<R>);
+  launch_fill_zero<R>(x, n * nrhs, c->st);
+  for (int cyc = 0; cyc < cycles; ++cyc)
+    for (int col = 0; col < 2; ++col) {
+      const bool x_zero = cyc == 0 && col == 0;
+      if (!x_zero) apply_op<R>(c, l, p, x, nrhs);
+      KPROF(c, WCMG_K_BLAS, (x_zero ? 1.5 : 2.0) * n * nrhs * s, 1.0 * n * nrhs,
+            launch_sap_residual<R>(r, b, x_zero ? nullptr : p, L.colour.p, col, L.g.V, L.nc, L.g.bvol, L.fine, nrhs,
+                                   c->st));
+      for (int k = 0; k < steps; ++k) {
+        apply_op<R>(c, l, p, r, nrhs, ST_BLOCK_INTERIOR);
+        KPROF(c, WCMG_K_BLAS, 2.5 * n * nrhs * s, 12.0 * n * nrhs,
+              launch_sap_block_mr<R>(x, r, p, L.colour.p, col, L.g.V, L.nc, L.g.bvol, L.fine, nrhs, c->st));
+      }
+    }
 }
 
 // ---------------- learned coarse correction (PTC network) ----------------
@@ -1686,6 +1724,7 @@ int wcmg_default_params(wcmg_params* p) {
   p->kcycle = 0;
   p->kcycle_steps = 5;
   p->kcycle_tol = 0.1;
+  p->sap_cycles = 1;
   return WCMG_OK;
 }
 
@@ -1707,8 +1746,9 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       throw Error(WCMG_ERR_ARG, "solver parameters out of range");
     if ((p->use_graphs != 0 && p->use_graphs != 1) || (p->autotune != 0 && p->autotune != 1))
       throw Error(WCMG_ERR_ARG, "use_graphs and autotune must be 0 or 1");
-    if (p->smoother != WCMG_SMOOTHER_MR && p->smoother != WCMG_SMOOTHER_GMRES)
-      throw Error(WCMG_ERR_ARG, "smoother must be WCMG_SMOOTHER_MR or WCMG_SMOOTHER_GMRES");
+    if (p->smoother != WCMG_SMOOTHER_MR && p->smoother != WCMG_SMOOTHER_GMRES && p->smoother != WCMG_SMOOTHER_SAP)
+      throw Error(WCMG_ERR_ARG, "smoother must be WCMG_SMOOTHER_MR, WCMG_SMOOTHER_GMRES or WCMG_SMOOTHER_SAP");
+    if (p->sap_cycles < 1 || p->sap_cycles > 16) throw Error(WCMG_ERR_ARG, "sap_cycles must be 1..16");
     if (p->smoother == WCMG_SMOOTHER_GMRES && p->smoother_steps > 64)
       throw Error(WCMG_ERR_ARG, "GMRES smoother: at most 64 steps");
     if ((p->kcycle != 0 && p->kcycle != 1) || p->kcycle_steps < 1 || p->kcycle_steps > 64 || !(p->kcycle_tol >= 0.0))
@@ -1774,6 +1814,18 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       G.d_nbr.ensure((size_t)8 * G.V);
       WCMG_CUDA(cudaMemcpy(G.d_perm.p, G.perm.data(), sizeof(int) * G.V, cudaMemcpyHostToDevice));
       WCMG_CUDA(cudaMemcpy(G.d_nbr.p, G.nbr.data(), sizeof(int) * 8 * G.V, cudaMemcpyHostToDevice));
+      if (l + 1 < nl) {
+        // SAP colours: aggregate B of this level is site B of the next level's storage
+        const HostGeom& Cg = c->L[l + 1].g;
+        std::vector<unsigned char> col(Cg.V);
+        for (int B = 0; B < Cg.V; ++B) {
+          int xc[4];
+          coords(Cg.perm[B], Cg.dims, xc);
+          col[B] = (unsigned char)((xc[0] + xc[1] + xc[2] + xc[3]) & 1);
+        }
+        c->L[l].colour.ensure(Cg.V);
+        WCMG_CUDA(cudaMemcpy(c->L[l].colour.p, col.data(), Cg.V, cudaMemcpyHostToDevice));
+      }
     }
     ensure_partials(c);
     for (auto& L : c->L) L.sc.ensure(max_rhs_all(c), std::max(c->p.outer_restart, c->p.coarse_restart));
@@ -2103,6 +2155,9 @@ static int krylov_ext(wcmg_ctx* c, int level, int kind, const double2* b, double
   if (kind == 0) {
     mr<R>(c, level, y, a, nrhs, sr);
     its = sr;
+  } else if (kind == 2) {
+    sap<R>(c, level, y, a, nrhs, sr, c->p.sap_cycles);
+    its = sr;
   } else {
     KrylovOut k = fgmres<R>(c, level, y, a, nrhs, sr, tol, maxiter, true, false, false);
     its = k.iterations;
@@ -2118,7 +2173,8 @@ int wcmg_krylov(wcmg_ctx* c, int level, int kind, const void* b, void* x, int nr
   c->st = (cudaStream_t)stream;
   check_level(c, level, 0, c->p.n_levels - 1);
   check_rhs(c, nrhs);
-  if (kind != 0 && kind != 1) throw Error(WCMG_ERR_ARG, "kind must be 0 (MR) or 1 (GMRES)");
+  if (kind != 0 && kind != 1 && kind != 2) throw Error(WCMG_ERR_ARG, "kind must be 0 (MR), 1 (GMRES) or 2 (SAP)");
+  if (kind == 2 && level >= c->p.n_levels - 1) throw Error(WCMG_ERR_ARG, "SAP needs a level with aggregates");
   if (steps_or_restart < 1 || steps_or_restart > 64) throw Error(WCMG_ERR_ARG, "steps/restart out of range");
   const size_t bytes = (size_t)nrhs * c->L[level].n() * 16;
   const double2* i = in_dev(c, b, bytes, where, 0);

@@ -35,7 +35,7 @@ KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen",
           "dslash64", "ptc"]
 PTC_HIDDEN, PTC_NWEIGHTS = 12, 3456
 COARSE_MG, COARSE_WARMSTART, COARSE_LEARNED = 0, 1, 2
-SMOOTHER_MR, SMOOTHER_GMRES = 0, 1
+SMOOTHER_MR, SMOOTHER_GMRES, SMOOTHER_SAP = 0, 1, 2
 
 
 class wcmg_params(ctypes.Structure):
@@ -65,6 +65,7 @@ class wcmg_params(ctypes.Structure):
         ("kcycle", ctypes.c_int),
         ("kcycle_steps", ctypes.c_int),
         ("kcycle_tol", ctypes.c_double),
+        ("sap_cycles", ctypes.c_int),
     ]
 
 

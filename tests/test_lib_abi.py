@@ -34,12 +34,13 @@ def test_graph_and_autotune_params_validated_without_gpu_work():
     p = wcmg.default_params()
     assert p.use_graphs == 0 and p.autotune == 0 and p.profile == 0 and p.max_rhs == 1
     h = ctypes.c_void_p()
-    for field, bad in (("use_graphs", 2), ("autotune", 2), ("smoother", 2), ("kcycle", 2), ("kcycle_steps", 0),
-                       ("kcycle_tol", -1.0)):
+    for field, bad in (("use_graphs", 2), ("autotune", 2), ("smoother", 3), ("kcycle", 2), ("kcycle_steps", 0),
+                       ("kcycle_tol", -1.0), ("sap_cycles", 0), ("sap_cycles", 17)):
         q = wcmg.default_params(**{field: bad})
         assert wcmg.wcmg_create(ctypes.byref(q), ctypes.byref(h)) == wcmg.ERR_ARG, field
     q = wcmg.default_params()
     assert q.kcycle == 0 and q.kcycle_steps == 5 and q.kcycle_tol == 0.1 and q.smoother == wcmg.SMOOTHER_MR
+    assert q.sap_cycles == 1 and wcmg.SMOOTHER_SAP == 2
 
 
 def test_batch_solve_rejects_empty_batch_without_gpu_work():
