@@ -268,11 +268,13 @@ __device__ __forceinline__ void applyBdag(T (&out)[2][3], const T (&v)[2][3]) {
 // One hop of the stencil for NR right-hand sides at once: the link (U_mu(x) forward,
 // U_mu(x - mu)^dag backward) is loaded once and applied to every rhs's
 // projected half spinor.
+// The neighbour spinor is read from `in` as component c at in[c * vin + yin] (the
+// field itself: vin = V, yin = the neighbour's site; a block staged in shared memory:
+// its own stride and local index); the link from U at storage site ls.
 template <typename R, int MU, bool FWD, int NR>
-__device__ __forceinline__ void hop(cplx<R> (&acc)[NR][12], const cplx<R>* __restrict__ in, long long rstride,
-                                    const cplx<R>* __restrict__ U, int V, int s, int y) {
+__device__ __forceinline__ void hop_at(cplx<R> (&acc)[NR][12], const cplx<R>* __restrict__ in, long long rstride,
+                                       int vin, int yin, const cplx<R>* __restrict__ U, int V, int ls) {
   using T = cplx<R>;
-  const int ls = FWD ? s : y;  // link U_mu(x) forward, U_mu(x - mu) backward
   T u[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) u[k] = U[((long long)MU * 9 + k) * V + ls];
@@ -284,8 +286,8 @@ __device__ __forceinline__ void hop(cplx<R> (&acc)[NR][12], const cplx<R>* __res
     for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        pu[sp][c] = iq[(long long)(3 * sp + c) * V + y];
-        pl[sp][c] = iq[(long long)(6 + 3 * sp + c) * V + y];
+        pu[sp][c] = iq[(long long)(3 * sp + c) * vin + yin];
+        pl[sp][c] = iq[(long long)(6 + 3 * sp + c) * vin + yin];
       }
     T Bpl[2][3], h[2][3];
     applyB<MU>(Bpl, pl);
@@ -317,6 +319,12 @@ __device__ __forceinline__ void hop(cplx<R> (&acc)[NR][12], const cplx<R>* __res
         else acc[q][6 + 3 * sp + c] += Bw[sp][c];
       }
   }
+}
+
+template <typename R, int MU, bool FWD, int NR>
+__device__ __forceinline__ void hop(cplx<R> (&acc)[NR][12], const cplx<R>* __restrict__ in, long long rstride,
+                                    const cplx<R>* __restrict__ U, int V, int s, int y) {
+  hop_at<R, MU, FWD, NR>(acc, in, rstride, V, y, U, V, FWD ? s : y);  // link U_mu(x) fwd, U_mu(x - mu) bwd
 }
 
 // acc_q = C(x) psi_q - acc_q / 2 for the components of chirality half h (NR rhs;
@@ -373,7 +381,8 @@ template <typename R, int MODE, bool DOTS, int NR>
 __global__ void __launch_bounds__(128, (sizeof(R) == 4 && NR == 1) ? 6 : (sizeof(R) == 4 ? 4 : 1))
     k_dslash(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in, const cplx<R>* __restrict__ U,
              const cplx<R>* __restrict__ clov, const int* __restrict__ nbr, int V, BlockInfo bi, int hopdir, int nrhs,
-             double2* __restrict__ pr_part, double* __restrict__ pp_part) {
+             double2* __restrict__ pr_part, double* __restrict__ pp_part,
+             const unsigned char* __restrict__ colour, int col) {
   using T = cplx<R>;
   // rhs groups fastest in the grid: the CTAs running together cover the same sites
   // for every rhs, so links and clover are fetched from HBM once
@@ -386,6 +395,8 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && NR == 1) ? 6 : (sizeof
   if (!DOTS && !valid) return;
   // single-face mode: sites off the face are never read by the face restriction
   if (MODE == ST_FACE_HOP && !on_face(bi, s, hopdir)) return;
+  // SAP residual: only the aggregates of one colour (the other sites are not written)
+  if (!DOTS && colour && colour[s / bi.bvol] != col) return;
   const long long rstride = 12LL * V;
   // a short last group re-reads its last rhs (nothing of it is stored)
   const long long off = (long long)r0 * rstride;
@@ -475,14 +486,15 @@ static int dslash_nr(int nrhs) { return (sizeof(R) == 4 && nrhs > 1) ? 2 : 1; }
 
 template <typename R>
 void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
-                   int nrhs, int mode, int hopdir, cudaStream_t st) {
+                   int nrhs, int mode, int hopdir, cudaStream_t st, const unsigned char* colour, int col) {
   BlockInfo bi;
   for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
   bi.bvol = g.bvol;
   const int nr = dslash_nr<R>(nrhs);
   const dim3 grid((unsigned)(nblk(g.V, 128) * (long long)((nrhs + nr - 1) / nr)));
 #define WCMG_DS(MODE, NR) \
-  k_dslash<R, MODE, false, NR><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs, nullptr, nullptr)
+  k_dslash<R, MODE, false, NR><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, hopdir, nrhs, nullptr, \
+                                                     nullptr, colour, col)
   if constexpr (sizeof(R) == 4) {
     if (nr == 2) {
       if (mode == ST_FULL) WCMG_DS(ST_FULL, 2);
@@ -498,6 +510,128 @@ void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const 
     else WCMG_DS(ST_FACE_HOP, 1);
   }
 #undef WCMG_DS
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---- SAP colour pass on the fine level (Sec. 4 smoother) ----
+// One CTA per aggregate of the pass's colour (blocks[blockIdx.x]), one thread per
+// site of it, one rhs per grid row.  The block's residual r = b - D x (b where x = 0)
+// stays in shared memory ([12][T], component-major like the field) for all `steps`
+// minimal-residual steps of the block-local operator D_B (D without the hops that
+// leave the aggregate): p = D_B r from the neighbours' r in shared memory and the
+// site's links and clover (HBM once, then L1/L2), alpha_B = <p, r>_B / <p, p>_B summed
+// over the block (FP64 across warps), e += alpha_B r, r -= alpha_B p.  x += e at the
+// end; only the CTA's own sites are written, so blocks of one colour run concurrently.
+constexpr int SAP_FINE_T = 256;
+template <typename R>
+__global__ void __launch_bounds__(SAP_FINE_T, sizeof(R) == 4 ? 2 : 1)
+    k_sap_fine(cplx<R>* __restrict__ x, const cplx<R>* __restrict__ b, const cplx<R>* __restrict__ Dx,
+               const cplx<R>* __restrict__ U, const cplx<R>* __restrict__ clov, int V, BlockInfo bi,
+               const int* __restrict__ blocks, int steps) {
+  using T = cplx<R>;
+  extern __shared__ __align__(16) unsigned char sap_smem[];
+  T* rs = reinterpret_cast<T*>(sap_smem);
+  const int NT = blockDim.x;
+  const int i = threadIdx.x;
+  const bool valid = i < bi.bvol;
+  const int s = blocks[blockIdx.x] * bi.bvol + i;
+  const long long off = (long long)blockIdx.y * 12 * V;
+  int l[4], st[4];
+  {
+    int loc = valid ? i : 0;
+    st[0] = 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      l[k] = loc % bi.b[k];
+      loc /= bi.b[k];
+      if (k < 3) st[k + 1] = st[k] * bi.b[k];
+    }
+  }
+  T r[12], e[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    T v = czero<R>();
+    if (valid) {
+      const long long o = off + (long long)c * V + s;
+      v = Dx ? b[o] - Dx[o] : b[o];
+    }
+    r[c] = v;
+    e[c] = czero<R>();
+    rs[c * NT + i] = v;
+  }
+  __syncthreads();
+  __shared__ double scratch[(SAP_FINE_T / 32) * 3], red[3];
+  for (int k = 0; k < steps; ++k) {
+    T acc[1][12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[0][c] = czero<R>();
+    R v3[3] = {R(0), R(0), R(0)};
+    if (valid) {
+#define WCMG_SAP_HOP(MU)                                                                                   \
+  if (l[MU] < bi.b[MU] - 1) hop_at<R, MU, true, 1>(acc, rs, 0, NT, i + st[MU], U, V, s);                  \
+  if (l[MU] > 0) hop_at<R, MU, false, 1>(acc, rs, 0, NT, i - st[MU], U, V, s - st[MU]);
+      WCMG_SAP_HOP(0)
+      WCMG_SAP_HOP(1)
+      WCMG_SAP_HOP(2)
+      WCMG_SAP_HOP(3)
+#undef WCMG_SAP_HOP
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        T p[1][6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) p[0][j] = r[6 * h + j];
+        clover_half<R, 1>(acc, clov, p, h, V, s);
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        const T o = acc[0][c];
+        v3[0] += o.x * r[c].x + o.y * r[c].y;
+        v3[1] += o.x * r[c].y - o.y * r[c].x;
+        v3[2] += o.x * o.x + o.y * o.y;
+      }
+    }
+    block_sum_mixed<R, 3>(v3, scratch, red);  // every thread's reads of rs are done here
+    const double pp = red[2];
+    const T a = pp != 0.0 ? cmk((R)(red[0] / pp), (R)(red[1] / pp)) : czero<R>();
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        cmac(e[c], a, r[c]);
+        r[c] = r[c] - cmul(a, acc[0][c]);
+        rs[c * NT + i] = r[c];
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const long long o = off + (long long)c * V + s;
+      x[o] = x[o] + e[c];
+    }
+  }
+}
+
+int sap_fine_threads(int bvol) {
+  if (bvol < 1 || bvol > SAP_FINE_T) return 0;
+  return (bvol + 31) / 32 * 32;
+}
+
+template <typename R>
+void launch_sap_fine(cplx<R>* x, const cplx<R>* b, const cplx<R>* Dx, const cplx<R>* gauge, const cplx<R>* clov,
+                     const LevelGeom& g, const int* blocks, int nblocks, int steps, int nrhs, cudaStream_t st) {
+  const int nt = sap_fine_threads(g.bvol);
+  if (!nt) throw Error(-1, "fused SAP pass needs aggregates of at most 256 sites");
+  if (nblocks <= 0) return;
+  BlockInfo bi;
+  for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
+  bi.bvol = g.bvol;
+  const size_t smem = (size_t)12 * nt * sizeof(cplx<R>);
+  // the FP64 block of 256 sites takes 48 KB, which with the static reduction scratch
+  // is above the default limit (set on the current device, every such launch)
+  if (smem > 40 * 1024)
+    WCMG_CUDA(cudaFuncSetAttribute(k_sap_fine<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_sap_fine<R><<<dim3(nblocks, nrhs), nt, smem, st>>>(x, b, Dx, gauge, clov, g.V, bi, blocks, steps);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -685,13 +819,13 @@ void launch_dslash_mr(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, con
   if constexpr (sizeof(R) == 4) {
     if (nr == 2) {
       k_dslash<R, ST_FULL, true, 2><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, 0, nrhs, pr_part,
-                                                           pp_part);
+                                                           pp_part, nullptr, 0);
       done = true;
     }
   }
   if (!done)
     k_dslash<R, ST_FULL, true, 1><<<grid, 128, 0, st>>>(out, in, gauge, clov, g.nbr, g.V, bi, 0, nrhs, pr_part,
-                                                         pp_part);
+                                                         pp_part, nullptr, 0);
   WCMG_LAUNCH_CHECK();
   k_mr_final<<<nrhs, 256, 0, st>>>(pr, pp, pr_part, pp_part, nsb);
   WCMG_LAUNCH_CHECK();
@@ -702,7 +836,9 @@ void launch_dslash_mr(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, con
   template void launch_unpack_fine<R>(double2*, const cplx<R>*, const int*, int, int, cudaStream_t);          \
   template void launch_pack_gauge<R>(cplx<R>*, const double2*, const int*, int, cudaStream_t);                \
   template void launch_dslash<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
-                                 int, int, int, cudaStream_t);                                               \
+                                 int, int, int, cudaStream_t, const unsigned char*, int);                    \
+  template void launch_sap_fine<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*,  \
+                                   const LevelGeom&, const int*, int, int, int, cudaStream_t);                \
   template void launch_dslash_mr<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
                                     int, double2*, double*, double2*, double*, cudaStream_t);                  \
   template void launch_dslash_chiral<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*,              \

@@ -26,9 +26,20 @@ void launch_pack_gauge(cplx<R>* out, const double2* ext, const int* perm, int V,
 void launch_clover_build(double2* clov, const double2* gauge64, const int* nbr, int V, double m0, double csw,
                          cudaStream_t st);
 void launch_clover_expand(double2* ext, const double2* clov, const int* perm, int V, cudaStream_t st);
+// colour non-null: only the sites of the aggregates B with colour[B] == col are computed
+// and written (the SAP residual of one colour pass); the others keep `out`.
 template <typename R>
 void launch_dslash(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, const cplx<R>* clov, const LevelGeom& g,
-                   int nrhs, int mode, int hopdir, cudaStream_t st);
+                   int nrhs, int mode, int hopdir, cudaStream_t st, const unsigned char* colour = nullptr,
+                   int col = 0);
+// One SAP colour pass on the fine level, fused: for each aggregate B in blocks[0 ..
+// nblocks) and every rhs, r = b - Dx on B (Dx null: b), `steps` MR steps of the
+// block-local D_B from e = 0 with alpha_B = <p, r>_B / <p, p>_B, then x += e on B.
+// Aggregates of at most 256 sites (sap_fine_threads(bvol) != 0).
+int sap_fine_threads(int bvol);
+template <typename R>
+void launch_sap_fine(cplx<R>* x, const cplx<R>* b, const cplx<R>* Dx, const cplx<R>* gauge, const cplx<R>* clov,
+                     const LevelGeom& g, const int* blocks, int nblocks, int steps, int nrhs, cudaStream_t st);
 // out = D in (full stencil) and, per rhs r, pr[r] = <out_r, in_r> = sum conj(out) in,
 // pp[r] = <out_r, out_r> (the minimal-residual step's two reductions, fused into the
 // stencil).  pr_part / pp_part: scratch of nrhs * dslash_partials(V) entries.

@@ -151,6 +151,8 @@ struct Level {
   LevelScalars sc;
   LevelScalars sc_s;  // the GMRES smoother's own Krylov state (it runs inside the outer FGMRES)
   DevBuf<unsigned char> colour;  // SAP: colour (coarse-coordinate parity) of each aggregate
+  DevBuf<int> sap_list;          // SAP: the aggregates of colour 0, then those of colour 1
+  int sap_count[2] = {0, 0};
   std::map<std::string, DevBuf<unsigned char>> ws;
   // coarse-apply launch shape per (nrhs, link storage): tuned or forced
   struct TileInfo {
@@ -918,21 +920,40 @@ static void smooth(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs) {
 //   r = b - D x on the blocks of colour c (0 elsewhere);
 //   `steps` block-local MR steps on D_B (D without the hops leaving a block), one
 //   step length per block, the steps added to x.
-// D_B r vanishes outside the blocks of colour c (r does), so every step needs one
-// block-interior stencil and one fused block-reduction + update kernel.
+// D x is needed on the blocks of colour c only (the fine stencil skips the others).
+// Fine level with aggregates of <= 256 sites: the steps of a pass run fused, one CTA
+// per block (launch_sap_fine).  Otherwise each step is one block-interior stencil and
+// one fused block-reduction + update kernel (D_B r vanishes where r does).
 template <typename R>
 static void sap(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int steps, int cycles) {
   Level& L = c->L[l];
   if (!L.colour.p) throw Error(WCMG_ERR_STATE, "SAP needs the level's aggregates");
+  if (l == 0 && !c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
   const long long n = L.n();
-  cplx<R>* r = ws<R>(L, "sap_r", nrhs);
+  const bool fused = l == 0 && sap_fine_threads(L.g.bvol) != 0;
+  cplx<R>* r = fused ? nullptr : ws<R>(L, "sap_r", nrhs);
   cplx<R>* p = ws<R>(L, "sap_p", nrhs);
   const double s = sizeof(cplx<R>);
+  const int cls = sizeof(R) == 8 ? WCMG_K_DSLASH64 : WCMG_K_DSLASH;
   launch_fill_zero<R>(x, n * nrhs, c->st);
   for (int cyc = 0; cyc < cycles; ++cyc)
     for (int col = 0; col < 2; ++col) {
       const bool x_zero = cyc == 0 && col == 0;
-      if (!x_zero) apply_op<R>(c, l, p, x, nrhs);
+      const double sites = (double)L.sap_count[col] * L.g.bvol;
+      if (!x_zero) {
+        if (l == 0)
+          KPROF(c, cls, sites * s * (24.0 * nrhs + 72.0), sites * 1872.0 * nrhs,
+                launch_dslash<R>(p, x, Prec<R>::gauge(c), Prec<R>::clover(c), L.g.lg(), nrhs, ST_FULL, 0, c->st,
+                                 L.colour.p, col));
+        else
+          apply_op<R>(c, l, p, x, nrhs);
+      }
+      if (fused) {
+        KPROF(c, cls, sites * s * ((x_zero ? 36.0 : 48.0) * nrhs + 72.0), sites * steps * 1900.0 * nrhs,
+              launch_sap_fine<R>(x, b, x_zero ? nullptr : p, Prec<R>::gauge(c), Prec<R>::clover(c), L.g.lg(),
+                                 L.sap_list.p + (col ? L.sap_count[0] : 0), L.sap_count[col], steps, nrhs, c->st));
+        continue;
+      }
       KPROF(c, WCMG_K_BLAS, (x_zero ? 1.5 : 2.0) * n * nrhs * s, 1.0 * n * nrhs,
             launch_sap_residual<R>(r, b, x_zero ? nullptr : p, L.colour.p, col, L.g.V, L.nc, L.g.bvol, L.fine, nrhs,
                                    c->st));
@@ -1823,8 +1844,17 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
           coords(Cg.perm[B], Cg.dims, xc);
           col[B] = (unsigned char)((xc[0] + xc[1] + xc[2] + xc[3]) & 1);
         }
-        c->L[l].colour.ensure(Cg.V);
-        WCMG_CUDA(cudaMemcpy(c->L[l].colour.p, col.data(), Cg.V, cudaMemcpyHostToDevice));
+        std::vector<int> list;
+        for (int k = 0; k < 2; ++k)
+          for (int B = 0; B < Cg.V; ++B)
+            if (col[B] == k) list.push_back(B);
+        Level& Lc = c->L[l];
+        Lc.sap_count[0] = (int)std::count(col.begin(), col.end(), 0);
+        Lc.sap_count[1] = Cg.V - Lc.sap_count[0];
+        Lc.colour.ensure(Cg.V);
+        Lc.sap_list.ensure(Cg.V);
+        WCMG_CUDA(cudaMemcpy(Lc.colour.p, col.data(), Cg.V, cudaMemcpyHostToDevice));
+        WCMG_CUDA(cudaMemcpy(Lc.sap_list.p, list.data(), sizeof(int) * Cg.V, cudaMemcpyHostToDevice));
       }
     }
     ensure_partials(c);

@@ -26,9 +26,12 @@ def fine_ctx(lib, dims, block, nvec, prec=0, seed=1201, **kw):
 
 
 # (dims, block, steps, cycles): the (6,4,4,4) lattice has an odd number of aggregates
-# along x, so two neighbouring aggregates across the boundary share a colour
+# along x, so two neighbouring aggregates across the boundary share a colour; aggregates
+# of up to 256 sites take the fused one-CTA-per-block pass (4^4; a ragged 24-thread
+# warp for 2x2x2x3), larger ones (4x4x4x5 = 320 sites) the per-step kernels
 CASES = [((4, 4, 4, 8), (2, 2, 2, 2), 4, 1), ((4, 4, 4, 8), (2, 2, 2, 4), 3, 2), ((6, 4, 4, 4), (2, 2, 2, 2), 2, 3),
-         ((4, 4, 4, 4), (1, 1, 1, 1), 5, 1), ((4, 4, 4, 4), (4, 4, 4, 4), 4, 1)]
+         ((4, 4, 4, 4), (1, 1, 1, 1), 5, 1), ((4, 4, 4, 4), (4, 4, 4, 4), 4, 1), ((8, 8, 8, 8), (4, 4, 4, 4), 4, 1),
+         ((4, 4, 4, 6), (2, 2, 2, 3), 3, 1), ((8, 4, 4, 10), (4, 4, 4, 5), 3, 1), ((4, 4, 4, 5), (4, 4, 4, 5), 2, 1)]
 
 
 @pytest.mark.parametrize("dims,block,steps,cycles", CASES)
