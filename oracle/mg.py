@@ -12,7 +12,8 @@ Sec. 2.1 describes the pieces but not the algorithmic parameters:
 Readings used here (each listed with the other readings of the paper):
   cycle  M_l(r):  e = P_l CoarseSolve_{l+1}(P_l^dag r);  e += S_k(D_l; r - D_l e);
          S_k is the smoother: MR_k, GMRES with k steps (zero initial guess, no
-         restart, no tolerance), or SAP over the level's aggregates (sap.py), the
+         restart, no tolerance), or SAP over the level's aggregates (sap.py; with
+         sap_eo its block solves on the finest level are even-odd preconditioned), the
          same smoother in the setup sweeps;
          on an intermediate level (neither finest nor coarsest) CoarseSolve is one
          cycle of that level (V-cycle) or, with kcycle, FGMRES(kcycle_steps) to
@@ -54,6 +55,7 @@ class MGParams:
     outer_maxiter: int = 1000
     smoother: str = "mr"                     # "mr", "gmres" or "sap"
     sap_cycles: int = 1                      # SAP: cycles; smoother_steps = MR steps per block solve
+    sap_eo: bool = False                     # SAP: even-odd preconditioned block solves on the finest level
     kcycle: bool = False                     # intermediate levels: FGMRES around the cycle
     kcycle_steps: int = 5
     kcycle_tol: float = 0.1
@@ -89,7 +91,8 @@ class Multigrid:
         if self.p.smoother == "gmres":
             return gmres(op, b, restart=k, tol=0.0, maxiter=k)[0]
         if self.p.smoother == "sap":
-            return sap(op, self.levels[l].dims, self.p.blocks[l], b, k, self.p.sap_cycles)
+            return sap(op, self.levels[l].dims, self.p.blocks[l], b, k, self.p.sap_cycles,
+                       eo=self.p.sap_eo and l == 0)
         raise ValueError(self.p.smoother)
 
     def _smooth_sweep(self, l):
