@@ -245,7 +245,8 @@ def params(wcmg, cfg, inner, links, profile=0, graphs=0, autotune=1):
                             use_graphs=graphs, autotune=autotune,
                             smoother={"mr": wcmg.SMOOTHER_MR, "gmres": wcmg.SMOOTHER_GMRES,
                                       "sap": wcmg.SMOOTHER_SAP}[cfg.get("smoother", "mr")],
-                            sap_cycles=int(cfg.get("sap_cycles", 1)), smoother_steps=int(cfg.get("smoother_steps", 4)),
+                            sap_cycles=int(cfg.get("sap_cycles", 1)), sap_eo=int(cfg.get("sap_eo", 0)),
+                            smoother_steps=int(cfg.get("smoother_steps", 4)),
                             kcycle=int(cfg.get("kcycle", 0)))
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
@@ -281,8 +282,11 @@ def run_gpu(args, rank, world, local):
         cfg["smoother"] = args.smoother
         cfg["sap_cycles"] = args.sap_cycles
         cfg["smoother_steps"] = k
+        cfg["sap_eo"] = int(args.sap_eo)
+        eo = ", even-odd preconditioned" if args.sap_eo else ""
         desc = {"mr": f"MR({k}) smoother", "gmres": f"GMRES({k}) smoother",
-                "sap": f"SAP smoother ({args.sap_cycles} cycle(s) over the aggregates, MR({k}) per block)"}[args.smoother]
+                "sap": f"SAP smoother ({args.sap_cycles} cycle(s) over the aggregates, MR({k}) per block{eo})"}[
+            args.smoother]
         w = cfg["workload"]
         cfg["workload"] = w.replace("MR(4) smoother", desc) if "MR(4) smoother" in w else w + ", " + desc
     nrhs = cfg.get("nrhs", 1)
@@ -894,6 +898,7 @@ def main(argv=None):
                     help="smoother of every level (the setup sweeps and the cycle)")
     ap.add_argument("--sap-cycles", type=int, default=1, help="SAP smoother: cycles")
     ap.add_argument("--smoother-steps", type=int, default=4, help="MR / GMRES steps (SAP: MR steps per block)")
+    ap.add_argument("--sap-eo", action="store_true", help="SAP: even-odd preconditioned block solves (fine level)")
     ap.add_argument("--pools", type=int, default=417,
                     help="c5: training pools of 48 fresh pairs (417 pools = 20016 pairs)")
     ap.add_argument("--ncu-region", action="store_true",

@@ -112,6 +112,17 @@ typedef struct wcmg_params {
   int kcycle_steps;                     /* 1 .. 64 */
   double kcycle_tol;                    /* relative residual of the intermediate FGMRES */
   int sap_cycles;                       /* SAP smoother: cycles (1 .. 16) */
+  int sap_eo;                           /* 1: even-odd (red-black) preconditioned SAP block solves on
+                                           the fine level (Sec. 4 lists red-black preconditioning
+                                           among the missing features): per block, with sites
+                                           even / odd by the parity of x + y + z + t,
+                                           r^_o = r_o - H_oe C_ee^-1 r_e, smoother_steps MR steps on
+                                           the Schur complement C_oo - H_oe C_ee^-1 H_eo (one step
+                                           length per block), e_e = C_ee^-1 (r_e - H_eo e_o); H the
+                                           hops inside the block, C the clover term, inverted once
+                                           per wcmg_set_gauge in FP64.  Fine aggregates of at most
+                                           256 sites with an even x extent (else WCMG_ERR_ARG).
+                                           Coarse levels keep the plain block solves. */
 } wcmg_params;
 
 typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1, WCMG_SMOOTHER_SAP = 2 } wcmg_smoother;
@@ -167,6 +178,10 @@ int wcmg_set_gauge(wcmg_ctx* ctx, const void* U, int where, void* stream);
 
 /* Read back C(x) (FP64), external clover layout. */
 int wcmg_get_clover(wcmg_ctx* ctx, void* C, int where, void* stream);
+
+/* C(x)^-1 in the layout of wcmg_get_clover (built by wcmg_set_gauge with params.sap_eo;
+ * WCMG_ERR_STATE otherwise). */
+int wcmg_get_clover_inverse(wcmg_ctx* ctx, void* C, int where, void* stream);
 
 /* out = D in on the fine lattice (Sec. 2.1: MG runs on D itself), nrhs fields. */
 int wcmg_apply_D(wcmg_ctx* ctx, const void* in, void* out, int nrhs, int prec, int where, void* stream);

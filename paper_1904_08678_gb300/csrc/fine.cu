@@ -635,6 +635,274 @@ void launch_sap_fine(cplx<R>* x, const cplx<R>* b, const cplx<R>* Dx, const cplx
   WCMG_LAUNCH_CHECK();
 }
 
+// ---- C(x)^-1 (even-odd preconditioned SAP block solves) ----
+// Per site and chirality half the 6x6 Hermitian block of C is inverted in FP64 by
+// Gauss-Jordan elimination with partial pivoting; the inverse is Hermitian and is
+// packed like C (three pairs of real diagonal entries, then the 15 entries above the
+// diagonal).  err receives 1 when a pivot vanishes (a singular site block).
+__global__ void k_clover_invert(double2* __restrict__ inv, const double2* __restrict__ clov, int V,
+                                int* __restrict__ err) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 2LL * V) return;
+  const int h = (int)(t / V), s = (int)(t - (long long)h * V);
+  double2 a[6][12];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 12; ++j) a[i][j] = make_double2(j == i + 6 ? 1.0 : 0.0, 0.0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double2 d = clov[(long long)(18 * h + k) * V + s];
+    a[2 * k][2 * k] = make_double2(d.x, 0.0);
+    a[2 * k + 1][2 * k + 1] = make_double2(d.y, 0.0);
+  }
+  int o = 3;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      const double2 c = clov[(long long)(18 * h + o++) * V + s];
+      a[i][j] = c;
+      a[j][i] = make_double2(c.x, -c.y);
+    }
+  for (int col = 0; col < 6; ++col) {
+    int p = col;
+    double best = a[col][col].x * a[col][col].x + a[col][col].y * a[col][col].y;
+    for (int r = col + 1; r < 6; ++r) {
+      const double m = a[r][col].x * a[r][col].x + a[r][col].y * a[r][col].y;
+      if (m > best) { best = m; p = r; }
+    }
+    if (!(best > 0.0)) {
+      *err = 1;
+      return;
+    }
+    if (p != col)
+      for (int j = 0; j < 12; ++j) {
+        const double2 tmp = a[p][j];
+        a[p][j] = a[col][j];
+        a[col][j] = tmp;
+      }
+    const double2 pv = a[col][col];
+    const double2 ip = make_double2(pv.x / best, -pv.y / best);  // 1 / pv
+    for (int j = 0; j < 12; ++j) {
+      const double2 v = a[col][j];
+      a[col][j] = make_double2(v.x * ip.x - v.y * ip.y, v.x * ip.y + v.y * ip.x);
+    }
+    for (int r = 0; r < 6; ++r) {
+      if (r == col) continue;
+      const double2 f = a[r][col];
+      for (int j = 0; j < 12; ++j) {
+        const double2 v = a[col][j];
+        a[r][j].x -= f.x * v.x - f.y * v.y;
+        a[r][j].y -= f.x * v.y + f.y * v.x;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    inv[(long long)(18 * h + k) * V + s] = make_double2(a[2 * k][6 + 2 * k].x, a[2 * k + 1][6 + 2 * k + 1].x);
+  o = 3;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) inv[(long long)(18 * h + o++) * V + s] = a[i][6 + j];
+}
+
+void launch_clover_invert(double2* inv, const double2* clov, int V, int* err, cudaStream_t st) {
+  k_clover_invert<<<nblk(2LL * V, 64), 64, 0, st>>>(inv, clov, V, err);
+  WCMG_LAUNCH_CHECK();
+}
+
+// ---- even-odd preconditioned SAP colour pass on the fine level ----
+// As k_sap_fine, but each block solve D_B e = r runs on the block's Schur complement on
+// its odd sites (sites even or odd by the parity of x + y + z + t; interior hops join
+// opposite parities): with H the interior hops,
+//   r^_o = r_o - H_oe C_ee^-1 r_e;  e_o = MR_k(S; r^_o), S = C_oo - H_oe C_ee^-1 H_eo,
+//   one step length per block;  e_e = C_ee^-1 (r_e - H_eo e_o).
+// The hop kernels accumulate sum_hops without the factor -1/2 of D, so H f = -acc/2.
+// Threads 0 .. bvol/2-1 take the even site of each x-pair of the block (local sites
+// 2q, 2q+1; b0 is even), the others the odd site, so a warp holds one parity when
+// bvol/2 is a multiple of 32.  One shared array holds the odd-site vector and the
+// even-site intermediate at once (each phase reads one parity and writes the other).
+// opar[B]: parity of block B's first site.
+template <typename R>
+__global__ void __launch_bounds__(SAP_FINE_T, sizeof(R) == 4 ? 2 : 1)
+    k_sap_fine_eo(cplx<R>* __restrict__ x, const cplx<R>* __restrict__ b, const cplx<R>* __restrict__ Dx,
+                  const cplx<R>* __restrict__ U, const cplx<R>* __restrict__ clov,
+                  const cplx<R>* __restrict__ cinv, int V, BlockInfo bi, const int* __restrict__ blocks,
+                  const unsigned char* __restrict__ opar, int steps) {
+  using T = cplx<R>;
+  extern __shared__ __align__(16) unsigned char sap_smem[];
+  T* rs = reinterpret_cast<T*>(sap_smem);
+  const int NT = blockDim.x;
+  const int half = bi.bvol / 2;
+  const int B = blocks[blockIdx.x];
+  const bool valid = (int)threadIdx.x < bi.bvol;
+  const bool even = (int)threadIdx.x < half;
+  const int q = valid ? (even ? threadIdx.x : threadIdx.x - half) : 0;
+  int l[4], st[4];
+  st[0] = 1;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) st[k + 1] = st[k] * bi.b[k];
+  int j;
+  {
+    // parity of the pair's first site 2q decides which of 2q, 2q+1 is even
+    int loc = 2 * q, par = opar[B];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      par += loc % bi.b[k];
+      loc /= bi.b[k];
+    }
+    j = 2 * q + (((par & 1) == 0) == even ? 0 : 1);
+    loc = j;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      l[k] = loc % bi.b[k];
+      loc /= bi.b[k];
+    }
+  }
+  const int s = B * bi.bvol + j;
+  const long long off = (long long)blockIdx.y * 12 * V;
+  // sum of the interior hops at this thread's site from the vector in rs
+  auto hops = [&](T (&acc)[1][12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[0][c] = czero<R>();
+#define WCMG_SAP_HOP(MU)                                                                  \
+  if (l[MU] < bi.b[MU] - 1) hop_at<R, MU, true, 1>(acc, rs, 0, NT, j + st[MU], U, V, s); \
+  if (l[MU] > 0) hop_at<R, MU, false, 1>(acc, rs, 0, NT, j - st[MU], U, V, s - st[MU]);
+    WCMG_SAP_HOP(0)
+    WCMG_SAP_HOP(1)
+    WCMG_SAP_HOP(2)
+    WCMG_SAP_HOP(3)
+#undef WCMG_SAP_HOP
+  };
+  // out = M in for the site's clover (or inverse clover) M
+  auto site_mul = [&](T (&out)[1][12], const T (&in)[12], const cplx<R>* __restrict__ M) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) out[0][c] = czero<R>();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      T p[1][6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) p[0][i] = in[6 * h + i];
+      clover_half<R, 1>(out, M, p, h, V, s);
+    }
+  };
+  T v[12], e[12], acc[1][12];
+  // r on this site; even threads keep r_e, odd threads turn it into r^_o below
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    T r = czero<R>();
+    if (valid) {
+      const long long o = off + (long long)c * V + s;
+      r = Dx ? b[o] - Dx[o] : b[o];
+    }
+    v[c] = r;
+    e[c] = czero<R>();
+  }
+  if (valid && even) {
+    site_mul(acc, v, cinv);  // t = C_ee^-1 r_e
+#pragma unroll
+    for (int c = 0; c < 12; ++c) rs[c * NT + j] = acc[0][c];
+  }
+  __syncthreads();
+  if (valid && !even) {
+    hops(acc);  // r^_o = r_o - H t = r_o + acc / 2
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      v[c] = v[c] + R(0.5) * acc[0][c];
+      rs[c * NT + j] = v[c];
+    }
+  }
+  __syncthreads();
+  __shared__ double scratch[(SAP_FINE_T / 32) * 3], red[3];
+  for (int k = 0; k < steps; ++k) {
+    if (valid && even) {
+      // w' = C_ee^-1 (acc / 2) = -C_ee^-1 H_eo v
+      hops(acc);
+      T u[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) u[c] = R(0.5) * acc[0][c];
+      T w[1][12];
+      site_mul(w, u, cinv);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) rs[c * NT + j] = w[0][c];
+    }
+    __syncthreads();
+    R v3[3] = {R(0), R(0), R(0)};
+    if (valid && !even) {
+      // p = S v = C v - H w = C v - acc / 2 with acc the hops of w' = -w
+      hops(acc);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        T p[1][6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) p[0][i] = v[6 * h + i];
+        clover_half<R, 1>(acc, clov, p, h, V, s);
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        const T o = acc[0][c];
+        v3[0] += o.x * v[c].x + o.y * v[c].y;
+        v3[1] += o.x * v[c].y - o.y * v[c].x;
+        v3[2] += o.x * o.x + o.y * o.y;
+      }
+    }
+    block_sum_mixed<R, 3>(v3, scratch, red);
+    const double pp = red[2];
+    const T a = pp != 0.0 ? cmk((R)(red[0] / pp), (R)(red[1] / pp)) : czero<R>();
+    if (valid && !even) {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        cmac(e[c], a, v[c]);
+        v[c] = v[c] - cmul(a, acc[0][c]);
+        rs[c * NT + j] = v[c];
+      }
+    }
+    __syncthreads();
+  }
+  if (valid && !even) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) rs[c * NT + j] = e[c];
+  }
+  __syncthreads();
+  if (valid && even) {
+    // e_e = C_ee^-1 (r_e - H e_o) = C_ee^-1 (r_e + acc / 2)
+    hops(acc);
+    T u[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) u[c] = v[c] + R(0.5) * acc[0][c];
+    T w[1][12];
+    site_mul(w, u, cinv);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) e[c] = w[0][c];
+  }
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      const long long o = off + (long long)c * V + s;
+      x[o] = x[o] + e[c];
+    }
+  }
+}
+
+template <typename R>
+void launch_sap_fine_eo(cplx<R>* x, const cplx<R>* b, const cplx<R>* Dx, const cplx<R>* gauge, const cplx<R>* clov,
+                        const cplx<R>* cinv, const LevelGeom& g, const int* blocks, const unsigned char* opar,
+                        int nblocks, int steps, int nrhs, cudaStream_t st) {
+  const int nt = sap_fine_threads(g.bvol);
+  if (!nt || (g.b[0] & 1)) throw Error(-1, "even-odd SAP pass needs aggregates of <= 256 sites, even in x");
+  if (nblocks <= 0) return;
+  BlockInfo bi;
+  for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
+  bi.bvol = g.bvol;
+  const size_t smem = (size_t)12 * nt * sizeof(cplx<R>);
+  if (smem > 40 * 1024)
+    WCMG_CUDA(cudaFuncSetAttribute(k_sap_fine_eo<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_sap_fine_eo<R><<<dim3(nblocks, nrhs), nt, smem, st>>>(x, b, Dx, gauge, clov, cinv, g.V, bi, blocks, opar, steps);
+  WCMG_LAUNCH_CHECK();
+}
+
 // ---- chirality pairs for CoarsenOperator (K5) ----
 // For each near-null vector v_i the Galerkin construction needs the masked stencil
 // applied to both chirality projections: out[i] = D_mode(Pi_+ v_i),
@@ -839,6 +1107,9 @@ void launch_dslash_mr(cplx<R>* out, const cplx<R>* in, const cplx<R>* gauge, con
                                  int, int, int, cudaStream_t, const unsigned char*, int);                    \
   template void launch_sap_fine<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*,  \
                                    const LevelGeom&, const int*, int, int, int, cudaStream_t);                \
+  template void launch_sap_fine_eo<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*,              \
+                                      const cplx<R>*, const cplx<R>*, const LevelGeom&, const int*,           \
+                                      const unsigned char*, int, int, int, cudaStream_t);                     \
   template void launch_dslash_mr<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*, const LevelGeom&, \
                                     int, double2*, double*, double2*, double*, cudaStream_t);                  \
   template void launch_dslash_chiral<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const cplx<R>*,              \

@@ -40,6 +40,16 @@ int sap_fine_threads(int bvol);
 template <typename R>
 void launch_sap_fine(cplx<R>* x, const cplx<R>* b, const cplx<R>* Dx, const cplx<R>* gauge, const cplx<R>* clov,
                      const LevelGeom& g, const int* blocks, int nblocks, int steps, int nrhs, cudaStream_t st);
+// C(x)^-1 in the packed clover layout (FP64 Gauss-Jordan per site and chirality);
+// err receives 1 on a singular site block.
+void launch_clover_invert(double2* inv, const double2* clov, int V, int* err, cudaStream_t st);
+// The same pass with even-odd preconditioned block solves: MR on each block's Schur
+// complement on its odd sites (cinv = C^-1; opar[B] = parity of block B's first site).
+// Aggregates of at most 256 sites with an even x extent.
+template <typename R>
+void launch_sap_fine_eo(cplx<R>* x, const cplx<R>* b, const cplx<R>* Dx, const cplx<R>* gauge, const cplx<R>* clov,
+                        const cplx<R>* cinv, const LevelGeom& g, const int* blocks, const unsigned char* opar,
+                        int nblocks, int steps, int nrhs, cudaStream_t st);
 // out = D in (full stencil) and, per rhs r, pr[r] = <out_r, in_r> = sum conj(out) in,
 // pp[r] = <out_r, out_r> (the minimal-residual step's two reductions, fused into the
 // stencil).  pr_part / pp_part: scratch of nrhs * dslash_partials(V) entries.

@@ -152,6 +152,7 @@ struct Level {
   LevelScalars sc_s;  // the GMRES smoother's own Krylov state (it runs inside the outer FGMRES)
   DevBuf<unsigned char> colour;  // SAP: colour (coarse-coordinate parity) of each aggregate
   DevBuf<int> sap_list;          // SAP: the aggregates of colour 0, then those of colour 1
+  DevBuf<unsigned char> opar;    // SAP: parity of each aggregate's first site (even-odd block solves)
   int sap_count[2] = {0, 0};
   std::map<std::string, DevBuf<unsigned char>> ws;
   // coarse-apply launch shape per (nrhs, link storage): tuned or forced
@@ -208,8 +209,9 @@ struct wcmg_ctx {
   wcmg_params p;
   std::string err;
   std::vector<Level> L;
-  DevBuf<double2> gauge64, clover64;
-  DevBuf<float2> gauge32, clover32;
+  DevBuf<double2> gauge64, clover64, cinv64;  // cinv: C(x)^-1 (even-odd SAP), same packing as C
+  DevBuf<float2> gauge32, clover32, cinv32;
+  DevBuf<int> cinv_err;
   bool have_gauge = false;
   DevBuf<double2> partial;
   DevBuf<double> partial_d;
@@ -346,12 +348,14 @@ template <typename R> struct Prec;
 template <> struct Prec<double> {
   static double2* gauge(wcmg_ctx* c) { return c->gauge64.p; }
   static double2* clover(wcmg_ctx* c) { return c->clover64.p; }
+  static double2* clover_inv(wcmg_ctx* c) { return c->cinv64.p; }
   static double2* vecs(wcmg_ctx*, Level& L) { return L.v64.p; }
   static DevBuf<double2>& raw(Level& L) { return L.raw64; }
 };
 template <> struct Prec<float> {
   static float2* gauge(wcmg_ctx* c) { return c->gauge32.p; }
   static float2* clover(wcmg_ctx* c) { return c->clover32.p; }
+  static float2* clover_inv(wcmg_ctx* c) { return c->cinv32.p; }
   static float2* vecs(wcmg_ctx* c, Level& L) {
     if (!L.v32_valid) {
       L.v32.ensure((size_t)L.nvec * L.n());
@@ -947,6 +951,13 @@ static void sap(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int 
                                  L.colour.p, col));
         else
           apply_op<R>(c, l, p, x, nrhs);
+      }
+      if (fused && c->p.sap_eo) {
+        KPROF(c, cls, sites * s * ((x_zero ? 36.0 : 48.0) * nrhs + 108.0), sites * (steps + 1) * 1900.0 * nrhs,
+              launch_sap_fine_eo<R>(x, b, x_zero ? nullptr : p, Prec<R>::gauge(c), Prec<R>::clover(c),
+                                    Prec<R>::clover_inv(c), L.g.lg(), L.sap_list.p + (col ? L.sap_count[0] : 0),
+                                    L.opar.p, L.sap_count[col], steps, nrhs, c->st));
+        continue;
       }
       if (fused) {
         KPROF(c, cls, sites * s * ((x_zero ? 36.0 : 48.0) * nrhs + 72.0), sites * steps * 1900.0 * nrhs,
@@ -1746,6 +1757,7 @@ int wcmg_default_params(wcmg_params* p) {
   p->kcycle_steps = 5;
   p->kcycle_tol = 0.1;
   p->sap_cycles = 1;
+  p->sap_eo = 0;
   return WCMG_OK;
 }
 
@@ -1770,6 +1782,13 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
     if (p->smoother != WCMG_SMOOTHER_MR && p->smoother != WCMG_SMOOTHER_GMRES && p->smoother != WCMG_SMOOTHER_SAP)
       throw Error(WCMG_ERR_ARG, "smoother must be WCMG_SMOOTHER_MR, WCMG_SMOOTHER_GMRES or WCMG_SMOOTHER_SAP");
     if (p->sap_cycles < 1 || p->sap_cycles > 16) throw Error(WCMG_ERR_ARG, "sap_cycles must be 1..16");
+    if (p->sap_eo != 0 && p->sap_eo != 1) throw Error(WCMG_ERR_ARG, "sap_eo must be 0 or 1");
+    if (p->sap_eo) {
+      const int* fb = p->block[0];
+      const int bv = fb[0] * fb[1] * fb[2] * fb[3];
+      if ((fb[0] & 1) || bv > 256)
+        throw Error(WCMG_ERR_ARG, "sap_eo needs fine aggregates of at most 256 sites with an even x extent");
+    }
     if (p->smoother == WCMG_SMOOTHER_GMRES && p->smoother_steps > 64)
       throw Error(WCMG_ERR_ARG, "GMRES smoother: at most 64 steps");
     if ((p->kcycle != 0 && p->kcycle != 1) || p->kcycle_steps < 1 || p->kcycle_steps > 64 || !(p->kcycle_tol >= 0.0))
@@ -1849,6 +1868,16 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
           for (int B = 0; B < Cg.V; ++B)
             if (col[B] == k) list.push_back(B);
         Level& Lc = c->L[l];
+        std::vector<unsigned char> op(Cg.V);
+        for (int B = 0; B < Cg.V; ++B) {
+          int xc[4];
+          coords(Cg.perm[B], Cg.dims, xc);
+          int par = 0;
+          for (int k = 0; k < 4; ++k) par += xc[k] * G.b[k];
+          op[B] = (unsigned char)(par & 1);
+        }
+        Lc.opar.ensure(Cg.V);
+        WCMG_CUDA(cudaMemcpy(Lc.opar.p, op.data(), Cg.V, cudaMemcpyHostToDevice));
         Lc.sap_count[0] = (int)std::count(col.begin(), col.end(), 0);
         Lc.sap_count[1] = Cg.V - Lc.sap_count[0];
         Lc.colour.ensure(Cg.V);
@@ -1891,6 +1920,19 @@ int wcmg_set_gauge(wcmg_ctx* c, const void* U, int where, void* stream) {
   KPROF(c, WCMG_K_CLOVER, 36.0 * V * 16 * 5, 0,
         launch_clover_build(c->clover64.p, c->gauge64.p, L.g.d_nbr.p, V, c->p.m0, c->p.csw, c->st));
   launch_convert<double, float>(c->clover32.p, c->clover64.p, (long long)36 * V, c->st);
+  if (c->p.sap_eo) {
+    c->cinv64.ensure((size_t)36 * V);
+    c->cinv32.ensure((size_t)36 * V);
+    c->cinv_err.ensure(1);
+    WCMG_CUDA(cudaMemsetAsync(c->cinv_err.p, 0, sizeof(int), c->st));
+    KPROF(c, WCMG_K_CLOVER, 36.0 * V * 16 * 2, 2.0 * V * 6 * 6 * 12 * 8,
+          launch_clover_invert(c->cinv64.p, c->clover64.p, V, c->cinv_err.p, c->st));
+    launch_convert<double, float>(c->cinv32.p, c->cinv64.p, (long long)36 * V, c->st);
+    int bad = 0;
+    WCMG_CUDA(cudaMemcpyAsync(&bad, c->cinv_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    WCMG_CUDA(cudaStreamSynchronize(c->st));
+    if (bad) throw Error(WCMG_ERR_NAN, "singular clover block: no even-odd SAP");
+  }
   c->have_gauge = true;
   WCMG_CUDA(cudaStreamSynchronize(c->st));
   c->prof.flush();
@@ -1905,6 +1947,19 @@ int wcmg_get_clover(wcmg_ctx* c, void* C, int where, void* stream) {
   const size_t bytes = (size_t)V * 144 * 16;
   double2* o = out_dev(c, C, bytes, where, 1);
   launch_clover_expand(o, c->clover64.p, c->L[0].g.d_perm.p, V, c->st);
+  out_finish(c, C, o, bytes, where);
+  API_END(c)
+}
+
+int wcmg_get_clover_inverse(wcmg_ctx* c, void* C, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+  if (!c->cinv64.p) throw Error(WCMG_ERR_STATE, "the inverse clover term is built only with params.sap_eo");
+  const int V = c->L[0].g.V;
+  const size_t bytes = (size_t)V * 144 * 16;
+  double2* o = out_dev(c, C, bytes, where, 1);
+  launch_clover_expand(o, c->cinv64.p, c->L[0].g.d_perm.p, V, c->st);
   out_finish(c, C, o, bytes, where);
   API_END(c)
 }

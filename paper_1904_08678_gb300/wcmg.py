@@ -66,6 +66,7 @@ class wcmg_params(ctypes.Structure):
         ("kcycle_steps", ctypes.c_int),
         ("kcycle_tol", ctypes.c_double),
         ("sap_cycles", ctypes.c_int),
+        ("sap_eo", ctypes.c_int),
     ]
 
 
@@ -127,6 +128,7 @@ _SIGS = {
     "wcmg_last_error": ([_PCTX], ctypes.c_char_p),
     "wcmg_set_gauge": ([_PCTX, _vp, _i, _vp], _i),
     "wcmg_get_clover": ([_PCTX, _vp, _i, _vp], _i),
+    "wcmg_get_clover_inverse": ([_PCTX, _vp, _i, _vp], _i),
     "wcmg_apply_D": ([_PCTX, _vp, _vp, _i, _i, _i, _vp], _i),
     "wcmg_set_nullvecs": ([_PCTX, _i, _vp, _i, _vp], _i),
     "wcmg_get_nullvecs": ([_PCTX, _i, _vp, _i, _vp], _i),
@@ -250,6 +252,10 @@ class Context:
     def get_clover(self, C, stream=None):
         p, w = _buf(C, True)
         return self._check(wcmg_get_clover(self.h, p, w, _stream(stream)))
+
+    def get_clover_inverse(self, C, stream=None):
+        p, w = _buf(C, True)
+        return self._check(wcmg_get_clover_inverse(self.h, p, w, _stream(stream)))
 
     def apply_D(self, inp, out, nrhs=1, prec=F64, stream=None):
         pi, wi = _buf(inp)

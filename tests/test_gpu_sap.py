@@ -145,3 +145,84 @@ def test_sap_on_coarsest_level_is_rejected(lib):
     with pytest.raises(lib.WcmgError) as e:
         ctx.krylov(1, 2, b, dev(np.zeros((1, 16, 8), dtype=complex)), nrhs=1, steps_or_restart=2)
     assert e.value.code == lib.ERR_ARG
+
+
+def test_clover_inverse_matches_dense_inverse(lib):
+    dims = (4, 4, 4, 8)
+    ctx, D = fine_ctx(lib, dims, (2, 2, 2, 2), 4, sap_eo=1)
+    V = int(np.prod(dims))
+    Ci = dev(np.zeros((V, 12, 12), dtype=complex))
+    ctx.get_clover_inverse(Ci)
+    want = np.linalg.inv(D.C).reshape(V, 12, 12)
+    assert rel(host(Ci), want) < 1e-13
+
+
+# even-odd block solves: x extents even; 2x2x2x3 aggregates have first sites of both
+# parities, 2x1x1x1 ones a single even-odd pair (ragged warps)
+EO_CASES = [((4, 4, 4, 8), (2, 2, 2, 2), 4, 1), ((4, 4, 4, 8), (2, 2, 2, 4), 3, 2), ((6, 4, 4, 4), (2, 2, 2, 2), 2, 3),
+            ((8, 8, 8, 8), (4, 4, 4, 4), 4, 1), ((4, 4, 4, 4), (4, 4, 4, 4), 3, 1), ((4, 4, 4, 6), (2, 2, 2, 3), 3, 1),
+            ((4, 2, 2, 4), (2, 1, 1, 1), 2, 2)]
+
+
+@pytest.mark.parametrize("dims,block,steps,cycles", EO_CASES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)], ids=["f64", "f32"])
+def test_fine_sap_even_odd_matches_oracle(lib, dims, block, steps, cycles, prec, tol):
+    nrhs = 2
+    ctx, D = fine_ctx(lib, dims, block, 2, prec, sap_cycles=cycles, sap_eo=1, max_rhs=nrhs)
+    V = int(np.prod(dims))
+    b = inputs.complex_gaussian(1208, 0, (nrhs, V, 12))
+    x = dev(np.zeros_like(b))
+    ctx.krylov(0, 2, dev(b), x, nrhs=nrhs, steps_or_restart=steps)
+    got = host(x)
+    for r, f in enumerate(fields(b, dims, 12)):
+        assert rel(got[r], sap(D, dims, block, f, steps, cycles, eo=True).reshape(V, 12)) < tol, r
+
+
+def test_sap_even_odd_setup_cycle_and_solve_match_oracle(lib):
+    dims, block, nvec = (4, 4, 4, 8), (2, 2, 2, 2), 8
+    ctx, D = fine_ctx(lib, dims, block, nvec, 0, setup_refine_sweeps=1, sap_eo=1)
+    iv = inputs.setup_vectors(dims, 12, nvec, 0, 1201)
+    ctx.setup(dev(iv))
+    mg = Multigrid(D, MGParams(blocks=[block], nvecs=[nvec], smoother="sap", sap_eo=True, refine_sweeps=1),
+                   [fields(iv, dims, 12)])
+    V = int(np.prod(dims))
+    P = dev(np.zeros((nvec, V, 12), dtype=complex))
+    ctx.get_nullvecs(0, P)
+    assert rel(host(P), mg.levels[0].agg.v.reshape(nvec, V, 12)) < 1e-9
+    r = inputs.complex_gaussian(1209, 0, (1, V, 12))
+    e = dev(np.zeros_like(r))
+    ctx.mg_cycle(dev(r), e)
+    assert rel(host(e)[0], mg.cycle(0, fields(r, dims, 12)[0]).reshape(V, 12)) < 1e-9
+    b = inputs.source(dims, 0)
+    x = dev(np.zeros_like(b))
+    st = ctx.solve(dev(b), x)
+    xo, info = mg.solve(fields(b, dims, 12)[0])
+    assert st.converged and st.true_residual <= 1e-10
+    assert rel(host(x)[0].reshape(V, 12), xo.reshape(V, 12)) < 1e-8
+    assert abs(st.outer_iterations - info.iterations) <= 1
+
+
+def test_sap_even_odd_graph_replay_matches_host_driven(lib):
+    dims, block = (8, 8, 8, 8), (4, 4, 4, 4)
+    ref, _ = fine_ctx(lib, dims, block, 6, 1, seed=1210, sap_eo=1)
+    ctx, _ = fine_ctx(lib, dims, block, 6, 1, seed=1210, sap_eo=1, use_graphs=1)
+    iv = dev(inputs.setup_vectors(dims, 12, 6, 0, 1210))
+    ref.setup(iv)
+    ctx.setup(iv)
+    b = inputs.source(dims, 0)
+    xe = dev(np.zeros_like(b))
+    se = ref.solve(dev(b), xe)
+    assert se.graph == 0 and se.converged
+    for call in range(3):
+        x = dev(np.zeros_like(b))
+        st = ctx.solve(dev(b), x)
+        assert st.graph == (1 if call else 0) and st.converged and st.true_residual <= 1e-10
+        assert st.outer_iterations == se.outer_iterations and st.coarse_iterations == se.coarse_iterations
+        assert rel(host(x), host(xe)) < 1e-13
+
+
+def test_clover_inverse_needs_sap_eo(lib):
+    ctx, _ = fine_ctx(lib, (4, 4, 4, 4), (2, 2, 2, 2), 4)
+    with pytest.raises(lib.WcmgError) as e:
+        ctx.get_clover_inverse(dev(np.zeros((256, 12, 12), dtype=complex)))
+    assert e.value.code == lib.ERR_STATE

@@ -35,12 +35,16 @@ def test_graph_and_autotune_params_validated_without_gpu_work():
     assert p.use_graphs == 0 and p.autotune == 0 and p.profile == 0 and p.max_rhs == 1
     h = ctypes.c_void_p()
     for field, bad in (("use_graphs", 2), ("autotune", 2), ("smoother", 3), ("kcycle", 2), ("kcycle_steps", 0),
-                       ("kcycle_tol", -1.0), ("sap_cycles", 0), ("sap_cycles", 17)):
+                       ("kcycle_tol", -1.0), ("sap_cycles", 0), ("sap_cycles", 17), ("sap_eo", 2)):
         q = wcmg.default_params(**{field: bad})
         assert wcmg.wcmg_create(ctypes.byref(q), ctypes.byref(h)) == wcmg.ERR_ARG, field
     q = wcmg.default_params()
     assert q.kcycle == 0 and q.kcycle_steps == 5 and q.kcycle_tol == 0.1 and q.smoother == wcmg.SMOOTHER_MR
-    assert q.sap_cycles == 1 and wcmg.SMOOTHER_SAP == 2
+    assert q.sap_cycles == 1 and q.sap_eo == 0 and wcmg.SMOOTHER_SAP == 2
+    # even-odd block solves need fine aggregates with an even x extent and <= 256 sites
+    for blk in ((3, 2, 2, 2), (4, 4, 4, 8)):
+        q = wcmg.default_params(dims=(12, 8, 8, 8), blocks=[blk], nvec=[4], sap_eo=1, smoother=wcmg.SMOOTHER_SAP)
+        assert wcmg.wcmg_create(ctypes.byref(q), ctypes.byref(h)) == wcmg.ERR_ARG, blk
 
 
 def test_batch_solve_rejects_empty_batch_without_gpu_work():
