@@ -243,55 +243,74 @@ static void restrict_few(cplx<R>* coarse, const cplx<R>* in, const cplx<R>* vecs
 // register-blocked GEMM per (aggregate, chirality): out[(s, i)][r] =
 // sum_e conj(v_i[e]) in_r[e] over the aggregate's (selected) elements e of
 // chirality s.  Each K-chunk of RST_KT elements of all vectors and all rhs of the
-// tile is staged once in shared memory (rhs fastest: conflict-free); thread
-// (ti, tr) of the 8 x TR threads owns vectors ti + 8 q (q < VI) and rhs tr + TR p
-// (p < RT): VI x RT complex accumulators per thread, VI + RT shared loads per
-// element for VI x RT complex MACs.
+// tile is staged once in shared memory; thread (ti, tr) of the 8 x TR threads owns
+// vectors ti + 8 q (q < VI) and rhs tr + TR p (p < RT): VI x RT complex accumulators
+// per thread, VI + RT shared loads per element for VI x RT complex MACs.
+// Staging: thread t loads element t % RST_KT of the chunk (coalesced along the
+// aggregate's sites) for rows t / RST_KT + ROWS j; the next chunk is loaded into
+// registers while the current one is multiplied.  Shared rows are padded to an odd
+// number of complex entries, so the staging stores (one row entry per lane) hit
+// distinct banks.
 constexpr int RST_KT = 32;
 template <typename R, int VI, int RT, int TR>
 __global__ void __launch_bounds__(8 * TR) k_restrict_gemm(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
                                                           const cplx<R>* __restrict__ vecs, int Vf, int nc, int bvol,
                                                           int nvec, int nrhs, bool fine, FaceSel fs) {
   using T = cplx<R>;
+  constexpr int NTH = 8 * TR;
   constexpr int NT = TR * RT;  // rhs per CTA
-  __shared__ T Xs[RST_KT][8 * VI];
-  __shared__ T Ts[RST_KT][NT];
-  __shared__ int off_s[RST_KT];
+  constexpr int NV = 8 * VI;   // vectors per CTA
+  constexpr int ROWS = NTH / RST_KT;
+  static_assert(NTH % RST_KT == 0, "staging rows");
+  constexpr int XJ = (NV + ROWS - 1) / ROWS, TJ = (NT + ROWS - 1) / ROWS;
+  constexpr int XP = NV | 1, TP = NT | 1;  // odd row strides
+  __shared__ T Xs[RST_KT][XP];
+  __shared__ T Ts[RST_KT][TP];
   const int blk = blockIdx.x, s = blockIdx.y, r0 = blockIdx.z * NT;
   const int tid = threadIdx.x, ti = tid / TR, tr = tid % TR;
+  const int kown = tid % RST_KT, row0 = tid / RST_KT;
   const int half = nc >> 1, nb = 2 * nvec;
   const int nsite = fs.fd < 0 ? bvol : bvol / fs.b[fs.fd >> 1];
   const int nelem = nsite * half;
   const int Vc = Vf / bvol;
   const long long fstride = (long long)Vf * nc;
+  T xr[XJ], trr[TJ];
+  auto fetch = [&](int c0) {
+    const int e = c0 + kown;
+    long long a = -1;
+    if (e < nelem) {
+      int c, f;
+      if (fine) { c = s * half + e / nsite; f = e % nsite; }
+      else { f = e / half; c = s * half + e % half; }
+      const int site = blk * bvol + face_site(fs, f);
+      a = fine ? (long long)c * Vf + site : (long long)site * nc + c;
+    }
+#pragma unroll
+    for (int j = 0; j < XJ; ++j) {
+      const int i = row0 + ROWS * j;
+      xr[j] = (a >= 0 && i < nvec) ? vecs[i * fstride + a] : czero<R>();
+    }
+#pragma unroll
+    for (int j = 0; j < TJ; ++j) {
+      const int r = row0 + ROWS * j;
+      trr[j] = (a >= 0 && r < NT && r0 + r < nrhs) ? in[(r0 + r) * fstride + a] : czero<R>();
+    }
+  };
   T acc[VI][RT];
 #pragma unroll
   for (int q = 0; q < VI; ++q)
 #pragma unroll
     for (int p = 0; p < RT; ++p) acc[q][p] = czero<R>();
+  fetch(0);
   for (int c0 = 0; c0 < nelem; c0 += RST_KT) {
-    if (tid < RST_KT) {
-      const int e = c0 + tid;
-      int a = -1;
-      if (e < nelem) {
-        int c, f;
-        if (fine) { c = s * half + e / nsite; f = e % nsite; }
-        else { f = e / half; c = s * half + e % half; }
-        const int site = blk * bvol + face_site(fs, f);
-        a = fine ? c * Vf + site : site * nc + c;
-      }
-      off_s[tid] = a;
-    }
+#pragma unroll
+    for (int j = 0; j < XJ; ++j)
+      if (row0 + ROWS * j < NV) Xs[kown][row0 + ROWS * j] = xr[j];
+#pragma unroll
+    for (int j = 0; j < TJ; ++j)
+      if (row0 + ROWS * j < NT) Ts[kown][row0 + ROWS * j] = trr[j];
     __syncthreads();
-    for (int k = tid; k < RST_KT * 8 * VI; k += blockDim.x) {
-      const int i = k / RST_KT, kk = k % RST_KT, a = off_s[kk];
-      Xs[kk][i] = (a >= 0 && i < nvec) ? vecs[i * fstride + a] : czero<R>();
-    }
-    for (int k = tid; k < RST_KT * NT; k += blockDim.x) {
-      const int r = k / RST_KT, kk = k % RST_KT, a = off_s[kk];
-      Ts[kk][r] = (a >= 0 && r0 + r < nrhs) ? in[(r0 + r) * fstride + a] : czero<R>();
-    }
-    __syncthreads();
+    if (c0 + RST_KT < nelem) fetch(c0 + RST_KT);
 #pragma unroll 4
     for (int kk = 0; kk < RST_KT; ++kk) {
       T x[VI], t[RT];
