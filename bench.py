@@ -71,7 +71,7 @@ ORACLE_SAMPLE_DIMS = (8, 8, 8, 8)
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture, valid only
 # while the sources that define the kernel are unchanged (src_hash of its class).
-NCU_TRAFFIC = {"ortho": {"src": "a664f000a9c2c94d", "bytes_per_launch": 4843696000, "profile": "profiles/k_block_ortho_config2.md"}}
+NCU_TRAFFIC = {"ortho": {"src": "da0bd40c58662ae5", "bytes_per_launch": 4823976960, "profile": "profiles/k_block_ortho_config2.md"}}
 
 KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen", "clover", "pack", "krylov",
           "dslash64", "other"]
