@@ -213,8 +213,12 @@ void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqr
   WCMG_LAUNCH_CHECK();
 }
 
-template <typename R>
-__global__ void k_mr_update(cplx<R>* __restrict__ x, cplx<R>* __restrict__ r, const cplx<R>* __restrict__ p,
+// The step reads the residual from rin and writes the new one to r (rin = r in place;
+// the first step reads b itself).  X_ZERO: x is known to be 0 (first step: not read);
+// R_NEXT = false: the new r is not needed (last step: not written).  Same arithmetic in
+// every variant.
+template <typename R, bool X_ZERO, bool R_NEXT>
+__global__ void k_mr_update(cplx<R>* __restrict__ x, cplx<R>* r, const cplx<R>* rin, const cplx<R>* __restrict__ p,
                             const double2* __restrict__ pr, const double* __restrict__ pp, long long n) {
   __shared__ cplx<R> a_s;
   const int q = blockIdx.y;
@@ -227,14 +231,21 @@ __global__ void k_mr_update(cplx<R>* __restrict__ x, cplx<R>* __restrict__ r, co
   if (e >= n) return;
   const cplx<R> a = a_s;
   const long long o = (long long)q * n + e;
-  const cplx<R> rv = r[o];
-  cmac(x[o], a, rv);
-  r[o] = rv - cmul(a, p[o]);
+  const cplx<R> rv = rin[o];
+  cplx<R> xv = X_ZERO ? czero<R>() : x[o];
+  cmac(xv, a, rv);
+  x[o] = xv;
+  if (R_NEXT) r[o] = rv - cmul(a, p[o]);
 }
 template <typename R>
 void launch_mr_update(cplx<R>* x, cplx<R>* r, const cplx<R>* p, const double2* pr, const double* pp, long long n,
-                      int nrhs, cudaStream_t st) {
-  k_mr_update<R><<<dim3(nblk(n, 256), nrhs), 256, 0, st>>>(x, r, p, pr, pp, n);
+                      int nrhs, cudaStream_t st, bool x_zero, bool r_next, const cplx<R>* rin) {
+  const dim3 grid(nblk(n, 256), nrhs);
+  if (!rin) rin = r;
+  if (x_zero && r_next) k_mr_update<R, true, true><<<grid, 256, 0, st>>>(x, r, rin, p, pr, pp, n);
+  else if (x_zero) k_mr_update<R, true, false><<<grid, 256, 0, st>>>(x, r, rin, p, pr, pp, n);
+  else if (r_next) k_mr_update<R, false, true><<<grid, 256, 0, st>>>(x, r, rin, p, pr, pp, n);
+  else k_mr_update<R, false, false><<<grid, 256, 0, st>>>(x, r, rin, p, pr, pp, n);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -604,7 +615,7 @@ void launch_gmres_mark_done(const GmresState& s, const double* nrm2, double tol,
   template void launch_scale_dev<R>(cplx<R>*, const cplx<R>*, const double*, int, long long, int, cudaStream_t,  \
                                     const int*, int, long long);                                                 \
   template void launch_mr_update<R>(cplx<R>*, cplx<R>*, const cplx<R>*, const double2*, const double*, long long, \
-                                    int, cudaStream_t);                                                          \
+                                    int, cudaStream_t, bool, bool, const cplx<R>*);                              \
   template void launch_mask_rhs<R>(cplx<R>*, const int*, long long, int, cudaStream_t);                          \
   template void launch_fill_zero<R>(cplx<R>*, long long, cudaStream_t);
 WCMG_INST(double)

@@ -149,9 +149,13 @@ void launch_scale_dev(cplx<R>* y, const cplx<R>* x, const double* s, int inv_sqr
                       cudaStream_t st, const int* ydev = nullptr, int yadd = 0, long long ystride = 0);
 // MR update with alpha[r] = pr[r] / pp[r] (0 if pp = 0), pr = <p, r>, pp = <p, p>:
 //   x += alpha r ; r -= alpha p
+// x_zero: x is taken as 0 and not read; r_next = false: r is not written (the last step
+// of a fixed-step MR, whose residual nobody reads); rin (nullable): read the residual
+// from rin instead of r (the first step reads b) and write the new one to r.
 template <typename R>
 void launch_mr_update(cplx<R>* x, cplx<R>* r, const cplx<R>* p, const double2* pr, const double* pp, long long n,
-                      int nrhs, cudaStream_t st);
+                      int nrhs, cudaStream_t st, bool x_zero = false, bool r_next = true,
+                      const cplx<R>* rin = nullptr);
 // x[r] = mask[r] ? 0 : x[r]
 template <typename R>
 void launch_mask_rhs(cplx<R>* x, const int* mask, long long n, int nrhs, cudaStream_t st);

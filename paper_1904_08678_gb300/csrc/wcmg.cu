@@ -576,9 +576,13 @@ static void mr(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int s
   cplx<R>* r = ws<R>(L, "mr_r", nrhs);
   cplx<R>* p = ws<R>(L, "mr_p", nrhs);
   L.sc.ensure(max_rhs_all(c), std::max(c->p.outer_restart, c->p.coarse_restart));
-  copy_fields<R>(c, r, b, n * nrhs);
-  launch_fill_zero<R>(x, n * nrhs, c->st);
+  if (steps == 0) {
+    launch_fill_zero<R>(x, n * nrhs, c->st);
+    return;
+  }
+  // the first step reads b as its residual and sets x = alpha r; the last one leaves r
   for (int k = 0; k < steps; ++k) {
+    const cplx<R>* rk = k == 0 ? b : r;
     if (l == 0) {
       // fine level: the two reductions come out of the Dslash epilogue
       if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
@@ -588,15 +592,17 @@ static void mr(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int s
       const double V = L.g.V, s = sizeof(cplx<R>);
       const int cls = sizeof(R) == 8 ? WCMG_K_DSLASH64 : WCMG_K_DSLASH;
       KPROF(c, cls, V * s * (24.0 * nrhs + 72.0), V * (1872.0 + 16.0) * nrhs,
-            launch_dslash_mr<R>(p, r, Prec<R>::gauge(c), Prec<R>::clover(c), L.g.lg(), nrhs, L.sc.pr(),
+            launch_dslash_mr<R>(p, rk, Prec<R>::gauge(c), Prec<R>::clover(c), L.g.lg(), nrhs, L.sc.pr(),
                                 L.sc.slot(4), c->mr_pr.p, c->mr_pp.p, c->st));
     } else {
-      apply_op<R>(c, l, p, r, nrhs);
-      dot_op<R>(c, L.sc.pr(), p, r, n, nrhs);
+      apply_op<R>(c, l, p, rk, nrhs);
+      dot_op<R>(c, L.sc.pr(), p, rk, n, nrhs);
       norm2_op<R>(c, L.sc.slot(4), p, n, nrhs);
     }
-    KPROF(c, WCMG_K_BLAS, 5.0 * n * nrhs * sizeof(cplx<R>), 16.0 * n * nrhs,
-          launch_mr_update<R>(x, r, p, L.sc.pr(), L.sc.slot(4), n, nrhs, c->st));
+    const bool first = k == 0, last = k + 1 == steps;
+    KPROF(c, WCMG_K_BLAS, ((first ? 2.0 : 3.0) + (last ? 0.0 : 2.0)) * n * nrhs * sizeof(cplx<R>),
+          16.0 * n * nrhs,
+          launch_mr_update<R>(x, r, p, L.sc.pr(), L.sc.slot(4), n, nrhs, c->st, first, !last, rk));
   }
 }
 
