@@ -980,9 +980,30 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1)
                     int nv) {
   using T = cplx<R>;
   const int i = blockIdx.x % nv;  // vector fastest: the CTAs running together share links and clover
-  const int s = (blockIdx.x / nv) * blockDim.x + threadIdx.x;
-  if (s >= V) return;
-  if (MODE == ST_FACE_HOP && !on_face(bi, s, hopdir)) return;
+  const int t = (blockIdx.x / nv) * blockDim.x + threadIdx.x;
+  int s = t;
+  if (MODE == ST_FACE_HOP) {
+    // one thread per site of the hopdir face of every aggregate: face site f of block
+    // t / nface has l[mu] fixed and the other local coordinates from f (x fastest)
+    const int mu = hopdir >> 1, nface = bi.bvol / bi.b[mu];
+    if (t >= V / bi.b[mu]) return;
+    int f = t % nface, loc = 0, stride = 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int lk;
+      if (k == mu) {
+        lk = (hopdir & 1) ? 0 : bi.b[mu] - 1;
+      } else {
+        lk = f % bi.b[k];
+        f /= bi.b[k];
+      }
+      loc += lk * stride;
+      stride *= bi.b[k];
+    }
+    s = (t / nface) * bi.bvol + loc;
+  } else if (s >= V) {
+    return;
+  }
   const long long rstride = 12LL * V;
   const cplx<R>* vi = in + (long long)i * rstride;
   T ap[12], am[12];
@@ -1041,11 +1062,14 @@ void launch_dslash_chiral(cplx<R>* out, const cplx<R>* vecs, const cplx<R>* gaug
   BlockInfo bi;
   for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
   bi.bvol = g.bvol;
-  const dim3 grid((unsigned)(nblk(g.V, 128) * (long long)nv));
-  if (mode == ST_BLOCK_INTERIOR)
+  if (mode == ST_BLOCK_INTERIOR) {
+    const dim3 grid((unsigned)(nblk(g.V, 128) * (long long)nv));
     k_dslash_chiral<R, ST_BLOCK_INTERIOR><<<grid, 128, 0, st>>>(out, vecs, gauge, clov, g.nbr, g.V, bi, hopdir, nv);
-  else if (mode == ST_FACE_HOP)
+  } else if (mode == ST_FACE_HOP) {
+    if (hopdir < 0 || hopdir > 7) throw Error(-1, "chirality-pair stencil: face direction out of range");
+    const dim3 grid((unsigned)(nblk(g.V / g.b[hopdir >> 1], 128) * (long long)nv));
     k_dslash_chiral<R, ST_FACE_HOP><<<grid, 128, 0, st>>>(out, vecs, gauge, clov, g.nbr, g.V, bi, hopdir, nv);
+  }
   else
     throw Error(-1, "chirality-pair stencil: block-interior or face mode only");
   WCMG_LAUNCH_CHECK();
