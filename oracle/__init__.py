@@ -17,7 +17,10 @@ invariants and brute force:
   aggregation.py  block orthonormalisation, P, P^dag    pinned: QR uniqueness, P^dag P = 1, adjointness, gamma5 P = P sigma3
   coarse.py       Galerkin coarse operator (9 blocks)   pinned: dense P^dag D P, sigma3-hermiticity, gauge invariance
   solvers.py      MR, GMRES, FGMRES                     pinned: MR step minimality, dense solve, lucky breakdown
-  mg.py           MG cycle, initial + iterative setup   pinned: block 1^4 exact preconditioner; setup is "parity unpinned"
+  mg.py           MG cycle, initial + iterative setup   pinned: block 1^4 exact preconditioner; setup sweeps = normalised
+                                                         inverse iteration (free-field spectrum) with an exact
+                                                         smoother / cycle; Rayleigh quotient falls with sweeps
+  sap.py          SAP smoother, even-odd block solves   pinned: red-black exact solves, dense per-block solves
   ptc.py          parallel-transport conv. network      pinned: gauge/translation equivariance, adjoint identity,
                                                          finite-difference gradients
 

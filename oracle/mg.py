@@ -28,8 +28,11 @@ Readings used here (each listed with the other readings of the paper):
          (all using the current hierarchy), then rebuild P_0 and D_1; every coarser
          non-coarsest level then runs one warm-started initial sweep on its current
          vectors with its new operator and rebuilds its own P and D.
-The outcome of the setup depends on every step, so it has no closed form: the
-setup is "parity unpinned" beyond its per-operator pins.
+The outcome of the setup with the real smoother has no closed form.  Its sweeps are
+pinned where they reduce to a textbook routine: with an exact smoother (GMRES with
+as many steps as the free operator has distinct eigenvalues) the initial sweeps, and
+with an exact cycle (one-site aggregates, Nvec 6, coarse solve to 1e-14) the refinement
+sweeps, are normalised inverse iteration, checked against the free-field spectrum.
 """
 from dataclasses import dataclass, field
 from typing import List, Sequence

@@ -143,3 +143,76 @@ def test_kcycle_solve_needs_no_more_iterations_than_the_vcycle():
     assert ik.converged and iv.converged and ik.true_residual <= 1e-10
     assert ik.iterations <= iv.iterations
     assert rel(xk, xv) < 1e-8
+
+
+# ---- the setup as inverse iteration (special cases with an exact smoother / cycle) ----
+# On the free field (U = 1) of a lattice with extent 2 in every direction the momenta are
+# p_mu in {0, pi}, so sin p_mu = 0 and the free Wilson operator is diagonal in momentum
+# space with the real eigenvalue lambda(p) = 4 + m0 - sum_mu cos p_mu = m0 + 2 n_pi
+# (n_pi: the number of components equal to pi), times the 12 x 12 identity.
+FREE = (2, 2, 2, 2)
+
+
+def free_operator(m0):
+    V = int(np.prod(FREE))
+    U = np.zeros((4, V, 3, 3), dtype=complex)
+    U[:, :] = np.eye(3)
+    return WilsonClover(U, FREE, m0, 1.0)
+
+
+def free_inverse_power(v, m0, s):
+    """D^-s v from the spectrum above (FFT over the four axes of the (T, Z, Y, X, 12) grid)."""
+    F = np.fft.fftn(v, axes=(0, 1, 2, 3))
+    p = [2 * np.pi * np.fft.fftfreq(n) for n in v.shape[:4]]
+    pt, pz, py, px = np.meshgrid(*p, indexing="ij")
+    lam = 4 + m0 - (np.cos(pt) + np.cos(pz) + np.cos(py) + np.cos(px))
+    return np.fft.ifftn(F / lam[..., None] ** s, axes=(0, 1, 2, 3))
+
+
+def free_vectors(n, seed):
+    return [to_grid(v, FREE) for v in inputs.setup_vectors(FREE, 12, n, 0, seed)]
+
+
+def test_free_spectrum_helper_inverts_the_operator():
+    D, v = free_operator(-0.1), free_vectors(1, 1301)[0]
+    assert rel(D(free_inverse_power(v, -0.1, 1)), v) < 1e-13
+
+
+def test_initial_setup_is_normalised_inverse_iteration_with_an_exact_smoother():
+    """GMRES with 5 steps solves the free operator exactly (5 distinct eigenvalues), so s
+    initial sweeps give D^-s v0 / ||D^-s v0|| for every random vector v0."""
+    m0 = -0.1
+    D, iv = free_operator(m0), free_vectors(6, 1302)
+    for s in (1, 3):
+        mg = Multigrid(D, MGParams(blocks=[(1, 1, 1, 1)], nvecs=[6], smoother="gmres", smoother_steps=5,
+                                   init_sweeps=s, refine_sweeps=0), [iv])
+        for v0, v in zip(iv, mg.levels[0].vecs):
+            want = free_inverse_power(v0, m0, s)
+            assert rel(v, want / np.linalg.norm(want)) < 1e-12
+
+
+def test_refinement_is_normalised_inverse_iteration_with_an_exact_cycle():
+    """One-site aggregates with Nvec 6 make P unitary, so with a coarse solve to 1e-14 the
+    cycle is D^-1 (the smoother then sees a zero residual): s refinement sweeps turn the
+    vectors of the initial setup v into D^-s v / ||D^-s v||."""
+    m0 = -0.1
+    D, iv = free_operator(m0), free_vectors(6, 1303)
+    kw = dict(blocks=[(1, 1, 1, 1)], nvecs=[6], init_sweeps=2, coarse_tol=1e-14, coarse_maxiter=200)
+    v_init = Multigrid(D, MGParams(refine_sweeps=0, **kw), [iv]).levels[0].vecs
+    v_ref = Multigrid(D, MGParams(refine_sweeps=2, **kw), [iv]).levels[0].vecs
+    for v0, v in zip(v_init, v_ref):
+        want = free_inverse_power(v0, m0, 2)
+        assert rel(v, want / np.linalg.norm(want)) < 1e-10
+
+
+def test_setup_sweeps_lower_the_rayleigh_quotient():
+    """The MR(4) setup sweeps on a random gauge field drive every vector towards the low
+    modes: ||D v|| / ||v|| falls with every sweep."""
+    dims, D, _ = config1()
+    iv = [to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 4, 0, 1304)]
+    quotients = []
+    for s in (0, 1, 2, 3):
+        mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[4], init_sweeps=s, refine_sweeps=0), [iv])
+        quotients.append([np.linalg.norm(D(v)) / np.linalg.norm(v) for v in mg.levels[0].vecs])
+    q = np.array(quotients)
+    assert np.all(q[1:] < q[:-1])
