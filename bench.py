@@ -766,8 +766,29 @@ def measure_coarse_isolated(ctx, wcmg, torch, dev, stream, flush, hbm, cfg, reps
     ctx.set_coarse_tile(1, 1, prec, kind=saved["kind"], rhs_per_cta=saved["rhs_per_cta"], parts=saved["parts"],
                         threads=saved["threads"], ntile=saved["ntile"])
     best = cold if cold["kernel_us"] <= warm["kernel_us"] else warm
+    # context for the ratio: the measured HBM peak is a 2 GiB + 2 GiB copy; a device copy
+    # moving the same bytes as one apply (half read, half written), timed the same way
+    # (L2 flushed before each, CUDA events on the stream), shows what a transfer of this
+    # size reaches at all
+    src = torch.empty(algo // 2, dtype=torch.uint8, device=dev)
+    dst = torch.empty_like(src)
+    times = []
+    for i in range(60):
+        flush.fill_(6)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dst.copy_(src)
+        b.record(stream)
+        b.synchronize()
+        if i >= 10:
+            times.append(a.elapsed_time(b) * 1e3)
+    copy_us = float(np.median(times))
+    copy_gbs = 2 * (algo // 2) / (copy_us * 1e-6) / 1e9
     return {"sites": Vc, "nbasis": nb, "link_bytes": link_b, "algorithmic_bytes": algo, "l2": "flushed before every apply",
             "kernel_us": best["kernel_us"], "GB/s": best["GB/s"], "frac_of_hbm": best["frac_of_hbm"],
+            "same_size_copy": {"bytes": 2 * (algo // 2), "us": round(copy_us, 2), "GB/s": round(copy_gbs, 1),
+                               "frac_of_hbm": round(copy_gbs / hbm, 4),
+                               "apply_frac_of_copy": round(best["GB/s"] / copy_gbs, 4)},
             "shape_tuned_for_solve": warm, "shape_tuned_for_streaming": cold}
 
 

@@ -37,9 +37,11 @@ sweeps, are normalised inverse iteration, checked against the free-field spectru
 from dataclasses import dataclass, field
 from typing import List, Sequence
 
+import numpy as np
+
 from .aggregation import Aggregation
 from .coarse import coarsen
-from .sap import sap
+from .sap import parity, sap, self_solve
 from .solvers import fgmres, gmres, mr, norm
 
 
@@ -159,3 +161,28 @@ class Multigrid:
         return fgmres(self.levels[0].op, b, lambda v: self.cycle(0, v),
                       restart=self.p.outer_restart, tol=self.p.outer_tol,
                       maxiter=self.p.outer_maxiter, x0=x0, verify=True)
+
+    def solve_even_odd(self, b):
+        """Even-odd (red-black) preconditioned outer solve (Sec. 4 lists red-black
+        preconditioning among the missing features).  With sites even / odd by the
+        parity of x + y + z + t, D = [[C_ee, H_eo], [H_oe, C_oo]]:
+          b^_o = b_o - H_oe C_ee^-1 b_e,
+          FGMRES on S = C_oo - H_oe C_ee^-1 H_eo, right-preconditioned by the odd-odd
+          block of the MG cycle (S^-1 is the odd-odd block of D^-1), stopping when
+          ||b^_o - S x_o|| <= outer_tol ||b|| (equal to the full residual),
+          x_e = C_ee^-1 (b_e - H_eo x_o).
+        Odd-site vectors are kept as full fields that vanish on even sites."""
+        D = self.levels[0].op
+        ev = (parity(self.levels[0].dims) == 0)[..., None]
+        od = ~ev
+        b_hat = np.where(od, b - D(np.where(ev, self_solve(D, b), 0)), 0)
+
+        def schur(v):
+            Dv = D(v)
+            return np.where(od, Dv - D(np.where(ev, self_solve(D, np.where(ev, Dv, 0)), 0)), 0)
+
+        tol = self.p.outer_tol * norm(b) / norm(b_hat)
+        x_o, info = fgmres(schur, b_hat, lambda v: np.where(od, self.cycle(0, v), 0),
+                           restart=self.p.outer_restart, tol=tol, maxiter=self.p.outer_maxiter, verify=True)
+        x_e = np.where(ev, self_solve(D, b - D(x_o)), 0)
+        return x_e + x_o, info

@@ -216,3 +216,19 @@ def test_setup_sweeps_lower_the_rayleigh_quotient():
         quotients.append([np.linalg.norm(D(v)) / np.linalg.norm(v) for v in mg.levels[0].vecs])
     q = np.array(quotients)
     assert np.all(q[1:] < q[:-1])
+
+
+def test_even_odd_outer_solve_reaches_the_dense_solution():
+    """The Schur-complement outer solve: its solution satisfies the full system to the
+    outer tolerance and equals the dense solution; the odd-odd block of the cycle
+    preconditions S about as well as the cycle preconditions D (within 2 iterations)."""
+    dims, D, b = config1()
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 8, 0, 1001)]]
+    mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[8]), iv)
+    x, info = mg.solve_even_odd(b)
+    assert info.converged
+    assert np.linalg.norm(b - D(x)) <= 1.01e-10 * np.linalg.norm(b)
+    x_ref, _ = gmres(D, b, restart=60, tol=1e-13, maxiter=5000, verify=True)
+    assert rel(x, x_ref) < 1e-8
+    _, plain = mg.solve(b)
+    assert abs(info.iterations - plain.iterations) <= 2
