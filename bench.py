@@ -1,8 +1,9 @@
 """Benchmark: Wilson-clover multigrid time-to-solution on one GB300 per rank.
 
 One step = one full pass of the hot path on the 16^3x32 two-level workload:
-set the gauge field (clover term built on the device), initial setup (3 MR(4)
-sweeps over 24 near-null vectors), 2 iterative-refinement sweeps (multigrid
+set the gauge field (clover term built on the device), initial setup (24 random
+near-null candidates drawn on the device from the seeded counter-based generator,
+3 MR(4) sweeps over them), 2 iterative-refinement sweeps (multigrid
 cycle over all 24 vectors), and the FGMRES(20) solve of D x = b to a true
 relative residual of 1e-10.  `value` is the time-to-solution in seconds
 (device CUDA events on the call's stream, max over ranks), inputs resident in
@@ -300,8 +301,10 @@ def run_gpu(args, rank, world, local):
                               autotune=args.autotune))
 
     def step(x, U_, iv_, b_):
+        # iv_ None: the near-null candidates come from the device generator (the same
+        # counter-based fields as inputs.setup_vectors), so no host copy of them
         ctx.set_gauge(U_, stream)
-        s1 = ctx.setup(iv_, stream)
+        s1 = ctx.setup(iv_, stream) if iv_ is not None else ctx.setup_seeded(cfg["gauge_seed"], stream)
         s2 = ctx.solve(b_, x, nrhs=nrhs, stream=stream)
         return s1, s2
 
@@ -316,7 +319,7 @@ def run_gpu(args, rank, world, local):
     first_solve = None
     for _ in range(args.warmup):
         flush.fill_(1)
-        s1, s2 = step(xd, Ud, ivd, bd)
+        s1, s2 = step(xd, Ud, None, bd)
         add_stats(acc, s1)
         add_stats(acc, s2)
         if first_solve is None:
@@ -342,7 +345,7 @@ def run_gpu(args, rank, world, local):
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             starts[i].record(stream)
-            s1, s2 = step(xd, Ud, ivd, bd)
+            s1, s2 = step(xd, Ud, None, bd)
             ends[i].record(stream)
             add_stats(acc, s1)
             add_stats(acc, s2)
@@ -406,7 +409,6 @@ def run_gpu(args, rank, world, local):
 
     # e2e: same step through the C-ABI with pinned host buffers
     Uh = torch.from_numpy(U).pin_memory()
-    ivh = torch.from_numpy(iv).pin_memory()
     bh = torch.from_numpy(b).pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
     ctx.set_profile(0)
@@ -417,12 +419,12 @@ def run_gpu(args, rank, world, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step(xh, Uh, ivh, bh)
+        step(xh, Uh, None, bh)
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms.append(e0.elapsed_time(e1))
     e2e_ms = max_over_ranks(dist, sum(e_ms) / len(e_ms), dev)
-    h2d = U.nbytes + iv.nbytes + b.nbytes
+    h2d = U.nbytes + b.nbytes  # the near-null candidates are generated on the device from the seed
     d2h = b.nbytes
 
     # plain FP64 GPU multigrid on the same field, source and setup parameters (one step)
@@ -466,7 +468,8 @@ def run_gpu(args, rank, world, local):
         med = lambda v: round(statistics.median(v), 2)
         line = {
             "metric": "time_to_solution_1e-10", "value": round(ms / 1e3, 5), "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "ms_each_step": [round(t, 3) for t in step_ms], "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.inner == "f32" else "f64", "data": "synthetic",
             "config": {"workload": cfg["workload"].replace("NRHS", str(nrhs)), "dims": list(cfg["dims"]),

@@ -214,6 +214,16 @@ int wcmg_apply_coarse(wcmg_ctx* ctx, int level, const void* in, void* out, int n
  * sweeps.  Fills every P_l and D_{l+1}. */
 int wcmg_setup(wcmg_ctx* ctx, const void* init_vecs, int where, void* stream, wcmg_stats* st);
 
+/* wcmg_setup with the random vectors generated on the device: vector i of level l is
+ * the complex Gaussian field of the counter-based generator with (seed, stream
+ * 1 + 1000 l + i), element j [site][component] (external order) from the counters
+ * 2j, 2j + 1: SplitMix64 finaliser of seed * 0x9E3779B97F4A7C15 + stream *
+ * 0xD1B54A32D192ED03 + k, u = (out >> 11) 2^-53, Box-Muller (re, im) = sqrt(-2 log(1 -
+ * u_2j)) (cos, sin)(2 pi u_2j+1), the transform in FP32.  The same fields as the host
+ * generator of the test inputs (which transforms in FP64) to FP32 rounding.  No host
+ * transfer of the Nvec fields. */
+int wcmg_setup_seeded(wcmg_ctx* ctx, unsigned long long seed, void* stream, wcmg_stats* st);
+
 /* One application of the multigrid preconditioner M_0 to nrhs fine fields. */
 int wcmg_mg_cycle(wcmg_ctx* ctx, const void* r, void* e, int nrhs, int where, void* stream);
 

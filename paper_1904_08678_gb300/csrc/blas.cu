@@ -602,6 +602,38 @@ void launch_gmres_mark_done(const GmresState& s, const double* nrm2, double tol,
   WCMG_LAUNCH_CHECK();
 }
 
+// ---- counter-based Gaussian fields (the generator of the seeded inputs) ----
+// Element j of field i (stream stream0 + i): the counter c = seed * 0x9E3779B97F4A7C15
+// + stream * 0xD1B54A32D192ED03 + k (mod 2^64) for k = 2j, 2j+1 goes through the
+// SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA 2014); u = (out >> 11) 2^-53 exactly;
+// Box-Muller: re = sqrt(-2 log(1 - u_2j)) cos(2 pi u_2j+1), im = the same with sin.  The
+// transform runs in FP32 (1 - u is formed exactly in FP64 first, so it never rounds to
+// 0): FP64 transcendentals on this part would cost more than copying the fields in.
+__device__ __forceinline__ double counter_uniform(unsigned long long base, unsigned long long k) {
+  unsigned long long z = base + k;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z = z ^ (z >> 31);
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+__global__ void k_counter_gaussian(double2* __restrict__ out, long long n, unsigned long long seed,
+                                   unsigned long long stream0) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const unsigned long long stream = stream0 + blockIdx.y;
+  const unsigned long long base = seed * 0x9E3779B97F4A7C15ULL + stream * 0xD1B54A32D192ED03ULL;
+  const double u1 = counter_uniform(base, 2ULL * j), u2 = counter_uniform(base, 2ULL * j + 1);
+  const float r = sqrtf(-2.0f * logf((float)(1.0 - u1)));
+  float sn, cs;
+  sincospif((float)(2.0 * u2), &sn, &cs);
+  out[(long long)blockIdx.y * n + j] = make_double2((double)(r * cs), (double)(r * sn));
+}
+void launch_counter_gaussian(double2* out, long long n, int nfields, unsigned long long seed,
+                             unsigned long long stream0, cudaStream_t st) {
+  k_counter_gaussian<<<dim3(nblk(n, 256), nfields), 256, 0, st>>>(out, n, seed, stream0);
+  WCMG_LAUNCH_CHECK();
+}
+
 #define WCMG_INST(R)                                                                                             \
   template void launch_dot<R>(double2*, const cplx<R>*, const cplx<R>*, long long, int, double2*, cudaStream_t); \
   template void launch_norm2<R>(double*, const cplx<R>*, long long, int, double*, cudaStream_t);                 \

@@ -161,6 +161,10 @@ template <typename R>
 void launch_mask_rhs(cplx<R>* x, const int* mask, long long n, int nrhs, cudaStream_t st);
 template <typename R>
 void launch_fill_zero(cplx<R>* x, long long n, cudaStream_t st);
+// nfields complex Gaussian fields of n entries, field i from the counter-based generator
+// with stream stream0 + i (SplitMix64 finaliser + Box-Muller, the seeded-input scheme)
+void launch_counter_gaussian(double2* out, long long n, int nfields, unsigned long long seed,
+                             unsigned long long stream0, cudaStream_t st);
 
 // ---- SAP smoother (sap.cu) ----
 // Blocks are the level's aggregates (block B = sites [B bvol, (B+1) bvol)); colour[B]

@@ -2183,6 +2183,10 @@ int wcmg_apply_coarse(wcmg_ctx* c, int level, const void* in, void* out, int nrh
   API_END(c)
 }
 
+extern "C++" {
+static void setup_from(wcmg_ctx* c, const double2* iv, wcmg_stats* st);
+}
+
 int wcmg_setup(wcmg_ctx* c, const void* init_vecs, int where, void* stream, wcmg_stats* st) {
   API_BEGIN(c)
   c->st = (cudaStream_t)stream;
@@ -2190,7 +2194,29 @@ int wcmg_setup(wcmg_ctx* c, const void* init_vecs, int where, void* stream, wcmg
   if (!init_vecs) throw Error(WCMG_ERR_ARG, "init_vecs is required");
   size_t tot = 0;
   for (int l = 0; l + 1 < c->p.n_levels; ++l) tot += (size_t)c->L[l].nvec * c->L[l].n() * 16;
-  const double2* iv = in_dev(c, init_vecs, tot, where, 2);
+  setup_from(c, in_dev(c, init_vecs, tot, where, 2), st);
+  API_END(c)
+}
+
+int wcmg_setup_seeded(wcmg_ctx* c, unsigned long long seed, void* stream, wcmg_stats* st) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+  size_t tot = 0;
+  for (int l = 0; l + 1 < c->p.n_levels; ++l) tot += (size_t)c->L[l].nvec * c->L[l].n() * 16;
+  double2* iv = (double2*)c->stage[2].ensure(tot);
+  long long off = 0;
+  for (int l = 0; l + 1 < c->p.n_levels; ++l) {
+    const long long n = c->L[l].n();
+    launch_counter_gaussian(iv + off, n, c->L[l].nvec, seed, 1ULL + 1000ULL * l, c->st);
+    off += (long long)c->L[l].nvec * n;
+  }
+  setup_from(c, iv, st);
+  API_END(c)
+}
+
+extern "C++" {
+static void setup_from(wcmg_ctx* c, const double2* iv, wcmg_stats* st) {
   if (st) std::memset(st, 0, sizeof(*st));
   c->prof.flush();
   wcmg_kstat k0[WCMG_NKCLASS];
@@ -2206,8 +2232,8 @@ int wcmg_setup(wcmg_ctx* c, const void* init_vecs, int where, void* stream, wcmg
     st->coarse_iterations = c->coarse_its;
     st->kernel_launches = launch_counter() - l0;
   }
-  API_END(c)
 }
+}  // extern "C++"
 
 int wcmg_mg_cycle(wcmg_ctx* c, const void* r, void* e, int nrhs, int where, void* stream) {
   API_BEGIN(c)

@@ -139,6 +139,7 @@ _SIGS = {
     "wcmg_prolong": ([_PCTX, _i, _vp, _vp, _i, _i, _i, _vp], _i),
     "wcmg_apply_coarse": ([_PCTX, _i, _vp, _vp, _i, _i, _i, _vp], _i),
     "wcmg_setup": ([_PCTX, _vp, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
+    "wcmg_setup_seeded": ([_PCTX, ctypes.c_ulonglong, _vp, ctypes.POINTER(wcmg_stats)], _i),
     "wcmg_mg_cycle": ([_PCTX, _vp, _vp, _i, _i, _vp], _i),
     "wcmg_krylov": ([_PCTX, _i, _i, _vp, _vp, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_i)], _i),
     "wcmg_solve": ([_PCTX, _vp, _vp, _i, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
@@ -304,6 +305,11 @@ class Context:
         p, w = _buf(init_vecs)
         st = wcmg_stats()
         self._check(wcmg_setup(self.h, p, w, _stream(stream), ctypes.byref(st)))
+        return st
+
+    def setup_seeded(self, seed, stream=None):
+        st = wcmg_stats()
+        self._check(wcmg_setup_seeded(self.h, ctypes.c_ulonglong(seed % 2**64), _stream(stream), ctypes.byref(st)))
         return st
 
     def mg_cycle(self, r, e, nrhs=1, stream=None):

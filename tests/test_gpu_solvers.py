@@ -245,3 +245,31 @@ def test_three_level_cycles_match_oracle(lib, kcycle):
     assert st.converged and st.true_residual <= 1e-10
     assert rel(host(x)[0].reshape(V, 12), xo.reshape(V, 12)) < 1e-8
     assert abs(st.outer_iterations - info.iterations) <= 1
+
+
+def test_seeded_setup_draws_the_fields_of_the_input_generator(lib):
+    """wcmg_setup_seeded generates the random vectors on the device with the counter-based
+    generator of the test inputs (exact uniforms, FP32 Box-Muller transform): with no
+    smoothing sweeps P is the block-orthonormalised random vectors, equal to those of the
+    host-generated (FP64-transformed) fields to FP32 rounding, on both levels; with setup
+    sweeps they still agree to that order."""
+    dims = (8, 8, 8, 8)
+    kw = dict(dims=dims, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvec=[6, 4], n_levels=3, m0=-0.1, csw=1.0)
+    U = inputs.random_gauge(dims, 0.3, 1401)
+    iv = np.concatenate([inputs.setup_vectors(dims, 12, 6, 0, 1401).ravel(),
+                         inputs.setup_vectors((4, 4, 4, 4), 12, 4, 1, 1401).ravel()])
+    for sweeps, tol in ((0, 1e-6), (3, 1e-5)):
+        P = []
+        for seeded in (False, True):
+            ctx = lib.Context(lib.default_params(setup_init_sweeps=sweeps, setup_refine_sweeps=min(sweeps, 1), **kw))
+            ctx.set_gauge(dev(U))
+            if seeded:
+                ctx.setup_seeded(1401)
+            else:
+                ctx.setup(dev(iv))
+            P0 = dev(np.zeros((6, 4096, 12), dtype=complex))
+            P1 = dev(np.zeros((4, 256, 12), dtype=complex))
+            ctx.get_nullvecs(0, P0)
+            ctx.get_nullvecs(1, P1)
+            P.append((host(P0), host(P1)))
+        assert rel(P[1][0], P[0][0]) < tol and rel(P[1][1], P[0][1]) < tol
