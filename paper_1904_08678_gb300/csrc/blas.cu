@@ -529,8 +529,12 @@ static int arnoldi_cluster_size() {
   return cached;
 }
 
+// The 16-CTA cluster reads the basis through 16 SMs only: it beats the seven
+// whole-GPU launches it replaces for short vectors (the coarsest levels: 10^4 - 4 x 10^4
+// entries) but not for fine-level ones (a 16^4 lattice, 7.9 x 10^5 entries: 300 us per
+// step against about 60 us), so it takes vectors of at most 2^17 entries.
 bool arnoldi_fused_ok(long long n, int nrhs, int m) {
-  return nrhs == 1 && m + 1 <= AC_MAXK && n <= (1LL << 20) && arnoldi_cluster_size() > 0;
+  return nrhs == 1 && m + 1 <= AC_MAXK && n <= (1LL << 17) && arnoldi_cluster_size() > 0;
 }
 
 template <typename R>

@@ -198,7 +198,7 @@ struct GmresState {
 // h1, h2: the two CGS passes' coefficients [nrhs][m+1]; hnorm2 = ||w||^2 after both.
 // `final_done`: a recurrence convergence also marks the rhs done (no true-residual check).
 // One fused Arnoldi step after the operator application, for one short rhs
-// (n <= 2^20, restart <= 64): CGS2 projections of w against V_0..V_j, the norm,
+// (n <= 2^17, restart <= 64): CGS2 projections of w against V_0..V_j, the norm,
 // the Givens update of Hessenberg column j and V_{j+1} = w / ||w||, in one launch
 // of a thread-block cluster (16 CTAs, else 8).  jdev (nullable): step on the device.
 bool arnoldi_fused_ok(long long n, int nrhs, int m);
