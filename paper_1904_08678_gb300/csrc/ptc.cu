@@ -52,6 +52,10 @@ __device__ __forceinline__ void ptc_transport(float2 (&t)[12], const float2* __r
 __device__ __forceinline__ int ptc_opp(int h) { return h == 0 ? 0 : (((h - 1) & 1) ? h - 1 : h + 1); }
 
 // Forward layer.  Thread per (site, output channel i, rhs); W in shared memory.
+// Each thread computes OG output fields at its site: the parallel transport of an
+// input field along a hop is formed once and applied to the OG spin weights (every
+// output still sums its terms in the same order).
+template <int OG>
 __global__ void __launch_bounds__(128) k_ptc_forward(float2* __restrict__ out, const float2* __restrict__ in,
                                                      const float2* __restrict__ W, const float2* __restrict__ U,
                                                      const int* __restrict__ nbr, int V, int nin, int nout, int nrhs) {
@@ -59,32 +63,43 @@ __global__ void __launch_bounds__(128) k_ptc_forward(float2* __restrict__ out, c
   const int nw = nout * nin * PTC_NHOP * 16;
   for (int k = threadIdx.x; k < nw; k += blockDim.x) Ws[k] = W[k];
   __syncthreads();
-  const int io = blockIdx.y % nout, r = blockIdx.y / nout;
+  const int ngrp = (nout + OG - 1) / OG;
+  const int io0 = (blockIdx.y % ngrp) * OG, r = blockIdx.y / ngrp;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= V || r >= nrhs) return;
   const long long fs = 12LL * V;
-  float2 acc[12];
+  float2 acc[OG][12];
 #pragma unroll
-  for (int c = 0; c < 12; ++c) acc[c] = make_float2(0.f, 0.f);
+  for (int g = 0; g < OG; ++g)
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[g][c] = make_float2(0.f, 0.f);
   for (int j = 0; j < nin; ++j) {
     const float2* f = in + ((long long)r * nin + j) * fs;
     for (int h = 0; h < PTC_NHOP; ++h) {
       float2 t[12];
       ptc_transport(t, f, U, nbr, V, x, h);
-      const float2* w = Ws + ((io * nin + j) * PTC_NHOP + h) * 16;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int g = 0; g < OG; ++g) {
+        if (io0 + g >= nout) break;
+        const float2* w = Ws + (((io0 + g) * nin + j) * PTC_NHOP + h) * 16;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const float2 wab = w[4 * a + b];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) cmac(acc[3 * a + c], wab, t[3 * b + c]);
-        }
+          for (int b = 0; b < 4; ++b) {
+            const float2 wab = w[4 * a + b];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cmac(acc[g][3 * a + c], wab, t[3 * b + c]);
+          }
+      }
     }
   }
-  float2* o = out + ((long long)r * nout + io) * fs;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) o[(long long)c * V + x] = acc[c];
+  for (int g = 0; g < OG; ++g) {
+    if (io0 + g >= nout) break;
+    float2* o = out + ((long long)r * nout + io0 + g) * fs;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o[(long long)c * V + x] = acc[g][c];
+  }
 }
 
 // Backward with respect to the layer input:
@@ -280,7 +295,11 @@ __global__ void k_gaussian_field(float2* __restrict__ out, long long n, unsigned
 void launch_ptc_forward(float2* out, const float2* in, const float2* W, const float2* U, const int* nbr, int V,
                         int nin, int nout, int nrhs, cudaStream_t st) {
   const size_t smem = (size_t)nout * nin * PTC_NHOP * 16 * sizeof(float2);
-  k_ptc_forward<<<dim3(nblk(V, 128), nout * nrhs), 128, smem, st>>>(out, in, W, U, nbr, V, nin, nout, nrhs);
+  if (nout >= 4)
+    k_ptc_forward<4><<<dim3(nblk(V, 128), ((nout + 3) / 4) * nrhs), 128, smem, st>>>(out, in, W, U, nbr, V, nin,
+                                                                                     nout, nrhs);
+  else
+    k_ptc_forward<1><<<dim3(nblk(V, 128), nout * nrhs), 128, smem, st>>>(out, in, W, U, nbr, V, nin, nout, nrhs);
   WCMG_LAUNCH_CHECK();
 }
 void launch_ptc_backward_data(float2* gin, const float2* gout, const float2* W, const float2* U, const int* nbr, int V,
