@@ -65,7 +65,7 @@ typedef struct wcmg_params {
   int nvec[WCMG_MAX_LEVELS - 1];        /* near-null vectors per coarsening (nbasis = 2 nvec) */
   double m0;                            /* bare mass: D has (4 + m0) on the diagonal */
   double csw;                           /* clover coefficient */
-  int smoother_steps;                   /* MR steps of the post-smoother and setup smoother */
+  int smoother_steps;                   /* MR steps of the post-smoother and setup smoother (0 .. 64) */
   int setup_init_sweeps;                /* initial-setup sweeps per level */
   int setup_refine_sweeps;              /* iterative-refinement sweeps */
   int coarse_restart;                   /* GMRES(m) on the coarsest level */

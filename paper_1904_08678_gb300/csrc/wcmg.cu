@@ -1795,8 +1795,7 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       if ((fb[0] & 1) || bv > 256)
         throw Error(WCMG_ERR_ARG, "sap_eo needs fine aggregates of at most 256 sites with an even x extent");
     }
-    if (p->smoother == WCMG_SMOOTHER_GMRES && p->smoother_steps > 64)
-      throw Error(WCMG_ERR_ARG, "GMRES smoother: at most 64 steps");
+    if (p->smoother_steps > 64) throw Error(WCMG_ERR_ARG, "smoother_steps: at most 64");
     if ((p->kcycle != 0 && p->kcycle != 1) || p->kcycle_steps < 1 || p->kcycle_steps > 64 || !(p->kcycle_tol >= 0.0))
       throw Error(WCMG_ERR_ARG, "kcycle must be 0 or 1, kcycle_steps 1..64, kcycle_tol >= 0");
     c->L.resize(nl);

@@ -35,7 +35,7 @@ def test_graph_and_autotune_params_validated_without_gpu_work():
     assert p.use_graphs == 0 and p.autotune == 0 and p.profile == 0 and p.max_rhs == 1
     h = ctypes.c_void_p()
     for field, bad in (("use_graphs", 2), ("autotune", 2), ("smoother", 3), ("kcycle", 2), ("kcycle_steps", 0),
-                       ("kcycle_tol", -1.0), ("sap_cycles", 0), ("sap_cycles", 17), ("sap_eo", 2)):
+                       ("kcycle_tol", -1.0), ("sap_cycles", 0), ("sap_cycles", 17), ("sap_eo", 2), ("smoother_steps", 65)):
         q = wcmg.default_params(**{field: bad})
         assert wcmg.wcmg_create(ctypes.byref(q), ctypes.byref(h)) == wcmg.ERR_ARG, field
     q = wcmg.default_params()
