@@ -145,20 +145,21 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
 
 // Multi-rhs coarse apply on the 5th-generation tensor cores (tcgen05, BF16
 // operands, FP32 accumulation in TMEM).  Per coarse site x the nine blocks form
-// Y = M(x) Phi(x), M: nb x 9 nb complex, Phi: 9 nb x N complex.  Real embedding
-// along K (k' = 2 k + 0 for the real, + 1 for the imaginary part):
-//   A[a][2k] = Re M[a][k],  A[a][2k+1] = -Im M[a][k]       (rows a < nb)
-//   A[nb+a][2k] = Im M[a][k], A[nb+a][2k+1] = Re M[a][k]
-//   B[n][2k] = Re Phi[k][n], B[n][2k+1] = Im Phi[k][n]
-// so D[a][n] = Re Y[a][n], D[nb+a][n] = Im Y[a][n]; M_mma = 128 (rows 2 nb .. 127
-// zero).  One CTA (4 warps) per (site, tile of <= 64 rhs).  K is walked in chunks
-// of 64: the chunk is read from global memory into registers one step ahead,
-// converted and stored into one of two shared-memory stages in the no-swizzle
-// K-major core-matrix layout, and one thread issues four K = 16 MMAs and commits
-// them to the stage's mbarrier.  Every wait is bounded; a timeout sets *err = 3,
-// frees the TMEM and ends the CTA.
+// Y = M(x) Phi(x), M: nb x 9 nb complex, Phi: 9 nb x N complex.  Real form along K
+// (k' = 2 k + 0 / + 1): A is M as stored, its BF16 (Re, Im) pairs side by side,
+//   A[a][2k] = Re M[a][k],  A[a][2k+1] = Im M[a][k]              (rows a < nb)
+// and the complex product goes into B, two columns per rhs n:
+//   B[n][2k] = Re Phi[k][n],  B[n][2k+1] = -Im Phi[k][n]         (D[a][n] = Re Y[a][n])
+//   B[N+n][2k] = Im Phi[k][n], B[N+n][2k+1] = Re Phi[k][n]       (D[a][N+n] = Im Y[a][n])
+// M_mma = 128 (rows nb .. 127 zero), N_mma = 2 N.  A chunk of A is then a plain
+// copy of 16-byte groups of the link rows (no conversion).  One CTA (4 warps) per
+// (site, tile of <= 64 rhs).  K is walked in chunks of 64: the chunk is read from
+// global memory into registers one step ahead and stored into one of two
+// shared-memory stages in the no-swizzle K-major core-matrix layout, and one
+// thread issues four K = 16 MMAs and commits them to the stage's mbarrier.  Every
+// wait is bounded; a timeout sets *err = 3, frees the TMEM and ends the CTA.
 constexpr int MMA_M = 128, MMA_KC = 64, MMA_LBO = 128, MMA_SBO = (MMA_KC / 8) * 128;
-constexpr int MMA_AE = 16, MMA_BE = 16;  // per-thread staging: nb <= 64, rhs tile <= 64
+constexpr int MMA_AQ = 4, MMA_BE = 16;  // per-thread staging: nb <= 64 rows x 8 groups, rhs tile <= 64
 
 __device__ __forceinline__ int mma_off(int row, int k) {
   return (row >> 3) * MMA_SBO + (k >> 3) * MMA_LBO + (row & 7) * 16 + (k & 7) * 2;
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(float2* __restrict__ o
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int nsite[9];
-  const int a_bytes = MMA_M * MMA_KC * 2, stage_bytes = a_bytes + ntile * MMA_KC * 2;
+  static_assert(sizeof(L) == 4, "links: one BF16 (Re, Im) pair per entry");
+  const int a_bytes = MMA_M * MMA_KC * 2, stage_bytes = a_bytes + 2 * ntile * MMA_KC * 2;
   const int site = blockIdx.x, r0 = blockIdx.y * ntile;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Kc = 9 * nb, nchunks = (2 * Kc + MMA_KC - 1) / MMA_KC;
@@ -194,18 +196,29 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(float2* __restrict__ o
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = umma_idesc_bf16(MMA_M, ntile);
+  const uint32_t idesc = umma_idesc_bf16(MMA_M, 2 * ntile);
   const L* lsite = links + (long long)site * nb * ld;
-  float2 ra[MMA_AE], rb[MMA_BE];
+  const uint32_t* lwords = reinterpret_cast<const uint32_t*>(lsite);
+  uint4 ra[MMA_AQ];
+  float2 rb[MMA_BE];
   auto load_chunk = [&](int c) {
     const int kc0 = c * (MMA_KC / 2);
+    // A: group g of row a = link entries kc0 + 4 g .. + 3 (16 bytes; ld and the row
+    // starts are multiples of 4 entries), entries at or beyond 9 nb read as 0
 #pragma unroll
-    for (int q = 0; q < MMA_AE; ++q) {
+    for (int q = 0; q < MMA_AQ; ++q) {
       const int e = tid + 128 * q;
-      float2 v = make_float2(0.f, 0.f);
-      if (e < nb * (MMA_KC / 2)) {
-        const int a = e >> 5, k = kc0 + (e & 31);
-        if (k < Kc) v = link_load<L, float>(lsite[(long long)a * ld + k]);
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (e < nb * 8) {
+        const int a = e >> 3, k = kc0 + 4 * (e & 7);
+        const long long o = (long long)a * ld + k;
+        if (k + 3 < Kc) {
+          v = *reinterpret_cast<const uint4*>(lsite + o);
+        } else {
+          if (k < Kc) v.x = lwords[o];
+          if (k + 1 < Kc) v.y = lwords[o + 1];
+          if (k + 2 < Kc) v.z = lwords[o + 2];
+        }
       }
       ra[q] = v;
     }
@@ -227,20 +240,17 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(float2* __restrict__ o
     unsigned char* A = smem + s * stage_bytes;
     unsigned char* B = A + a_bytes;
 #pragma unroll
-    for (int q = 0; q < MMA_AE; ++q) {
+    for (int q = 0; q < MMA_AQ; ++q) {
       const int e = tid + 128 * q;
-      if (e < nb * (MMA_KC / 2)) {
-        const int a = e >> 5, kk = 2 * (e & 31);
-        *reinterpret_cast<uint32_t*>(A + mma_off(a, kk)) = pack_bf16x2(ra[q].x, -ra[q].y);
-        *reinterpret_cast<uint32_t*>(A + mma_off(nb + a, kk)) = pack_bf16x2(ra[q].y, ra[q].x);
-      }
+      if (e < nb * 8) *reinterpret_cast<uint4*>(A + mma_off(e >> 3, 8 * (e & 7))) = ra[q];
     }
 #pragma unroll
     for (int q = 0; q < MMA_BE; ++q) {
       const int e = tid + 128 * q;
       if (e < ntile * (MMA_KC / 2)) {
         const int n = e >> 5, kk = 2 * (e & 31);
-        *reinterpret_cast<uint32_t*>(B + mma_off(n, kk)) = pack_bf16x2(rb[q].x, rb[q].y);
+        *reinterpret_cast<uint32_t*>(B + mma_off(n, kk)) = pack_bf16x2(rb[q].x, -rb[q].y);
+        *reinterpret_cast<uint32_t*>(B + mma_off(ntile + n, kk)) = pack_bf16x2(rb[q].y, rb[q].x);
       }
     }
   };
@@ -276,16 +286,14 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(float2* __restrict__ o
     tc_fence_after();
     const int m = 32 * warp + lane;
     float* o = reinterpret_cast<float*>(out);
-    for (int j = 0; j < ntile / 16; ++j) {
+    // column np < ntile: Re Y[m][np]; np >= ntile: Im Y[m][np - ntile]
+    for (int j = 0; j < 2 * ntile / 16; ++j) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * j, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int n = 16 * j + i;
-        if (n < nvalid && m < 2 * nb) {
-          const int a = m < nb ? m : m - nb;
-          o[2 * (((long long)(r0 + n) * Vc + site) * nb + a) + (m < nb ? 0 : 1)] = v[i];
-        }
+        const int np = 16 * j + i, part = np < ntile ? 0 : 1, n = np - part * ntile;
+        if (n < nvalid && m < nb) o[2 * (((long long)(r0 + n) * Vc + site) * nb + m) + part] = v[i];
       }
     }
   } else if (tid == 0) {
@@ -347,8 +355,8 @@ template <typename L>
 static void coarse_apply_mma(float2* out, const float2* in, const L* links, const LevelGeom& g, int nb, int nrhs,
                              int ntile, int* err, cudaStream_t st) {
   const int ld = links_ld(nb);
-  const int tmem_cols = ntile <= 32 ? 32 : 64;
-  const size_t smem = 2 * ((size_t)MMA_M * MMA_KC * 2 + (size_t)ntile * MMA_KC * 2);
+  const int tmem_cols = ntile <= 16 ? 32 : (ntile <= 32 ? 64 : 128);  // 2 ntile FP32 columns
+  const size_t smem = 2 * ((size_t)MMA_M * MMA_KC * 2 + (size_t)2 * ntile * MMA_KC * 2);
   auto kern = k_coarse_apply_mma<L>;
   WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<dim3(g.V, (nrhs + ntile - 1) / ntile), 128, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, nrhs, ntile,
