@@ -176,6 +176,23 @@ const char* wcmg_last_error(const wcmg_ctx* ctx);
  * four-leaf field strength) with params.m0 / params.csw. */
 int wcmg_set_gauge(wcmg_ctx* ctx, const void* U, int where, void* stream);
 
+/* Sec. 1 / Sec. 2.1 (Wilson-clover D): rebuild the clover term C(x) from the gauge
+ * field already set, with clover coefficient csw (params.m0 unchanged; the context's
+ * csw becomes this value).  A setup built before the call still describes the old D:
+ * run wcmg_setup (or wcmg_coarsen) again for the hierarchy to follow.  ERR_STATE
+ * before wcmg_set_gauge, ERR_ARG for a non-finite csw. */
+int wcmg_set_clover(wcmg_ctx* ctx, double csw, void* stream);
+
+/* The same with caller-given site blocks: C is [V][12][12] complex128 (external clover
+ * layout, (4 + m0) included, row index 3 * spin + colour), for tests and for clover
+ * terms built elsewhere.  The library stores the two chiral 6x6 blocks of a Hermitian
+ * C(x) (the SW clover term commutes with gamma5 in the chiral basis), so every site
+ * block must be Hermitian and have no entries coupling spins {0, 1} to {2, 3}, to
+ * 1e-12 of its largest entry: otherwise (or with a non-finite entry) the call returns
+ * ERR_ARG and the context keeps its previous clover term.  As for wcmg_set_clover the
+ * setup must be rebuilt.  ERR_STATE before wcmg_set_gauge. */
+int wcmg_set_clover_raw(wcmg_ctx* ctx, const void* C, int where, void* stream);
+
 /* Read back C(x) (FP64), external clover layout. */
 int wcmg_get_clover(wcmg_ctx* ctx, void* C, int where, void* stream);
 
@@ -242,6 +259,22 @@ int wcmg_krylov(wcmg_ctx* ctx, int level, int kind, const void* b, void* x, int 
  * Returns ERR_NOT_CONVERGED (x and *st valid) at outer_maxiter. */
 int wcmg_solve(wcmg_ctx* ctx, const void* b, void* x, int nrhs, int where, void* stream, wcmg_stats* st);
 
+/* Options of wcmg_solve_ex. */
+typedef struct wcmg_solve_opts {
+  int zero_guess;       /* 1: x is output only and the solve starts from x = 0 (wcmg_solve);
+                           0: x holds an initial guess x0 on entry (same layout and `where`
+                           as the solution) and the solve starts from r = b - D x0; the
+                           stopping test stays ||b - D x|| / ||b|| <= outer_tol */
+  int reserved[3];      /* set to 0 */
+} wcmg_solve_opts;
+
+/* Sec. 2.1 outer solver with options: wcmg_solve with an in/out initial guess
+ * (opts->zero_guess = 0).  A guess that already meets outer_tol returns it unchanged
+ * with 0 iterations.  With params.use_graphs the CUDA graph is captured separately for
+ * the two kinds of start.  ERR_ARG for a null opts or zero_guess not 0 or 1. */
+int wcmg_solve_ex(wcmg_ctx* ctx, const void* b, void* x, int nrhs, const wcmg_solve_opts* opts, int where,
+                  void* stream, wcmg_stats* st);
+
 /* Batched solve over n independent contexts, e.g. lattices of uneven sizes: each
  * ctxs[i] solves D_i x_i = b_i (nrhs[i] fields, layouts of ctxs[i]) exactly as
  * wcmg_solve with params.use_graphs = 1 would.  All n solves are captured into ONE
@@ -296,6 +329,21 @@ int wcmg_set_profile(wcmg_ctx* ctx, int mask);
  * (out: WCMG_NKCLASS entries).  wcmg_setup / wcmg_solve report their own share. */
 int wcmg_get_kstats(wcmg_ctx* ctx, wcmg_kstat* out);
 
+/* Operator applications the context has issued from the host since wcmg_create, by
+ * kind and level (out: WCMG_NOPC x WCMG_MAX_LEVELS entries, kind-major):
+ *   WCMG_OPC_APPLY     D_level applied to one field (the full nine-point operator at
+ *                      any precision, the smoother's included; counted per rhs)
+ *   WCMG_OPC_RESTRICT  P_level^dag applied to one field (per rhs)
+ *   WCMG_OPC_PROLONG   P_level applied to one field (per rhs)
+ *   WCMG_OPC_ORTHO     block orthonormalisations of level's near-null vectors (calls)
+ *   WCMG_OPC_COARSEN   coarsenings D_{level+1} = P^dag D P (calls; their masked stencils
+ *                      and restrictions are not counted under the other kinds)
+ * Work inside a replayed CUDA graph is issued by the device and is not counted; a
+ * host-driven solve counts every application.  No GPU work. */
+#define WCMG_NOPC 5
+enum { WCMG_OPC_APPLY = 0, WCMG_OPC_RESTRICT = 1, WCMG_OPC_PROLONG = 2, WCMG_OPC_ORTHO = 3, WCMG_OPC_COARSEN = 4 };
+int wcmg_get_opcounts(wcmg_ctx* ctx, long long* out);
+
 /* Allocation-free block orthonormalisation of fine-level near-null vectors.
  * The paper has no counterpart.  It is for callers that cannot allocate device
  * memory: code whose device memory all belongs to another allocator (for example
@@ -316,9 +364,11 @@ int wcmg_get_kstats(wcmg_ctx* ctx, wcmg_kstat* out);
  * device before any stream capture.  Every call uses the same array, which keeps
  * the last call's contents: calls whose GPU work overlaps (several streams or
  * host threads) race and must be serialised by the caller.  No cudaMalloc,
- * cudaFree or allocating library routine is called.  Synchronises `stream` to
- * read the rank check.  Errors: WCMG_ERR_ARG (null pointer, sizes, nvec outside
- * 1..32), WCMG_ERR_NAN (rank-deficient aggregate), WCMG_ERR_CUDA. */
+ * cudaFree or allocating library routine is called.  Every call ends by copying
+ * the rank-check word to a host variable and waiting for `stream` to finish
+ * (cudaStreamSynchronize), so it returns only after its GPU work is complete.
+ * Errors: WCMG_ERR_ARG (null pointer, sizes, nvec outside 1..32), WCMG_ERR_NAN
+ * (rank-deficient aggregate), WCMG_ERR_CUDA. */
 #define WCMG_NOALLOC_MAX_ELEMS 262144
 int wcmg_block_orthonormalise_noalloc(const void* vecs_in, void* vecs_out, const int dims[4], const int block[4],
                                       int nvec, void* stream);
@@ -366,6 +416,14 @@ typedef struct wcmg_train_stats {
  * F32) and fit the PTC weights with Adam on the loss ||N(r) - e||^2 / ||e||^2
  * (Wirtinger gradients, the real gradient is twice their real/imaginary parts). */
 int wcmg_ptc_train(wcmg_ctx* ctx, const wcmg_train_opts* opts, wcmg_train_stats* st, void* stream);
+
+/* Checkpoint of the network: the weights as the network holds them (FP32 complex),
+ * written bit for bit after an 8-byte tag "WCMGNET1" and four ints (hidden fields,
+ * weight count, bytes per real, 0).  wcmg_load_net accepts only a file of this
+ * network's shape (else ERR_ARG) and replaces the context's weights with it.
+ * wcmg_save_net: ERR_STATE when the context has no weights. */
+int wcmg_save_net(wcmg_ctx* ctx, const char* path);
+int wcmg_load_net(wcmg_ctx* ctx, const char* path);
 
 /* Coarse correction used by wcmg_solve's cycle (inner_prec F32 for the learned modes):
  *   WCMG_COARSE_MG          plain multigrid (default)

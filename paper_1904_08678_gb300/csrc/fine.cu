@@ -199,6 +199,41 @@ __global__ void k_clover_expand(double2* __restrict__ ext, const double2* __rest
   }
 }
 
+// Inverse of k_clover_expand for caller-given site blocks (wcmg_set_clover_raw).
+// The packed layout keeps the two chiral 6x6 blocks only, with the diagonal real
+// and the upper triangle: a block that is not Hermitian and block diagonal could
+// not be represented, so such a site raises *bad instead of being truncated.
+__global__ void k_clover_pack(double2* __restrict__ clov, const double2* __restrict__ ext,
+                              const int* __restrict__ perm, int V, double tol, int* __restrict__ bad) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  const double2* e = ext + (long long)perm[s] * 144;
+  double scale = 0.0, dev = 0.0;
+  bool finite = true;
+  for (int i = 0; i < 12; ++i)
+    for (int j = 0; j < 12; ++j) {
+      const double2 a = e[i * 12 + j];
+      finite &= isfinite(a.x) && isfinite(a.y);
+      const double m = fabs(a.x) + fabs(a.y);
+      scale = fmax(scale, m);
+      if ((i < 6) != (j < 6)) {
+        dev = fmax(dev, m);  // couples the two chiralities
+      } else if (j >= i) {
+        const double2 b = e[j * 12 + i];
+        dev = fmax(dev, fabs(a.x - b.x) + fabs(a.y + b.y));  // a != conj(b)
+      }
+    }
+  if (!finite || dev > tol * scale) atomicOr(bad, 1);
+  for (int h = 0; h < 2; ++h) {
+    for (int k = 0; k < 3; ++k)
+      clov[(long long)(18 * h + k) * V + s] =
+          make_double2(e[(6 * h + 2 * k) * 12 + 6 * h + 2 * k].x, e[(6 * h + 2 * k + 1) * 12 + 6 * h + 2 * k + 1].x);
+    int o = 3;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j) clov[(long long)(18 * h + o++) * V + s] = e[(6 * h + i) * 12 + 6 * h + j];
+  }
+}
+
 static CloverSigma make_sigma() {
   // B_mu as 2x2 complex (row-major)
   double2 B[4][4];
@@ -239,6 +274,11 @@ void launch_clover_build(double2* clov, const double2* gauge64, const int* nbr, 
 }
 void launch_clover_expand(double2* ext, const double2* clov, const int* perm, int V, cudaStream_t st) {
   k_clover_expand<<<nblk(V, 128), 128, 0, st>>>(ext, clov, perm, V);
+  WCMG_LAUNCH_CHECK();
+}
+void launch_clover_pack(double2* clov, const double2* ext, const int* perm, int V, double tol, int* bad,
+                        cudaStream_t st) {
+  k_clover_pack<<<nblk(V, 128), 128, 0, st>>>(clov, ext, perm, V, tol, bad);
   WCMG_LAUNCH_CHECK();
 }
 

@@ -26,6 +26,11 @@ void launch_pack_gauge(cplx<R>* out, const double2* ext, const int* perm, int V,
 void launch_clover_build(double2* clov, const double2* gauge64, const int* nbr, int V, double m0, double csw,
                          cudaStream_t st);
 void launch_clover_expand(double2* ext, const double2* clov, const int* perm, int V, cudaStream_t st);
+// External [V][12][12] site blocks -> packed clover layout; *bad (zeroed by the
+// caller) becomes nonzero at a site whose block is not Hermitian and block diagonal
+// in chirality to tol relative to the block's largest entry, or is not finite.
+void launch_clover_pack(double2* clov, const double2* ext, const int* perm, int V, double tol, int* bad,
+                        cudaStream_t st);
 // colour non-null: only the sites of the aggregates B with colour[B] == col are computed
 // and written (the SAP residual of one colour pass); the others keep `out`.
 template <typename R>

@@ -225,6 +225,8 @@ struct wcmg_ctx {
   double* h_vals = nullptr; // pinned host mirror of per-rhs values
   int hcap = 0;
   Prof prof;
+  long long opc[WCMG_NOPC][WCMG_MAX_LEVELS] = {};  // operator applications (wcmg_get_opcounts)
+  bool in_coarsen = false;                         // the coarsening's stencils and restrictions are its own
   cudaStream_t st = nullptr;
   long long coarse_its = 0;
   // learned coarse correction (PTC network)
@@ -254,6 +256,7 @@ struct wcmg_ctx {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
     int nrhs = 0;
+    bool guess = false;                  // captured with the caller's initial guess (else x = 0)
     unsigned long long gen = 0;
     long long top_launches = 0;  // kernels outside conditional bodies
     void reset() {
@@ -265,6 +268,7 @@ struct wcmg_ctx {
     }
   } graph;
   std::vector<int> warm_rhs;              // nrhs values already solved once (every workspace allocated)
+  bool guess = false;                     // the solve being run or captured starts from the given x
   long long graph_top = 0;                // kernels of the last capture outside conditional bodies
   Graph batch;                            // wcmg_solve_batch graph (cached on the first context)
   std::vector<const void*> batch_key;
@@ -479,6 +483,7 @@ template <typename R>
 static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nrhs, int mode = ST_FULL,
                      int hopdir = 0) {
   Level& L = c->L[l];
+  if (mode == ST_FULL && !c->in_coarsen && !c->capturing) c->opc[WCMG_OPC_APPLY][l] += nrhs;
   if (l == 0) {
     if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
     const double V = L.g.V, s = sizeof(cplx<R>);
@@ -530,6 +535,7 @@ template <typename R>
 static void restrict_op(wcmg_ctx* c, int l, cplx<R>* coarse, const cplx<R>* fine, int nrhs, int face = -1) {
   Level& L = c->L[l];
   if (!L.have_P) throw Error(WCMG_ERR_STATE, "prolongator of level not built");
+  if (!c->in_coarsen && !c->capturing) c->opc[WCMG_OPC_RESTRICT][l] += nrhs;
   const double s = sizeof(cplx<R>);
   const double frac = face < 0 ? 1.0 : 1.0 / L.g.b[face >> 1];  // share of the sites read
   KPROF(c, WCMG_K_RESTRICT,
@@ -542,6 +548,7 @@ template <typename R>
 static void prolong_op(wcmg_ctx* c, int l, cplx<R>* fine, const cplx<R>* coarse, int nrhs) {
   Level& L = c->L[l];
   if (!L.have_P) throw Error(WCMG_ERR_STATE, "prolongator of level not built");
+  if (!c->capturing) c->opc[WCMG_OPC_PROLONG][l] += nrhs;
   const double s = sizeof(cplx<R>);
   KPROF(c, WCMG_K_PROLONG, (double)L.n() * s * (L.nvec + nrhs) + (double)L.g.V / L.g.bvol * 2 * L.nvec * s * nrhs,
         (double)L.n() * 8.0 * L.nvec * nrhs,
@@ -591,6 +598,7 @@ static void mr(wcmg_ctx* c, int l, cplx<R>* x, const cplx<R>* b, int nrhs, int s
       c->mr_pp.ensure(np);
       const double V = L.g.V, s = sizeof(cplx<R>);
       const int cls = sizeof(R) == 8 ? WCMG_K_DSLASH64 : WCMG_K_DSLASH;
+      if (!c->capturing) c->opc[WCMG_OPC_APPLY][0] += nrhs;
       KPROF(c, cls, V * s * (24.0 * nrhs + 72.0), V * (1872.0 + 16.0) * nrhs,
             launch_dslash_mr<R>(p, rk, Prec<R>::gauge(c), Prec<R>::clover(c), L.g.lg(), nrhs, L.sc.pr(),
                                 L.sc.slot(4), c->mr_pr.p, c->mr_pp.p, c->st));
@@ -1090,7 +1098,7 @@ static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
 
 // ---------------- setup ----------------
 template <typename R>
-static void coarsen(wcmg_ctx* c, int l) {
+static void coarsen_body(wcmg_ctx* c, int l) {
   Level& F = c->L[l];
   Level& C = c->L[l + 1];
   const int nb = 2 * F.nvec, Vc = C.g.V;
@@ -1163,6 +1171,17 @@ static void coarsen(wcmg_ctx* c, int l) {
   }
 }
 
+template <typename R>
+static void coarsen(wcmg_ctx* c, int l) {
+  struct Guard {
+    wcmg_ctx* c;
+    ~Guard() { c->in_coarsen = false; }
+  } guard{c};
+  c->in_coarsen = true;
+  c->opc[WCMG_OPC_COARSEN][l] += 1;
+  coarsen_body<R>(c, l);
+}
+
 // P_l from the level's raw vectors at precision R: FP64 block orthonormalisation.
 template <typename R>
 static void build_P(wcmg_ctx* c, int l) {
@@ -1171,6 +1190,7 @@ static void build_P(wcmg_ctx* c, int l) {
   L.v64.ensure(n);
   launch_convert<R, double>(L.v64.p, Prec<R>::raw(L).p, n, c->st);
   WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
+  c->opc[WCMG_OPC_ORTHO][l] += 1;
   const double V = L.g.V;
   // algorithmic work: one Gram-Schmidt pass, nvec (nvec - 1) complex MAC per panel row
   // (dots + updates); a second pass, when the cancellation test asks for it, is extra.
@@ -1238,14 +1258,27 @@ static void setup_all(wcmg_ctx* c, const double2* init, wcmg_stats* st) {
 
 // ---------------- outer solve ----------------
 static void solve_f64(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcmg_stats* st) {
-  KrylovOut k = fgmres<double>(c, 0, x, b, nrhs, c->p.outer_restart, c->p.outer_tol, c->p.outer_maxiter, true, true,
-                               true);
+  KrylovOut k = fgmres<double>(c, 0, x, b, nrhs, c->p.outer_restart, c->p.outer_tol, c->p.outer_maxiter, !c->guess,
+                               true, true);
   st->outer_iterations = k.iterations;
   st->converged = k.converged;
 }
 
 // relative tolerance of each FP32 FGMRES cycle between two FP64 defect corrections
 constexpr double kInnerTol = 1e-5;
+
+// r = b - D x for the caller's initial guess (c->guess), else x = 0 and r = b (FP64).
+static void start_residual(wcmg_ctx* c, double2* x, double2* r, double2* t, const double2* b, int nrhs) {
+  const long long n = c->L[0].n();
+  if (c->guess) {
+    apply_op<double>(c, 0, t, x, nrhs);
+    copy_fields<double>(c, r, b, n * nrhs);
+    launch_axpby<double>(r, -1.0, t, 1.0, n, nrhs, c->st);
+  } else {
+    launch_fill_zero<double>(x, n * nrhs, c->st);
+    copy_fields<double>(c, r, b, n * nrhs);
+  }
+}
 
 // Precision change (Sec. 2.1): FP64 iterate and true residual, FP32 FGMRES cycles
 // preconditioned by the FP32 multigrid; every restart is a defect correction.
@@ -1264,8 +1297,7 @@ static void solve_mixed(wcmg_ctx* c, double2* x, const double2* b, int nrhs, wcm
     const double* h = read_doubles(c, bn2, nrhs);
     for (int q = 0; q < nrhs; ++q) bnorm[q] = std::sqrt(h[q]);
   }
-  launch_fill_zero<double>(x, n * nrhs, c->st);
-  copy_fields<double>(c, r64, b, n * nrhs);
+  start_residual(c, x, r64, t64, b, nrhs);
   DevBuf<int>& mask = c->errflag;  // errflag has room for max rhs + 1
   std::vector<int> done(nrhs, 0);
   int its = 0, restarts = 0;
@@ -1320,8 +1352,7 @@ static void solve_mixed_body(wcmg_ctx* c, double2* x, const double2* b, int nrhs
   KCtl* Kmx = c->kctl.p;
   KCtl* Kfg = c->kctl.p + 1;
   norm2_op<double>(c, bn2, b, n, nrhs);
-  launch_fill_zero<double>(x, n * nrhs, c->st);
-  copy_fields<double>(c, r64, b, n * nrhs);
+  start_residual(c, x, r64, t64, b, nrhs);
   norm2_op<double>(c, L.sc.slot(1), r64, n, nrhs);
   const cudaGraphConditionalHandle h = cond_handle(c);
   launch_kctl_init(Kmx, c->p.outer_maxiter, nullptr, 0, h, 0, c->st);
@@ -1344,8 +1375,8 @@ static void solve_mixed_body(wcmg_ctx* c, double2* x, const double2* b, int nrhs
 }
 
 static void solve_f64_body(wcmg_ctx* c, double2* x, const double2* b, int nrhs) {
-  fgmres_g<double>(c, 0, x, b, nrhs, c->p.outer_restart, c->p.outer_tol, c->p.outer_maxiter, true, true, true, 0,
-                   c->kctl.p + 1, nullptr, 0, nullptr);
+  fgmres_g<double>(c, 0, x, b, nrhs, c->p.outer_restart, c->p.outer_tol, c->p.outer_maxiter, !c->guess, true,
+                   true, 0, c->kctl.p + 1, nullptr, 0, nullptr);
 }
 
 // Device buffers of the graph path and every lazily converted operand, made
@@ -1647,6 +1678,26 @@ static void ptc_train(wcmg_ctx* c, const wcmg_train_opts* o, wcmg_train_stats* s
   c->learned_on = saved_on;
 }
 
+// FP32 copy of the clover term and, for the even-odd SAP smoother, C^-1 (FP64 and
+// FP32), after clover64 changed.
+static void clover_derived(wcmg_ctx* c) {
+  const int V = c->L[0].g.V;
+  launch_convert<double, float>(c->clover32.p, c->clover64.p, (long long)36 * V, c->st);
+  if (c->p.sap_eo) {
+    c->cinv64.ensure((size_t)36 * V);
+    c->cinv32.ensure((size_t)36 * V);
+    c->cinv_err.ensure(1);
+    WCMG_CUDA(cudaMemsetAsync(c->cinv_err.p, 0, sizeof(int), c->st));
+    KPROF(c, WCMG_K_CLOVER, 36.0 * V * 16 * 2, 2.0 * V * 6 * 6 * 12 * 8,
+          launch_clover_invert(c->cinv64.p, c->clover64.p, V, c->cinv_err.p, c->st));
+    launch_convert<double, float>(c->cinv32.p, c->cinv64.p, (long long)36 * V, c->st);
+    int bad = 0;
+    WCMG_CUDA(cudaMemcpyAsync(&bad, c->cinv_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    WCMG_CUDA(cudaStreamSynchronize(c->st));
+    if (bad) throw Error(WCMG_ERR_NAN, "singular clover block: no even-odd SAP");
+  }
+}
+
 // ---------------- external I/O ----------------
 static const double2* in_dev(wcmg_ctx* c, const void* ptr, size_t bytes, int where, int slot) {
   if (where == WCMG_DEVICE) return (const double2*)ptr;
@@ -1924,21 +1975,49 @@ int wcmg_set_gauge(wcmg_ctx* c, const void* U, int where, void* stream) {
   launch_pack_gauge<float>(c->gauge32.p, u, L.g.d_perm.p, V, c->st);
   KPROF(c, WCMG_K_CLOVER, 36.0 * V * 16 * 5, 0,
         launch_clover_build(c->clover64.p, c->gauge64.p, L.g.d_nbr.p, V, c->p.m0, c->p.csw, c->st));
-  launch_convert<double, float>(c->clover32.p, c->clover64.p, (long long)36 * V, c->st);
-  if (c->p.sap_eo) {
-    c->cinv64.ensure((size_t)36 * V);
-    c->cinv32.ensure((size_t)36 * V);
-    c->cinv_err.ensure(1);
-    WCMG_CUDA(cudaMemsetAsync(c->cinv_err.p, 0, sizeof(int), c->st));
-    KPROF(c, WCMG_K_CLOVER, 36.0 * V * 16 * 2, 2.0 * V * 6 * 6 * 12 * 8,
-          launch_clover_invert(c->cinv64.p, c->clover64.p, V, c->cinv_err.p, c->st));
-    launch_convert<double, float>(c->cinv32.p, c->cinv64.p, (long long)36 * V, c->st);
-    int bad = 0;
-    WCMG_CUDA(cudaMemcpyAsync(&bad, c->cinv_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    WCMG_CUDA(cudaStreamSynchronize(c->st));
-    if (bad) throw Error(WCMG_ERR_NAN, "singular clover block: no even-odd SAP");
-  }
+  clover_derived(c);
   c->have_gauge = true;
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_set_clover(wcmg_ctx* c, double csw, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+  if (!std::isfinite(csw)) throw Error(WCMG_ERR_ARG, "csw must be finite");
+  c->p.csw = csw;
+  Level& L = c->L[0];
+  const int V = L.g.V;
+  KPROF(c, WCMG_K_CLOVER, 36.0 * V * 16 * 5, 0,
+        launch_clover_build(c->clover64.p, c->gauge64.p, L.g.d_nbr.p, V, c->p.m0, c->p.csw, c->st));
+  clover_derived(c);
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  c->prof.flush();
+  API_END(c)
+}
+
+int wcmg_set_clover_raw(wcmg_ctx* c, const void* C, int where, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
+  if (!C) throw Error(WCMG_ERR_ARG, "null clover");
+  Level& L = c->L[0];
+  const int V = L.g.V;
+  const double2* e = in_dev(c, C, (size_t)V * 144 * 16, where, 0);
+  c->cinv_err.ensure(1);
+  WCMG_CUDA(cudaMemsetAsync(c->cinv_err.p, 0, sizeof(int), c->st));
+  DevBuf<double2> packed;  // the context's clover stays untouched if the blocks are rejected
+  packed.ensure((size_t)36 * V);
+  KPROF(c, WCMG_K_CLOVER, (double)V * (144 + 36) * 16, 0,
+        launch_clover_pack(packed.p, e, L.g.d_perm.p, V, 1e-12, c->cinv_err.p, c->st));
+  int bad = 0;
+  WCMG_CUDA(cudaMemcpyAsync(&bad, c->cinv_err.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  WCMG_CUDA(cudaStreamSynchronize(c->st));
+  if (bad) throw Error(WCMG_ERR_ARG, "clover blocks must be Hermitian and block diagonal in chirality");
+  WCMG_CUDA(cudaMemcpyAsync(c->clover64.p, packed.p, sizeof(double2) * 36 * V, cudaMemcpyDeviceToDevice, c->st));
+  clover_derived(c);
   WCMG_CUDA(cudaStreamSynchronize(c->st));
   c->prof.flush();
   API_END(c)
@@ -2303,9 +2382,20 @@ int wcmg_krylov(wcmg_ctx* c, int level, int kind, const void* b, void* x, int nr
 }
 
 int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* stream, wcmg_stats* st) {
+  wcmg_solve_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.zero_guess = 1;
+  return wcmg_solve_ex(c, b, x, nrhs, &o, where, stream, st);
+}
+
+int wcmg_solve_ex(wcmg_ctx* c, const void* b, void* x, int nrhs, const wcmg_solve_opts* opts, int where,
+                  void* stream, wcmg_stats* st) {
   API_BEGIN(c)
   c->st = (cudaStream_t)stream;
   check_rhs(c, nrhs);
+  if (!opts || (opts->zero_guess != 0 && opts->zero_guess != 1))
+    throw Error(WCMG_ERR_ARG, "opts must be given with zero_guess 0 or 1");
+  const bool guess = opts->zero_guess == 0;
   for (int l = 0; l + 1 < c->p.n_levels; ++l)
     if (!c->L[l].have_P || !c->L[l + 1].have_op) throw Error(WCMG_ERR_STATE, "setup not done");
   wcmg_stats local;
@@ -2334,12 +2424,21 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
   double2* b64 = ws<double>(L, "sv_b", nrhs);
   double2* x64 = ws<double>(L, "sv_x", nrhs);
   pack_level<double>(c, 0, b64, bi, nrhs);
+  if (guess) {  // x holds the initial guess on entry
+    const double2* xi = static_cast<const double2*>(x);
+    if (where == WCMG_HOST) {
+      WCMG_CUDA(cudaMemcpyAsync(xo, x, bytes, cudaMemcpyHostToDevice, c->st));
+      xi = xo;
+    }
+    pack_level<double>(c, 0, x64, xi, nrhs);
+  }
+  c->guess = guess;
   const bool want_graph = c->p.use_graphs && c->coarse_mode == WCMG_COARSE_MG;
   long long graph_kernels = 0;
   if (want_graph) graph_prepare(c, nrhs);
   if (want_graph && is_warm(c, nrhs)) {
     auto& G = c->graph;
-    if (!G.exec || G.nrhs != nrhs || G.gen != graph_epoch()) {
+    if (!G.exec || G.nrhs != nrhs || G.gen != graph_epoch() || G.guess != guess) {
       wcmg_ctx* cs[1] = {c};
       double2* xs[1] = {x64};
       const double2* bs[1] = {b64};
@@ -2347,6 +2446,7 @@ int wcmg_solve(wcmg_ctx* c, const void* b, void* x, int nrhs, int where, void* s
       const long long lc = launch_counter();
       capture_group(cs, 1, xs, bs, nr, G);
       G.nrhs = nrhs;
+      G.guess = guess;
       l0 += launch_counter() - lc;  // captured, not launched
     }
     WCMG_CUDA(cudaGraphLaunch(G.exec, c->st));
@@ -2411,6 +2511,7 @@ int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* c
     S(i).ms_setup_refine = mr;
     c->coarse_its = 0;
     c->learned_on = false;
+    c->guess = false;
     Level& L = c->L[0];
     bytes[i] = (size_t)nrhs[i] * L.n() * 16;
     const double2* bi = in_dev(c, b[i], bytes[i], where, 0);
@@ -2581,6 +2682,14 @@ int wcmg_set_profile(wcmg_ctx* c, int mask) {
   API_END(c)
 }
 
+int wcmg_get_opcounts(wcmg_ctx* c, long long* out) {
+  API_BEGIN(c)
+  if (!out) throw Error(WCMG_ERR_ARG, "null output");
+  for (int k = 0; k < WCMG_NOPC; ++k)
+    for (int l = 0; l < WCMG_MAX_LEVELS; ++l) out[k * WCMG_MAX_LEVELS + l] = c->opc[k][l];
+  API_END(c)
+}
+
 int wcmg_get_kstats(wcmg_ctx* c, wcmg_kstat* out) {
   API_BEGIN(c)
   if (!out) throw Error(WCMG_ERR_ARG, "out");
@@ -2669,6 +2778,45 @@ int wcmg_set_coarse_mode(wcmg_ctx* c, int mode, double fallback_ratio) {
   if (mode < WCMG_COARSE_MG || mode > WCMG_COARSE_LEARNED) throw Error(WCMG_ERR_ARG, "coarse mode");
   c->coarse_mode = mode;
   c->fallback_ratio = fallback_ratio;
+  API_END(c)
+}
+
+int wcmg_save_net(wcmg_ctx* c, const char* path) {
+  API_BEGIN(c)
+  if (!path) throw Error(WCMG_ERR_ARG, "path");
+  if (!c->have_ptc) throw Error(WCMG_ERR_STATE, "no PTC weights to save");
+  std::vector<float2> h(WCMG_PTC_NWEIGHTS);
+  WCMG_CUDA(cudaDeviceSynchronize());
+  WCMG_CUDA(cudaMemcpy(h.data(), c->ptcW.p, sizeof(float2) * h.size(), cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) throw Error(WCMG_ERR_ARG, std::string("cannot open ") + path);
+  const char magic[8] = {'W', 'C', 'M', 'G', 'N', 'E', 'T', '1'};
+  const int hdr[4] = {WCMG_PTC_HIDDEN, WCMG_PTC_NWEIGHTS, 4 /* bytes per real */, 0};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 4, f) == 4 &&
+            std::fwrite(h.data(), sizeof(float2), h.size(), f) == h.size();
+  ok &= std::fclose(f) == 0;
+  if (!ok) throw Error(WCMG_ERR_ARG, std::string("cannot write ") + path);
+  API_END(c)
+}
+
+int wcmg_load_net(wcmg_ctx* c, const char* path) {
+  API_BEGIN(c)
+  if (!path) throw Error(WCMG_ERR_ARG, "path");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) throw Error(WCMG_ERR_ARG, std::string("cannot open ") + path);
+  char magic[8] = {};
+  int hdr[4] = {};
+  std::vector<float2> h(WCMG_PTC_NWEIGHTS);
+  const bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "WCMGNET1", 8) == 0 &&
+                  std::fread(hdr, sizeof(int), 4, f) == 4 && hdr[0] == WCMG_PTC_HIDDEN &&
+                  hdr[1] == WCMG_PTC_NWEIGHTS && hdr[2] == 4 &&
+                  std::fread(h.data(), sizeof(float2), h.size(), f) == h.size();
+  std::fclose(f);
+  if (!ok) throw Error(WCMG_ERR_ARG, std::string("not a PTC network file of this shape: ") + path);
+  ptc_alloc(c);
+  WCMG_CUDA(cudaDeviceSynchronize());
+  WCMG_CUDA(cudaMemcpy(c->ptcW.p, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice));
+  c->have_ptc = true;
   API_END(c)
 }
 

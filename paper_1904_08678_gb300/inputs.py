@@ -96,15 +96,47 @@ def _reunitarise(U: np.ndarray) -> np.ndarray:
     return np.stack([r0, r1, r2], axis=-2)
 
 
-def random_gauge(dims, eps: float, seed: int) -> np.ndarray:
-    """SU(3) links U_mu(x) = exp(i eps X), external layout [4][V][3][3]."""
-    Lx, Ly, Lz, Lt = dims
-    V = Lx * Ly * Lz * Lt
-    xi = normal(seed, 0, 4 * V * 8).reshape(4 * V, 8)
-    X = np.einsum("na,aij->nij", xi, gell_mann())
+def _links(eps: float, seed: int, start: int, count: int) -> np.ndarray:
+    """Links start .. start + count - 1 (flat index mu * V + s) of random_gauge.
+
+    Link n takes the normals 8n .. 8n + 7 of stream 0, which Box-Muller makes from
+    the uniforms 8n .. 8n + 7 (four whole pairs), so any range of links comes out
+    exactly as in one pass over all of them."""
+    u = uniform(seed, 0, 8 * count, offset=8 * start)
+    u1, u2 = u[0::2], u[1::2]
+    r = np.sqrt(-2.0 * np.log1p(-u1))
+    z = np.empty(8 * count)
+    z[0::2] = r * np.cos(2.0 * np.pi * u2)
+    z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    X = np.einsum("na,aij->nij", z.reshape(count, 8), gell_mann())
     w, Q = np.linalg.eigh(X)
     U = np.einsum("nij,nj,nkj->nik", Q, np.exp(1j * eps * w), np.conj(Q))
-    return _reunitarise(U).reshape(4, V, 3, 3)
+    return _reunitarise(U)
+
+
+def _links_job(a):
+    return _links(*a)
+
+
+def random_gauge(dims, eps: float, seed: int, workers: int = 0) -> np.ndarray:
+    """SU(3) links U_mu(x) = exp(i eps X), external layout [4][V][3][3].
+
+    workers > 1: the links are computed in contiguous ranges by that many spawned
+    processes (identical values: every link depends on its own counters only)."""
+    Lx, Ly, Lz, Lt = dims
+    V = Lx * Ly * Lz * Lt
+    n = 4 * V
+    if workers <= 1 or n < (1 << 20):
+        return _links(eps, seed, 0, n).reshape(4, V, 3, 3)
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    chunk = -(-n // (4 * workers))
+    jobs = [(eps, seed, s, min(chunk, n - s)) for s in range(0, n, chunk)]
+    out = np.empty((n, 3, 3), dtype=np.complex128)
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for (_, _, s, c), part in zip(jobs, ex.map(_links_job, jobs)):
+            out[s:s + c] = part
+    return out.reshape(4, V, 3, 3)
 
 
 def unit_gauge(dims) -> np.ndarray:

@@ -36,6 +36,8 @@ KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen",
 PTC_HIDDEN, PTC_NWEIGHTS = 12, 3456
 COARSE_MG, COARSE_WARMSTART, COARSE_LEARNED = 0, 1, 2
 SMOOTHER_MR, SMOOTHER_GMRES, SMOOTHER_SAP = 0, 1, 2
+NOPC = 5
+OPC = ["apply", "restrict", "prolong", "ortho", "coarsen"]
 
 
 class wcmg_params(ctypes.Structure):
@@ -108,6 +110,10 @@ class wcmg_tile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class wcmg_solve_opts(ctypes.Structure):
+    _fields_ = [("zero_guess", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
 class wcmg_train_opts(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int), ("batch", ctypes.c_int), ("steps", ctypes.c_int), ("refresh", ctypes.c_int),
                 ("lr", ctypes.c_double), ("target_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
@@ -127,6 +133,8 @@ _SIGS = {
     "wcmg_destroy": ([_PCTX], None),
     "wcmg_last_error": ([_PCTX], ctypes.c_char_p),
     "wcmg_set_gauge": ([_PCTX, _vp, _i, _vp], _i),
+    "wcmg_set_clover": ([_PCTX, _d, _vp], _i),
+    "wcmg_set_clover_raw": ([_PCTX, _vp, _i, _vp], _i),
     "wcmg_get_clover": ([_PCTX, _vp, _i, _vp], _i),
     "wcmg_get_clover_inverse": ([_PCTX, _vp, _i, _vp], _i),
     "wcmg_apply_D": ([_PCTX, _vp, _vp, _i, _i, _i, _vp], _i),
@@ -143,6 +151,8 @@ _SIGS = {
     "wcmg_mg_cycle": ([_PCTX, _vp, _vp, _i, _i, _vp], _i),
     "wcmg_krylov": ([_PCTX, _i, _i, _vp, _vp, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_i)], _i),
     "wcmg_solve": ([_PCTX, _vp, _vp, _i, _i, _vp, ctypes.POINTER(wcmg_stats)], _i),
+    "wcmg_solve_ex": ([_PCTX, _vp, _vp, _i, ctypes.POINTER(wcmg_solve_opts), _i, _vp, ctypes.POINTER(wcmg_stats)],
+                      _i),
     "wcmg_solve_batch": ([ctypes.POINTER(_PCTX), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i), _i,
                           _vp, ctypes.POINTER(wcmg_stats)], _i),
     "wcmg_set_profile": ([_PCTX, _i], _i),
@@ -150,6 +160,7 @@ _SIGS = {
     "wcmg_tune_coarse": ([_PCTX, _i, _i, _i, _i, _vp, ctypes.POINTER(wcmg_tile)], _i),
     "wcmg_set_coarse_tile": ([_PCTX, _i, _i, _i, ctypes.POINTER(wcmg_tile)], _i),
     "wcmg_get_kstats": ([_PCTX, ctypes.POINTER(wcmg_kstat)], _i),
+    "wcmg_get_opcounts": ([_PCTX, ctypes.POINTER(ctypes.c_longlong)], _i),
     "wcmg_block_orthonormalise_noalloc": ([_vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _vp], _i),
     "wcmg_ptc_set_weights": ([_PCTX, _vp, _i, _vp], _i),
     "wcmg_ptc_get_weights": ([_PCTX, _vp, _i, _vp], _i),
@@ -157,6 +168,8 @@ _SIGS = {
     "wcmg_ptc_backward": ([_PCTX, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
     "wcmg_ptc_train": ([_PCTX, ctypes.POINTER(wcmg_train_opts), ctypes.POINTER(wcmg_train_stats), _vp], _i),
     "wcmg_set_coarse_mode": ([_PCTX, _i, _d], _i),
+    "wcmg_save_net": ([_PCTX, ctypes.c_char_p], _i),
+    "wcmg_load_net": ([_PCTX, ctypes.c_char_p], _i),
     "wcmg_save_setup": ([_PCTX, ctypes.c_char_p], _i),
     "wcmg_load_setup": ([_PCTX, ctypes.c_char_p], _i),
 }
@@ -250,6 +263,13 @@ class Context:
         p, w = _buf(U)
         return self._check(wcmg_set_gauge(self.h, p, w, _stream(stream)))
 
+    def set_clover(self, csw, stream=None):
+        return self._check(wcmg_set_clover(self.h, float(csw), _stream(stream)))
+
+    def set_clover_raw(self, C, stream=None):
+        p, w = _buf(C)
+        return self._check(wcmg_set_clover_raw(self.h, p, w, _stream(stream)))
+
     def get_clover(self, C, stream=None):
         p, w = _buf(C, True)
         return self._check(wcmg_get_clover(self.h, p, w, _stream(stream)))
@@ -336,6 +356,17 @@ class Context:
                     allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return st
 
+    def solve_ex(self, b, x, nrhs=1, zero_guess=1, stream=None, allow_not_converged=False):
+        """wcmg_solve_ex: zero_guess = 0 starts from the initial guess held in x."""
+        pi, wi = _buf(b)
+        po, wo = _buf(x, True)
+        assert wi == wo
+        o = wcmg_solve_opts(zero_guess=int(zero_guess))
+        st = wcmg_stats()
+        self._check(wcmg_solve_ex(self.h, pi, po, nrhs, ctypes.byref(o), wi, _stream(stream), ctypes.byref(st)),
+                    allow=(ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return st
+
     def set_profile(self, mask):
         return self._check(wcmg_set_profile(self.h, mask))
 
@@ -377,6 +408,12 @@ class Context:
         return {KCLASS[i]: dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes, flops=arr[i].flops)
                 for i in range(NKCLASS)}
 
+    def opcounts(self):
+        """{kind: [count per level]} of wcmg_get_opcounts."""
+        arr = (ctypes.c_longlong * (NOPC * MAX_LEVELS))()
+        self._check(wcmg_get_opcounts(self.h, arr))
+        return {k: [arr[i * MAX_LEVELS + l] for l in range(MAX_LEVELS)] for i, k in enumerate(OPC)}
+
     def ptc_set_weights(self, W, stream=None):
         p, w = _buf(W)
         return self._check(wcmg_ptc_set_weights(self.h, p, w, _stream(stream)))
@@ -408,6 +445,12 @@ class Context:
 
     def set_coarse_mode(self, mode, fallback_ratio=0.9):
         return self._check(wcmg_set_coarse_mode(self.h, mode, fallback_ratio))
+
+    def save_net(self, path):
+        return self._check(wcmg_save_net(self.h, path.encode()))
+
+    def load_net(self, path):
+        return self._check(wcmg_load_net(self.h, path.encode()))
 
     def save_setup(self, path):
         return self._check(wcmg_save_setup(self.h, path.encode()))

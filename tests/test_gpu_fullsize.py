@@ -60,7 +60,11 @@ def block_of(x_c):
     return (x + DIMS[0] * (y + DIMS[1] * (z + DIMS[2] * t))).ravel()
 
 
-SAMPLES = [(0, 0, 0, 0), (3, 1, 2, 7), (1, 3, 0, 4)]
+# 16 sampled aggregates: the corners of the coarse lattice (their hops wrap around the
+# periodic boundary in every direction) and seeded interior ones
+SAMPLES = [(0, 0, 0, 0), (3, 3, 3, 7), (3, 0, 0, 0), (0, 3, 0, 7), (0, 0, 3, 0), (3, 3, 0, 7), (3, 1, 2, 7),
+           (1, 3, 0, 4)] + [tuple(int(v) for v in x) for x in
+                            np.random.default_rng(65).integers(0, [4, 4, 4, 8], size=(8, 4))]
 
 
 def test_fullsize_nullvecs_are_block_orthonormal(full):
@@ -98,30 +102,34 @@ def test_fullsize_transfers_match_oracle_on_sampled_aggregates(lib, full):
 
 def test_fullsize_galerkin_blocks_match_oracle_on_samples(full):
     """A_d(x_c)[:, b] = sum over B(x_c) of <Pi_s v_i, (face-masked D-piece of column b)>,
-    recomputed with the oracle's D from the library's near-null vectors (FP32
-    coarsening: 1e-5)."""
+    recomputed with the oracle's D from the library's near-null vectors, for all nine
+    blocks d and all 48 columns b of 16 sampled aggregates (FP32 coarsening: 1e-5,
+    element-wise per block)."""
     D, v, A = full["D"], full["vecs"], full["A"]
-    for b in (0, 29):
+    faces = {(mu, sign): from_grid(face_mask(DIMS, BLOCK, mu, sign)[..., None].astype(float))[:, 0] > 0
+             for mu in range(4) for sign in (+1, -1)}
+    sites = [block_of(x_c) for x_c in SAMPLES]
+    lexs = [x_c[0] + CD[0] * (x_c[1] + CD[1] * (x_c[2] + CD[2] * x_c[3])) for x_c in SAMPLES]
+    want = np.zeros((9, len(SAMPLES), NB, NB), dtype=complex)   # [d][sample][row][column]
+    for b in range(NB):
         s_b, i_b = divmod(b, NVEC)
         col = np.zeros((V, 12), dtype=complex)
         col[:, 6 * s_b:6 * s_b + 6] = v[i_b][:, 6 * s_b:6 * s_b + 6]
         Vb = to_grid(col, DIMS)
         pieces = {0: from_grid(D.apply_self(Vb))}
-        inner = np.zeros_like(pieces[0])
         for mu in range(4):
             for sign in (+1, -1):
                 W = from_grid(D.apply_hop(mu, sign, Vb))
-                f = from_grid(face_mask(DIMS, BLOCK, mu, sign)[..., None].astype(float))[:, 0] > 0
+                f = faces[(mu, sign)]
                 pieces[block_index(mu, sign)] = np.where(f[:, None], W, 0)
-                inner += np.where(f[:, None], 0, W)
-        pieces[0] = pieces[0] + inner
-        for x_c in SAMPLES:
-            sites = block_of(x_c)
-            lex = x_c[0] + CD[0] * (x_c[1] + CD[1] * (x_c[2] + CD[2] * x_c[3]))
+                pieces[0] = pieces[0] + np.where(f[:, None], 0, W)
+        for k, st in enumerate(sites):
             for d, fld in pieces.items():
-                want = np.concatenate([np.einsum("isc,sc->i", v[:, sites, 6 * s:6 * s + 6].conj(),
-                                                 fld[sites, 6 * s:6 * s + 6]) for s in range(2)])
-                assert rel(A[d, lex, :, b], want) < 1e-5, (b, x_c, d)
+                want[d, k, :, b] = np.concatenate([np.einsum("isc,sc->i", v[:, st, 6 * s:6 * s + 6].conj(),
+                                                             fld[st, 6 * s:6 * s + 6]) for s in range(2)])
+    for k, lex in enumerate(lexs):
+        for d in range(9):
+            assert rel(A[d, lex], want[d, k]) < 1e-5, (SAMPLES[k], d)
 
 
 def test_fullsize_coarse_apply_matches_oracle(lib, full):

@@ -123,7 +123,7 @@ def random_links(seed, Vc, nb):
 
 
 @pytest.mark.parametrize("dims,block,nvec", CASES)
-@pytest.mark.parametrize("prec,lp,tol", [(0, 0, 1e-12), (1, 1, 1e-5), (1, 2, 2e-2), (1, 3, 3e-3)])
+@pytest.mark.parametrize("prec,lp,tol", [(0, 0, 1e-12), (1, 1, 1e-5), (1, 2, 5e-3), (1, 3, 1e-3)])
 def test_coarse_apply_matches_oracle(lib, dims, block, nvec, prec, lp, tol):
     cd = coarse_dims(dims, block)
     Vc = int(np.prod(cd))
@@ -214,7 +214,9 @@ def test_tensor_core_coarse_apply_exact_on_bf16_representable_data(lib):
 
 @pytest.mark.parametrize("nvec", [8, 24, 32])
 def test_tensor_core_coarse_apply_matches_oracle(lib, nvec):
-    """Random data: BF16 rounding of links and vectors (unit roundoff 2^-8) bounds the error."""
+    """Random data: BF16 rounding of links and vectors (unit roundoff 2^-8 each) bounds the
+    error.  Rounding errors of random sign make it about 2^-8 / sqrt(3) per operand,
+    ~2e-3 for the product; the bar is 3x that."""
     dims, block = (8, 8, 8, 8), (2, 2, 2, 2)
     cd = coarse_dims(dims, block)
     Vc, nb = int(np.prod(cd)), 2 * nvec
@@ -229,7 +231,7 @@ def test_tensor_core_coarse_apply_matches_oracle(lib, nvec):
     ctx.apply_coarse(1, dev(phi), out, nrhs=20, prec=lib.F32)
     got = host(out)
     for r, f in enumerate(fields(phi, cd, nb)):
-        assert rel(got[r], op(f).reshape(Vc, nb)) < 2e-2
+        assert rel(got[r], op(f).reshape(Vc, nb)) < 6e-3
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])

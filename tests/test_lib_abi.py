@@ -58,3 +58,16 @@ def test_tile_and_stats_structs_match_header_sizes():
     assert ctypes.sizeof(wcmg.wcmg_tile) == 8 * 4 + 2 * 8
     assert wcmg.wcmg_stats.k.offset % 8 == 0
     assert ctypes.sizeof(wcmg.wcmg_stats) == wcmg.wcmg_stats.k.offset + wcmg.NKCLASS * ctypes.sizeof(wcmg.wcmg_kstat)
+
+
+def test_new_boundary_calls_reject_null_context_without_gpu_work():
+    """set_clover / set_clover_raw / solve_ex / save_net / load_net check their context
+    before any device work; wcmg_solve_opts is four ints."""
+    wcmg = pytest.importorskip("paper_1904_08678_gb300.wcmg")
+    assert ctypes.sizeof(wcmg.wcmg_solve_opts) == 16
+    assert wcmg.wcmg_set_clover(None, 1.0, None) == wcmg.ERR_ARG
+    assert wcmg.wcmg_set_clover_raw(None, None, wcmg.DEVICE, None) == wcmg.ERR_ARG
+    o = wcmg.wcmg_solve_opts(zero_guess=1)
+    assert wcmg.wcmg_solve_ex(None, None, None, 1, ctypes.byref(o), wcmg.DEVICE, None, None) == wcmg.ERR_ARG
+    assert wcmg.wcmg_save_net(None, b"x") == wcmg.ERR_ARG
+    assert wcmg.wcmg_load_net(None, b"x") == wcmg.ERR_ARG
