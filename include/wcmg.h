@@ -291,16 +291,21 @@ int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* c
 
 /* Launch shape of the nine-point coarse apply (K4 / K4m).  Fixed rule: one rhs ->
  * the one-rhs kernel (kind 0); several rhs -> the rhs-tile kernel (kind 1); BF16
- * links with >= 8 rhs -> the tcgen05 tensor-core kernel (kind 2). */
+ * links with >= 8 rhs -> the tcgen05 tensor-core kernel (kind 2).  Kind 3 (one rhs)
+ * is a persistent streaming pipeline: each CTA keeps `stages` bulk copies of
+ * `parts`-row chunks of the link matrices in flight ahead of the arithmetic. */
 typedef struct wcmg_tile {
-  int kind;             /* 0 one-rhs kernel, 1 rhs-tile SIMT kernel, 2 tensor-core kernel, -1 none */
+  int kind;             /* 0 one-rhs kernel, 1 rhs-tile SIMT kernel, 2 tensor-core kernel,
+                           3 one-rhs streaming kernel, -1 none */
   int rhs_per_cta;      /* kind 1: 1, 4 or 8 rhs per CTA */
-  int parts;            /* kinds 0, 1: CTAs sharing one coarse site's rows (kind 1: 0 = automatic) */
-  int threads;          /* kind 0: threads per CTA (64 .. 512, multiple of 32) */
+  int parts;            /* kinds 0, 1: CTAs sharing one coarse site's rows (kind 1: 0 = automatic);
+                           kind 3: link rows per staged chunk */
+  int threads;          /* kinds 0, 3: threads per CTA (kind 0: 64 .. 512, multiple of 32;
+                           kind 3: 128, 256 or 512) */
   int ntile;            /* kind 2: rhs per MMA N tile (16, 32, 48 or 64) */
   int source;           /* 0 fixed rule, 1 autotuner, 2 wcmg_set_coarse_tile */
   int candidates;       /* shapes the autotuner timed (fixed rule included) */
-  int reserved;
+  int stages;           /* kind 3: chunks in flight (2 .. 8) */
   double us;            /* autotuner: time per apply of the chosen shape (back-to-back applies) */
   double us_default;    /* autotuner: time per apply of the fixed rule */
 } wcmg_tile;

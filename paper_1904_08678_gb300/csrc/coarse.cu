@@ -143,6 +143,97 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
   }
 }
 
+// Single-rhs coarse apply as a streaming pipeline (kind 3).  Persistent CTAs walk
+// the work items (site, chunk of `cr` link rows) in the order blockIdx.x + k
+// gridDim.x; thread 0 keeps `stages` bulk copies (cp.async.bulk of one contiguous
+// chunk of the row-major link matrix each, completion counted on the stage's
+// mbarrier) in flight ahead of the arithmetic, so the link stream never waits on a
+// dependent load the way a CTA per site does.  When an item's site changes, the
+// nine neighbour vectors are gathered into shared memory; each warp then reduces
+// whole rows of the staged chunk (16-byte shared loads, warp-shuffle sum).  Every
+// wait is bounded: a timeout sets *err = 3, waits (bounded) for the copies still
+// in flight and ends the CTA.
+constexpr int STREAM_MAX_STAGES = 8;
+
+template <typename R, typename L>
+__global__ void __launch_bounds__(512) k_coarse_apply1_stream(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                              const L* __restrict__ links, const int* __restrict__ nbr,
+                                                              int Vc, int nb, int ld, int cr, int stages,
+                                                              int* __restrict__ err) {
+  using T = cplx<R>;
+  constexpr int VEC = 16 / sizeof(L);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[STREAM_MAX_STAGES];
+  T* phi = reinterpret_cast<T*>(smem);  // [ld]: the nine gathered neighbour vectors, zero padded
+  const int phi_bytes = (ld * (int)sizeof(T) + 127) / 128 * 128;
+  const int stage_bytes = (cr * ld * (int)sizeof(L) + 127) / 128 * 128;
+  unsigned char* stage0 = smem + phi_bytes;
+  const int cps = (nb + cr - 1) / cr;  // chunks per site
+  const long long items = (long long)Vc * cps;
+  const long long nmine = items > blockIdx.x ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < stages; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long k) {
+    const long long it = blockIdx.x + k * gridDim.x;
+    const int site = (int)(it / cps), r0 = (int)(it % cps) * cr;
+    const int rows = min(cr, nb - r0);
+    const uint32_t bytes = (uint32_t)rows * ld * sizeof(L);
+    uint64_t* bar = &full[k % stages];
+    mbar_expect_tx(bar, bytes);
+    tma_load_1d(stage0 + (k % stages) * stage_bytes, links + ((long long)site * nb + r0) * ld, bytes, bar);
+  };
+  if (threadIdx.x == 0)
+    for (long long k = 0; k < stages && k < nmine; ++k) issue(k);
+  int cur = -1;
+  long long k = 0;
+  bool ok = true;
+  for (; k < nmine; ++k) {
+    const long long it = blockIdx.x + k * gridDim.x;
+    const int site = (int)(it / cps), r0 = (int)(it % cps) * cr;
+    const int rows = min(cr, nb - r0);
+    if (site != cur) {  // uniform over the CTA; the previous item's barrier ended every read of phi
+      for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+        T v = czero<R>();
+        if (i < 9 * nb) {
+          const int d = i / nb, c = i - d * nb;
+          v = in[(long long)(d == 0 ? site : nbr[(d - 1) * Vc + site]) * nb + c];
+        }
+        phi[i] = v;
+      }
+      cur = site;
+    }
+    const int s = (int)(k % stages);
+    const int good = mbar_wait_bounded(&full[s], (uint32_t)((k / stages) & 1)) ? 1 : 0;
+    if (!__syncthreads_and(good)) {
+      ok = false;
+      break;
+    }
+    const L* chunk = reinterpret_cast<const L*>(stage0 + s * stage_bytes);
+    for (int row = warp; row < rows; row += nw) {
+      const L* lr = chunk + row * ld;
+      T acc = czero<R>();
+      for (int g = lane; g * VEC < ld; g += 32) {
+        const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + g * VEC);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(lv.v[v]), phi[g * VEC + v]);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) out[(long long)site * nb + r0 + row] = acc;
+    }
+    __syncthreads();  // stage s consumed
+    if (threadIdx.x == 0 && k + stages < nmine) issue(k + stages);
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicExch(err, 3);
+    for (long long q = k; q < k + stages && q < nmine; ++q)  // copies still in flight
+      mbar_wait_bounded(&full[q % stages], (uint32_t)((q / stages) & 1));
+  }
+}
+
 // Multi-rhs coarse apply on the 5th-generation tensor cores (tcgen05, BF16
 // operands, FP32 accumulation in TMEM).  Per coarse site x the nine blocks form
 // Y = M(x) Phi(x), M: nb x 9 nb complex, Phi: 9 nb x N complex.  Real form along K
@@ -351,6 +442,37 @@ static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const
   WCMG_LAUNCH_CHECK();
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    WCMG_CUDA(cudaGetDevice(&dev));
+    WCMG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+
+size_t coarse_stream_smem(int nb, int cr, int stages, int vec_bytes, int link_bytes) {
+  const int ld = links_ld(nb);
+  return (size_t)(ld * vec_bytes + 127) / 128 * 128 + (size_t)stages * ((cr * ld * link_bytes + 127) / 128 * 128);
+}
+
+template <typename R, typename L>
+static void coarse_apply1_stream(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb,
+                                 int threads, int cr, int stages, int* err, cudaStream_t st) {
+  const int ld = links_ld(nb);
+  const size_t smem = coarse_stream_smem(nb, cr, stages, sizeof(cplx<R>), sizeof(L));
+  auto kern = k_coarse_apply1_stream<R, L>;
+  WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  WCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  if (per_sm < 1) throw Error(-1, "coarse apply: streaming tile does not fit on an SM");
+  const long long items = (long long)g.V * ((nb + cr - 1) / cr);
+  const int grid = (int)std::min<long long>(items, (long long)sm_count() * per_sm);
+  kern<<<grid, threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, cr, stages, err);
+  WCMG_LAUNCH_CHECK();
+}
+
 template <typename L>
 static void coarse_apply_mma(float2* out, const float2* in, const L* links, const LevelGeom& g, int nb, int nrhs,
                              int ntile, int* err, cudaStream_t st) {
@@ -407,6 +529,13 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
     case 2:
       return link_kind == 2 && mode == ST_FULL && nb <= 64 &&
              (t.ntile == 16 || t.ntile == 32 || t.ntile == 48 || t.ntile == 64);
+    case 3: {
+      const int lb = link_kind == 0 ? 16 : link_kind == 1 ? 8 : 4;
+      const int vb = link_kind == 0 ? 16 : 8;
+      return nrhs == 1 && mode == ST_FULL && (t.threads == 128 || t.threads == 256 || t.threads == 512) &&
+             t.parts >= 1 && t.parts <= nb && t.stages >= 2 && t.stages <= STREAM_MAX_STAGES &&
+             coarse_stream_smem(nb, t.parts, t.stages, vb, lb) <= 200 * 1024;
+    }
     default:
       return false;
   }
@@ -429,8 +558,13 @@ void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const 
     }
     throw Error(-1, "coarse apply: tensor-core tile needs BF16 links");
   }
+  if (t.kind == 3 && !err) t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
   if (t.kind == 0) {
     coarse_apply1<R, L>(out, in, links, g, nb, t.parts, t.threads, st);
+    return;
+  }
+  if (t.kind == 3) {
+    coarse_apply1_stream<R, L>(out, in, links, g, nb, t.threads, t.parts, t.stages, err, st);
     return;
   }
   if (t.rr == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, t.parts, st);

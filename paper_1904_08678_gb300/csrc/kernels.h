@@ -102,9 +102,13 @@ void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int 
 // site, threads per CTA); kind 1: rhs-tile kernel (rr rhs per CTA, parts CTAs
 // per site, 0 = automatic); kind 2: tcgen05 tensor-core kernel (BF16 links, N
 // tile ntile).  kind -1: the fixed rule of coarse_default_tile.
+// kind 3: one-rhs streaming pipeline (threads per CTA, parts = link rows per staged
+// chunk, stages = chunks in flight).
 struct CoarseTile {
-  int kind = -1, rr = 0, parts = 0, threads = 0, ntile = 0;
+  int kind = -1, rr = 0, parts = 0, threads = 0, ntile = 0, stages = 0;
 };
+// Shared memory of the one-rhs streaming kernel (kind 3).
+size_t coarse_stream_smem(int nb, int cr, int stages, int vec_bytes, int link_bytes);
 // link_kind: 0 FP64, 1 FP32, 2 BF16, 3 FP16 link storage
 CoarseTile coarse_default_tile(int nb, int nrhs, int mode, int Vc, int link_kind);
 bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link_kind);

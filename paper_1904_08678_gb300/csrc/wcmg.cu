@@ -377,15 +377,19 @@ static double sz(int prec) { return prec == WCMG_F64 ? 16.0 : prec == WCMG_F32 ?
 // Candidate launch shapes of the full nine-point coarse apply (K4 / K4m).
 static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
   std::vector<CoarseTile> v;
-  auto add = [&](int kind, int rr, int parts, int threads, int ntile) {
+  auto add = [&](int kind, int rr, int parts, int threads, int ntile, int stages = 0) {
     CoarseTile t;
-    t.kind = kind; t.rr = rr; t.parts = parts; t.threads = threads; t.ntile = ntile;
+    t.kind = kind; t.rr = rr; t.parts = parts; t.threads = threads; t.ntile = ntile; t.stages = stages;
     if (coarse_tile_valid(t, nb, nrhs, ST_FULL, lk)) v.push_back(t);
   };
   if (nrhs == 1) {
     for (int th : {256, 512})
       for (int p : {1, 2, 4, 8}) add(0, 1, p, th, 0);
     for (int p : {1, 2, 4, 8, 16}) add(1, 1, p, 0, 0);
+    // streaming pipeline: chunks of 8 / 16 rows, 3 .. 6 in flight
+    for (int th : {256, 512})
+      for (int cr : {8, 16})
+        for (int stg : {3, 4, 6}) add(3, 0, cr, th, 0, stg);
     return v;
   }
   for (int rr : {1, 4, 8})
@@ -2600,6 +2604,7 @@ static void tile_out(const Level::TileInfo& ti, wcmg_tile* o) {
   o->parts = ti.t.parts;
   o->threads = ti.t.threads;
   o->ntile = ti.t.ntile;
+  o->stages = ti.t.stages;
   o->source = ti.source;
   o->candidates = ti.candidates;
   o->us = ti.us;
@@ -2666,6 +2671,7 @@ int wcmg_set_coarse_tile(wcmg_ctx* c, int level, int nrhs, int prec, const wcmg_
     ti.t.parts = t->parts;
     ti.t.threads = t->threads;
     ti.t.ntile = t->ntile;
+    ti.t.stages = t->stages;
     if (!coarse_tile_valid(ti.t, L.nc, nrhs, ST_FULL, lk)) throw Error(WCMG_ERR_ARG, "tile not valid for this level");
     ti.source = 2;
     L.tiles[{nrhs, lk}] = ti;

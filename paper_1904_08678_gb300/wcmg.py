@@ -103,11 +103,11 @@ class wcmg_stats(ctypes.Structure):
 class wcmg_tile(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("rhs_per_cta", ctypes.c_int), ("parts", ctypes.c_int),
                 ("threads", ctypes.c_int), ("ntile", ctypes.c_int), ("source", ctypes.c_int),
-                ("candidates", ctypes.c_int), ("reserved", ctypes.c_int), ("us", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("stages", ctypes.c_int), ("us", ctypes.c_double),
                 ("us_default", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class wcmg_solve_opts(ctypes.Structure):
@@ -380,8 +380,8 @@ class Context:
         self._check(wcmg_tune_coarse(self.h, level, nrhs, prec, cold, _stream(stream), ctypes.byref(t)))
         return t.as_dict()
 
-    def set_coarse_tile(self, level, nrhs=1, prec=F32, kind=-1, rhs_per_cta=0, parts=0, threads=0, ntile=0):
-        t = wcmg_tile(kind=kind, rhs_per_cta=rhs_per_cta, parts=parts, threads=threads, ntile=ntile)
+    def set_coarse_tile(self, level, nrhs=1, prec=F32, kind=-1, rhs_per_cta=0, parts=0, threads=0, ntile=0, stages=0):
+        t = wcmg_tile(kind=kind, rhs_per_cta=rhs_per_cta, parts=parts, threads=threads, ntile=ntile, stages=stages)
         return self._check(wcmg_set_coarse_tile(self.h, level, nrhs, prec, ctypes.byref(t)))
 
     @staticmethod

@@ -13,6 +13,13 @@ def host(t):
     return t.cpu().numpy()
 
 
+def residual(Dx, b):
+    """True relative residual ||b - D x|| / ||b|| (2-norm over the whole field): the
+    stopping test of the solver, checked with the oracle's D."""
+    Dx = np.asarray(Dx); b = np.asarray(b)
+    return float(np.linalg.norm((b - Dx).ravel()) / np.linalg.norm(b.ravel()))
+
+
 def rel(a, b):
     """Relative error of `a` against the reference `b`, the larger of two measures:
     the 2-norm ratio ||a - b|| / ||b|| over the whole array, and the element-wise

@@ -16,6 +16,14 @@ pytestmark = pytest.mark.gpu
 DIMS, BLOCK, NVEC = (8, 8, 8, 8), (2, 2, 2, 2), 24
 
 
+def stream_fits(lk, nb, rows, stages):
+    """Shared memory of the streaming one-rhs kernel (kind 3) within its 200 KiB limit."""
+    ld = (9 * nb + 3) // 4 * 4
+    lb, vb = {"f64": (16, 16), "f32": (8, 8), "bf16": (4, 8), "f16": (4, 8)}[lk]
+    r128 = lambda x: (x + 127) // 128 * 128
+    return r128(ld * vb) + stages * r128(rows * ld * lb) <= 200 * 1024
+
+
 def candidate_tiles(nrhs, lk, nb):
     """Shapes the library's autotuner times, plus extreme valid ones."""
     t = []
@@ -23,6 +31,11 @@ def candidate_tiles(nrhs, lk, nb):
         t += [dict(kind=0, threads=th, parts=p) for th in (256, 512) for p in (1, 2, 4, 8)]
         t += [dict(kind=0, threads=64, parts=nb), dict(kind=0, threads=96, parts=3)]
         t += [dict(kind=1, rhs_per_cta=1, parts=p) for p in (1, 2, 4, 8, 16, nb)]
+        # streaming pipeline: the autotuner's shapes, a ragged last chunk (48 % 5, 48 % 7)
+        # and the shallowest / deepest pipelines
+        shapes = [(th, cr, st) for th in (256, 512) for cr in (8, 16) for st in (3, 4, 6)]
+        shapes += [(128, 5, 2), (512, 3, 8), (256, 7, 5), (128, nb, 2)]
+        t += [dict(kind=3, threads=th, parts=cr, stages=st) for th, cr, st in shapes if stream_fits(lk, nb, cr, st)]
     else:
         t += [dict(kind=1, rhs_per_cta=rr, parts=p) for rr in (1, 4, 8) if rr <= nrhs or rr == 4
               for p in (0, 1, 2, 4, 8, 16)]
@@ -115,6 +128,10 @@ def test_invalid_tiles_are_rejected(lib):
            (4, dict(kind=1, rhs_per_cta=3, parts=1)),   # no such rhs tile
            (1, dict(kind=0, threads=48, parts=1)),      # threads not a multiple of 32
            (1, dict(kind=0, threads=512, parts=0)),
+           (1, dict(kind=3, threads=256, parts=8, stages=1)),   # a pipeline needs >= 2 stages
+           (1, dict(kind=3, threads=96, parts=8, stages=4)),    # 128, 256 or 512 threads
+           (4, dict(kind=3, threads=256, parts=8, stages=4)),   # one rhs only
+           (1, dict(kind=3, threads=256, parts=48, stages=8)),  # beyond the shared-memory limit
            (1, dict(kind=7))]
     for nrhs, t in bad:
         with pytest.raises(lib.WcmgError) as e:
