@@ -123,6 +123,11 @@ typedef struct wcmg_params {
                                            per wcmg_set_gauge in FP64.  Fine aggregates of at most
                                            256 sites with an even x extent (else WCMG_ERR_ARG).
                                            Coarse levels keep the plain block solves. */
+  int ortho_df;                         /* arithmetic of the block orthonormalisation (Sec. 2.2 Q factor
+                                           per aggregate and chirality): 0 FP64; 1 double-float on
+                                           the FP32 pipe (each value the unevaluated sum of two
+                                           floats, 48-bit significands, compensated dot products),
+                                           FP64 input and output.  Same algorithm and stopping rule. */
 } wcmg_params;
 
 typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1, WCMG_SMOOTHER_SAP = 2 } wcmg_smoother;

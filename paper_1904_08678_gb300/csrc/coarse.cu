@@ -395,6 +395,210 @@ __global__ void __launch_bounds__(128) k_coarse_apply_mma(float2* __restrict__ o
   if (warp == 0) tmem_dealloc(tmem, tmem_cols);
 }
 
+// Multi-rhs coarse apply on tcgen05 with every operand moved by bulk copies
+// (kind 4).  Per coarse site x: Y = M(x) Phi(x) in the real form of the kind-2
+// kernel (A = the links' BF16 (Re, Im) pairs along K, the complex product in B).
+// Operands are pre-arranged in global memory in the no-swizzle K-major layout of
+// the MMA, so that one contiguous bulk copy fills an operand of a neighbour block:
+//   A (links, "MMA copy"): [site][d][g][a][8 BF16]: group g of row a of block A_d is
+//     the 16 bytes of link entries 4 g .. 4 g + 3 (nb / 4 groups, nb rows);
+//   B (built by k_mma_bprep for each apply): [y][tile][g][j][8 BF16] with rows
+//     j < N: (Re phi, -Im phi) of rhs tile N + j at site y, j >= N: (Im phi, Re phi).
+// In shared memory a stage then holds A_d (nb rows x 2 nb K) and B (2 N rows x 2 nb
+// K) with leading byte offsets 16 nb and 32 N; an MMA of M rows (64 or 128; rows
+// beyond nb read neighbouring data and are never stored) and N_mma = 2 N runs over
+// K = 16 per instruction.  Warp roles, persistent over (site, tile) items: warp 0
+// issues the bulk copies into a ring of stages (full barriers with transaction
+// counts), warp 1 allocates TMEM and issues the MMAs (committing each stage back to
+// its empty barrier and each finished item to an accumulator barrier; two TMEM
+// accumulators alternate), warps 2-5 read the accumulator of the previous item and
+// store it while the next one is being formed.  Every wait is bounded: a timeout
+// sets *err = 3; the CTA then waits (bounded) for its copies and MMAs in flight,
+// frees its TMEM and ends.
+constexpr int MMA4_MAX_STAGES = 8;
+
+__global__ void k_mma_bprep(uint4* __restrict__ bp, const float2* __restrict__ in, int Vc, int nb, int nrhs,
+                            int ntile, int ntiles) {
+  // one thread per 16-byte group: (y, tile, g, j)
+  const int kg = nb / 4, rows = 2 * ntile;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)Vc * ntiles * kg * rows;
+  if (idx >= total) return;
+  const int j = (int)(idx % rows);
+  const int g = (int)((idx / rows) % kg);
+  const long long yt = idx / ((long long)rows * kg);
+  const int t = (int)(yt % ntiles), y = (int)(yt / ntiles);
+  const int n = t * ntile + (j < ntile ? j : j - ntile);
+  uint4 w = make_uint4(0, 0, 0, 0);
+  if (n < nrhs) {
+    const float4* src = reinterpret_cast<const float4*>(in + ((long long)n * Vc + y) * nb + 4 * g);
+    const float4 a = src[0], b = src[1];  // phi entries 4 g .. 4 g + 3
+    if (j < ntile) {
+      w.x = pack_bf16x2(a.x, -a.y); w.y = pack_bf16x2(a.z, -a.w);
+      w.z = pack_bf16x2(b.x, -b.y); w.w = pack_bf16x2(b.z, -b.w);
+    } else {
+      w.x = pack_bf16x2(a.y, a.x); w.y = pack_bf16x2(a.w, a.z);
+      w.z = pack_bf16x2(b.y, b.x); w.w = pack_bf16x2(b.w, b.z);
+    }
+  }
+  bp[idx] = w;
+}
+
+// links (row-major nb x ld per site, BF16 pairs) -> the MMA copy [site][d][g][a]
+__global__ void k_links_to_mma(uint4* __restrict__ dst, const uint4* __restrict__ src, int Vc, int nb, int ld) {
+  const int kg = nb / 4;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)Vc * 9 * kg * nb;
+  if (idx >= total) return;
+  const int a = (int)(idx % nb);
+  const int g = (int)((idx / nb) % kg);
+  const int d = (int)((idx / ((long long)nb * kg)) % 9);
+  const long long site = idx / ((long long)nb * kg * 9);
+  dst[idx] = src[((site * nb + a) * ld + d * nb + 4 * g) / 4];
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// 32 lanes x 8 columns of FP32 from TMEM
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int MM>
+__global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict__ out, const uint4* __restrict__ amma,
+                                                              const uint4* __restrict__ bpre,
+                                                              const int* __restrict__ nbr, int Vc, int nb, int nrhs,
+                                                              int ntile, int ntiles, int stages,
+                                                              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[MMA4_MAX_STAGES], empty[MMA4_MAX_STAGES], tfull[2], tempty[2], fin;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kg = nb / 4, rows_b = 2 * ntile;
+  const uint32_t a_bytes = (uint32_t)kg * nb * 16, b_bytes = (uint32_t)kg * rows_b * 16;
+  const uint32_t a_alloc = (a_bytes + (uint32_t)(MM > nb ? MM - nb : 0) * 16 + 1023) / 1024 * 1024;
+  const uint32_t stage_bytes = a_alloc + (b_bytes + 1023) / 1024 * 1024;
+  const long long items = (long long)Vc * ntiles;
+  const long long limit = 1LL << 26;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < stages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&tfull[q], 1);
+      mbar_init(&tempty[q], 128);
+    }
+    mbar_init(&fin, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t s0 = smem_u32(smem);
+  auto fail = [&]() {
+    *(volatile int*)&abort_flag = 1;
+    atomicExch(err, 3);
+  };
+  long long issued = 0;  // producer: chunks whose copies were issued
+  if (warp == 0) {
+    if (lane == 0) {
+      long long c = 0;
+      for (long long it = blockIdx.x; it < items && !*(volatile int*)&abort_flag; it += gridDim.x) {
+        const int site = (int)(it / ntiles), t = (int)(it % ntiles);
+        for (int d = 0; d < 9; ++d, ++c) {
+          const int s = (int)(c % stages);
+          if (!mbar_wait_bounded(&empty[s], (uint32_t)(((c / stages) & 1) ^ 1), limit)) { fail(); break; }
+          const int y = d == 0 ? site : nbr[(d - 1) * Vc + site];
+          unsigned char* st = smem + (size_t)s * stage_bytes;
+          mbar_expect_tx(&full[s], a_bytes + b_bytes);
+          tma_load_1d(st, amma + ((long long)site * 9 + d) * kg * nb, a_bytes, &full[s]);
+          tma_load_1d(st + a_alloc, bpre + ((long long)y * ntiles + t) * kg * rows_b, b_bytes, &full[s]);
+          issued = c + 1;
+        }
+        if (*(volatile int*)&abort_flag) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_bf16(MM, rows_b);
+      long long c = 0, i = 0;
+      bool ok = true;
+      for (long long it = blockIdx.x; it < items && ok; it += gridDim.x, ++i) {
+        const int tb = (int)(i & 1);
+        if (!mbar_wait_bounded(&tempty[tb], (uint32_t)(((i >> 1) & 1) ^ 1), limit)) { fail(); ok = false; break; }
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)tb * 128;
+        for (int d = 0; d < 9; ++d, ++c) {
+          const int s = (int)(c % stages);
+          if (!mbar_wait_bounded(&full[s], (uint32_t)((c / stages) & 1), limit)) { fail(); ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = s0 + (uint32_t)s * stage_bytes, b0 = a0 + a_alloc;
+          for (int q = 0; q < kg / 2; ++q)
+            umma_bf16(dt, umma_desc(a0 + (uint32_t)q * 2 * nb * 16, (uint32_t)nb * 16, 128),
+                      umma_desc(b0 + (uint32_t)q * 2 * rows_b * 16, (uint32_t)rows_b * 16, 128), idesc,
+                      (d > 0 || q > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&tfull[tb]);
+      }
+      umma_commit(&fin);  // every MMA issued by this CTA has completed once fin flips
+      if (!mbar_wait_bounded(&fin, 0, limit)) fail();
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) ..; row m of D sits in lane m (M = 128)
+    // or lane 32 (m / 16) + m % 16 (M = 64)
+    const int quad = warp & 3;
+    const int m = MM == 128 ? 32 * quad + lane : (lane < 16 ? 16 * quad + lane : nb);
+    long long i = 0;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x, ++i) {
+      const int tb = (int)(i & 1);
+      const int good = mbar_wait_bounded(&tfull[tb], (uint32_t)((i >> 1) & 1), limit) ? 1 : 0;
+      if (!good || *(volatile int*)&abort_flag) {
+        if (!good) fail();
+        break;
+      }
+      tc_fence_after();
+      const int site = (int)(it / ntiles), t = (int)(it % ntiles);
+      const uint32_t dt = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)tb * 128;
+      for (int j0 = 0; j0 < ntile; j0 += 8) {
+        float re[8], im[8];
+        tmem_ld8(dt + j0, re);
+        tmem_ld8(dt + ntile + j0, im);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int n = t * ntile + j0 + q;
+          if (m < nb && j0 + q < ntile && n < nrhs) out[((long long)n * Vc + site) * nb + m] = make_float2(re[q], im[q]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[tb]);
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && *(volatile int*)&abort_flag) {
+    // copies still in flight land before the CTA's shared memory is released
+    for (long long q = issued - stages; q < issued; ++q)
+      if (q >= 0) mbar_wait_bounded(&full[q % stages], (uint32_t)((q / stages) & 1), limit);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 256);
+}
+
 template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
 
 template <typename R, typename L, int RR>
@@ -486,6 +690,43 @@ static void coarse_apply_mma(float2* out, const float2* in, const L* links, cons
   WCMG_LAUNCH_CHECK();
 }
 
+size_t coarse_mma4_smem(int nb, int ntile, int mm, int stages) {
+  const size_t kg = nb / 4;
+  const size_t a_alloc = (kg * nb * 16 + (size_t)(mm > nb ? mm - nb : 0) * 16 + 1023) / 1024 * 1024;
+  const size_t b_alloc = (kg * 2 * ntile * 16 + 1023) / 1024 * 1024;
+  return (size_t)stages * (a_alloc + b_alloc);
+}
+
+size_t coarse_mma4_scratch_bytes(int Vc, int nb, int nrhs) {
+  // B operands of every site for any rhs tile of at most 64: Vc x tiles x 2 N x nb x 4 bytes
+  return (size_t)Vc * nb * 8 * (size_t)(nrhs + 63);
+}
+
+void launch_links_to_mma(bf16c* dst, const bf16c* src, int Vc, int nb, cudaStream_t st) {
+  const long long total = (long long)Vc * 9 * (nb / 4) * nb;
+  k_links_to_mma<<<nblk(total, 256), 256, 0, st>>>(reinterpret_cast<uint4*>(dst), reinterpret_cast<const uint4*>(src),
+                                                   Vc, nb, links_ld(nb));
+  WCMG_LAUNCH_CHECK();
+}
+
+static void coarse_apply_mma4(float2* out, const float2* in, const bf16c* lmma, const LevelGeom& g, int nb, int nrhs,
+                              const CoarseTile& t, void* scratch, size_t scratch_bytes, int* err, cudaStream_t st) {
+  const int ntiles = (nrhs + t.ntile - 1) / t.ntile;
+  const long long groups = (long long)g.V * ntiles * (nb / 4) * 2 * t.ntile;
+  if ((size_t)groups * 16 > scratch_bytes) throw Error(-1, "coarse apply: tensor-core scratch too small");
+  uint4* bp = reinterpret_cast<uint4*>(scratch);
+  k_mma_bprep<<<nblk(groups, 256), 256, 0, st>>>(bp, in, g.V, nb, nrhs, t.ntile, ntiles);
+  WCMG_LAUNCH_CHECK();
+  const size_t smem = coarse_mma4_smem(nb, t.ntile, t.threads, t.stages);
+  auto kern = t.threads == 64 ? k_coarse_apply_mma4<64> : k_coarse_apply_mma4<128>;
+  WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long items = (long long)g.V * ntiles;
+  const int grid = (int)std::min<long long>(items, sm_count());
+  kern<<<grid, 192, smem, st>>>(out, reinterpret_cast<const uint4*>(lmma), bp, g.nbr, g.V, nb, nrhs, t.ntile, ntiles,
+                                t.stages, err);
+  WCMG_LAUNCH_CHECK();
+}
+
 // The fixed launch rule (used unless a tile is given):
 //  - BF16 links, full stencil, >= 8 rhs, nbasis <= 64: tensor cores, N tile = rhs rounded to 16 (<= 64);
 //  - one rhs, full stencil: the one-rhs kernel, 512 threads, a site split in up to 4
@@ -529,6 +770,11 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
     case 2:
       return link_kind == 2 && mode == ST_FULL && nb <= 64 &&
              (t.ntile == 16 || t.ntile == 32 || t.ntile == 48 || t.ntile == 64);
+    case 4:
+      return link_kind == 2 && mode == ST_FULL && nrhs >= 2 && nb % 8 == 0 && nb <= 64 &&
+             (t.threads == 64 || t.threads == 128) && t.threads >= nb && t.ntile % 8 == 0 && t.ntile >= 8 &&
+             t.ntile <= 64 && t.stages >= 2 && t.stages <= MMA4_MAX_STAGES &&
+             coarse_mma4_smem(nb, t.ntile, t.threads, t.stages) <= 220 * 1024;
     case 3: {
       const int lb = link_kind == 0 ? 16 : link_kind == 1 ? 8 : 4;
       const int vb = link_kind == 0 ? 16 : 8;
@@ -543,7 +789,8 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
 
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
-                         int mode, int hopdir, cudaStream_t st, int* err, const CoarseTile* tile) {
+                         int mode, int hopdir, cudaStream_t st, int* err, const CoarseTile* tile, const bf16c* lmma,
+                         void* scratch, size_t scratch_bytes) {
   constexpr int lk = LinkKind<L>::v;
   CoarseTile t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
   if (tile && tile->kind >= 0) {
@@ -559,6 +806,14 @@ void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const 
     throw Error(-1, "coarse apply: tensor-core tile needs BF16 links");
   }
   if (t.kind == 3 && !err) t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
+  if (t.kind == 4 && (!err || !lmma || !scratch)) t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
+  if (t.kind == 4) {
+    if constexpr (std::is_same<L, bf16c>::value) {
+      coarse_apply_mma4((float2*)out, (const float2*)in, lmma, g, nb, nrhs, t, scratch, scratch_bytes, err, st);
+      return;
+    }
+    throw Error(-1, "coarse apply: tensor-core tile needs BF16 links");
+  }
   if (t.kind == 0) {
     coarse_apply1<R, L>(out, in, links, g, nb, t.parts, t.threads, st);
     return;
@@ -675,13 +930,17 @@ void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int 
 }
 
 template void launch_coarse_apply<double, double2>(double2*, const double2*, const double2*, const LevelGeom&, int,
-                                                   int, int, int, cudaStream_t, int*, const CoarseTile*);
+                                                   int, int, int, cudaStream_t, int*, const CoarseTile*,
+                                                   const bf16c*, void*, size_t);
 template void launch_coarse_apply<float, float2>(float2*, const float2*, const float2*, const LevelGeom&, int, int,
-                                                 int, int, cudaStream_t, int*, const CoarseTile*);
+                                                 int, int, cudaStream_t, int*, const CoarseTile*,
+                                                   const bf16c*, void*, size_t);
 template void launch_coarse_apply<float, bf16c>(float2*, const float2*, const bf16c*, const LevelGeom&, int, int, int,
-                                                int, cudaStream_t, int*, const CoarseTile*);
+                                                int, cudaStream_t, int*, const CoarseTile*,
+                                                const bf16c*, void*, size_t);
 template void launch_coarse_apply<float, f16c>(float2*, const float2*, const f16c*, const LevelGeom&, int, int, int,
-                                               int, cudaStream_t, int*, const CoarseTile*);
+                                               int, cudaStream_t, int*, const CoarseTile*,
+                                                const bf16c*, void*, size_t);
 #define WCMG_INST_L(L)                                                                                   \
   template void launch_pack_links<L>(L*, const double2*, const int*, int, int, cudaStream_t);           \
   template void launch_unpack_links<L>(double2*, const L*, const int*, int, int, cudaStream_t);

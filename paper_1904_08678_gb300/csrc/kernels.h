@@ -81,6 +81,10 @@ void launch_prolong(cplx<R>* out, const cplx<R>* coarse, const cplx<R>* vecs, in
                     int nrhs, bool fine, cudaStream_t st);
 // FP64 block orthonormalisation in place; err receives 1 on a rank-deficient panel.
 void launch_block_ortho(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st);
+// The same in double-float arithmetic on the FP32 pipe (48-bit significands, FP64
+// input and output); qdf: scratch of as many float4 as vecs has complex entries.
+void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
+                           cudaStream_t st);
 // cols[b] = Pi_s v_i with (s, i) = divmod(b0 + b, nvec), for b < ncols.
 template <typename R>
 void launch_make_columns(cplx<R>* cols, const cplx<R>* vecs, int Vf, int nc, int nvec, int b0, int ncols, bool fine,
@@ -103,7 +107,8 @@ void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int 
 // per site, 0 = automatic); kind 2: tcgen05 tensor-core kernel (BF16 links, N
 // tile ntile).  kind -1: the fixed rule of coarse_default_tile.
 // kind 3: one-rhs streaming pipeline (threads per CTA, parts = link rows per staged
-// chunk, stages = chunks in flight).
+// chunk, stages = chunks in flight); kind 4: tcgen05 multi-rhs apply fed by bulk copies
+// (ntile rhs per N tile, threads = MMA M (64 or 128), stages).
 struct CoarseTile {
   int kind = -1, rr = 0, parts = 0, threads = 0, ntile = 0, stages = 0;
 };
@@ -115,10 +120,18 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
 // err (device int, may be null): receives 3 if a bounded wait of the tensor-core
 // path gave up; a null err keeps the SIMT kernels.  tile (nullable): launch shape
 // (validated; an invalid tile throws).
+// lmma / scratch: the MMA copy of BF16 links (launch_links_to_mma) and a scratch of at
+// least coarse_mma4_scratch_bytes bytes, both needed by kind 4 (otherwise the fixed rule).
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
                          int mode, int hopdir, cudaStream_t st, int* err = nullptr,
-                         const CoarseTile* tile = nullptr);
+                         const CoarseTile* tile = nullptr, const bf16c* lmma = nullptr, void* scratch = nullptr,
+                         size_t scratch_bytes = 0);
+// kind 4 (tcgen05 fed by bulk copies): the links in the MMA's K-major core-matrix order,
+// [site][d][16-byte group g][row a]; its shared memory; its scratch for any rhs tile.
+void launch_links_to_mma(bf16c* dst, const bf16c* src, int Vc, int nb, cudaStream_t st);
+size_t coarse_mma4_smem(int nb, int ntile, int mm, int stages);
+size_t coarse_mma4_scratch_bytes(int Vc, int nb, int nrhs);
 // links[x][a][d*nb + b0 + j] = res[j][x][a] for j < ncols (res: restrict output of the column fields)
 template <typename R, typename L>
 void launch_scatter_links(L* links, const cplx<R>* res, int Vc, int nb, int d, int b0, int ncols, cudaStream_t st);

@@ -501,6 +501,242 @@ __global__ void __launch_bounds__(256, 2) k_block_ortho(double2* __restrict__ ve
   }
 }
 
+// ---------------- block orthonormalisation in double-float arithmetic ----------------
+// The same Gram-Schmidt (classical, with the selective second pass and the
+// normalisation of k_block_ortho) with every multiply-add on the FP32 pipe in
+// double-float ("DF") form: a value is the unevaluated sum h + l of two floats
+// (|l| <= ulp(h) / 2 once normalised: 48 significand bits).  Error-free
+// transformations give the exact rounding error of a float sum (Knuth's TwoSum) and
+// of a float product (by FMA); the dot products accumulate them as in the
+// compensated dot product of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005), so each projection is as accurate as one formed in
+// twice the float precision.  The input and the returned Q stay FP64 (the value of
+// h + l rounded to double); the Q columns are also kept in DF in `qdf` (float4 per
+// complex entry: re.h, re.l, im.h, im.l), from which later columns re-read them.
+// FP32 arithmetic runs 64x faster than FP64 on this part, and one DF multiply-add
+// costs 12 FP32 operations.
+struct dfr { float h, l; };
+struct dfc { dfr re, im; };
+
+__device__ __forceinline__ dfr df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dfr a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ dfr df_neg(dfr a) { return {-a.h, -a.l}; }
+// TwoSum: s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+// acc += x y  (low parts of the product beyond x.l y.l kept; acc left unnormalised)
+__device__ __forceinline__ void df_mac(dfr& acc, dfr x, dfr y) {
+  const float p = x.h * y.h;
+  float pe = fmaf(x.h, y.h, -p);
+  pe = fmaf(x.h, y.l, pe);
+  pe = fmaf(x.l, y.h, pe);
+  float s, e;
+  two_sum(acc.h, p, s, e);
+  acc.h = s;
+  acc.l += e + pe;
+}
+__device__ __forceinline__ dfr df_norm(dfr a) {
+  const float h = a.h + a.l;
+  return {h, a.l - (h - a.h)};
+}
+__device__ __forceinline__ dfr df_add(dfr a, dfr b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return df_norm({s, e + (a.l + b.l)});
+}
+__device__ __forceinline__ dfr df_mul(dfr x, dfr y) {
+  const float p = x.h * y.h;
+  float pe = fmaf(x.h, y.h, -p);
+  pe = fmaf(x.h, y.l, pe);
+  pe = fmaf(x.l, y.h, pe);
+  return df_norm({p, pe});
+}
+__device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_norm(dfc a) { return {df_norm(a.re), df_norm(a.im)}; }
+// acc += conj(q) a
+__device__ __forceinline__ void dfc_cjmac(dfc& acc, const dfc& q, const dfc& a) {
+  df_mac(acc.re, q.re, a.re);
+  df_mac(acc.re, q.im, a.im);
+  df_mac(acc.im, q.re, a.im);
+  df_mac(acc.im, df_neg(q.im), a.re);
+}
+// acc -= r q
+__device__ __forceinline__ void dfc_nmac(dfc& acc, const dfc& r, const dfc& q) {
+  df_mac(acc.re, df_neg(r.re), q.re);
+  df_mac(acc.re, r.im, q.im);
+  df_mac(acc.im, df_neg(r.re), q.im);
+  df_mac(acc.im, df_neg(r.im), q.re);
+}
+__device__ __forceinline__ dfc dfc_load(const float4* p) {
+  const float4 v = *p;
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ dfc dfc_shfl_xor(const dfc& v, int o) {
+  return {{__shfl_xor_sync(0xffffffffu, v.re.h, o), __shfl_xor_sync(0xffffffffu, v.re.l, o)},
+          {__shfl_xor_sync(0xffffffffu, v.im.h, o), __shfl_xor_sync(0xffffffffu, v.im.l, o)}};
+}
+// warp_sum8_transposed in DF: on return v[0] of lane l holds the warp sum of value
+// warp_sum8_index(l)
+__device__ __forceinline__ void dfc_warp_sum8_transposed(dfc (&v)[8], int lane) {
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const dfc send = up ? v[j] : v[j + 4];
+      const dfc keep = up ? v[j + 4] : v[j];
+      v[j] = dfc_add(keep, dfc_shfl_xor(send, 16));
+    }
+  }
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const dfc send = up ? v[j] : v[j + 2];
+      const dfc keep = up ? v[j + 2] : v[j];
+      v[j] = dfc_add(keep, dfc_shfl_xor(send, 8));
+    }
+  }
+  {
+    const bool up = lane & 4;
+    const dfc send = up ? v[0] : v[1];
+    const dfc keep = up ? v[1] : v[0];
+    v[0] = dfc_add(keep, dfc_shfl_xor(send, 4));
+  }
+  v[0] = dfc_add(v[0], dfc_shfl_xor(v[0], 2));
+  v[0] = dfc_add(v[0], dfc_shfl_xor(v[0], 1));
+}
+__device__ __forceinline__ dfr df_warp_sum(dfr v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+  return v;
+}
+
+template <int MAXE>
+__global__ void __launch_bounds__(256, 2) k_block_ortho_df(double2* __restrict__ vecs, float4* __restrict__ qdf, int Vf,
+                                                        int nc, int bvol, int nvec, bool fine, int* __restrict__ err) {
+  constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
+  __shared__ dfc scratch[8][MV];
+  __shared__ dfc red[MV];
+  const int blk = blockIdx.x, s = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nelem = bvol * (nc >> 1);
+  const long long fstride = (long long)Vf * nc;
+  long long addr[MAXE];
+#pragma unroll
+  for (int q = 0; q < MAXE; ++q) {
+    const int e = threadIdx.x + q * blockDim.x;
+    addr[q] = e < nelem ? elem_addr(fine, blk, e, s, Vf, nc, bvol) : -1;
+  }
+  const dfc zero = {{0.f, 0.f}, {0.f, 0.f}};
+  // block-wide DF sums of slots [0, n) and the norm slot
+  auto reduce = [&](int n, bool with_norm) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      dfc t = scratch[0][i];
+      for (int w = 1; w < nw; ++w) t = dfc_add(t, scratch[w][i]);
+      red[i] = t;
+    }
+    if (with_norm && threadIdx.x == 0) {
+      dfc t = scratch[0][MV - 1];
+      for (int w = 1; w < nw; ++w) t = dfc_add(t, scratch[w][MV - 1]);
+      red[MV - 1] = t;
+    }
+    __syncthreads();
+  };
+  auto norm2 = [&](const dfc (&a)[MAXE]) {
+    dfr n = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+      df_mac(n, a[q].re, a[q].re);
+      df_mac(n, a[q].im, a[q].im);
+    }
+    n = df_warp_sum(df_norm(n));
+    if (lane == 0) scratch[warp][MV - 1] = {n, {0.f, 0.f}};
+  };
+  for (int k = 0; k < nvec; ++k) {
+    dfc a[MAXE];
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+      if (addr[q] >= 0) {
+        const double2 v = vecs[k * fstride + addr[q]];
+        a[q] = {df_from(v.x), df_from(v.y)};
+      } else {
+        a[q] = zero;
+      }
+    }
+    double before2 = 0.0, after2 = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      // projections <q_i, a> for i < k, eight at a time (one transposing warp reduction)
+      for (int i0 = 0; i0 < k; i0 += 8) {
+        dfc p[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          p[g] = zero;
+          if (i0 + g < k) {
+            const float4* qi = qdf + (i0 + g) * fstride;
+#pragma unroll
+            for (int q = 0; q < MAXE; ++q)
+              if (addr[q] >= 0) dfc_cjmac(p[g], dfc_load(qi + addr[q]), a[q]);
+          }
+          p[g] = dfc_norm(p[g]);
+        }
+        dfc_warp_sum8_transposed(p, lane);
+        const int g = warp_sum8_index(lane);
+        if ((lane & 3) == 0 && i0 + g < k) scratch[warp][i0 + g] = p[0];
+      }
+      norm2(a);
+      reduce(k, true);
+      if (pass == 0) before2 = df_to(red[MV - 1].re);
+      for (int i = 0; i < k; ++i) {
+        const dfc r = red[i];
+        const float4* qi = qdf + i * fstride;
+#pragma unroll
+        for (int q = 0; q < MAXE; ++q)
+          if (addr[q] >= 0) dfc_nmac(a[q], r, dfc_load(qi + addr[q]));
+      }
+#pragma unroll
+      for (int q = 0; q < MAXE; ++q) a[q] = dfc_norm(a[q]);
+      norm2(a);
+      reduce(0, true);
+      after2 = df_to(red[MV - 1].re);
+      if (k == 0 || after2 >= 1e-4 * before2) break;  // uniform over the block
+    }
+    const double nrm = sqrt(after2);
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+      if (threadIdx.x == 0) *err = 1;
+    }
+    const dfr inv = df_from(nrm > 0.0 ? 1.0 / nrm : 0.0);
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q)
+      if (addr[q] >= 0) {
+        const dfr re = df_mul(a[q].re, inv), im = df_mul(a[q].im, inv);
+        vecs[k * fstride + addr[q]] = make_double2(df_to(re), df_to(im));
+        qdf[k * fstride + addr[q]] = make_float4(re.h, re.l, im.h, im.l);
+      }
+    __syncthreads();
+  }
+}
+
+void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
+                           cudaStream_t st) {
+  const int nelem = bvol * (nc / 2);
+  if (nvec > 32) throw Error(-1, "block orthonormalisation supports nvec <= 32");
+  if (nelem > 256 * 8) throw Error(-1, "aggregate too large for block orthonormalisation");
+  const dim3 grid(Vf / bvol, 2);
+  if (nelem <= 256 * 2) k_block_ortho_df<2><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+  else if (nelem <= 256 * 4) k_block_ortho_df<4><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+  else if (nelem <= 256 * 6) k_block_ortho_df<6><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+  else k_block_ortho_df<8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+  WCMG_LAUNCH_CHECK();
+}
+
 void launch_block_ortho(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st) {
   const int nelem = bvol * (nc / 2);
   if (nvec > 32) throw Error(-1, "block orthonormalisation supports nvec <= 32");

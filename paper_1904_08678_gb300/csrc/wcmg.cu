@@ -146,6 +146,8 @@ struct Level {
   DevBuf<double2> L64;
   DevBuf<float2> L32;
   DevBuf<bf16c> Lbf;
+  DevBuf<bf16c> Lmma;  // BF16 links in the tcgen05 operand order (kind-4 coarse apply)
+  bool mma_valid = false;
   DevBuf<f16c> Lh;
   bool L32_valid = false, low_valid = false;
   LevelScalars sc;
@@ -373,6 +375,34 @@ template <> struct Prec<float> {
 
 static double sz(int prec) { return prec == WCMG_F64 ? 16.0 : prec == WCMG_F32 ? 8.0 : 4.0; }
 
+// The kind-4 (tcgen05, bulk-copy) coarse apply reads the BF16 links in the MMA's
+// operand order: refreshed with every new BF16 copy of a level's links.
+static void build_mma_links(wcmg_ctx* c, int l) {
+  Level& L = c->L[l];
+  L.mma_valid = false;
+  if (L.nc % 8 || L.nc > 64) return;
+  L.Lmma.ensure((size_t)L.g.V * L.nc * 9 * L.nc);
+  launch_links_to_mma(L.Lmma.p, L.Lbf.p, L.g.V, L.nc, c->st);
+  L.mma_valid = true;
+}
+
+// Operands of the kind-4 apply for nrhs rhs at level l (BF16 links only): the MMA copy
+// of the links and a workspace large enough for any rhs tile.
+struct MmaOps {
+  const bf16c* lmma = nullptr;
+  void* scratch = nullptr;
+  size_t bytes = 0;
+};
+static MmaOps mma_ops(wcmg_ctx* c, int l, int nrhs, int lk) {
+  Level& L = c->L[l];
+  MmaOps m;
+  if (lk != 2 || nrhs < 2 || !L.mma_valid) return m;
+  m.lmma = L.Lmma.p;
+  m.scratch = ws<float>(L, "mma_b", nrhs + 63);
+  m.bytes = coarse_mma4_scratch_bytes(L.g.V, L.nc, nrhs);
+  return m;
+}
+
 // ---------------- coarse-apply autotuner ----------------
 // Candidate launch shapes of the full nine-point coarse apply (K4 / K4m).
 static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
@@ -391,6 +421,15 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
       for (int cr : {8, 16})
         for (int stg : {3, 4, 6}) add(3, 0, cr, th, 0, stg);
     return v;
+  }
+  if (lk == 2) {  // tcgen05 fed by bulk copies: MMA M, rhs tile, pipeline depth
+    const int full = std::min(64, (nrhs + 7) / 8 * 8);
+    std::vector<int> nts;
+    for (int nt : {16, 32, full})
+      if (nt <= full && std::find(nts.begin(), nts.end(), nt) == nts.end()) nts.push_back(nt);
+    for (int mm : {64, 128})
+      for (int nt : nts)
+        for (int stg : {4, 6}) add(4, 0, 0, mm, nt, stg);
   }
   for (int rr : {1, 4, 8})
     if (rr <= nrhs || rr == 4)
@@ -419,15 +458,19 @@ static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs
   WCMG_CUDA(cudaEventCreate(&e0));
   WCMG_CUDA(cudaEventCreate(&e1));
   const int reps = 10;
+  const MmaOps mo = mma_ops(c, l, nrhs, lk);
+  auto launch = [&](const CoarseTile* t) {
+    launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t, mo.lmma,
+                               mo.scratch, mo.bytes);
+  };
   auto time_one = [&](const CoarseTile* t) -> double {
-    for (int i = 0; i < 2; ++i)
-      launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
+    for (int i = 0; i < 2; ++i) launch(t);
     if (cold) {
       std::vector<float> ms(9);
       for (int i = 0; i < 9; ++i) {
         WCMG_CUDA(cudaMemsetAsync(c->l2flush.p, i & 0xFF, flush_bytes, c->st));
         WCMG_CUDA(cudaEventRecord(e0, c->st));
-        launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
+        launch(t);
         WCMG_CUDA(cudaEventRecord(e1, c->st));
         WCMG_CUDA(cudaEventSynchronize(e1));
         WCMG_CUDA(cudaEventElapsedTime(&ms[i], e0, e1));
@@ -436,8 +479,7 @@ static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs
       return 1e3 * ms[4];
     }
     WCMG_CUDA(cudaEventRecord(e0, c->st));
-    for (int i = 0; i < reps; ++i)
-      launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t);
+    for (int i = 0; i < reps; ++i) launch(t);
     WCMG_CUDA(cudaEventRecord(e1, c->st));
     WCMG_CUDA(cudaEventSynchronize(e1));
     float ms = 0.0f;
@@ -512,9 +554,10 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
   if (mode == ST_FULL && L.low_valid && (lp == WCMG_BF16 || lp == WCMG_F16)) {
     if (lp == WCMG_BF16) {
       const CoarseTile* t = coarse_tile<float, bf16c>(c, l, L.Lbf.p, nrhs, 2);
+      const MmaOps mo = mma_ops(c, l, nrhs, 2);
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
             (launch_coarse_apply<float, bf16c>((float2*)out, (const float2*)in, L.Lbf.p, L.g.lg(), nb, nrhs, mode,
-                                               hopdir, c->st, c->tma_err.p, t)));
+                                               hopdir, c->st, c->tma_err.p, t, mo.lmma, mo.scratch, mo.bytes)));
     } else {
       const CoarseTile* t = coarse_tile<float, f16c>(c, l, L.Lh.p, nrhs, 3);
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
@@ -1167,6 +1210,7 @@ static void coarsen_body(wcmg_ctx* c, int l) {
     if (c->p.coarse_link_prec == WCMG_BF16) {
       C.Lbf.ensure(nl);
       launch_convert_links<float2, bf16c>(C.Lbf.p, C.L32.p, nl, c->st);
+      build_mma_links(c, l + 1);
     } else {
       C.Lh.ensure(nl);
       launch_convert_links<float2, f16c>(C.Lh.p, C.L32.p, nl, c->st);
@@ -1198,8 +1242,14 @@ static void build_P(wcmg_ctx* c, int l) {
   const double V = L.g.V;
   // algorithmic work: one Gram-Schmidt pass, nvec (nvec - 1) complex MAC per panel row
   // (dots + updates); a second pass, when the cancellation test asks for it, is extra.
-  KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0, 8.0 * n * (L.nvec - 1),
-        launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
+  if (c->p.ortho_df) {
+    float4* qdf = reinterpret_cast<float4*>(ws<double>(L, "ortho_qdf", L.nvec));
+    KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0, 8.0 * n * (L.nvec - 1),
+          launch_block_ortho_df(L.v64.p, qdf, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
+  } else {
+    KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0, 8.0 * n * (L.nvec - 1),
+          launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
+  }
   (void)V;
   const int* e = read_ints(c, c->errflag.p, 1);
   if (e[0]) throw Error(WCMG_ERR_NAN, "rank-deficient aggregate in block orthonormalisation");
@@ -1819,6 +1869,7 @@ int wcmg_default_params(wcmg_params* p) {
   p->kcycle_tol = 0.1;
   p->sap_cycles = 1;
   p->sap_eo = 0;
+  p->ortho_df = 0;
   return WCMG_OK;
 }
 
@@ -1844,6 +1895,7 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       throw Error(WCMG_ERR_ARG, "smoother must be WCMG_SMOOTHER_MR, WCMG_SMOOTHER_GMRES or WCMG_SMOOTHER_SAP");
     if (p->sap_cycles < 1 || p->sap_cycles > 16) throw Error(WCMG_ERR_ARG, "sap_cycles must be 1..16");
     if (p->sap_eo != 0 && p->sap_eo != 1) throw Error(WCMG_ERR_ARG, "sap_eo must be 0 or 1");
+    if (p->ortho_df != 0 && p->ortho_df != 1) throw Error(WCMG_ERR_ARG, "ortho_df must be 0 or 1");
     if (p->sap_eo) {
       const int* fb = p->block[0];
       const int bv = fb[0] * fb[1] * fb[2] * fb[3];
@@ -2174,6 +2226,7 @@ int wcmg_set_coarse_links(wcmg_ctx* c, int level, const void* A, int where, void
     if (c->p.coarse_link_prec == WCMG_BF16) {
       L.Lbf.ensure(nl);
       launch_convert_links<double2, bf16c>(L.Lbf.p, L.L64.p, nl, c->st);
+      build_mma_links(c, level);
       L.low_valid = true;
     } else if (c->p.coarse_link_prec == WCMG_F16) {
       L.Lh.ensure(nl);

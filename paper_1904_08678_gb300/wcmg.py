@@ -69,6 +69,7 @@ class wcmg_params(ctypes.Structure):
         ("kcycle_tol", ctypes.c_double),
         ("sap_cycles", ctypes.c_int),
         ("sap_eo", ctypes.c_int),
+        ("ortho_df", ctypes.c_int),
     ]
 
 

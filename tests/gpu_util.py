@@ -13,6 +13,12 @@ def host(t):
     return t.cpu().numpy()
 
 
+def rel_norm(a, b):
+    """The 2-norm ratio ||a - b|| / ||b|| alone (for claims stated in that norm)."""
+    a = np.asarray(a); b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
 def residual(Dx, b):
     """True relative residual ||b - D x|| / ||b|| (2-norm over the whole field): the
     stopping test of the solver, checked with the oracle's D."""

@@ -10,7 +10,7 @@ from oracle.mg import MGParams, Multigrid
 from oracle.solvers import gmres, mr
 from oracle.wilson import WilsonClover
 from paper_1904_08678_gb300 import inputs
-from tests.gpu_util import dev, fields, host, rel, residual
+from tests.gpu_util import dev, fields, host, rel, rel_norm, residual
 
 pytestmark = pytest.mark.gpu
 
@@ -81,8 +81,9 @@ def oracle_mg(D, iv, **kw):
     return Multigrid(D, MGParams(blocks=[BLOCK], nvecs=[NVEC], **kw), [fields(iv, DIMS, 12)])
 
 
-def test_setup_and_cycle_match_oracle(lib):
-    ctx, D = config1_ctx(lib)
+@pytest.mark.parametrize("ortho_df", [0, 1], ids=["fp64_ortho", "double_float_ortho"])
+def test_setup_and_cycle_match_oracle(lib, ortho_df):
+    ctx, D = config1_ctx(lib, ortho_df=ortho_df)
     iv = inputs.setup_vectors(DIMS, 12, NVEC, 0, 1001)
     ctx.setup(dev(iv))
     mg = oracle_mg(D, iv)
@@ -101,8 +102,9 @@ def test_setup_and_cycle_match_oracle(lib):
     assert rel(host(e)[0], ref.reshape(V, 12)) < 1e-9
 
 
-def test_setup_with_refinement_matches_oracle(lib):
-    ctx, D = config1_ctx(lib, setup_refine_sweeps=2)
+@pytest.mark.parametrize("ortho_df", [0, 1], ids=["fp64_ortho", "double_float_ortho"])
+def test_setup_with_refinement_matches_oracle(lib, ortho_df):
+    ctx, D = config1_ctx(lib, setup_refine_sweeps=2, ortho_df=ortho_df)
     iv = inputs.setup_vectors(DIMS, 12, NVEC, 0, 1001)
     ctx.setup(dev(iv))
     mg = oracle_mg(D, iv, refine_sweeps=2)
@@ -252,7 +254,9 @@ def test_seeded_setup_draws_the_fields_of_the_input_generator(lib):
     generator of the test inputs (exact uniforms, FP32 Box-Muller transform): with no
     smoothing sweeps P is the block-orthonormalised random vectors, equal to those of the
     host-generated (FP64-transformed) fields to FP32 rounding, on both levels; with setup
-    sweeps they still agree to that order."""
+    sweeps they still agree to that order.  Compared in the 2-norm: element-wise, FP32
+    evaluation of log(1 - u) for tiny u leaves samples of small radius an absolute error of
+    ~1e-5, up to 4e-5 of the largest entry."""
     dims = (8, 8, 8, 8)
     kw = dict(dims=dims, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvec=[6, 4], n_levels=3, m0=-0.1, csw=1.0)
     U = inputs.random_gauge(dims, 0.3, 1401)
@@ -272,4 +276,4 @@ def test_seeded_setup_draws_the_fields_of_the_input_generator(lib):
             ctx.get_nullvecs(0, P0)
             ctx.get_nullvecs(1, P1)
             P.append((host(P0), host(P1)))
-        assert rel(P[1][0], P[0][0]) < tol and rel(P[1][1], P[0][1]) < tol
+        assert rel_norm(P[1][0], P[0][0]) < tol and rel_norm(P[1][1], P[0][1]) < tol

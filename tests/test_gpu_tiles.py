@@ -24,6 +24,14 @@ def stream_fits(lk, nb, rows, stages):
     return r128(ld * vb) + stages * r128(rows * ld * lb) <= 200 * 1024
 
 
+def mma4_fits(nb, ntile, mm, stages):
+    """Shared memory of the bulk-copy tensor-core kernel (kind 4) within its 220 KiB limit."""
+    r1k = lambda x: (x + 1023) // 1024 * 1024
+    a = r1k(nb // 4 * nb * 16 + max(mm - nb, 0) * 16)
+    b = r1k(nb // 4 * 2 * ntile * 16)
+    return stages * (a + b) <= 220 * 1024
+
+
 def candidate_tiles(nrhs, lk, nb):
     """Shapes the library's autotuner times, plus extreme valid ones."""
     t = []
@@ -41,6 +49,10 @@ def candidate_tiles(nrhs, lk, nb):
               for p in (0, 1, 2, 4, 8, 16)]
         if lk == "bf16":
             t += [dict(kind=2, ntile=n) for n in (16, 32, 48, 64) if n <= (nrhs + 15) // 16 * 16]
+            # bulk-copy tensor cores: both MMA heights, rhs tiles from 8 (many tiles, a
+            # ragged last one) to 64, shallow and deep pipelines
+            t += [dict(kind=4, threads=mm, ntile=n, stages=st) for mm in (64, 128) for n in (8, 16, 40, 64)
+                  for st in (2, 4, 6) if n <= max(8, (nrhs + 7) // 8 * 8) and mma4_fits(nb, n, mm, st)]
     return t
 
 
@@ -61,7 +73,7 @@ def int_phi(rng, nrhs, Vc, nb):
     return (rng.integers(-2, 3, size=(nrhs, Vc, nb)) + 1j * rng.integers(-2, 3, size=(nrhs, Vc, nb))).astype(complex)
 
 
-CASES = [("f64", 1), ("f64", 5), ("f32", 1), ("f32", 6), ("bf16", 1), ("bf16", 37), ("f16", 3)]
+CASES = [("f64", 1), ("f64", 5), ("f32", 1), ("f32", 6), ("bf16", 1), ("bf16", 8), ("bf16", 37), ("f16", 3)]
 
 
 @pytest.mark.parametrize("lk,nrhs", CASES)
@@ -132,6 +144,7 @@ def test_invalid_tiles_are_rejected(lib):
            (1, dict(kind=3, threads=96, parts=8, stages=4)),    # 128, 256 or 512 threads
            (4, dict(kind=3, threads=256, parts=8, stages=4)),   # one rhs only
            (1, dict(kind=3, threads=256, parts=48, stages=8)),  # beyond the shared-memory limit
+           (8, dict(kind=4, threads=128, ntile=16, stages=4)),  # tensor cores need BF16 links
            (1, dict(kind=7))]
     for nrhs, t in bad:
         with pytest.raises(lib.WcmgError) as e:
