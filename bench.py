@@ -268,6 +268,7 @@ def make_inputs(cfg, nrhs=None):
 
 def params(wcmg, cfg, inner, links=None, profile=0, graphs=0, autotune=1, nrhs=None):
     links = links or cfg.get("links", "f32")
+    ortho_df = int(cfg.get("ortho", "fp64") == "df")
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
                             n_levels=len(cfg["blocks"]) + 1, max_rhs=nrhs or cfg.get("nrhs", 1), profile=profile,
@@ -276,7 +277,7 @@ def params(wcmg, cfg, inner, links=None, profile=0, graphs=0, autotune=1, nrhs=N
                                       "sap": wcmg.SMOOTHER_SAP}[cfg.get("smoother", "mr")],
                             sap_cycles=int(cfg.get("sap_cycles", 1)), sap_eo=int(cfg.get("sap_eo", 0)),
                             smoother_steps=int(cfg.get("smoother_steps", 4)),
-                            kcycle=int(cfg.get("kcycle", 0)))
+                            kcycle=int(cfg.get("kcycle", 0)), ortho_df=ortho_df)
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -504,6 +505,7 @@ def run_gpu(args, rank, world, local):
     cfg = dict(WORKLOADS[name])
     if args.links:
         cfg["links"] = args.links
+    cfg["ortho"] = args.ortho
     if args.kcycle:
         cfg["kcycle"] = 1
         cfg["workload"] = cfg["workload"] + ", K-cycle (FGMRES(5) to 0.1 on the intermediate levels)"
@@ -1079,6 +1081,59 @@ def run_table2(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_probe(args, local):
+    """One kernel family of the workload, isolated, for an ncu capture on a small case:
+    'ortho' runs wcmg_set_nullvecs on the fine level (its FP64 or double-float block
+    orthonormalisation) 3 times; 'coarse:L:N' runs one setup, then 5 coarse applies of level
+    L with N rhs (the autotuned launch shape)."""
+    import torch
+    torch.cuda.set_device(local)
+    env = Env(local, None)
+    torch_, wcmg, stream = env.torch, env.wcmg, env.stream
+    cfg = dict(WORKLOADS[args.workload])
+    if args.links:
+        cfg["links"] = args.links
+    cfg["ortho"] = args.ortho
+    from paper_1904_08678_gb300 import inputs
+    ld = level_dims(cfg)
+    out = {"probe": args.probe, "workload": cfg["workload"], "ortho": args.ortho}
+    if args.probe == "ortho":
+        nv = cfg["nvec"][0]
+        ctx = wcmg.Context(params(wcmg, cfg, "f32", profile=1 << KCLASS.index("ortho"), nrhs=1))
+        V = int(np.prod(ld[0]))
+        vecs = env.to_dev(inputs.complex_gaussian(31, 0, (nv, V, 12)))
+        ms = [timed_call(torch_, stream, env.flush, lambda: ctx.set_nullvecs(0, vecs, stream), i)[1] for i in range(3)]
+        k = ctx.kstats()["ortho"]
+        out.update(ms_per_call=[round(t, 3) for t in ms], kernel_ms=round(k["ms"] / max(k["launches"], 1), 3),
+                   gflop_per_launch=round(k["flops"] / max(k["launches"], 1) / 1e9, 2))
+    else:
+        _, lev, nr = args.probe.split(":")
+        lev, nr = int(lev), int(nr)
+        U, b = make_inputs(cfg, 1)
+        ctx = wcmg.Context(params(wcmg, cfg, "f32", profile=0, autotune=1, nrhs=max(nr, 1)))
+        ctx.set_gauge(env.to_dev(U), stream)
+        ctx.setup_seeded(cfg["gauge_seed"], stream)
+        Vc, nb = int(np.prod(ld[lev])), 2 * cfg["nvec"][lev - 1]
+        phi = env.to_dev(inputs.complex_gaussian(32, 0, (nr, Vc, nb)))
+        y = torch_.zeros_like(phi)
+        ctx.apply_coarse(lev, phi, y, nrhs=nr, prec=wcmg.F32, stream=stream)  # autotune
+        ctx.set_profile(1 << KCLASS.index("coarse"))
+        k0 = ctx.kstats()["coarse"]
+        ms = [timed_call(torch_, stream, env.flush,
+                         lambda: ctx.apply_coarse(lev, phi, y, nrhs=nr, prec=wcmg.F32, stream=stream), i)[1]
+              for i in range(5)]
+        k1 = ctx.kstats()["coarse"]
+        n = max(k1["launches"] - k0["launches"], 1)
+        kus = (k1["ms"] - k0["ms"]) / n * 1e3
+        lb = {"f32": 8, "bf16": 4, "f16": 4}[cfg.get("links", "f32")]
+        algo = Vc * (9 * nb * nb * lb + 2 * nb * 8 * nr)
+        out.update(level=lev, nrhs=nr, tile=ctx.get_coarse_tile(lev, nr, wcmg.F32), ms_per_call=[round(t, 3) for t in ms],
+                   kernel_us=round(kus, 2), algorithmic_bytes=algo,
+                   frac_of_hbm=round(algo / (kus * 1e-6) / 1e9 / peaks()[0], 4))
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1107,6 +1162,12 @@ def main(argv=None):
     ap.add_argument("--sap-eo", action="store_true", help="SAP: even-odd preconditioned block solves (fine level)")
     ap.add_argument("--pools", type=int, default=417,
                     help="c5: training pools of 48 fresh pairs (417 pools = 20016 pairs)")
+    ap.add_argument("--ortho", default="fp64", choices=["fp64", "df"],
+                    help="block orthonormalisation arithmetic: FP64, or double-float on the FP32 pipe")
+    ap.add_argument("--probe", default=None,
+                    help="kernel probe for ncu instead of the bench: 'ortho' (the fine-level block "
+                         "orthonormalisation of Nvec Gaussian fields, 3 times) or 'coarse:LEVEL:NRHS' (5 coarse "
+                         "applies after one setup); prints one JSON line of CUDA-event times")
     ap.add_argument("--ncu-region", action="store_true",
                     help="bracket the timed steps of the headline workload with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -1114,7 +1175,9 @@ def main(argv=None):
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank, world, local = dist_env()
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args, local)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     elif args.workload == "table2":
         run_table2(args, rank, world, local)

@@ -46,6 +46,20 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
   const int row0 = part * rpc, row1 = min(nb, row0 + rpc);
   const int r0 = blockIdx.y * RR;
   const int K = 9 * nb;
+  // link blocks this site needs: all nine for the full stencil; the self block and the
+  // hops that stay inside the aggregate for the block interior; for a face hop only the
+  // crossing block, and only on the face (a site off the face contributes nothing and
+  // its output is never read: the face restriction reads face sites only)
+  unsigned dmask = 0x1FFu;
+  if (mode == ST_BLOCK_INTERIOR) {
+    dmask = 1u;
+    for (int d = 1; d < 9; ++d)
+      if (!c_on_face(bi, site, d - 1)) dmask |= 1u << d;
+  } else if (mode == ST_FACE_HOP) {
+    dmask = c_on_face(bi, site, hopdir) ? 1u << (hopdir + 1) : 0u;
+  }
+  if (dmask == 0u) return;  // uniform over the CTA
+  const bool blockwise = mode != ST_FULL && nb % VEC == 0;
   for (int idx = threadIdx.x; idx < RR * ld; idx += blockDim.x) {
     const int r = idx / ld, k = idx % ld;
     T v = czero<R>();
@@ -68,14 +82,29 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
     T acc[RR];
 #pragma unroll
     for (int r = 0; r < RR; ++r) acc[r] = czero<R>();
+    if (blockwise) {  // stream only the needed blocks of the row
+      for (int d = 0; d < 9; ++d) {
+        if (!((dmask >> d) & 1u)) continue;
+        for (int k0 = d * nb + lane * VEC; k0 < (d + 1) * nb; k0 += 32 * VEC) {
+          const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + k0);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const T a = link_load<L, R>(lv.v[v]);
+#pragma unroll
+            for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + k0 + v]);
+          }
+        }
+      }
+    } else {
 #pragma unroll 4
-    for (int k0 = lane * VEC; k0 < ld; k0 += 32 * VEC) {
-      const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + k0);
+      for (int k0 = lane * VEC; k0 < ld; k0 += 32 * VEC) {
+        const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + k0);
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) {
-        const T a = link_load<L, R>(lv.v[v]);
+        for (int v = 0; v < VEC; ++v) {
+          const T a = link_load<L, R>(lv.v[v]);
 #pragma unroll
-        for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + k0 + v]);
+          for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + k0 + v]);
+        }
       }
     }
 #pragma unroll
@@ -162,75 +191,95 @@ __global__ void __launch_bounds__(512) k_coarse_apply1_stream(cplx<R>* __restric
                                                               int* __restrict__ err) {
   using T = cplx<R>;
   constexpr int VEC = 16 / sizeof(L);
+  constexpr int PF = 4;  // gathered entries per thread kept in registers for the next site (ld <= PF x threads)
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[STREAM_MAX_STAGES];
-  T* phi = reinterpret_cast<T*>(smem);  // [ld]: the nine gathered neighbour vectors, zero padded
   const int phi_bytes = (ld * (int)sizeof(T) + 127) / 128 * 128;
+  T* phi[2] = {reinterpret_cast<T*>(smem), reinterpret_cast<T*>(smem + phi_bytes)};  // [ld] each, zero padded
   const int stage_bytes = (cr * ld * (int)sizeof(L) + 127) / 128 * 128;
-  unsigned char* stage0 = smem + phi_bytes;
+  unsigned char* stage0 = smem + 2 * phi_bytes;
   const int cps = (nb + cr - 1) / cr;  // chunks per site
-  const long long items = (long long)Vc * cps;
-  const long long nmine = items > blockIdx.x ? (items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // this CTA's sites: blockIdx.x + k gridDim.x; chunk q = k cps + c of them
+  const long long nsites = Vc > (int)blockIdx.x ? (Vc - 1 - (int)blockIdx.x) / gridDim.x + 1 : 0;
+  const long long nq = nsites * cps;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
     for (int q = 0; q < stages; ++q) mbar_init(&full[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](long long k) {
-    const long long it = blockIdx.x + k * gridDim.x;
-    const int site = (int)(it / cps), r0 = (int)(it % cps) * cr;
+  auto issue = [&](long long q) {
+    const int site = (int)(blockIdx.x + (q / cps) * gridDim.x), r0 = (int)(q % cps) * cr;
     const int rows = min(cr, nb - r0);
     const uint32_t bytes = (uint32_t)rows * ld * sizeof(L);
-    uint64_t* bar = &full[k % stages];
+    uint64_t* bar = &full[q % stages];
     mbar_expect_tx(bar, bytes);
-    tma_load_1d(stage0 + (k % stages) * stage_bytes, links + ((long long)site * nb + r0) * ld, bytes, bar);
+    tma_load_1d(stage0 + (q % stages) * stage_bytes, links + ((long long)site * nb + r0) * ld, bytes, bar);
+  };
+  auto gather = [&](int site, T (&v)[PF]) {
+#pragma unroll
+    for (int p = 0; p < PF; ++p) {
+      const int i = threadIdx.x + p * blockDim.x;
+      v[p] = czero<R>();
+      if (i < 9 * nb) {
+        const int d = i / nb, c = i - d * nb;
+        v[p] = in[(long long)(d == 0 ? site : nbr[(d - 1) * Vc + site]) * nb + c];
+      }
+    }
+  };
+  auto store = [&](T* dst, const T (&v)[PF]) {
+#pragma unroll
+    for (int p = 0; p < PF; ++p) {
+      const int i = threadIdx.x + p * blockDim.x;
+      if (i < ld) dst[i] = v[p];
+    }
   };
   if (threadIdx.x == 0)
-    for (long long k = 0; k < stages && k < nmine; ++k) issue(k);
-  int cur = -1;
-  long long k = 0;
+    for (long long q = 0; q < stages && q < nq; ++q) issue(q);
+  T pf[PF];
+  if (nsites > 0) {
+    gather((int)blockIdx.x, pf);
+    store(phi[0], pf);
+  }
+  __syncthreads();
+  long long q = 0;
   bool ok = true;
-  for (; k < nmine; ++k) {
-    const long long it = blockIdx.x + k * gridDim.x;
-    const int site = (int)(it / cps), r0 = (int)(it % cps) * cr;
-    const int rows = min(cr, nb - r0);
-    if (site != cur) {  // uniform over the CTA; the previous item's barrier ended every read of phi
-      for (int i = threadIdx.x; i < ld; i += blockDim.x) {
-        T v = czero<R>();
-        if (i < 9 * nb) {
-          const int d = i / nb, c = i - d * nb;
-          v = in[(long long)(d == 0 ? site : nbr[(d - 1) * Vc + site]) * nb + c];
-        }
-        phi[i] = v;
+  for (long long k = 0; k < nsites && ok; ++k) {
+    const int site = (int)(blockIdx.x + k * gridDim.x);
+    const T* ph = phi[k & 1];
+    if (k + 1 < nsites) gather((int)(blockIdx.x + (k + 1) * gridDim.x), pf);  // in flight during this site
+    for (int c = 0; c < cps; ++c, ++q) {
+      const int r0 = c * cr, rows = min(cr, nb - r0);
+      const int s = (int)(q % stages);
+      const int good = mbar_wait_bounded(&full[s], (uint32_t)((q / stages) & 1)) ? 1 : 0;
+      if (!__syncthreads_and(good)) {
+        ok = false;
+        break;
       }
-      cur = site;
-    }
-    const int s = (int)(k % stages);
-    const int good = mbar_wait_bounded(&full[s], (uint32_t)((k / stages) & 1)) ? 1 : 0;
-    if (!__syncthreads_and(good)) {
-      ok = false;
-      break;
-    }
-    const L* chunk = reinterpret_cast<const L*>(stage0 + s * stage_bytes);
-    for (int row = warp; row < rows; row += nw) {
-      const L* lr = chunk + row * ld;
-      T acc = czero<R>();
-      for (int g = lane; g * VEC < ld; g += 32) {
-        const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + g * VEC);
+      const L* chunk = reinterpret_cast<const L*>(stage0 + s * stage_bytes);
+      for (int row = warp; row < rows; row += nw) {
+        const L* lr = chunk + row * ld;
+        T acc = czero<R>();
+        for (int g = lane; g * VEC < ld; g += 32) {
+          const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + g * VEC);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(lv.v[v]), phi[g * VEC + v]);
+          for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(lv.v[v]), ph[g * VEC + v]);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) out[(long long)site * nb + r0 + row] = acc;
       }
-      acc = warp_sum(acc);
-      if (lane == 0) out[(long long)site * nb + r0 + row] = acc;
+      __syncthreads();  // stage s consumed
+      if (threadIdx.x == 0 && q + stages < nq) issue(q + stages);
     }
-    __syncthreads();  // stage s consumed
-    if (threadIdx.x == 0 && k + stages < nmine) issue(k + stages);
+    if (ok && k + 1 < nsites) {
+      store(phi[(k + 1) & 1], pf);
+      __syncthreads();
+    }
   }
   if (!ok && threadIdx.x == 0) {
     atomicExch(err, 3);
-    for (long long q = k; q < k + stages && q < nmine; ++q)  // copies still in flight
-      mbar_wait_bounded(&full[q % stages], (uint32_t)((q / stages) & 1));
+    for (long long r = q; r < q + stages && r < nq; ++r)  // copies still in flight
+      mbar_wait_bounded(&full[r % stages], (uint32_t)((r / stages) & 1));
   }
 }
 
@@ -658,7 +707,7 @@ static int sm_count() {
 
 size_t coarse_stream_smem(int nb, int cr, int stages, int vec_bytes, int link_bytes) {
   const int ld = links_ld(nb);
-  return (size_t)(ld * vec_bytes + 127) / 128 * 128 + (size_t)stages * ((cr * ld * link_bytes + 127) / 128 * 128);
+  return 2 * ((size_t)(ld * vec_bytes + 127) / 128 * 128) + (size_t)stages * ((cr * ld * link_bytes + 127) / 128 * 128);
 }
 
 template <typename R, typename L>
@@ -671,8 +720,8 @@ static void coarse_apply1_stream(cplx<R>* out, const cplx<R>* in, const L* links
   int per_sm = 0;
   WCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
   if (per_sm < 1) throw Error(-1, "coarse apply: streaming tile does not fit on an SM");
-  const long long items = (long long)g.V * ((nb + cr - 1) / cr);
-  const int grid = (int)std::min<long long>(items, (long long)sm_count() * per_sm);
+  if (ld > 4 * threads) throw Error(-1, "coarse apply: streaming tile needs more threads for this nbasis");
+  const int grid = (int)std::min<long long>(g.V, (long long)sm_count() * per_sm);
   kern<<<grid, threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, cr, stages, err);
   WCMG_LAUNCH_CHECK();
 }
@@ -779,6 +828,7 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
       const int lb = link_kind == 0 ? 16 : link_kind == 1 ? 8 : 4;
       const int vb = link_kind == 0 ? 16 : 8;
       return nrhs == 1 && mode == ST_FULL && (t.threads == 128 || t.threads == 256 || t.threads == 512) &&
+             4 * t.threads >= links_ld(nb) &&
              t.parts >= 1 && t.parts <= nb && t.stages >= 2 && t.stages <= STREAM_MAX_STAGES &&
              coarse_stream_smem(nb, t.parts, t.stages, vb, lb) <= 200 * 1024;
     }

@@ -416,10 +416,9 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
     for (int th : {256, 512})
       for (int p : {1, 2, 4, 8}) add(0, 1, p, th, 0);
     for (int p : {1, 2, 4, 8, 16}) add(1, 1, p, 0, 0);
-    // streaming pipeline: chunks of 8 / 16 rows, 3 .. 6 in flight
-    for (int th : {256, 512})
-      for (int cr : {8, 16})
-        for (int stg : {3, 4, 6}) add(3, 0, cr, th, 0, stg);
+    // streaming pipeline: chunks of 8 rows up to a whole site, 2 .. 6 in flight
+    for (int cr : {8, 16, 24, nb})
+      for (int stg : {2, 3, 4, 6}) add(3, 0, cr, 256, 0, stg);
     return v;
   }
   if (lk == 2) {  // tcgen05 fed by bulk copies: MMA M, rhs tile, pipeline depth

@@ -21,7 +21,7 @@ def stream_fits(lk, nb, rows, stages):
     ld = (9 * nb + 3) // 4 * 4
     lb, vb = {"f64": (16, 16), "f32": (8, 8), "bf16": (4, 8), "f16": (4, 8)}[lk]
     r128 = lambda x: (x + 127) // 128 * 128
-    return r128(ld * vb) + stages * r128(rows * ld * lb) <= 200 * 1024
+    return 2 * r128(ld * vb) + stages * r128(rows * ld * lb) <= 200 * 1024
 
 
 def mma4_fits(nb, ntile, mm, stages):
@@ -43,7 +43,9 @@ def candidate_tiles(nrhs, lk, nb):
         # and the shallowest / deepest pipelines
         shapes = [(th, cr, st) for th in (256, 512) for cr in (8, 16) for st in (3, 4, 6)]
         shapes += [(128, 5, 2), (512, 3, 8), (256, 7, 5), (128, nb, 2)]
-        t += [dict(kind=3, threads=th, parts=cr, stages=st) for th, cr, st in shapes if stream_fits(lk, nb, cr, st)]
+        ld = (9 * nb + 3) // 4 * 4
+        t += [dict(kind=3, threads=th, parts=cr, stages=st) for th, cr, st in shapes
+              if stream_fits(lk, nb, cr, st) and 4 * th >= ld]
     else:
         t += [dict(kind=1, rhs_per_cta=rr, parts=p) for rr in (1, 4, 8) if rr <= nrhs or rr == 4
               for p in (0, 1, 2, 4, 8, 16)]
