@@ -1107,8 +1107,9 @@ def run_probe(args, local):
         out.update(ms_per_call=[round(t, 3) for t in ms], kernel_ms=round(k["ms"] / max(k["launches"], 1), 3),
                    gflop_per_launch=round(k["flops"] / max(k["launches"], 1) / 1e9, 2))
     else:
-        _, lev, nr = args.probe.split(":")
-        lev, nr = int(lev), int(nr)
+        fields_ = args.probe.split(":")
+        lev, nr = int(fields_[1]), int(fields_[2])
+        forced = [int(x) for x in fields_[3:]]  # optional kind:threads:parts:stages:ntile
         U, b = make_inputs(cfg, 1)
         ctx = wcmg.Context(params(wcmg, cfg, "f32", profile=0, autotune=1, nrhs=max(nr, 1)))
         ctx.set_gauge(env.to_dev(U), stream)
@@ -1116,7 +1117,10 @@ def run_probe(args, local):
         Vc, nb = int(np.prod(ld[lev])), 2 * cfg["nvec"][lev - 1]
         phi = env.to_dev(inputs.complex_gaussian(32, 0, (nr, Vc, nb)))
         y = torch_.zeros_like(phi)
-        ctx.apply_coarse(lev, phi, y, nrhs=nr, prec=wcmg.F32, stream=stream)  # autotune
+        if forced:
+            f = forced + [0] * (5 - len(forced))
+            ctx.set_coarse_tile(lev, nr, wcmg.F32, kind=f[0], threads=f[1], parts=f[2], stages=f[3], ntile=f[4])
+        ctx.apply_coarse(lev, phi, y, nrhs=nr, prec=wcmg.F32, stream=stream)  # autotune (unless forced)
         ctx.set_profile(1 << KCLASS.index("coarse"))
         k0 = ctx.kstats()["coarse"]
         ms = [timed_call(torch_, stream, env.flush,

@@ -564,12 +564,25 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
   if (warp == 0) {
     if (lane == 0) {
       long long c = 0;
+      // neighbour indices of the next item, loaded one item ahead so that no copy waits
+      // on a dependent global load
+      int ny[8];
+      auto load_nbr = [&](long long it) {
+        const int site = (int)(it / ntiles);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) ny[d] = it < items ? nbr[d * Vc + site] : 0;
+      };
+      load_nbr(blockIdx.x);
       for (long long it = blockIdx.x; it < items && !*(volatile int*)&abort_flag; it += gridDim.x) {
         const int site = (int)(it / ntiles), t = (int)(it % ntiles);
+        int cur[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) cur[d] = ny[d];
+        load_nbr(it + gridDim.x);
         for (int d = 0; d < 9; ++d, ++c) {
           const int s = (int)(c % stages);
           if (!mbar_wait_bounded(&empty[s], (uint32_t)(((c / stages) & 1) ^ 1), limit)) { fail(); break; }
-          const int y = d == 0 ? site : nbr[(d - 1) * Vc + site];
+          const int y = d == 0 ? site : cur[d - 1];
           unsigned char* st = smem + (size_t)s * stage_bytes;
           mbar_expect_tx(&full[s], a_bytes + b_bytes);
           tma_load_1d(st, amma + ((long long)site * 9 + d) * kg * nb, a_bytes, &full[s]);

@@ -1229,16 +1229,13 @@ static void coarsen(wcmg_ctx* c, int l) {
   coarsen_body<R>(c, l);
 }
 
-// P_l from the level's raw vectors at precision R: FP64 block orthonormalisation.
-template <typename R>
-static void build_P(wcmg_ctx* c, int l) {
+// Block orthonormalisation of L.v64 in place (Sec. 2.2: Q factor per aggregate and
+// chirality), in FP64 or, with params.ortho_df, in double-float arithmetic.
+static void ortho_level(wcmg_ctx* c, int l) {
   Level& L = c->L[l];
   const long long n = (long long)L.nvec * L.n();
-  L.v64.ensure(n);
-  launch_convert<R, double>(L.v64.p, Prec<R>::raw(L).p, n, c->st);
   WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
   c->opc[WCMG_OPC_ORTHO][l] += 1;
-  const double V = L.g.V;
   // algorithmic work: one Gram-Schmidt pass, nvec (nvec - 1) complex MAC per panel row
   // (dots + updates); a second pass, when the cancellation test asks for it, is extra.
   if (c->p.ortho_df) {
@@ -1249,9 +1246,18 @@ static void build_P(wcmg_ctx* c, int l) {
     KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0, 8.0 * n * (L.nvec - 1),
           launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
   }
-  (void)V;
   const int* e = read_ints(c, c->errflag.p, 1);
   if (e[0]) throw Error(WCMG_ERR_NAN, "rank-deficient aggregate in block orthonormalisation");
+}
+
+// P_l from the level's raw vectors at precision R.
+template <typename R>
+static void build_P(wcmg_ctx* c, int l) {
+  Level& L = c->L[l];
+  const long long n = (long long)L.nvec * L.n();
+  L.v64.ensure(n);
+  launch_convert<R, double>(L.v64.p, Prec<R>::raw(L).p, n, c->st);
+  ortho_level(c, l);
   L.v32_valid = false;
   L.have_P = true;
 }
@@ -2147,10 +2153,7 @@ int wcmg_set_nullvecs(wcmg_ctx* c, int level, const void* vecs, int where, void*
     // orthonormalise from the FP64 input directly
     L.v64.ensure((size_t)L.nvec * L.n());
     copy_fields<double>(c, L.v64.p, L.raw64.p, (long long)L.nvec * L.n());
-    WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
-    launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st);
-    const int* e = read_ints(c, c->errflag.p, 1);
-    if (e[0]) throw Error(WCMG_ERR_NAN, "rank-deficient aggregate in block orthonormalisation");
+    ortho_level(c, level);
     launch_convert<double, float>(L.raw32.p, L.raw64.p, (long long)L.nvec * L.n(), c->st);
     L.v32_valid = false;
     L.have_P = true;
