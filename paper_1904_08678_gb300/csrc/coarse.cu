@@ -31,6 +31,14 @@ __device__ __forceinline__ bool c_on_face(const BlockInfoC& bi, int s, int d) {
 
 template <typename L, int VEC> struct alignas(16) LinkVec { L v[VEC]; };
 
+// The gathered neighbour vectors sit in shared memory "transposed" by 16-byte link
+// chunk: entry k = VEC g + v at v (ld / VEC) + g.  A lane that multiplies the VEC
+// entries of link chunk g then reads, for each v, the word next to its neighbour
+// lane's (no bank conflicts); in plain order the lanes' reads would be VEC entries
+// apart, a VEC-way conflict for FP32 vectors and BF16 links.
+template <int VEC>
+__device__ __forceinline__ int phi_slot(int k, int ld) { return (k % VEC) * (ld / VEC) + k / VEC; }
+
 template <typename R, typename L, int RR, int VEC>
 __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
                                                       const L* __restrict__ links, const int* __restrict__ nbr,
@@ -73,10 +81,11 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
         v = in[((long long)(r0 + r) * Vc + n) * nb + c];
       }
     }
-    phi[idx] = v;
+    phi[(idx / ld) * ld + phi_slot<VEC>(idx % ld, ld)] = v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = ld / VEC;
   for (int row = row0 + warp; row < row1; row += nw) {
     const L* lr = links + ((long long)site * nb + row) * ld;
     T acc[RR];
@@ -91,7 +100,7 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
           for (int v = 0; v < VEC; ++v) {
             const T a = link_load<L, R>(lv.v[v]);
 #pragma unroll
-            for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + k0 + v]);
+            for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + v * G + k0 / VEC]);
           }
         }
       }
@@ -103,7 +112,7 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
         for (int v = 0; v < VEC; ++v) {
           const T a = link_load<L, R>(lv.v[v]);
 #pragma unroll
-          for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + k0 + v]);
+          for (int r = 0; r < RR; ++r) cmac(acc[r], a, phi[r * ld + v * G + k0 / VEC]);
         }
       }
     }
@@ -147,9 +156,10 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
       const int n = d == 0 ? site : nbr[(d - 1) * Vc + site];
       v = in[(long long)n * nb + c];
     }
-    phi[idx] = v;
+    phi[phi_slot<VEC>(idx, ld)] = v;
   }
   __syncthreads();
+  const int G = ld / VEC;
   for (; row < row1; row += nw) {
     if (row != row0 + warp) {
 #pragma unroll
@@ -164,7 +174,7 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
       const int k0 = VEC * (lane + 32 * j);
       if (k0 < ld) {
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(cur[j].v[v]), phi[k0 + v]);
+        for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(cur[j].v[v]), phi[v * G + k0 / VEC]);
       }
     }
     acc = warp_sum(acc);
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(512) k_coarse_apply1_stream(cplx<R>* __restric
 #pragma unroll
     for (int p = 0; p < PF; ++p) {
       const int i = threadIdx.x + p * blockDim.x;
-      if (i < ld) dst[i] = v[p];
+      if (i < ld) dst[phi_slot<VEC>(i, ld)] = v[p];
     }
   };
   if (threadIdx.x == 0)
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(512) k_coarse_apply1_stream(cplx<R>* __restric
         for (int g = lane; g * VEC < ld; g += 32) {
           const LinkVec<L, VEC> lv = *reinterpret_cast<const LinkVec<L, VEC>*>(lr + g * VEC);
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(lv.v[v]), ph[g * VEC + v]);
+          for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(lv.v[v]), ph[v * (ld / VEC) + g]);
         }
         acc = warp_sum(acc);
         if (lane == 0) out[(long long)site * nb + r0 + row] = acc;
@@ -782,8 +792,12 @@ static void coarse_apply_mma4(float2* out, const float2* in, const bf16c* lmma, 
   const size_t smem = coarse_mma4_smem(nb, t.ntile, t.threads, t.stages);
   auto kern = t.threads == 64 ? k_coarse_apply_mma4<64> : k_coarse_apply_mma4<128>;
   WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // CTAs per SM as shared memory allows, at most 2: each holds 256 of the SM's 512 TMEM columns
+  int per_sm = 0;
+  WCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, smem));
+  per_sm = std::max(1, std::min(per_sm, 2));
   const long long items = (long long)g.V * ntiles;
-  const int grid = (int)std::min<long long>(items, sm_count());
+  const int grid = (int)std::min<long long>(items, (long long)sm_count() * per_sm);
   kern<<<grid, 192, smem, st>>>(out, reinterpret_cast<const uint4*>(lmma), bp, g.nbr, g.V, nb, nrhs, t.ntile, ntiles,
                                 t.stages, err);
   WCMG_LAUNCH_CHECK();

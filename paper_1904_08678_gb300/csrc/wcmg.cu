@@ -428,7 +428,7 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
       if (nt <= full && std::find(nts.begin(), nts.end(), nt) == nts.end()) nts.push_back(nt);
     for (int mm : {64, 128})
       for (int nt : nts)
-        for (int stg : {4, 6}) add(4, 0, 0, mm, nt, stg);
+        for (int stg : {3, 4, 6}) add(4, 0, 0, mm, nt, stg);
   }
   for (int rr : {1, 4, 8})
     if (rr <= nrhs || rr == 4)
