@@ -411,7 +411,7 @@ def measure(env, cfg, steps, warmup, nrhs=None, inner="f32", graphs=1, autotune=
            "nrhs": nrhs, "inner_prec": inner, "coarse_links": cfg.get("links", "f32") if inner == "f32" else "f64"}
 
     if roofline:
-        out["roofline"] = roofline_of(acc, dominant, ms, steps)
+        out["roofline"] = roofline_of(acc, dominant, ms, steps, cfg.get("ortho") == "df")
         out["kernel_shares_timed"] = {dominant: round(acc[dominant][1] / (ms * steps), 4)}
     co = first_solve.k[KCLASS.index("coarse")]
     out["coarse_in_first_solve"] = {
@@ -451,13 +451,26 @@ def measure(env, cfg, steps, warmup, nrhs=None, inner="f32", graphs=1, autotune=
     return out
 
 
-def roofline_of(acc, dominant, ms, steps):
+# FP32 lane instructions per second of GB300: 152 SMs x 128 lanes x 2070 MHz.
+FP32_INSTR_PEAK_T = 152 * 128 * 2.070e9 / 1e12
+# FP32 instructions of one double-float real multiply-add (1 FMUL, 3 FFMA, 8 FADD)
+DF_INSTR_PER_MAC = 12
+
+
+def roofline_of(acc, dominant, ms, steps, ortho_df=False):
     hbm, bf16, peak_kind = peaks()
     d = acc[dominant]
     bound = "alu" if dominant in ("dslash64", "ortho") else "hbm"
     if bound == "hbm":
         achieved, peak, unit = d[2] / (d[1] * 1e-3) / 1e9, hbm, "GB/s"
         src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peak_kind == "measured" else "fallback 6.8 TB/s"
+    elif dominant == "ortho" and ortho_df:
+        # double-float on the FP32 pipe: the algorithmic real multiply-adds of one
+        # Gram-Schmidt pass (flops / 2), 12 FP32 instructions each
+        achieved = d[3] / 2 * DF_INSTR_PER_MAC / (d[1] * 1e-3) / 1e12
+        peak, unit = FP32_INSTR_PEAK_T, "T FP32 instructions/s"
+        src = ("FP32 lanes x max SM clock (derived: 152 x 128 x 2.07 GHz); algorithmic work = one Gram-Schmidt "
+               "pass in double-float, 12 FP32 instructions per real multiply-add")
     else:
         achieved, peak, unit = d[3] / (d[1] * 1e-3) / 1e12, ALU_PEAK_TFLOPS["f64"], "TFLOP/s"
         src = "FP64 unit count x max SM clock (derived; a DFMA probe measured 1.20 TFLOP/s at 1.99 GHz)"
@@ -1170,8 +1183,9 @@ def main(argv=None):
                     help="block orthonormalisation arithmetic: FP64, or double-float on the FP32 pipe")
     ap.add_argument("--probe", default=None,
                     help="kernel probe for ncu instead of the bench: 'ortho' (the fine-level block "
-                         "orthonormalisation of Nvec Gaussian fields, 3 times) or 'coarse:LEVEL:NRHS' (5 coarse "
-                         "applies after one setup); prints one JSON line of CUDA-event times")
+                         "orthonormalisation of Nvec Gaussian fields, 3 times) or 'coarse:LEVEL:NRHS[:KIND:THREADS:"
+                         "PARTS:STAGES:NTILE]' (5 coarse applies after one setup with the autotuned or the given "
+                         "launch shape); prints one JSON line of CUDA-event times")
     ap.add_argument("--ncu-region", action="store_true",
                     help="bracket the timed steps of the headline workload with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")

@@ -310,7 +310,8 @@ typedef struct wcmg_tile {
   int ntile;            /* kind 2: rhs per MMA N tile (16, 32, 48 or 64) */
   int source;           /* 0 fixed rule, 1 autotuner, 2 wcmg_set_coarse_tile */
   int candidates;       /* shapes the autotuner timed (fixed rule included) */
-  int stages;           /* kind 3: chunks in flight (2 .. 8) */
+  int stages;           /* kind 0: link rows in flight per warp (0 or 1: one, 2: two);
+                           kind 3: chunks in flight (2 .. 8) */
   double us;            /* autotuner: time per apply of the chosen shape (back-to-back applies) */
   double us_default;    /* autotuner: time per apply of the fixed rule */
 } wcmg_tile;

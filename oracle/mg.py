@@ -61,6 +61,7 @@ class MGParams:
     smoother: str = "mr"                     # "mr", "gmres" or "sap"
     sap_cycles: int = 1                      # SAP: cycles; smoother_steps = MR steps per block solve
     sap_eo: bool = False                     # SAP: even-odd preconditioned block solves on the finest level
+    coarse_eo: bool = False                  # coarsest solve on the odd-site Schur complement (even-odd)
     kcycle: bool = False                     # intermediate levels: FGMRES around the cycle
     kcycle_steps: int = 5
     kcycle_tol: float = 0.1
@@ -72,6 +73,33 @@ class Level:
     dims: tuple
     vecs: list = field(default_factory=list)   # raw (normalised) near-null vectors
     agg: object = None
+
+
+def coarse_eo_solve(op, dims, b, restart, tol, maxiter):
+    """Even-odd (red-black) preconditioned coarsest solve (Sec. 4 lists red-black
+    preconditioning among Grid's missing features; DDalphaAMG, its comparison, uses it on
+    every level).  With coarse sites even / odd by the parity of x + y + z + t, the hops
+    of the nine-block operator join sites of opposite parity and the self blocks A_0 form
+    the diagonal: D_c = [[A_ee, A_eo], [A_oe, A_oo]] with A_ee, A_oo block diagonal.
+      b^_o = b_o - A_oe A_ee^-1 b_e,
+      GMRES(restart) on S = A_oo - A_oe A_ee^-1 A_eo to tol relative to ||b^_o||
+        (reading: the coarse tolerance applies to the system GMRES solves),
+      x_e = A_ee^-1 (b_e - A_eo x_o).
+    Needs even coarse extents (an odd one would join equal parities across the
+    boundary).  Odd-site vectors are full fields that vanish on even sites."""
+    if any(L % 2 for L in dims):
+        raise ValueError("even-odd coarsest solve needs even coarse extents")
+    ev = (parity(dims) == 0)[..., None]
+    od = ~ev
+    b_hat = np.where(od, b - op(np.where(ev, self_solve(op, b), 0)), 0)
+
+    def schur(v):
+        Dv = op(v)
+        return np.where(od, Dv - op(np.where(ev, self_solve(op, np.where(ev, Dv, 0)), 0)), 0)
+
+    x_o, _ = gmres(schur, b_hat, restart=restart, tol=tol, maxiter=maxiter)
+    x_e = np.where(ev, self_solve(op, b - op(x_o)), 0)
+    return x_e + x_o
 
 
 class Multigrid:
@@ -143,6 +171,9 @@ class Multigrid:
         """Solve on level l (l >= 1): GMRES at the coarsest level, else one cycle
         (V-cycle) or a short FGMRES preconditioned by the cycle (K-cycle)."""
         if l == self.nlevels - 1:
+            if self.p.coarse_eo:
+                return coarse_eo_solve(self.levels[l].op, self.levels[l].dims, r, self.p.coarse_restart,
+                                       self.p.coarse_tol, self.p.coarse_maxiter)
             x, _ = gmres(self.levels[l].op, r, restart=self.p.coarse_restart,
                          tol=self.p.coarse_tol, maxiter=self.p.coarse_maxiter)
             return x

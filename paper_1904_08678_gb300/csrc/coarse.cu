@@ -126,10 +126,11 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
 
 // Single-rhs coarse apply.  One CTA per (site, block of rows): the nine
 // neighbour vectors are gathered once into shared memory; each warp owns rows
-// and loads a whole row (NK 16-byte chunks per lane) before reducing it; the
-// first row is requested before the gather and the barrier, so every warp has
-// a full row (NK x 512 B) of the link stream in flight.
-template <typename R, typename L, int VEC, int NK>
+// and loads RPW whole rows (NK 16-byte chunks per lane each) before reducing them;
+// the first rows are requested before the gather and the barrier, so every warp has
+// RPW rows (RPW x NK x 512 B) of the link stream in flight.  RPW = 2 keeps as many
+// bytes in flight per warp for 4-byte (BF16 / FP16) links as RPW = 1 does for FP32.
+template <typename R, typename L, int VEC, int NK, int RPW>
 __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
                                                        const L* __restrict__ links, const int* __restrict__ nbr,
                                                        int Vc, int nb, int ld, int parts) {
@@ -141,13 +142,20 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
   const int row0 = part * rpc, row1 = min(nb, row0 + rpc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const L* base = links + (long long)site * nb * ld;
-  LinkVec<L, VEC> cur[NK];
-  int row = row0 + warp;
+  LinkVec<L, VEC> cur[RPW][NK];
+  auto load_rows = [&](int row) {
 #pragma unroll
-  for (int j = 0; j < NK; ++j) {
-    const int k0 = VEC * (lane + 32 * j);
-    if (row < row1 && k0 < ld) cur[j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)row * ld + k0);
-  }
+    for (int u = 0; u < RPW; ++u) {
+      const int r = row + u * nw;
+#pragma unroll
+      for (int j = 0; j < NK; ++j) {
+        const int k0 = VEC * (lane + 32 * j);
+        if (r < row1 && k0 < ld) cur[u][j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)r * ld + k0);
+      }
+    }
+  };
+  int row = row0 + warp;
+  load_rows(row);
   const int K = 9 * nb;
   for (int idx = threadIdx.x; idx < ld; idx += blockDim.x) {
     T v = czero<R>();
@@ -160,25 +168,28 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
   }
   __syncthreads();
   const int G = ld / VEC;
-  for (; row < row1; row += nw) {
-    if (row != row0 + warp) {
+  for (; row < row1; row += RPW * nw) {
+    if (row != row0 + warp) load_rows(row);
+    T acc[RPW];
 #pragma unroll
-      for (int j = 0; j < NK; ++j) {
-        const int k0 = VEC * (lane + 32 * j);
-        if (k0 < ld) cur[j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)row * ld + k0);
-      }
-    }
-    T acc = czero<R>();
+    for (int u = 0; u < RPW; ++u) acc[u] = czero<R>();
 #pragma unroll
     for (int j = 0; j < NK; ++j) {
       const int k0 = VEC * (lane + 32 * j);
       if (k0 < ld) {
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) cmac(acc, link_load<L, R>(cur[j].v[v]), phi[v * G + k0 / VEC]);
+        for (int v = 0; v < VEC; ++v) {
+          const T p = phi[v * G + k0 / VEC];
+#pragma unroll
+          for (int u = 0; u < RPW; ++u) cmac(acc[u], link_load<L, R>(cur[u][j].v[v]), p);
+        }
       }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) out[(long long)site * nb + row] = acc;
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) {
+      const T a = warp_sum(acc[u]);
+      if (lane == 0 && row + u * nw < row1) out[(long long)site * nb + row + u * nw] = a;
+    }
   }
 }
 
@@ -261,7 +272,8 @@ __global__ void __launch_bounds__(512) k_coarse_apply1_stream(cplx<R>* __restric
     for (int c = 0; c < cps; ++c, ++q) {
       const int r0 = c * cr, rows = min(cr, nb - r0);
       const int s = (int)(q % stages);
-      const int good = mbar_wait_bounded(&full[s], (uint32_t)((q / stages) & 1)) ? 1 : 0;
+      // one thread polls the barrier; the CTA barrier then orders the copied data for all
+      const int good = threadIdx.x != 0 || mbar_wait_bounded(&full[s], (uint32_t)((q / stages) & 1)) ? 1 : 0;
       if (!__syncthreads_and(good)) {
         ok = false;
         break;
@@ -637,7 +649,9 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
     long long i = 0;
     for (long long it = blockIdx.x; it < items; it += gridDim.x, ++i) {
       const int tb = (int)(i & 1);
-      const int good = mbar_wait_bounded(&tfull[tb], (uint32_t)((i >> 1) & 1), limit) ? 1 : 0;
+      // one lane per warp polls the accumulator barrier, the others wait at the warp barrier
+      int good = lane != 0 || mbar_wait_bounded(&tfull[tb], (uint32_t)((i >> 1) & 1), limit) ? 1 : 0;
+      good = __shfl_sync(0xffffffffu, good, 0);
       if (!good || *(volatile int*)&abort_flag) {
         if (!good) fail();
         break;
@@ -701,19 +715,22 @@ static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, con
 
 template <typename R, typename L>
 static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int parts,
-                          int threads, cudaStream_t st) {
+                          int threads, int rpw, cudaStream_t st) {
   constexpr int VEC = VecOf<L>::v;
   const int ld = links_ld(nb);
   const int nk = (ld + 32 * VEC - 1) / (32 * VEC);
   const size_t smem = (size_t)ld * sizeof(cplx<R>);
   const unsigned grid = (unsigned)(g.V * parts);
-#define WCMG_C1(NKV) \
-  k_coarse_apply1<R, L, VEC, NKV><<<grid, threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, parts)
-  if (nk <= 4) WCMG_C1(4);
-  else if (nk <= 8) WCMG_C1(8);
-  else if (nk <= 12) WCMG_C1(12);
-  else if (nk <= 18) WCMG_C1(18);
+#define WCMG_C1(NKV, RP) \
+  k_coarse_apply1<R, L, VEC, NKV, RP><<<grid, threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, parts)
+#define WCMG_C1R(NKV) \
+  if (rpw == 2) WCMG_C1(NKV, 2); else WCMG_C1(NKV, 1)
+  if (nk <= 4) { WCMG_C1R(4); }
+  else if (nk <= 8) { WCMG_C1R(8); }
+  else if (nk <= 12) { WCMG_C1(12, 1); }
+  else if (nk <= 18) { WCMG_C1(18, 1); }
   else throw Error(-1, "coarse apply: nbasis too large");
+#undef WCMG_C1R
 #undef WCMG_C1
   WCMG_LAUNCH_CHECK();
 }
@@ -838,9 +855,13 @@ template <> struct LinkKind<f16c> { static constexpr int v = 3; };
 
 bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link_kind) {
   switch (t.kind) {
-    case 0:
+    case 0: {
+      // stages: rows in flight per warp (0 or 1: one, 2: two; two only while a row is <= 8 chunks per lane)
+      const int vec = link_kind == 0 ? 1 : link_kind == 1 ? 2 : 4;
+      const int nk = (links_ld(nb) + 32 * vec - 1) / (32 * vec);
       return nrhs == 1 && mode == ST_FULL && t.parts >= 1 && t.parts <= nb && t.threads >= 64 && t.threads <= 512 &&
-             t.threads % 32 == 0;
+             t.threads % 32 == 0 && t.stages >= 0 && t.stages <= 2 && (t.stages < 2 || nk <= 8);
+    }
     case 1:
       return (t.rr == 1 || t.rr == 4 || t.rr == 8) && t.parts >= 0 && t.parts <= nb;
     case 2:
@@ -892,7 +913,7 @@ void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const 
     throw Error(-1, "coarse apply: tensor-core tile needs BF16 links");
   }
   if (t.kind == 0) {
-    coarse_apply1<R, L>(out, in, links, g, nb, t.parts, t.threads, st);
+    coarse_apply1<R, L>(out, in, links, g, nb, t.parts, t.threads, t.stages == 2 ? 2 : 1, st);
     return;
   }
   if (t.kind == 3) {

@@ -522,7 +522,6 @@ __device__ __forceinline__ dfr df_from(double x) {
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double df_to(dfr a) { return (double)a.h + (double)a.l; }
 __device__ __forceinline__ dfr df_neg(dfr a) { return {-a.h, -a.l}; }
 // TwoSum: s + e = a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -618,6 +617,34 @@ __device__ __forceinline__ dfr df_warp_sum(dfr v) {
   return v;
 }
 
+// FP64 -> DF without the FP64 pipe: h = x truncated to 24 significant bits (its
+// float bit pattern built from the double's sign, exponent and top mantissa bits),
+// l = the remaining 29 mantissa bits as a float (rounded) scaled by the exponent.
+// Exact for h; l carries x - h to float precision.  Magnitudes outside [2^-74, 2^127)
+// take the FP64 conversion path.
+__device__ __forceinline__ dfr df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 949 || e > 1149) return df_from(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned hb = sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu);
+  const unsigned low = (unsigned)(b & 0x1FFFFFFFull);
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e - 1075)
+  const float l = __uint2float_rn(low) * scale;
+  return {__uint_as_float(hb), __uint_as_float(__float_as_uint(l) | sign)};
+}
+// DF -> FP64: both floats widened exactly by their bit patterns, one FP64 add
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0 || e == 255) return (double)f;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double df_to_fast(dfr a) { return f2d_exact(a.h) + f2d_exact(a.l); }
+
 template <int MAXE>
 __global__ void __launch_bounds__(256, 2) k_block_ortho_df(double2* __restrict__ vecs, float4* __restrict__ qdf, int Vf,
                                                         int nc, int bvol, int nvec, bool fine, int* __restrict__ err) {
@@ -666,7 +693,7 @@ __global__ void __launch_bounds__(256, 2) k_block_ortho_df(double2* __restrict__
     for (int q = 0; q < MAXE; ++q) {
       if (addr[q] >= 0) {
         const double2 v = vecs[k * fstride + addr[q]];
-        a[q] = {df_from(v.x), df_from(v.y)};
+        a[q] = {df_split(v.x), df_split(v.y)};
       } else {
         a[q] = zero;
       }
@@ -693,7 +720,7 @@ __global__ void __launch_bounds__(256, 2) k_block_ortho_df(double2* __restrict__
       }
       norm2(a);
       reduce(k, true);
-      if (pass == 0) before2 = df_to(red[MV - 1].re);
+      if (pass == 0) before2 = df_to_fast(red[MV - 1].re);
       for (int i = 0; i < k; ++i) {
         const dfc r = red[i];
         const float4* qi = qdf + i * fstride;
@@ -705,228 +732,28 @@ __global__ void __launch_bounds__(256, 2) k_block_ortho_df(double2* __restrict__
       for (int q = 0; q < MAXE; ++q) a[q] = dfc_norm(a[q]);
       norm2(a);
       reduce(0, true);
-      after2 = df_to(red[MV - 1].re);
+      after2 = df_to_fast(red[MV - 1].re);
       if (k == 0 || after2 >= 1e-4 * before2) break;  // uniform over the block
     }
     const double nrm = sqrt(after2);
     if (!(nrm > 0.0) || !isfinite(nrm)) {
       if (threadIdx.x == 0) *err = 1;
     }
-    const dfr inv = df_from(nrm > 0.0 ? 1.0 / nrm : 0.0);
+    const dfr inv = df_split(nrm > 0.0 ? 1.0 / nrm : 0.0);
 #pragma unroll
     for (int q = 0; q < MAXE; ++q)
       if (addr[q] >= 0) {
         const dfr re = df_mul(a[q].re, inv), im = df_mul(a[q].im, inv);
-        vecs[k * fstride + addr[q]] = make_double2(df_to(re), df_to(im));
+        vecs[k * fstride + addr[q]] = make_double2(df_to_fast(re), df_to_fast(im));
         qdf[k * fstride + addr[q]] = make_float4(re.h, re.l, im.h, im.l);
       }
     __syncthreads();
   }
 }
 
-// FP64 -> DF without the FP64 pipe: h = x truncated to 24 significant bits (its
-// float bit pattern built from the double's sign, exponent and top mantissa bits),
-// l = the remaining 29 mantissa bits as a float (rounded) scaled by the exponent.
-// Exact for h; l carries x - h to float precision.  Magnitudes outside [2^-74, 2^127)
-// take the FP64 conversion path.
-__device__ __forceinline__ dfr df_split(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e < 949 || e > 1149) return df_from(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const unsigned hb = sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu);
-  const unsigned low = (unsigned)(b & 0x1FFFFFFFull);
-  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e - 1075)
-  const float l = __uint2float_rn(low) * scale;
-  return {__uint_as_float(hb), __uint_as_float(__float_as_uint(l) | sign)};
-}
-// DF -> FP64: both floats widened exactly by their bit patterns, one FP64 add
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFF;
-  if (e == 0 || e == 255) return (double)f;
-  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e - 127 + 1023) << 52) |
-                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)b);
-}
-__device__ __forceinline__ double df_to_fast(dfr a) { return f2d_exact(a.h) + f2d_exact(a.l); }
-
-void launch_block_ortho_df_cols(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
-                                cudaStream_t st);
-
-// Block version (block classical Gram-Schmidt applied twice, "BCGS2"): columns in
-// blocks of 4; each block is projected twice against all earlier columns (each earlier
-// column read once per pass for all four dot products and once for the four updates),
-// then orthonormalised inside the block by classical Gram-Schmidt applied twice.  For
-// a full-rank panel this is the same Q factor (positive real diag(R)) as the
-// column-by-column form; "twice is enough" keeps it orthonormal to the working
-// precision.  512 threads, MAXE <= 4 panel rows per thread.
-template <int MAXE>
-__global__ void __launch_bounds__(512, 1) k_block_ortho_bcgs(double2* __restrict__ vecs, float4* __restrict__ qdf,
-                                                          int Vf, int nc, int bvol, int nvec, bool fine,
-                                                          int* __restrict__ err) {
-  constexpr int NB = 4, NW = 16, MAXR = 32 * NB;  // <= 28 earlier columns x 4 dots (+ norms)
-  __shared__ dfc scratch[NW][MAXR];
-  __shared__ dfc red[MAXR];
-  const int blk = blockIdx.x, s = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nelem = bvol * (nc >> 1);
-  const long long fstride = (long long)Vf * nc;
-  long long addr[MAXE];
-#pragma unroll
-  for (int q = 0; q < MAXE; ++q) {
-    const int e = threadIdx.x + q * blockDim.x;
-    addr[q] = e < nelem ? elem_addr(fine, blk, e, s, Vf, nc, bvol) : -1;
-  }
-  const dfc zero = {{0.f, 0.f}, {0.f, 0.f}};
-  // block-wide DF sums of the first n slots of every warp's scratch row into red[]
-  auto reduce = [&](int n) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      dfc t = scratch[0][i];
-      for (int w = 1; w < nw; ++w) t = dfc_add(t, scratch[w][i]);
-      red[i] = t;
-    }
-    __syncthreads();
-  };
-  for (int j0 = 0; j0 < nvec; j0 += NB) {
-    const int nbk = min(NB, nvec - j0);
-    dfc a[NB][MAXE];
-#pragma unroll
-    for (int c = 0; c < NB; ++c)
-#pragma unroll
-      for (int q = 0; q < MAXE; ++q) {
-        a[c][q] = zero;
-        if (c < nbk && addr[q] >= 0) {
-          const double2 v = vecs[(j0 + c) * fstride + addr[q]];
-          a[c][q] = {df_split(v.x), df_split(v.y)};
-        }
-      }
-    // two block projections against the earlier columns
-    for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
-      for (int i0 = 0; i0 < j0; i0 += 2) {  // 2 earlier columns x 4 block columns per reduction
-        dfc p[8];
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-#pragma unroll
-          for (int c = 0; c < NB; ++c) p[NB * g + c] = zero;
-          if (i0 + g < j0) {
-            const float4* qi = qdf + (i0 + g) * fstride;
-#pragma unroll
-            for (int q = 0; q < MAXE; ++q)
-              if (addr[q] >= 0) {
-                const dfc qv = dfc_load(qi + addr[q]);
-#pragma unroll
-                for (int c = 0; c < NB; ++c) dfc_cjmac(p[NB * g + c], qv, a[c][q]);
-              }
-          }
-        }
-#pragma unroll
-        for (int v = 0; v < 8; ++v) p[v] = dfc_norm(p[v]);
-        dfc_warp_sum8_transposed(p, lane);
-        const int idx = warp_sum8_index(lane);  // (g, c) = (idx / 4, idx % 4)
-        if ((lane & 3) == 0 && i0 + idx / NB < j0) scratch[warp][NB * i0 + idx] = p[0];
-      }
-      reduce(NB * j0);
-      for (int i = 0; i < j0; ++i) {
-        dfc r[NB];
-#pragma unroll
-        for (int c = 0; c < NB; ++c) r[c] = red[NB * i + c];
-        const float4* qi = qdf + i * fstride;
-#pragma unroll
-        for (int q = 0; q < MAXE; ++q)
-          if (addr[q] >= 0) {
-            const dfc qv = dfc_load(qi + addr[q]);
-#pragma unroll
-            for (int c = 0; c < NB; ++c) dfc_nmac(a[c][q], r[c], qv);
-          }
-      }
-#pragma unroll
-      for (int c = 0; c < NB; ++c)
-#pragma unroll
-        for (int q = 0; q < MAXE; ++q) a[c][q] = dfc_norm(a[c][q]);
-    }
-    // inside the block: classical Gram-Schmidt applied twice, then normalisation
-#pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      if (c >= nbk) break;
-      for (int pass = 0; pass < 2 && c > 0; ++pass) {
-        dfc p[NB];
-#pragma unroll
-        for (int cp = 0; cp < NB; ++cp) {
-          p[cp] = zero;
-          if (cp < c) {
-#pragma unroll
-            for (int q = 0; q < MAXE; ++q) dfc_cjmac(p[cp], a[cp][q], a[c][q]);
-            p[cp] = dfc_norm(p[cp]);
-          }
-        }
-#pragma unroll
-        for (int cp = 0; cp < NB; ++cp) {
-          if (cp < c) {
-            dfc t = p[cp];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t = dfc_add(t, dfc_shfl_xor(t, o));
-            if (lane == 0) scratch[warp][cp] = t;
-          }
-        }
-        reduce(c);
-#pragma unroll
-        for (int cp = 0; cp < NB; ++cp)
-          if (cp < c) {
-            const dfc r = red[cp];
-#pragma unroll
-            for (int q = 0; q < MAXE; ++q) dfc_nmac(a[c][q], r, a[cp][q]);
-          }
-#pragma unroll
-        for (int q = 0; q < MAXE; ++q) a[c][q] = dfc_norm(a[c][q]);
-      }
-      dfr n = {0.f, 0.f};
-#pragma unroll
-      for (int q = 0; q < MAXE; ++q) {
-        df_mac(n, a[c][q].re, a[c][q].re);
-        df_mac(n, a[c][q].im, a[c][q].im);
-      }
-      n = df_warp_sum(df_norm(n));
-      if (lane == 0) scratch[warp][0] = {n, {0.f, 0.f}};
-      reduce(1);
-      const double nrm2 = df_to_fast(red[0].re);
-      const double nrm = sqrt(nrm2);
-      if (!(nrm > 0.0) || !isfinite(nrm)) {
-        if (threadIdx.x == 0) *err = 1;
-      }
-      const dfr inv = df_split(nrm > 0.0 ? 1.0 / nrm : 0.0);
-#pragma unroll
-      for (int q = 0; q < MAXE; ++q) {
-        a[c][q] = {df_mul(a[c][q].re, inv), df_mul(a[c][q].im, inv)};
-        if (addr[q] >= 0) {
-          vecs[(j0 + c) * fstride + addr[q]] = make_double2(df_to_fast(a[c][q].re), df_to_fast(a[c][q].im));
-          qdf[(j0 + c) * fstride + addr[q]] = make_float4(a[c][q].re.h, a[c][q].re.l, a[c][q].im.h, a[c][q].im.l);
-        }
-      }
-    }
-    __syncthreads();  // the block's Q columns are in global memory before the next block reads them
-  }
-}
 
 void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
                            cudaStream_t st) {
-  const int nelem = bvol * (nc / 2);
-  if (nvec <= 32 && nelem <= 512 * 4) {  // blocked form (scratch: up to 28 earlier columns x 4 dots)
-    const dim3 grid(Vf / bvol, 2);
-    if (nelem <= 512) k_block_ortho_bcgs<1><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
-    else if (nelem <= 1024) k_block_ortho_bcgs<2><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
-    else if (nelem <= 1536) k_block_ortho_bcgs<3><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
-    else k_block_ortho_bcgs<4><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
-    WCMG_LAUNCH_CHECK();
-    return;
-  }
-  launch_block_ortho_df_cols(vecs, qdf, Vf, nc, bvol, nvec, fine, err, st);
-}
-
-void launch_block_ortho_df_cols(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
-                                cudaStream_t st) {
   const int nelem = bvol * (nc / 2);
   if (nvec > 32) throw Error(-1, "block orthonormalisation supports nvec <= 32");
   if (nelem > 256 * 8) throw Error(-1, "aggregate too large for block orthonormalisation");

@@ -414,7 +414,8 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
   };
   if (nrhs == 1) {
     for (int th : {256, 512})
-      for (int p : {1, 2, 4, 8}) add(0, 1, p, th, 0);
+      for (int p : {1, 2, 4, 8})
+        for (int rp : {1, 2}) add(0, 1, p, th, 0, rp);
     for (int p : {1, 2, 4, 8, 16}) add(1, 1, p, 0, 0);
     // streaming pipeline: chunks of 8 rows up to a whole site, 2 .. 6 in flight
     for (int cr : {8, 16, 24, nb})

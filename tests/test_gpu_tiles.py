@@ -38,6 +38,8 @@ def candidate_tiles(nrhs, lk, nb):
     if nrhs == 1:
         t += [dict(kind=0, threads=th, parts=p) for th in (256, 512) for p in (1, 2, 4, 8)]
         t += [dict(kind=0, threads=64, parts=nb), dict(kind=0, threads=96, parts=3)]
+        if lk != "f64":  # two link rows in flight per warp (rows of at most 8 chunks per lane)
+            t += [dict(kind=0, threads=th, parts=p, stages=2) for th, p in ((256, 1), (512, 2), (96, 5), (64, nb))]
         t += [dict(kind=1, rhs_per_cta=1, parts=p) for p in (1, 2, 4, 8, 16, nb)]
         # streaming pipeline: the autotuner's shapes, a ragged last chunk (48 % 5, 48 % 7)
         # and the shallowest / deepest pipelines
@@ -143,6 +145,7 @@ def test_invalid_tiles_are_rejected(lib):
            (1, dict(kind=0, threads=48, parts=1)),      # threads not a multiple of 32
            (1, dict(kind=0, threads=512, parts=0)),
            (1, dict(kind=3, threads=256, parts=8, stages=1)),   # a pipeline needs >= 2 stages
+           (1, dict(kind=0, threads=256, parts=1, stages=3)),   # one or two rows in flight
            (1, dict(kind=3, threads=96, parts=8, stages=4)),    # 128, 256 or 512 threads
            (4, dict(kind=3, threads=256, parts=8, stages=4)),   # one rhs only
            (1, dict(kind=3, threads=256, parts=48, stages=8)),  # beyond the shared-memory limit

@@ -139,3 +139,50 @@ def test_block_storage_convention():
     out = Dc2(phi)
     assert np.abs(out[0, 0, 0, 1] - Dc2.A[1][0, 0, 0, 1][:, 1]).max() < 1e-14   # x_c = 1 reads +x at 2
     assert np.abs(out[0, 0, 0, 3] - Dc2.A[2][0, 0, 0, 3][:, 1]).max() < 1e-14   # x_c = 3 reads -x at 2
+
+
+def _coarse_system(dims=(4, 4, 4, 8), block=(2, 2, 2, 2), nvec=3):
+    U, D, agg, _ = setup_two_level(dims, block, nvec=nvec)
+    Dc = coarsen(D, agg)
+    Vc = int(np.prod(agg.cdims))
+    b = to_grid(inputs.complex_gaussian(33, 0, (Vc, agg.nbasis)), agg.cdims)
+    return Dc, agg, b
+
+
+def test_even_odd_coarsest_solve_is_the_dense_solution():
+    """Sec. 4 red-black preconditioning on the coarsest level: run to convergence, the
+    Schur-complement solve (b^_o, GMRES on S, back substitution on the even sites) is the
+    solution of the dense coarse system.  A flipped sign in b^_o, a dropped A_oe A_ee^-1 A_eo
+    term in S or a dropped A_eo x_o in the back substitution each miss it by O(1)."""
+    from oracle.mg import coarse_eo_solve
+    Dc, agg, b = _coarse_system()
+    M = dense(Dc, agg.cdims, agg.nbasis)
+    want = np.linalg.solve(M, b.ravel()).reshape(b.shape)
+    got = coarse_eo_solve(Dc, agg.cdims, b, restart=80, tol=1e-14, maxiter=2000)
+    assert rel(got, want) < 1e-10
+
+
+def test_even_odd_schur_complement_matches_the_dense_one():
+    """The odd-site Schur complement of the nine-block operator equals
+    D_oo - D_oe D_ee^-1 D_eo of the dense coarse matrix split by site parity."""
+    from oracle.mg import coarse_eo_solve  # noqa: F401  (the reading under test)
+    from oracle.sap import parity, self_solve
+    Dc, agg, b = _coarse_system()
+    cd, nb = agg.cdims, agg.nbasis
+    M = dense(Dc, cd, nb)
+    par = np.repeat(parity(cd).reshape(-1), nb)  # parity of every dense index
+    e, o = np.where(par == 0)[0], np.where(par == 1)[0]
+    S = M[np.ix_(o, o)] - M[np.ix_(o, e)] @ np.linalg.solve(M[np.ix_(e, e)], M[np.ix_(e, o)])
+    ev = (parity(cd) == 0)[..., None]
+    v = np.where(ev, 0, b)
+    Dv = Dc(v)
+    Sv = np.where(ev, 0, Dv - Dc(np.where(ev, self_solve(Dc, np.where(ev, Dv, 0)), 0)))
+    assert rel(Sv.ravel()[o], S @ v.ravel()[o]) < 1e-12
+    assert np.abs(Sv.ravel()[e]).max() == 0.0
+
+
+def test_even_odd_coarsest_solve_needs_even_extents():
+    from oracle.mg import coarse_eo_solve
+    Dc, agg, b = _coarse_system(dims=(4, 4, 4, 6), block=(2, 2, 2, 2))  # coarse t extent 3
+    with pytest.raises(ValueError):
+        coarse_eo_solve(Dc, agg.cdims, b, restart=10, tol=1e-6, maxiter=10)

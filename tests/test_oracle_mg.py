@@ -238,3 +238,20 @@ def test_even_odd_outer_solve_reaches_the_dense_solution():
     assert rel(x, x_ref) < 1e-8
     _, plain = mg.solve(b)
     assert abs(info.iterations - plain.iterations) <= 2
+
+
+def test_even_odd_coarsest_level_solve_reaches_the_dense_solution():
+    """MG with the coarsest GMRES on the odd-site Schur complement (coarse_eo) preconditions
+    FGMRES to the dense solution, in no more outer iterations than the plain coarsest
+    solve (the Schur system is better conditioned, so its 0.05 GMRES is not worse)."""
+    dims, D, b = config1()
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 8, 0, 1001)]]
+    its = {}
+    x_ref, _ = gmres(D, b, restart=60, tol=1e-13, maxiter=5000, verify=True)
+    for eo in (False, True):
+        mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[8], coarse_eo=eo), iv)
+        x, info = mg.solve(b)
+        assert info.converged and info.true_residual <= 1e-10
+        its[eo] = info.iterations
+        assert rel(x, x_ref) < 1e-8
+    assert its[True] <= its[False] + 1
