@@ -269,6 +269,7 @@ def make_inputs(cfg, nrhs=None):
 def params(wcmg, cfg, inner, links=None, profile=0, graphs=0, autotune=1, nrhs=None):
     links = links or cfg.get("links", "f32")
     ortho_df = int(cfg.get("ortho", "fp64") == "df")
+    coarse_eo = int(cfg.get("coarse_eo", 0))
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
                             n_levels=len(cfg["blocks"]) + 1, max_rhs=nrhs or cfg.get("nrhs", 1), profile=profile,
@@ -277,7 +278,7 @@ def params(wcmg, cfg, inner, links=None, profile=0, graphs=0, autotune=1, nrhs=N
                                       "sap": wcmg.SMOOTHER_SAP}[cfg.get("smoother", "mr")],
                             sap_cycles=int(cfg.get("sap_cycles", 1)), sap_eo=int(cfg.get("sap_eo", 0)),
                             smoother_steps=int(cfg.get("smoother_steps", 4)),
-                            kcycle=int(cfg.get("kcycle", 0)), ortho_df=ortho_df)
+                            kcycle=int(cfg.get("kcycle", 0)), ortho_df=ortho_df, coarse_eo=coarse_eo)
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -519,6 +520,9 @@ def run_gpu(args, rank, world, local):
     if args.links:
         cfg["links"] = args.links
     cfg["ortho"] = args.ortho
+    if args.coarse_eo:
+        cfg["coarse_eo"] = 1
+        cfg["workload"] = cfg["workload"] + ", even-odd preconditioned coarsest solve"
     if args.kcycle:
         cfg["kcycle"] = 1
         cfg["workload"] = cfg["workload"] + ", K-cycle (FGMRES(5) to 0.1 on the intermediate levels)"
@@ -1172,6 +1176,8 @@ def main(argv=None):
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="1: coarse-apply launch shapes picked by the autotuner; 0: fixed rule")
     ap.add_argument("--kcycle", action="store_true", help="K-cycle on the intermediate levels (3-level workloads)")
+    ap.add_argument("--coarse-eo", action="store_true",
+                    help="even-odd (Schur complement) preconditioned coarsest solve")
     ap.add_argument("--smoother", default="mr", choices=["mr", "gmres", "sap"],
                     help="smoother of every level (the setup sweeps and the cycle)")
     ap.add_argument("--sap-cycles", type=int, default=1, help="SAP smoother: cycles")

@@ -128,6 +128,15 @@ typedef struct wcmg_params {
                                            the FP32 pipe (each value the unevaluated sum of two
                                            floats, 48-bit significands, compensated dot products),
                                            FP64 input and output.  Same algorithm and stopping rule. */
+  int coarse_eo;                        /* 1: even-odd (red-black) preconditioned coarsest solve (Sec. 4
+                                           lists red-black preconditioning among the missing features):
+                                           with coarse sites even / odd by the parity of x + y + z + t,
+                                           b^_o = b_o - A_oe A_ee^-1 b_e, GMRES(coarse_restart) on the
+                                           Schur complement S = A_oo - A_oe A_ee^-1 A_eo to coarse_tol
+                                           relative to ||b^_o||, x_e = A_ee^-1 (b_e - A_eo x_o); A_ee^-1 =
+                                           the inverses of the self blocks A_0 (FP64 Gauss-Jordan, once
+                                           per coarse operator).  Needs even extents of the coarsest
+                                           lattice (else WCMG_ERR_ARG). */
 } wcmg_params;
 
 typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1, WCMG_SMOOTHER_SAP = 2 } wcmg_smoother;

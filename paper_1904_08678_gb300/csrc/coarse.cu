@@ -39,11 +39,22 @@ template <typename L, int VEC> struct alignas(16) LinkVec { L v[VEC]; };
 template <int VEC>
 __device__ __forceinline__ int phi_slot(int k, int ld) { return (k % VEC) * (ld / VEC) + k / VEC; }
 
+template <typename L> __device__ __forceinline__ double2 link_to_c64(const L& l);
+template <> __device__ __forceinline__ double2 link_to_c64<double2>(const double2& l) { return l; }
+template <> __device__ __forceinline__ double2 link_to_c64<float2>(const float2& l) { return make_double2(l.x, l.y); }
+template <> __device__ __forceinline__ double2 link_to_c64<bf16c>(const bf16c& l) {
+  float2 f = __bfloat1622float2(l.v); return make_double2(f.x, f.y);
+}
+template <> __device__ __forceinline__ double2 link_to_c64<f16c>(const f16c& l) {
+  float2 f = __half22float2(l.v); return make_double2(f.x, f.y);
+}
+
+
 template <typename R, typename L, int RR, int VEC>
 __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
                                                       const L* __restrict__ links, const int* __restrict__ nbr,
                                                       int Vc, int nb, int ld, int nrhs, int mode, int hopdir,
-                                                      BlockInfoC bi) {
+                                                      BlockInfoC bi, const unsigned char* __restrict__ par) {
   using T = cplx<R>;
   extern __shared__ unsigned char smem_raw[];
   T* phi = reinterpret_cast<T*>(smem_raw);  // [RR][ld]
@@ -67,7 +78,14 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
     dmask = c_on_face(bi, site, hopdir) ? 1u << (hopdir + 1) : 0u;
   }
   if (dmask == 0u) return;  // uniform over the CTA
-  const bool blockwise = mode != ST_FULL && nb % VEC == 0;
+  if (mode == ST_PARITY && par[site] != hopdir) {  // off-parity site: zero rows
+    for (int idx = threadIdx.x; idx < RR * (row1 - row0); idx += blockDim.x) {
+      const int r = idx / (row1 - row0), row = row0 + idx % (row1 - row0);
+      if (r0 + r < nrhs) out[((long long)(r0 + r) * Vc + site) * nb + row] = czero<R>();
+    }
+    return;
+  }
+  const bool blockwise = (mode == ST_BLOCK_INTERIOR || mode == ST_FACE_HOP) && nb % VEC == 0;
   for (int idx = threadIdx.x; idx < RR * ld; idx += blockDim.x) {
     const int r = idx / ld, k = idx % ld;
     T v = czero<R>();
@@ -687,6 +705,119 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
 
 template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
 
+// ---------------- even-odd coarsest solve: self-block inverses ----------------
+template <typename L>
+__global__ void k_self_invert(double2* __restrict__ inv, const L* __restrict__ links, int nb, int ld,
+                              int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* M = reinterpret_cast<double2*>(smem_raw);  // [nb][2 nb]: [A_0 | 1]
+  __shared__ int piv;
+  const int site = blockIdx.x, w = 2 * nb;
+  for (int idx = threadIdx.x; idx < nb * w; idx += blockDim.x) {
+    const int i = idx / w, j = idx % w;
+    M[idx] = j < nb ? link_to_c64<L>(links[((long long)site * nb + i) * ld + j]) : make_double2(j - nb == i ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    if (threadIdx.x == 0) {  // partial pivoting: the largest |entry| of column k at or below row k
+      int best = k;
+      double bv = -1.0;
+      for (int i = k; i < nb; ++i) {
+        const double v = cnorm2(M[i * w + k]);
+        if (v > bv) { bv = v; best = i; }
+      }
+      piv = best;
+      if (!(bv > 0.0) || !isfinite(bv)) *err = 1;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k)
+      for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        const double2 t = M[k * w + j];
+        M[k * w + j] = M[p * w + j];
+        M[p * w + j] = t;
+      }
+    __syncthreads();
+    const double2 d = M[k * w + k];
+    const double dn = cnorm2(d);
+    const double2 dinv = dn > 0.0 ? make_double2(d.x / dn, -d.y / dn) : make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < w; j += blockDim.x) M[k * w + j] = cmul(dinv, M[k * w + j]);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * w; idx += blockDim.x) {
+      const int i = idx / w, j = idx % w;
+      if (i != k) cnmac(M[idx], M[i * w + k], M[k * w + j]);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    inv[(long long)site * nb * nb + idx] = M[i * w + nb + j];
+  }
+}
+
+template <typename L>
+void launch_self_invert(double2* inv, const L* links, int Vc, int nb, int* err, cudaStream_t st) {
+  const size_t smem = (size_t)nb * 2 * nb * sizeof(double2);
+  auto kern = k_self_invert<L>;
+  WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<Vc, 256, smem, st>>>(inv, links, nb, links_ld(nb), err);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_blockinv_apply(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                 const cplx<R>* __restrict__ inv, const unsigned char* __restrict__ par, int p, int Vc,
+                                 int nb) {
+  const int site = blockIdx.x, r = blockIdx.y;
+  const cplx<R>* x = in + ((long long)r * Vc + site) * nb;
+  cplx<R>* y = out + ((long long)r * Vc + site) * nb;
+  const bool on = par[site] == p;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    cplx<R> acc = czero<R>();
+    if (on) {
+      const cplx<R>* row = inv + ((long long)site * nb + i) * nb;
+      for (int j = 0; j < nb; ++j) cmac(acc, row[j], x[j]);
+    }
+    y[i] = acc;
+  }
+}
+
+template <typename R>
+void launch_blockinv_apply(cplx<R>* out, const cplx<R>* in, const cplx<R>* inv, const unsigned char* par, int p,
+                           int Vc, int nb, int nrhs, cudaStream_t st) {
+  k_blockinv_apply<R><<<dim3(Vc, nrhs), 64, 0, st>>>(out, in, inv, par, p, Vc, nb);
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename R>
+__global__ void k_parity_axpy(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ a, const cplx<R>* __restrict__ b,
+                              R beta, const unsigned char* __restrict__ par, int p, int Vc, int nb, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int site = (int)((i / nb) % Vc);
+  out[i] = par[site] == p ? a[i] + beta * b[i] : czero<R>();
+}
+
+template <typename R>
+void launch_parity_axpy(cplx<R>* out, const cplx<R>* a, const cplx<R>* b, double beta, const unsigned char* par, int p,
+                        int Vc, int nb, int nrhs, cudaStream_t st) {
+  const long long n = (long long)nrhs * Vc * nb;
+  k_parity_axpy<R><<<nblk(n, 256), 256, 0, st>>>(out, a, b, (R)beta, par, p, Vc, nb, n);
+  WCMG_LAUNCH_CHECK();
+}
+
+template void launch_self_invert<double2>(double2*, const double2*, int, int, int*, cudaStream_t);
+template void launch_self_invert<float2>(double2*, const float2*, int, int, int*, cudaStream_t);
+#define WCMG_INST_EO(R)                                                                                         \
+  template void launch_blockinv_apply<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, const unsigned char*, int, int, \
+                                         int, int, cudaStream_t);                                               \
+  template void launch_parity_axpy<R>(cplx<R>*, const cplx<R>*, const cplx<R>*, double, const unsigned char*, int, \
+                                      int, int, int, cudaStream_t);
+WCMG_INST_EO(double)
+WCMG_INST_EO(float)
+#undef WCMG_INST_EO
+
 template <typename R, typename L, int RR>
 static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
                             int mode, int hopdir, int parts, cudaStream_t st) {
@@ -708,8 +839,9 @@ static void coarse_apply_rr(cplx<R>* out, const cplx<R>* in, const L* links, con
   const int rpc = (nb + parts - 1) / parts;
   const int rpw = (rpc + 15) / 16;  // rows per warp, at most 16 warps
   const int threads = std::max(64, 32 * ((rpc + rpw - 1) / rpw));
+  if (mode == ST_PARITY && !g.par) throw Error(-1, "coarse apply: parity mode needs the site parities");
   kern<<<dim3(g.V * parts, ncta_y), threads, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, nrhs, mode, hopdir,
-                                                          bi);
+                                                          bi, g.par);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -940,16 +1072,6 @@ __global__ void k_pack_links(L* __restrict__ links, const double2* __restrict__ 
     }
     links[(long long)s * nb * ld + idx] = link_store<L>(v);
   }
-}
-
-template <typename L> __device__ __forceinline__ double2 link_to_c64(const L& l);
-template <> __device__ __forceinline__ double2 link_to_c64<double2>(const double2& l) { return l; }
-template <> __device__ __forceinline__ double2 link_to_c64<float2>(const float2& l) { return make_double2(l.x, l.y); }
-template <> __device__ __forceinline__ double2 link_to_c64<bf16c>(const bf16c& l) {
-  float2 f = __bfloat1622float2(l.v); return make_double2(f.x, f.y);
-}
-template <> __device__ __forceinline__ double2 link_to_c64<f16c>(const f16c& l) {
-  float2 f = __half22float2(l.v); return make_double2(f.x, f.y);
 }
 
 template <typename L>

@@ -12,9 +12,12 @@ struct LevelGeom {
   const int* nbr;   // [8][V] storage index of x + mu (2 mu) and x - mu (2 mu + 1)
   int b[4];         // aggregate extents towards the next level (1s on the coarsest)
   int bvol;         // b0 * b1 * b2 * b3
+  const unsigned char* par = nullptr;  // [V] site parity (x + y + z + t) % 2 (ST_PARITY)
 };
 
-enum StencilMode { ST_FULL = 0, ST_BLOCK_INTERIOR = 1, ST_FACE_HOP = 2 };
+// ST_PARITY (coarse levels): the full nine-point stencil on the sites whose parity is
+// `hopdir`, zero on the others (the even-odd Schur complement of the coarsest solve).
+enum StencilMode { ST_FULL = 0, ST_BLOCK_INTERIOR = 1, ST_FACE_HOP = 2, ST_PARITY = 3 };
 
 // ---- fine level (fine.cu) ----
 template <typename R>
@@ -91,6 +94,18 @@ void launch_make_columns(cplx<R>* cols, const cplx<R>* vecs, int Vf, int nc, int
                          cudaStream_t st);
 
 // ---- coarse levels (coarse.cu) ----
+// Even-odd coarsest solve: inv[x] = A_0(x)^-1 (row-major nb x nb, FP64) of every site by
+// Gauss-Jordan with partial pivoting; *err = 1 on a singular block.
+template <typename L>
+void launch_self_invert(double2* inv, const L* links, int Vc, int nb, int* err, cudaStream_t st);
+// out[x] = inv[x] in[x] on the sites of parity p, 0 elsewhere (nrhs fields [nrhs][Vc][nb]).
+template <typename R>
+void launch_blockinv_apply(cplx<R>* out, const cplx<R>* in, const cplx<R>* inv, const unsigned char* par, int p,
+                           int Vc, int nb, int nrhs, cudaStream_t st);
+// out = a + beta b on the sites of parity p, 0 elsewhere.
+template <typename R>
+void launch_parity_axpy(cplx<R>* out, const cplx<R>* a, const cplx<R>* b, double beta, const unsigned char* par, int p,
+                        int Vc, int nb, int nrhs, cudaStream_t st);
 // Coarse links: per site a row-major nb x ld matrix, ld = round_up(9 nb, 4),
 // column d*nb + c of row a holds A_d(x)[a][c].
 inline int links_ld(int nb) { return (9 * nb + 3) / 4 * 4; }

@@ -646,7 +646,7 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __device__ __forceinline__ double df_to_fast(dfr a) { return f2d_exact(a.h) + f2d_exact(a.l); }
 
 template <int MAXE>
-__global__ void __launch_bounds__(256, 2) k_block_ortho_df(double2* __restrict__ vecs, float4* __restrict__ qdf, int Vf,
+__global__ void __launch_bounds__(256, 3) k_block_ortho_df(double2* __restrict__ vecs, float4* __restrict__ qdf, int Vf,
                                                         int nc, int bvol, int nvec, bool fine, int* __restrict__ err) {
   constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
   __shared__ dfc scratch[8][MV];

@@ -68,10 +68,12 @@ struct HostGeom {
   int bvol = 1;
   std::vector<int> perm, inv, nbr;
   DevBuf<int> d_perm, d_nbr;
+  DevBuf<unsigned char> d_par;  // site parity (x + y + z + t) % 2 in storage order
   LevelGeom lg() const {
     LevelGeom g;
     g.V = V;
     g.nbr = d_nbr.p;
+    g.par = d_par.p;
     for (int k = 0; k < 4; ++k) g.b[k] = b[k];
     g.bvol = bvol;
     return g;
@@ -148,6 +150,9 @@ struct Level {
   DevBuf<bf16c> Lbf;
   DevBuf<bf16c> Lmma;  // BF16 links in the tcgen05 operand order (kind-4 coarse apply)
   bool mma_valid = false;
+  DevBuf<double2> Ainv64;  // even-odd coarsest solve: A_0(x)^-1 per site (FP64, FP32 copy)
+  DevBuf<float2> Ainv32;
+  bool ainv_valid = false;
   DevBuf<f16c> Lh;
   bool L32_valid = false, low_valid = false;
   LevelScalars sc;
@@ -229,6 +234,7 @@ struct wcmg_ctx {
   Prof prof;
   long long opc[WCMG_NOPC][WCMG_MAX_LEVELS] = {};  // operator applications (wcmg_get_opcounts)
   bool in_coarsen = false;                         // the coarsening's stencils and restrictions are its own
+  bool eo_schur = false;                           // the coarsest GMRES is running on the Schur complement
   cudaStream_t st = nullptr;
   long long coarse_its = 0;
   // learned coarse correction (PTC network)
@@ -527,8 +533,55 @@ static const CoarseTile* coarse_tile(wcmg_ctx* c, int l, const Lt* links, int nr
 // ---------------- operators ----------------
 template <typename R>
 static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nrhs, int mode = ST_FULL,
-                     int hopdir = 0) {
+                     int hopdir = 0);
+
+// Even-odd coarsest solve (Sec. 4 red-black preconditioning): the parity-restricted
+// nine-point stencil, the self-block inverses and the odd-site Schur complement
+//   S v = [D (v - A_ee^-1 [D v]_e)]_o   (v vanishing on the even sites)
+// = A_oo v_o - A_oe A_ee^-1 A_eo v_o, zero on the even sites.
+template <typename R>
+static void apply_parity(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nrhs, int parity) {
+  apply_op<R>(c, l, out, in, nrhs, ST_PARITY, parity);
+}
+static void ensure_ainv(wcmg_ctx* c, int l) {
   Level& L = c->L[l];
+  if (L.ainv_valid) return;
+  if (c->capturing) throw Error(WCMG_ERR_STATE, "self-block inverses built inside a capture");
+  const int nb = L.nc;
+  L.Ainv64.ensure((size_t)L.g.V * nb * nb);
+  L.Ainv32.ensure((size_t)L.g.V * nb * nb);
+  WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
+  if (L.op64) launch_self_invert<double2>(L.Ainv64.p, L.L64.p, L.g.V, nb, c->errflag.p, c->st);
+  else launch_self_invert<float2>(L.Ainv64.p, L.L32.p, L.g.V, nb, c->errflag.p, c->st);
+  const int* e = read_ints(c, c->errflag.p, 1);
+  if (e[0]) throw Error(WCMG_ERR_NAN, "singular coarse self block: no even-odd coarsest solve");
+  launch_convert<double, float>(L.Ainv32.p, L.Ainv64.p, (long long)L.g.V * nb * nb, c->st);
+  L.ainv_valid = true;
+}
+template <typename R> static const cplx<R>* ainv_of(Level& L);
+template <> const double2* ainv_of<double>(Level& L) { return L.Ainv64.p; }
+template <> const float2* ainv_of<float>(Level& L) { return L.Ainv32.p; }
+
+template <typename R>
+static void eo_schur_apply(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nrhs) {
+  Level& L = c->L[l];
+  const int nb = L.nc;
+  cplx<R>* t = ws<R>(L, "eo_t", nrhs);
+  cplx<R>* z = ws<R>(L, "eo_z", nrhs);
+  apply_parity<R>(c, l, t, in, nrhs, 0);  // [D v]_e
+  KPROF(c, WCMG_K_COARSE, (double)L.g.V * nb * (nb + 2.0 * nrhs) * sizeof(cplx<R>), 8.0 * L.g.V / 2 * nb * nb * nrhs,
+        launch_blockinv_apply<R>(z, t, ainv_of<R>(L), L.g.d_par.p, 0, L.g.V, nb, nrhs, c->st));
+  launch_axpby<R>(z, 1.0, in, -1.0, L.n(), nrhs, c->st);  // v - A_ee^-1 [D v]_e
+  apply_parity<R>(c, l, out, z, nrhs, 1);
+}
+
+template <typename R>
+static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nrhs, int mode, int hopdir) {
+  Level& L = c->L[l];
+  if (mode == ST_FULL && c->eo_schur && l == c->p.n_levels - 1) {
+    eo_schur_apply<R>(c, l, out, in, nrhs);
+    return;
+  }
   if (mode == ST_FULL && !c->in_coarsen && !c->capturing) c->opc[WCMG_OPC_APPLY][l] += nrhs;
   if (l == 0) {
     if (!c->have_gauge) throw Error(WCMG_ERR_STATE, "gauge field not set");
@@ -1090,6 +1143,53 @@ static void ptc_alloc(wcmg_ctx* c) {
 // ---------------- multigrid cycle ----------------
 // M_l(r): e = P_l CoarseSolve_{l+1}(P_l^dag r); e += MR_k(D_l; r - D_l e).
 // CoarseSolve is GMRES at the coarsest level and one cycle of level l+1 between.
+// The coarsest solve: GMRES on D_c, or with params.coarse_eo on the odd-site Schur
+// complement: b^_o = [b - D A_ee^-1 b_e]_o, GMRES on S to the coarse tolerance of
+// ||b^_o||, x_e = A_ee^-1 [b - D x_o]_e.
+template <typename R>
+static void coarsest_gmres(wcmg_ctx* c, int lc, cplx<R>* x, const cplx<R>* b, int nrhs, bool x0) {
+  if (c->capturing) {
+    fgmres_g<R>(c, lc, x, b, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter, !x0, false, false, 0,
+                c->kctl.p + 2 + lc, nullptr, 0, c->gstat.p + 1);
+  } else {
+    KrylovOut k = fgmres<R>(c, lc, x, b, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter, !x0, false,
+                            false);
+    c->coarse_its += k.iterations;
+  }
+}
+template <typename R>
+static void coarsest_solve(wcmg_ctx* c, int lc, cplx<R>* x, const cplx<R>* b, int nrhs, bool x0) {
+  if (!c->p.coarse_eo) {
+    coarsest_gmres<R>(c, lc, x, b, nrhs, x0);
+    return;
+  }
+  Level& C = c->L[lc];
+  ensure_ainv(c, lc);
+  const int nb = C.nc;
+  const unsigned char* par = C.g.d_par.p;
+  cplx<R>* bh = ws<R>(C, "eo_b", nrhs);
+  cplx<R>* u = ws<R>(C, "eo_u", nrhs);
+  cplx<R>* y = ws<R>(C, "eo_y", nrhs);
+  KPROF(c, WCMG_K_COARSE, 0.0, 0.0,
+        launch_blockinv_apply<R>(u, b, ainv_of<R>(C), par, 0, C.g.V, nb, nrhs, c->st));  // A_ee^-1 b_e
+  apply_parity<R>(c, lc, y, u, nrhs, 1);                                             // [D A_ee^-1 b_e]_o
+  launch_parity_axpy<R>(bh, b, y, -1.0, par, 1, C.g.V, nb, nrhs, c->st);             // b^_o
+  if (x0) launch_parity_axpy<R>(x, x, x, 0.0, par, 1, C.g.V, nb, nrhs, c->st);        // odd part of the guess
+  c->eo_schur = true;
+  try {
+    coarsest_gmres<R>(c, lc, x, bh, nrhs, x0);
+  } catch (...) {
+    c->eo_schur = false;
+    throw;
+  }
+  c->eo_schur = false;
+  apply_parity<R>(c, lc, y, x, nrhs, 0);                                             // [D x_o]_e
+  launch_parity_axpy<R>(u, b, y, -1.0, par, 0, C.g.V, nb, nrhs, c->st);              // [b - D x_o]_e
+  KPROF(c, WCMG_K_COARSE, 0.0, 0.0,
+        launch_blockinv_apply<R>(y, u, ainv_of<R>(C), par, 0, C.g.V, nb, nrhs, c->st));  // x_e
+  launch_axpby<R>(x, 1.0, y, 1.0, C.n(), nrhs, c->st);
+}
+
 template <typename R>
 static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
   Level& L = c->L[l];
@@ -1114,14 +1214,7 @@ static void cycle(wcmg_ctx* c, int l, cplx<R>* e, const cplx<R>* r, int nrhs) {
         ++c->learned_cycles;
         x0 = true;
       }
-      if (c->capturing) {
-        fgmres_g<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol, c->p.coarse_maxiter, !x0, false,
-                    false, 0, c->kctl.p + 2 + (l + 1), nullptr, 0, c->gstat.p + 1);
-      } else {
-        KrylovOut k = fgmres<R>(c, l + 1, ec, rc, nrhs, c->p.coarse_restart, c->p.coarse_tol,
-                                c->p.coarse_maxiter, !x0, false, false);
-        c->coarse_its += k.iterations;
-      }
+      coarsest_solve<R>(c, l + 1, ec, rc, nrhs, x0);
     } else if (c->p.kcycle) {
       // K-cycle: a short FGMRES on the intermediate level, preconditioned by its cycle
       const int ks = c->p.kcycle_steps;
@@ -1205,6 +1298,7 @@ static void coarsen_body(wcmg_ctx* c, int l) {
     }
   }
   C.have_op = true;
+  C.ainv_valid = false;
   C.low_valid = false;
   if (sizeof(R) == 4 && (c->p.coarse_link_prec == WCMG_BF16 || c->p.coarse_link_prec == WCMG_F16)) {
     if (c->p.coarse_link_prec == WCMG_BF16) {
@@ -1217,6 +1311,9 @@ static void coarsen_body(wcmg_ctx* c, int l) {
     }
     C.low_valid = true;
   }
+  // the even-odd coarsest solve's self-block inverses follow every new coarsest operator
+  // (built here, outside any capture, so that a replayed solve never sees stale ones)
+  if (c->p.coarse_eo && l + 1 == c->p.n_levels - 1) ensure_ainv(c, l + 1);
 }
 
 template <typename R>
@@ -1876,6 +1973,7 @@ int wcmg_default_params(wcmg_params* p) {
   p->sap_cycles = 1;
   p->sap_eo = 0;
   p->ortho_df = 0;
+  p->coarse_eo = 0;
   return WCMG_OK;
 }
 
@@ -1902,6 +2000,7 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
     if (p->sap_cycles < 1 || p->sap_cycles > 16) throw Error(WCMG_ERR_ARG, "sap_cycles must be 1..16");
     if (p->sap_eo != 0 && p->sap_eo != 1) throw Error(WCMG_ERR_ARG, "sap_eo must be 0 or 1");
     if (p->ortho_df != 0 && p->ortho_df != 1) throw Error(WCMG_ERR_ARG, "ortho_df must be 0 or 1");
+    if (p->coarse_eo != 0 && p->coarse_eo != 1) throw Error(WCMG_ERR_ARG, "coarse_eo must be 0 or 1");
     if (p->sap_eo) {
       const int* fb = p->block[0];
       const int bv = fb[0] * fb[1] * fb[2] * fb[3];
@@ -1937,6 +2036,11 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
         if (L.g.bvol * (L.nc / 2) > 2048) throw Error(WCMG_ERR_ARG, "aggregate panel larger than 2048 rows");
       }
     }
+    if (p->coarse_eo) {
+      const HostGeom& Gc = c->L[nl - 1].g;
+      for (int k = 0; k < 4; ++k)
+        if (Gc.dims[k] % 2) throw Error(WCMG_ERR_ARG, "coarse_eo needs even extents of the coarsest lattice");
+    }
     // storage orders, coarsest first
     for (int l = nl - 1; l >= 0; --l) {
       HostGeom& G = c->L[l].g;
@@ -1970,6 +2074,16 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
       }
       G.d_perm.ensure(G.V);
       G.d_nbr.ensure((size_t)8 * G.V);
+      {
+        std::vector<unsigned char> par(G.V);
+        for (int st = 0; st < G.V; ++st) {
+          int x[4];
+          coords(G.perm[st], G.dims, x);
+          par[st] = (unsigned char)((x[0] + x[1] + x[2] + x[3]) & 1);
+        }
+        G.d_par.ensure(G.V);
+        WCMG_CUDA(cudaMemcpy(G.d_par.p, par.data(), G.V, cudaMemcpyHostToDevice));
+      }
       WCMG_CUDA(cudaMemcpy(G.d_perm.p, G.perm.data(), sizeof(int) * G.V, cudaMemcpyHostToDevice));
       WCMG_CUDA(cudaMemcpy(G.d_nbr.p, G.nbr.data(), sizeof(int) * 8 * G.V, cudaMemcpyHostToDevice));
       if (l + 1 < nl) {
@@ -2238,6 +2352,8 @@ int wcmg_set_coarse_links(wcmg_ctx* c, int level, const void* A, int where, void
     }
   }
   L.have_op = true;
+  L.ainv_valid = false;
+  if (c->p.coarse_eo && level == c->p.n_levels - 1) ensure_ainv(c, level);
   WCMG_CUDA(cudaStreamSynchronize(c->st));
   API_END(c)
 }

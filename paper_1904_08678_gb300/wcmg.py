@@ -70,6 +70,7 @@ class wcmg_params(ctypes.Structure):
         ("sap_cycles", ctypes.c_int),
         ("sap_eo", ctypes.c_int),
         ("ortho_df", ctypes.c_int),
+        ("coarse_eo", ctypes.c_int),
     ]
 
 

@@ -277,3 +277,63 @@ def test_seeded_setup_draws_the_fields_of_the_input_generator(lib):
             ctx.get_nullvecs(1, P1)
             P.append((host(P0), host(P1)))
         assert rel_norm(P[1][0], P[0][0]) < tol and rel_norm(P[1][1], P[0][1]) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32_inner"])
+def test_even_odd_coarsest_solve_matches_oracle(lib, prec):
+    """coarse_eo: the coarsest GMRES runs on the odd-site Schur complement (Sec. 4
+    red-black preconditioning).  The MG cycle equals the oracle's cycle with the same
+    even-odd coarsest solve; the solve reaches the oracle's solution."""
+    ctx, D = config1_ctx(lib, prec=prec, coarse_eo=1)
+    iv = inputs.setup_vectors(DIMS, 12, NVEC, 0, 1001)
+    ctx.setup(dev(iv))
+    mg = oracle_mg(D, iv, coarse_eo=True)
+    V = 256
+    r = inputs.complex_gaussian(27, 0, (1, V, 12))
+    e = dev(np.zeros_like(r))
+    ctx.mg_cycle(dev(r), e)
+    ref = mg.cycle(0, fields(r, DIMS, 12)[0]).reshape(V, 12)
+    assert rel(host(e)[0], ref) < (1e-9 if prec == 0 else 1e-4)
+    b = inputs.source(DIMS, 0)
+    x = dev(np.zeros_like(b))
+    st = ctx.solve(dev(b), x)
+    assert st.converged and st.true_residual <= 1e-10
+    xo, info = mg.solve(fields(b, DIMS, 12)[0])
+    assert rel(host(x)[0].reshape(V, 12), xo.reshape(V, 12)) < 1e-8
+    if prec == 0:
+        assert abs(st.outer_iterations - info.iterations) <= 1
+
+
+def test_even_odd_coarsest_solve_three_levels_and_graph_replay(lib):
+    """Three levels (8^4 -> 4^4 -> 2^4) with the even-odd coarsest solve: the cycle equals
+    the oracle's; FP32 inner levels under CUDA-graph replay reproduce the host-driven
+    solve."""
+    dims = (8, 8, 8, 8)
+    kw = dict(dims=dims, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvec=[6, 4], n_levels=3, m0=-0.1, csw=1.0, coarse_eo=1)
+    U = inputs.random_gauge(dims, 0.3, 1061)
+    iv0 = inputs.setup_vectors(dims, 12, 6, 0, 1061)
+    iv1 = inputs.setup_vectors((4, 4, 4, 4), 12, 4, 1, 1061)
+    ctx = lib.Context(lib.default_params(**kw))
+    ctx.set_gauge(dev(U))
+    ctx.setup(dev(np.concatenate([iv0.ravel(), iv1.ravel()])))
+    D = WilsonClover(U, dims, -0.1, 1.0)
+    mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nvecs=[6, 4], coarse_eo=True),
+                   [fields(iv0, dims, 12), fields(iv1, (4, 4, 4, 4), 12)])
+    V = 4096
+    r = inputs.complex_gaussian(28, 0, (1, V, 12))
+    e = dev(np.zeros_like(r))
+    ctx.mg_cycle(dev(r), e)
+    assert rel(host(e)[0], mg.cycle(0, fields(r, dims, 12)[0]).reshape(V, 12)) < 1e-9
+    g = lib.Context(lib.default_params(inner_prec=lib.F32, use_graphs=1, **kw))
+    g.set_gauge(dev(U))
+    g.setup(dev(np.concatenate([iv0.ravel(), iv1.ravel()])))
+    b = inputs.source(dims, 0)
+    runs = []
+    for _ in range(3):
+        x = dev(np.zeros_like(b))
+        runs.append((g.solve(dev(b), x), host(x)))
+    assert [st.graph for st, _ in runs] == [0, 1, 1]
+    for st, x in runs:
+        assert st.converged and st.true_residual <= 1e-10
+        assert st.outer_iterations == runs[0][0].outer_iterations
+        assert rel(x, runs[0][1]) < 1e-13

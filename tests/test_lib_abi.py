@@ -71,3 +71,14 @@ def test_new_boundary_calls_reject_null_context_without_gpu_work():
     assert wcmg.wcmg_solve_ex(None, None, None, 1, ctypes.byref(o), wcmg.DEVICE, None, None) == wcmg.ERR_ARG
     assert wcmg.wcmg_save_net(None, b"x") == wcmg.ERR_ARG
     assert wcmg.wcmg_load_net(None, b"x") == wcmg.ERR_ARG
+
+
+def test_even_odd_coarsest_solve_needs_even_coarse_extents_without_gpu_work():
+    """coarse_eo is rejected when the coarsest lattice has an odd extent (a hop across its
+    periodic boundary would join sites of equal parity)."""
+    wcmg = pytest.importorskip("paper_1904_08678_gb300.wcmg")
+    h = ctypes.c_void_p()
+    p = wcmg.default_params(dims=(4, 4, 4, 6), blocks=[(2, 2, 2, 2)], nvec=[4], coarse_eo=1)  # coarse t = 3
+    assert wcmg.wcmg_create(ctypes.byref(p), ctypes.byref(h)) == wcmg.ERR_ARG
+    p = wcmg.default_params(coarse_eo=2)
+    assert wcmg.wcmg_create(ctypes.byref(p), ctypes.byref(h)) == wcmg.ERR_ARG
