@@ -268,7 +268,7 @@ def make_inputs(cfg, nrhs=None):
 
 def params(wcmg, cfg, inner, links=None, profile=0, graphs=0, autotune=1, nrhs=None):
     links = links or cfg.get("links", "f32")
-    ortho_df = int(cfg.get("ortho", "fp64") == "df")
+    ortho_df = int(cfg.get("ortho", "fp64") == "df" and inner == "f32")  # plain FP64 MG: FP64 throughout
     coarse_eo = int(cfg.get("coarse_eo", 0))
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
@@ -606,17 +606,17 @@ def sub_records(env, args):
     """The other workloads, a few timed steps each (3 warm-up steps, --sub-steps timed)."""
     k = args.sub_steps
     out = {}
-    c2 = dict(WORKLOADS["c2"])
+    c2 = dict(WORKLOADS["c2"], ortho=args.ortho)
     r = measure(env, c2, k, 3, e2e_steps=k, fp64=True, roofline=False)
     r["workload"] = c2["workload"]
     r["learned"] = learned_variant(env, c2, args)
     out["c2"] = r
-    c4 = dict(WORKLOADS["c4"])
+    c4 = dict(WORKLOADS["c4"], ortho=args.ortho)
     out["c4"] = {"workload": c4["workload"].replace("NRHS", "12 or 48")}
     for nr in (12, 48):
         out["c4"][f"rhs{nr}"] = measure(env, c4, k, 3, nrhs=nr, fp64=(nr == 12), roofline=False)
     out["c4"]["uneven_batch"] = measure_uneven_batch(env, args)
-    c5 = dict(WORKLOADS["c5"])
+    c5 = dict(WORKLOADS["c5"], ortho=args.ortho)
     out["c5"] = {"workload": c5["workload"].replace("POOLS", str(args.pools))}
     out["c5"].update(learned_c5(env, c5, args))
     return out
@@ -665,7 +665,7 @@ def learned_c5(env, cfg, args, reps=3):
     place of the coarse correction and as a warm start of the coarsest GMRES, against
     plain FP32 and FP64 multigrid on the same field, source and seeded setup."""
     torch, wcmg, stream, flush = env.torch, env.wcmg, env.stream, env.flush
-    src = dict(WORKLOADS[cfg["learned_from"]])
+    src = dict(WORKLOADS[cfg["learned_from"]], ortho=cfg.get("ortho", "fp64"))
     tr = dict(cfg["train"])
     Us, _ = make_inputs(src)
     c = wcmg.Context(params(wcmg, src, "f32", profile=0))
@@ -850,7 +850,7 @@ def measure_uneven_batch(env, args, reps=5):
     sets = {"f32_graph": [], "f32_host": [], "f64_host": []}
     bs, xs = [], []
     for k, dims in enumerate(ub["lattices"]):
-        cfg = dict(WORKLOADS["c2"], dims=dims, nrhs=nr, gauge_seed=1040 + k)
+        cfg = dict(WORKLOADS["c2"], dims=dims, nrhs=nr, gauge_seed=1040 + k, ortho=args.ortho)
         U, _ = make_inputs(cfg)
         b = inputs.source(dims, k, nrhs=nr)
         Ud = env.to_dev(U)
@@ -1185,8 +1185,9 @@ def main(argv=None):
     ap.add_argument("--sap-eo", action="store_true", help="SAP: even-odd preconditioned block solves (fine level)")
     ap.add_argument("--pools", type=int, default=417,
                     help="c5: training pools of 48 fresh pairs (417 pools = 20016 pairs)")
-    ap.add_argument("--ortho", default="fp64", choices=["fp64", "df"],
-                    help="block orthonormalisation arithmetic: FP64, or double-float on the FP32 pipe")
+    ap.add_argument("--ortho", default="df", choices=["fp64", "df"],
+                    help="block orthonormalisation arithmetic of the FP32-inner runs: double-float on the FP32 "
+                         "pipe (default; the same Q to 1e-14) or FP64; plain FP64 multigrid always uses FP64")
     ap.add_argument("--probe", default=None,
                     help="kernel probe for ncu instead of the bench: 'ortho' (the fine-level block "
                          "orthonormalisation of Nvec Gaussian fields, 3 times) or 'coarse:LEVEL:NRHS[:KIND:THREADS:"
