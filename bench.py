@@ -331,9 +331,10 @@ def measure(env, cfg, steps, warmup, nrhs=None, inner="f32", graphs=1, autotune=
             clocks=None, roofline=True, extra=None):
     """Time `steps` steps (set_gauge + seeded setup + solve) of workload cfg after
     `warmup` untimed ones.  The first warm-up step runs host-driven (the solve graph is
-    captured on the second) and every kernel class is event-timed during the warm-up;
-    in the timed steps only the dominant class is, for the roofline.  Returns the
-    fields of a bench line (or sub-record)."""
+    captured on the second) and every kernel class is event-timed during the warm-up.
+    The timed steps run with no per-launch timing; after them, up to two more steps
+    time every launch of the dominant class for the roofline.  Returns the fields of a
+    bench line (or sub-record)."""
     torch, wcmg, stream, flush = env.torch, env.wcmg, env.stream, env.flush
     nrhs = nrhs or cfg.get("nrhs", 1)
     U, b = make_inputs(cfg, nrhs)
@@ -360,7 +361,7 @@ def measure(env, cfg, steps, warmup, nrhs=None, inner="f32", graphs=1, autotune=
     torch.cuda.synchronize()
     warm_ms = {k: round(v[1] / warmup, 3) for k, v in acc.items() if v[1] > 0}
     dominant = max(acc, key=lambda k: acc[k][1])
-    ctx.set_profile((1 << KCLASS.index(dominant)) if roofline else 0)
+    ctx.set_profile(0)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -398,7 +399,6 @@ def measure(env, cfg, steps, warmup, nrhs=None, inner="f32", graphs=1, autotune=
             clocks.__exit__(None, None, None)
     t_wall = time.perf_counter() - t_wall
     barrier(env.dist, env.local)
-    ctx.set_profile(0)
     step_ms = [starts[i].elapsed_time(ends[i]) for i in range(steps)]
     ms = max_over_ranks(env.dist, sum(step_ms) / len(step_ms), env.dev)
     med = lambda v: round(statistics.median(v), 2)
@@ -412,8 +412,16 @@ def measure(env, cfg, steps, warmup, nrhs=None, inner="f32", graphs=1, autotune=
            "nrhs": nrhs, "inner_prec": inner, "coarse_links": cfg.get("links", "f32") if inner == "f32" else "f64"}
 
     if roofline:
-        out["roofline"] = roofline_of(acc, dominant, ms, steps, cfg.get("ortho") == "df")
-        out["kernel_shares_timed"] = {dominant: round(acc[dominant][1] / (ms * steps), 4)}
+        # the roofline pass: the dominant class's launches event-timed, outside the timed steps
+        ctx.set_profile(1 << KCLASS.index(dominant))
+        racc, rms, rsteps = {}, 0.0, min(2, steps)
+        for i in range(rsteps):
+            (s1, s2), t = timed_call(torch, stream, flush, lambda: step(xd, Ud, bd), i)
+            add_stats(racc, s1)
+            add_stats(racc, s2)
+            rms += t
+        ctx.set_profile(0)
+        out["roofline"] = roofline_of(racc, dominant, rms / rsteps, rsteps, cfg.get("ortho") == "df")
     co = first_solve.k[KCLASS.index("coarse")]
     out["coarse_in_first_solve"] = {
         "launches": co.launches, "avg_launch_us": round(co.ms / max(co.launches, 1) * 1e3, 2),
@@ -483,7 +491,8 @@ def roofline_of(acc, dominant, ms, steps, ortho_df=False):
             "launches": d[0], "avg_launch_us": round(d[1] / max(d[0], 1) * 1e3, 2),
             "algorithmic_bytes_per_launch": d[2] / max(d[0], 1), "algorithmic_flops_per_launch": d[3] / max(d[0], 1),
             "share_of_step": round(d[1] / (ms * steps), 4),
-            "timing": "CUDA-event pair around every launch of this class in the timed steps (the library's stream)"}
+            "timing": f"CUDA-event pair around every launch of this class (the library's stream) in {steps} extra "
+                      "step(s) after the timed ones; the timed steps carry no per-launch events"}
 
 
 def fp64_reference(env, cfg, Ud, bd, nrhs, graphs=1):
@@ -1111,6 +1120,13 @@ def run_probe(args, local):
     if args.links:
         cfg["links"] = args.links
     cfg["ortho"] = args.ortho
+    if args.probe_fine:
+        # a smaller fine lattice whose first blocking gives the same coarse levels (the
+        # coarse applies' shapes and bytes unchanged, the device memory much smaller)
+        d, b = args.probe_fine.split("/")
+        cfg["dims"] = tuple(int(x) for x in d.split("x"))
+        cfg["blocks"] = [tuple(int(x) for x in b.split("x"))] + list(cfg["blocks"][1:])
+        cfg["workload"] += f"; fine lattice replaced by {d} with blocks {b} for the probe"
     from paper_1904_08678_gb300 import inputs
     ld = level_dims(cfg)
     out = {"probe": args.probe, "workload": cfg["workload"], "ortho": args.ortho}
@@ -1140,9 +1156,13 @@ def run_probe(args, local):
         ctx.apply_coarse(lev, phi, y, nrhs=nr, prec=wcmg.F32, stream=stream)  # autotune (unless forced)
         ctx.set_profile(1 << KCLASS.index("coarse"))
         k0 = ctx.kstats()["coarse"]
+        if args.ncu_region:
+            torch_.cuda.profiler.start()  # ncu --profile-from-start off: the timed applies only
         ms = [timed_call(torch_, stream, env.flush,
                          lambda: ctx.apply_coarse(lev, phi, y, nrhs=nr, prec=wcmg.F32, stream=stream), i)[1]
               for i in range(5)]
+        if args.ncu_region:
+            torch_.cuda.profiler.stop()
         k1 = ctx.kstats()["coarse"]
         n = max(k1["launches"] - k0["launches"], 1)
         kus = (k1["ms"] - k0["ms"]) / n * 1e3
@@ -1193,9 +1213,12 @@ def main(argv=None):
                          "orthonormalisation of Nvec Gaussian fields, 3 times) or 'coarse:LEVEL:NRHS[:KIND:THREADS:"
                          "PARTS:STAGES:NTILE]' (5 coarse applies after one setup with the autotuned or the given "
                          "launch shape); prints one JSON line of CUDA-event times")
+    ap.add_argument("--probe-fine", default=None,
+                    help="probe only: replace the fine lattice and its blocking, e.g. 12x12x12x24/2x2x2x2 keeps "
+                         "the 24^3x48 workload's 6^3x12 level 1 on a fine lattice 8x smaller")
     ap.add_argument("--ncu-region", action="store_true",
-                    help="bracket the timed steps of the headline workload with cudaProfilerStart/Stop "
-                         "(for ncu --profile-from-start off)")
+                    help="bracket the timed steps of the headline workload (or a coarse probe's timed applies) "
+                         "with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
