@@ -270,6 +270,7 @@ def params(wcmg, cfg, inner, links=None, profile=0, graphs=0, autotune=1, nrhs=N
     links = links or cfg.get("links", "f32")
     ortho_df = int(cfg.get("ortho", "fp64") == "df" and inner == "f32")  # plain FP64 MG: FP64 throughout
     coarse_eo = int(cfg.get("coarse_eo", 0))
+    sigma3 = int(cfg.get("sigma3", 0))
     p = wcmg.default_params(dims=cfg["dims"], blocks=cfg["blocks"], nvec=cfg["nvec"], m0=cfg["m0"], csw=cfg["csw"],
                             setup_init_sweeps=cfg["init_sweeps"], setup_refine_sweeps=cfg["refine_sweeps"],
                             n_levels=len(cfg["blocks"]) + 1, max_rhs=nrhs or cfg.get("nrhs", 1), profile=profile,
@@ -278,7 +279,8 @@ def params(wcmg, cfg, inner, links=None, profile=0, graphs=0, autotune=1, nrhs=N
                                       "sap": wcmg.SMOOTHER_SAP}[cfg.get("smoother", "mr")],
                             sap_cycles=int(cfg.get("sap_cycles", 1)), sap_eo=int(cfg.get("sap_eo", 0)),
                             smoother_steps=int(cfg.get("smoother_steps", 4)),
-                            kcycle=int(cfg.get("kcycle", 0)), ortho_df=ortho_df, coarse_eo=coarse_eo)
+                            kcycle=int(cfg.get("kcycle", 0)), ortho_df=ortho_df, coarse_eo=coarse_eo,
+                            coarse_sigma3=sigma3)
     p.inner_prec = {"f64": wcmg.F64, "f32": wcmg.F32}[inner]
     p.coarse_link_prec = {"f32": wcmg.F32, "bf16": wcmg.BF16, "f16": wcmg.F16}[links]
     return p
@@ -532,6 +534,9 @@ def run_gpu(args, rank, world, local):
     if args.coarse_eo:
         cfg["coarse_eo"] = 1
         cfg["workload"] = cfg["workload"] + ", even-odd preconditioned coarsest solve"
+    if args.sigma3:
+        cfg["sigma3"] = 1
+        cfg["workload"] = cfg["workload"] + ", five-block (sigma3) coarse-link copies available to the autotuner"
     if args.kcycle:
         cfg["kcycle"] = 1
         cfg["workload"] = cfg["workload"] + ", K-cycle (FGMRES(5) to 0.1 on the intermediate levels)"
@@ -837,8 +842,68 @@ def coarse_isolated_levels(env, ctx, cfg, hbm, refs, reps=200):
                                        "frac_of_hbm": round(copy_gbs / hbm, 4),
                                        "apply_frac_of_copy": round(out["level1"][f"links_{lk}"]["GB/s"] / copy_gbs, 4),
                                        "links": lk}
+    if cfg.get("sigma3"):
+        five_block_isolated(env, ctx, cfg, hbm, out, reps)
     out["l2"] = "flushed before every apply (256 MiB write + 256 MiB read); launch shape from the cold autotuner"
     return out
+
+
+def five_block_isolated(env, ctx, cfg, hbm, out, reps):
+    """The one-rhs apply from the five-block storage (launch kind 5) on the workload's own
+    Galerkin links (the headline context, its link storage, FP32 vectors), L2 flushed
+    before every apply: the fastest of its launch shapes, with GB/s of its own bytes
+    V_c (5 nb^2 s_link + 2 nb s_vec) and of the nine-block bytes of the same apply."""
+    torch, wcmg, stream, flush = env.torch, env.wcmg, env.stream, env.flush
+    from paper_1904_08678_gb300 import inputs
+    ld = level_dims(cfg)
+    lk = cfg.get("links", "f32")
+    link_b = {"f32": 8, "bf16": 4, "f16": 4}[lk]
+    ctx.set_profile(1 << KCLASS.index("coarse"))
+    try:
+        for l in range(1, len(cfg["blocks"]) + 1):
+            Vc = int(np.prod(ld[l]))
+            nb = 2 * cfg["nvec"][l - 1]
+            phi = env.to_dev(inputs.complex_gaussian(5, 5, (1, Vc, nb)))
+            y = torch.zeros_like(phi)
+            saved = ctx.get_coarse_tile(l, 1, wcmg.F32)
+
+            def time_apply(n):
+                k0 = ctx.kstats()["coarse"]
+                for _ in range(n):
+                    flush.fill_(5)
+                    ctx.apply_coarse(l, phi, y, prec=wcmg.F32, stream=stream)
+                torch.cuda.synchronize()
+                k1 = ctx.kstats()["coarse"]
+                return (k1["ms"] - k0["ms"]) / max(k1["launches"] - k0["launches"], 1)
+
+            best = None
+            for th in (256, 512):
+                for parts in (1, 2):
+                    for stg in (1, 2):
+                        ctx.set_coarse_tile(l, 1, wcmg.F32, kind=5, threads=th, parts=parts, stages=stg)
+                        time_apply(3)
+                        kms = time_apply(20)
+                        if best is None or kms < best[0]:
+                            best = (kms, dict(threads=th, parts=parts, stages=stg))
+            ctx.set_coarse_tile(l, 1, wcmg.F32, kind=5, **best[1])
+            kms = time_apply(reps)
+            algo5 = Vc * (5 * nb * nb * link_b + 2 * nb * 8)
+            algo9 = Vc * (9 * nb * nb * link_b + 2 * nb * 8)
+            out[f"level{l}"][f"links_{lk}_five_block"] = {
+                "link_bytes": link_b, "vector_bytes": 8, "algorithmic_bytes": algo5,
+                "kernel_us": round(kms * 1e3, 2), "GB/s": round(algo5 / (kms * 1e-3) / 1e9, 1),
+                "frac_of_hbm": round(algo5 / (kms * 1e-3) / 1e9 / hbm, 4),
+                "nine_block_equivalent_frac": round(algo9 / (kms * 1e-3) / 1e9 / hbm, 4),
+                "tile": dict(kind=5, **best[1]), "applies": reps}
+            # back to the shape the headline used
+            if saved.get("source") == 2:
+                ctx.set_coarse_tile(l, 1, wcmg.F32, kind=saved["kind"], rhs_per_cta=saved["rhs_per_cta"],
+                                    parts=saved["parts"], threads=saved["threads"], ntile=saved["ntile"],
+                                    stages=saved["stages"])
+            else:
+                ctx.set_coarse_tile(l, 1, wcmg.F32, kind=-1)
+    finally:
+        ctx.set_profile(0)
 
 
 UNEVEN_BATCH = dict(
@@ -1120,6 +1185,8 @@ def run_probe(args, local):
     if args.links:
         cfg["links"] = args.links
     cfg["ortho"] = args.ortho
+    if args.sigma3:
+        cfg["sigma3"] = 1
     if args.probe_fine:
         # a smaller fine lattice whose first blocking gives the same coarse levels (the
         # coarse applies' shapes and bytes unchanged, the device memory much smaller)
@@ -1198,6 +1265,9 @@ def main(argv=None):
     ap.add_argument("--kcycle", action="store_true", help="K-cycle on the intermediate levels (3-level workloads)")
     ap.add_argument("--coarse-eo", action="store_true",
                     help="even-odd (Schur complement) preconditioned coarsest solve")
+    ap.add_argument("--sigma3", action="store_true",
+                    help="keep five-block (sigma3) copies of the Galerkin coarse links: the autotuner may pick the "
+                         "five-block one-rhs apply (kind 5); coarse_stencil reports it with its own byte count")
     ap.add_argument("--smoother", default="mr", choices=["mr", "gmres", "sap"],
                     help="smoother of every level (the setup sweeps and the cycle)")
     ap.add_argument("--sap-cycles", type=int, default=1, help="SAP smoother: cycles")

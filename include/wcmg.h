@@ -137,6 +137,17 @@ typedef struct wcmg_params {
                                            the inverses of the self blocks A_0 (FP64 Gauss-Jordan, once
                                            per coarse operator).  Needs even extents of the coarsest
                                            lattice (else WCMG_ERR_ARG). */
+  int coarse_sigma3;                    /* 1: keep, next to the nine-block links of every coarse operator
+                                           that the setup builds (D_c = P^dag D P), a five-block copy
+                                           [A_0 | A_{+x} | A_{+y} | A_{+z} | A_{+t}] (Sec. 4: DDalphaAMG's
+                                           5 stencil points against Grid's 9): gamma5-hermiticity of D
+                                           with gamma5 P = P sigma3 gives A_{-mu}(x) = sigma3
+                                           A_{+mu}(x - mu)^dag sigma3, so one-rhs applies may stream 5/9
+                                           of the link bytes (launch kind 5, chosen by the autotuner or
+                                           set with wcmg_set_coarse_tile).  Links given through
+                                           wcmg_set_coarse_links or wcmg_load_setup are not assumed to
+                                           have this symmetry and keep the nine-block kernels.
+                                           0 (default): nine blocks only. */
 } wcmg_params;
 
 typedef enum { WCMG_SMOOTHER_MR = 0, WCMG_SMOOTHER_GMRES = 1, WCMG_SMOOTHER_SAP = 2 } wcmg_smoother;
@@ -307,20 +318,26 @@ int wcmg_solve_batch(wcmg_ctx* const* ctxs, int n, const void* const* b, void* c
  * the one-rhs kernel (kind 0); several rhs -> the rhs-tile kernel (kind 1); BF16
  * links with >= 8 rhs -> the tcgen05 tensor-core kernel (kind 2).  Kind 3 (one rhs)
  * is a persistent streaming pipeline: each CTA keeps `stages` bulk copies of
- * `parts`-row chunks of the link matrices in flight ahead of the arithmetic. */
+ * `parts`-row chunks of the link matrices in flight ahead of the arithmetic.  Kind 4
+ * (BF16 links, >= 2 rhs) is the tcgen05 kernel fed by bulk copies: warp-specialised,
+ * persistent over (site, rhs tile), `stages` operand stages, MMA M = `threads`.
+ * Kind 5 (one rhs) reads the five-block copy of params.coarse_sigma3 (Galerkin
+ * operators only). */
 typedef struct wcmg_tile {
   int kind;             /* 0 one-rhs kernel, 1 rhs-tile SIMT kernel, 2 tensor-core kernel,
-                           3 one-rhs streaming kernel, -1 none */
+                           3 one-rhs streaming kernel, 4 tensor-core kernel fed by bulk copies,
+                           5 one-rhs kernel on the five-block storage, -1 none */
   int rhs_per_cta;      /* kind 1: 1, 4 or 8 rhs per CTA */
-  int parts;            /* kinds 0, 1: CTAs sharing one coarse site's rows (kind 1: 0 = automatic);
+  int parts;            /* kinds 0, 1, 5: CTAs sharing one coarse site's rows (kind 1: 0 = automatic);
                            kind 3: link rows per staged chunk */
-  int threads;          /* kinds 0, 3: threads per CTA (kind 0: 64 .. 512, multiple of 32;
-                           kind 3: 128, 256 or 512) */
-  int ntile;            /* kind 2: rhs per MMA N tile (16, 32, 48 or 64) */
+  int threads;          /* kinds 0, 3, 5: threads per CTA (kinds 0, 5: 64 .. 512, multiple of 32;
+                           kind 3: 128, 256 or 512); kind 4: MMA M, 64 or 128 (>= nbasis) */
+  int ntile;            /* kinds 2, 4: rhs per MMA N tile (kind 2: 16, 32, 48 or 64; kind 4: a
+                           multiple of 8 up to 64) */
   int source;           /* 0 fixed rule, 1 autotuner, 2 wcmg_set_coarse_tile */
   int candidates;       /* shapes the autotuner timed (fixed rule included) */
-  int stages;           /* kind 0: link rows in flight per warp (0 or 1: one, 2: two);
-                           kind 3: chunks in flight (2 .. 8) */
+  int stages;           /* kinds 0, 5: link rows in flight per warp (0 or 1: one, 2: two);
+                           kind 3: chunks in flight (2 .. 8); kind 4: operand stages (2 .. 8) */
   double us;            /* autotuner: time per apply of the chosen shape (back-to-back applies) */
   double us_default;    /* autotuner: time per apply of the fixed rule */
 } wcmg_tile;
@@ -340,7 +357,8 @@ int wcmg_tune_coarse(wcmg_ctx* ctx, int level, int nrhs, int prec, int cold, voi
 
 /* Force a tile for (level, nrhs, prec); t->kind = -1 clears it (back to the
  * fixed rule, or the autotuner when params.autotune = 1).  ERR_ARG if the shape
- * is not valid for the level (e.g. kind 2 without BF16 links). */
+ * is not valid for the level (e.g. kind 2 without BF16 links, kind 5 without the
+ * five-block copy of params.coarse_sigma3). */
 int wcmg_set_coarse_tile(wcmg_ctx* ctx, int level, int nrhs, int prec, const wcmg_tile* t);
 
 /* Change params.profile of an existing context (no GPU work). */

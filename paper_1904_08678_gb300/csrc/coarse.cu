@@ -211,6 +211,121 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
   }
 }
 
+// One-rhs coarse apply from the five-block storage (kind 5).  D_c = P^dag D P inherits
+// gamma5-hermiticity: gamma5 P = P sigma3 for the chirality-split basis (sigma3 = +1
+// on a site's first Nvec basis vectors, -1 on the rest), so D_c^dag = sigma3 D_c
+// sigma3, and since each fine hop and its reverse cross the same face, face by face
+//   A_{-mu}(x) = sigma3 A_{+mu}(x - mu)^dag sigma3.
+// Only M5(x) = [A_0 | A_{+x} | A_{+y} | A_{+z} | A_{+t}] is kept (row-major nb x ld5,
+// ld5 = 5 nb rounded up to 4), 5/9 of the nine-block bytes:
+//   y(x)_a = sum_k M5(x)_{ak} Phi5(x)_k + s_a sum_mu sum_b conj(A_{+mu}(x - mu)_{ba}) s_b phi(x - mu)_b.
+// The forward part is the nine-block kernel's (one warp per row, 16-byte loads,
+// RPW rows in flight, conflict-free gathered vectors).  In the backward part thread
+// (mu, a) walks column a of the neighbour's block; at each b the lanes of a warp read
+// consecutive entries of one row.  That block was streamed from HBM by the
+// neighbour's own CTA shortly before (sites go in storage order; the -t neighbour is
+// one time slice back), so it mostly comes from L2.  `parts` CTAs split a site's rows
+// (forward) and columns (backward).
+template <typename R, typename L, int VEC, int NK, int RPW>
+__global__ void __launch_bounds__(512) k_coarse_apply5(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                       const L* __restrict__ links5, const int* __restrict__ nbr,
+                                                       int Vc, int nb, int ld5, int parts) {
+  using T = cplx<R>;
+  extern __shared__ unsigned char smem_raw[];
+  T* phi = reinterpret_cast<T*>(smem_raw);  // [ld5] forward vectors (phi_slot order)
+  T* phib = phi + ld5;                      // [4][nb] s_b phi(x - mu)_b
+  T* yb = phib + 4 * nb;                    // [4][nb] backward sums, sign s_a applied
+  const int site = blockIdx.x / parts, part = blockIdx.x % parts;
+  const int rpc = (nb + parts - 1) / parts;
+  const int row0 = part * rpc, row1 = min(nb, row0 + rpc), nrow = max(row1 - row0, 0);
+  const int half = nb >> 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const L* base = links5 + (long long)site * nb * ld5;
+  LinkVec<L, VEC> cur[RPW][NK];
+  auto load_rows = [&](int row) {
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) {
+      const int r = row + u * nw;
+#pragma unroll
+      for (int j = 0; j < NK; ++j) {
+        const int k0 = VEC * (lane + 32 * j);
+        if (r < row1 && k0 < ld5) cur[u][j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)r * ld5 + k0);
+      }
+    }
+  };
+  int row = row0 + warp;
+  load_rows(row);
+  for (int idx = threadIdx.x; idx < ld5; idx += blockDim.x) {
+    T v = czero<R>();
+    if (idx < 5 * nb) {
+      const int d = idx / nb, c = idx - d * nb;
+      const int n = d == 0 ? site : nbr[(2 * (d - 1)) * Vc + site];  // +mu neighbour
+      v = in[(long long)n * nb + c];
+    }
+    phi[phi_slot<VEC>(idx, ld5)] = v;
+  }
+  for (int idx = threadIdx.x; idx < 4 * nb; idx += blockDim.x) {
+    const int mu = idx / nb, b = idx - mu * nb;
+    const T v = in[(long long)nbr[(2 * mu + 1) * Vc + site] * nb + b];  // -mu neighbour
+    phib[idx] = b < half ? v : -v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 4 * nrow; t += blockDim.x) {
+    const int mu = t / nrow, a = row0 + (t - mu * nrow);
+    const int n = nbr[(2 * mu + 1) * Vc + site];
+    const L* col = links5 + (long long)n * nb * ld5 + (1 + mu) * nb + a;
+    const T* pb = phib + mu * nb;
+    T acc = czero<R>();
+#pragma unroll 8
+    for (int b = 0; b < nb; ++b) cjmac(acc, link_load<L, R>(col[(long long)b * ld5]), pb[b]);
+    yb[mu * nb + a] = a < half ? acc : -acc;
+  }
+  __syncthreads();
+  const int G = ld5 / VEC;
+  for (; row < row1; row += RPW * nw) {
+    if (row != row0 + warp) load_rows(row);
+    T acc[RPW];
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) acc[u] = czero<R>();
+#pragma unroll
+    for (int j = 0; j < NK; ++j) {
+      const int k0 = VEC * (lane + 32 * j);
+      if (k0 < ld5) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const T p = phi[v * G + k0 / VEC];
+#pragma unroll
+          for (int u = 0; u < RPW; ++u) cmac(acc[u], link_load<L, R>(cur[u][j].v[v]), p);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) {
+      const T a = warp_sum(acc[u]);
+      const int r = row + u * nw;
+      if (lane == 0 && r < row1) out[(long long)site * nb + r] = a + yb[r] + yb[nb + r] + yb[2 * nb + r] + yb[3 * nb + r];
+    }
+  }
+}
+
+// nine-block rows [A_0 | A_{+x} | A_{-x} | ... ] -> five-block rows [A_0 | A_{+x} | A_{+y} | A_{+z} | A_{+t}]
+template <typename L>
+__global__ void k_links_to_5(L* __restrict__ dst, const L* __restrict__ src, int Vc, int nb, int ld, int ld5) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)Vc * nb * ld5;
+  if (idx >= total) return;
+  const int k = (int)(idx % ld5);
+  const long long row = idx / ld5;  // site * nb + a
+  L v;
+  memset(&v, 0, sizeof(L));
+  if (k < 5 * nb) {
+    const int d5 = k / nb, c = k - d5 * nb;
+    const int d9 = d5 == 0 ? 0 : 2 * d5 - 1;
+    v = src[row * ld + (long long)d9 * nb + c];
+  }
+  dst[idx] = v;
+}
+
 // Single-rhs coarse apply as a streaming pipeline (kind 3).  Persistent CTAs walk
 // the work items (site, chunk of `cr` link rows) in the order blockIdx.x + k
 // gridDim.x; thread 0 keeps `stages` bulk copies (cp.async.bulk of one contiguous
@@ -867,6 +982,35 @@ static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const
   WCMG_LAUNCH_CHECK();
 }
 
+template <typename R, typename L>
+static void coarse_apply5(cplx<R>* out, const cplx<R>* in, const L* links5, const LevelGeom& g, int nb, int parts,
+                          int threads, int rpw, cudaStream_t st) {
+  constexpr int VEC = VecOf<L>::v;
+  const int ld5 = links5_ld(nb);
+  const int nk = (ld5 + 32 * VEC - 1) / (32 * VEC);
+  const size_t smem = (size_t)(ld5 + 8 * nb) * sizeof(cplx<R>);
+  const unsigned grid = (unsigned)(g.V * parts);
+#define WCMG_C5(NKV, RP) \
+  k_coarse_apply5<R, L, VEC, NKV, RP><<<grid, threads, smem, st>>>(out, in, links5, g.nbr, g.V, nb, ld5, parts)
+#define WCMG_C5R(NKV) \
+  if (rpw == 2) WCMG_C5(NKV, 2); else WCMG_C5(NKV, 1)
+  if (nk <= 2) { WCMG_C5R(2); }
+  else if (nk <= 4) { WCMG_C5R(4); }
+  else if (nk <= 8) { WCMG_C5(8, 1); }
+  else if (nk <= 12) { WCMG_C5(12, 1); }
+  else throw Error(-1, "coarse apply: nbasis too large for the five-block kernel");
+#undef WCMG_C5R
+#undef WCMG_C5
+  WCMG_LAUNCH_CHECK();
+}
+
+template <typename L>
+void launch_links_to_5(L* dst, const L* src, int Vc, int nb, cudaStream_t st) {
+  const long long total = (long long)Vc * nb * links5_ld(nb);
+  k_links_to_5<L><<<nblk(total, 256), 256, 0, st>>>(dst, src, Vc, nb, links_ld(nb), links5_ld(nb));
+  WCMG_LAUNCH_CHECK();
+}
+
 static int sm_count() {
   static int n = 0;
   if (!n) {
@@ -875,6 +1019,29 @@ static int sm_count() {
     WCMG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
   }
   return n;
+}
+
+// Resident CTAs per SM of a kernel launched with `threads` threads and `smem` bytes of
+// dynamic shared memory, from the SM's own limits (shared memory with the maximum
+// carveout, threads, registers).  The occupancy calculator was seen to answer 1 where
+// two CTAs of 80 KB fit the 228 KB of an SM, so the limits are computed here.
+static int blocks_per_sm(const void* kern, int threads, size_t smem) {
+  WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  cudaFuncAttributes fa;
+  WCMG_CUDA(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, smem_sm = 0, reserved = 0, thr_sm = 0, regs_sm = 0;
+  WCMG_CUDA(cudaGetDevice(&dev));
+  WCMG_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  WCMG_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  WCMG_CUDA(cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+  WCMG_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = (std::max(fa.numRegs, 1) + 7) / 8 * 8 * 32;
+  const int by_smem = (int)((size_t)smem_sm / per_cta);
+  const int by_threads = thr_sm / (warps * 32);
+  const int by_regs = regs_sm / (regs_warp * warps);
+  return std::min(by_smem, std::min(by_threads, by_regs));
 }
 
 size_t coarse_stream_smem(int nb, int cr, int stages, int vec_bytes, int link_bytes) {
@@ -889,8 +1056,7 @@ static void coarse_apply1_stream(cplx<R>* out, const cplx<R>* in, const L* links
   const size_t smem = coarse_stream_smem(nb, cr, stages, sizeof(cplx<R>), sizeof(L));
   auto kern = k_coarse_apply1_stream<R, L>;
   WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  WCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  const int per_sm = blocks_per_sm((const void*)kern, threads, smem);
   if (per_sm < 1) throw Error(-1, "coarse apply: streaming tile does not fit on an SM");
   if (ld > 4 * threads) throw Error(-1, "coarse apply: streaming tile needs more threads for this nbasis");
   const int grid = (int)std::min<long long>(g.V, (long long)sm_count() * per_sm);
@@ -942,9 +1108,7 @@ static void coarse_apply_mma4(float2* out, const float2* in, const bf16c* lmma, 
   auto kern = t.threads == 64 ? k_coarse_apply_mma4<64> : k_coarse_apply_mma4<128>;
   WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // CTAs per SM as shared memory allows, at most 2: each holds 256 of the SM's 512 TMEM columns
-  int per_sm = 0;
-  WCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, smem));
-  per_sm = std::max(1, std::min(per_sm, 2));
+  const int per_sm = std::max(1, std::min(blocks_per_sm((const void*)kern, 192, smem), 2));
   const long long items = (long long)g.V * ntiles;
   const int grid = (int)std::min<long long>(items, (long long)sm_count() * per_sm);
   kern<<<grid, 192, smem, st>>>(out, reinterpret_cast<const uint4*>(lmma), bp, g.nbr, g.V, nb, nrhs, t.ntile, ntiles,
@@ -1004,6 +1168,13 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
              (t.threads == 64 || t.threads == 128) && t.threads >= nb && t.ntile % 8 == 0 && t.ntile >= 8 &&
              t.ntile <= 64 && t.stages >= 2 && t.stages <= MMA4_MAX_STAGES &&
              coarse_mma4_smem(nb, t.ntile, t.threads, t.stages) <= 220 * 1024;
+    case 5: {
+      // stages: rows in flight per warp (0 or 1: one, 2: two while a row is <= 4 chunks per lane)
+      const int vec = link_kind == 0 ? 1 : link_kind == 1 ? 2 : 4;
+      const int nk = (links5_ld(nb) + 32 * vec - 1) / (32 * vec);
+      return nrhs == 1 && mode == ST_FULL && t.parts >= 1 && t.parts <= nb && t.threads >= 64 && t.threads <= 512 &&
+             t.threads % 32 == 0 && t.stages >= 0 && t.stages <= 2 && (t.stages < 2 || nk <= 4) && nk <= 12;
+    }
     case 3: {
       const int lb = link_kind == 0 ? 16 : link_kind == 1 ? 8 : 4;
       const int vb = link_kind == 0 ? 16 : 8;
@@ -1020,7 +1191,7 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
                          int mode, int hopdir, cudaStream_t st, int* err, const CoarseTile* tile, const bf16c* lmma,
-                         void* scratch, size_t scratch_bytes) {
+                         void* scratch, size_t scratch_bytes, const L* links5) {
   constexpr int lk = LinkKind<L>::v;
   CoarseTile t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
   if (tile && tile->kind >= 0) {
@@ -1043,6 +1214,11 @@ void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const 
       return;
     }
     throw Error(-1, "coarse apply: tensor-core tile needs BF16 links");
+  }
+  if (t.kind == 5 && !links5) t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
+  if (t.kind == 5) {
+    coarse_apply5<R, L>(out, in, links5, g, nb, t.parts, t.threads, t.stages == 2 ? 2 : 1, st);
+    return;
   }
   if (t.kind == 0) {
     coarse_apply1<R, L>(out, in, links, g, nb, t.parts, t.threads, t.stages == 2 ? 2 : 1, st);
@@ -1151,17 +1327,18 @@ void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int 
 
 template void launch_coarse_apply<double, double2>(double2*, const double2*, const double2*, const LevelGeom&, int,
                                                    int, int, int, cudaStream_t, int*, const CoarseTile*,
-                                                   const bf16c*, void*, size_t);
+                                                   const bf16c*, void*, size_t, const double2*);
 template void launch_coarse_apply<float, float2>(float2*, const float2*, const float2*, const LevelGeom&, int, int,
                                                  int, int, cudaStream_t, int*, const CoarseTile*,
-                                                   const bf16c*, void*, size_t);
+                                                   const bf16c*, void*, size_t, const float2*);
 template void launch_coarse_apply<float, bf16c>(float2*, const float2*, const bf16c*, const LevelGeom&, int, int, int,
                                                 int, cudaStream_t, int*, const CoarseTile*,
-                                                const bf16c*, void*, size_t);
+                                                const bf16c*, void*, size_t, const bf16c*);
 template void launch_coarse_apply<float, f16c>(float2*, const float2*, const f16c*, const LevelGeom&, int, int, int,
                                                int, cudaStream_t, int*, const CoarseTile*,
-                                                const bf16c*, void*, size_t);
+                                                const bf16c*, void*, size_t, const f16c*);
 #define WCMG_INST_L(L)                                                                                   \
+  template void launch_links_to_5<L>(L*, const L*, int, int, cudaStream_t);                             \
   template void launch_pack_links<L>(L*, const double2*, const int*, int, int, cudaStream_t);           \
   template void launch_unpack_links<L>(double2*, const L*, const int*, int, int, cudaStream_t);
 WCMG_INST_L(double2)

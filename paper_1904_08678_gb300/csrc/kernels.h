@@ -109,6 +109,8 @@ void launch_parity_axpy(cplx<R>* out, const cplx<R>* a, const cplx<R>* b, double
 // Coarse links: per site a row-major nb x ld matrix, ld = round_up(9 nb, 4),
 // column d*nb + c of row a holds A_d(x)[a][c].
 inline int links_ld(int nb) { return (9 * nb + 3) / 4 * 4; }
+// row stride of the five-block storage [A_0 | A_{+x} | A_{+y} | A_{+z} | A_{+t}] (kind 5)
+inline int links5_ld(int nb) { return (5 * nb + 3) / 4 * 4; }
 template <typename L>
 void launch_pack_links(L* links, const double2* ext, const int* perm, int Vc, int nb, cudaStream_t st);
 template <typename L>
@@ -123,7 +125,8 @@ void launch_unpack_coarse(double2* ext, const cplx<R>* in, const int* perm, int 
 // tile ntile).  kind -1: the fixed rule of coarse_default_tile.
 // kind 3: one-rhs streaming pipeline (threads per CTA, parts = link rows per staged
 // chunk, stages = chunks in flight); kind 4: tcgen05 multi-rhs apply fed by bulk copies
-// (ntile rhs per N tile, threads = MMA M (64 or 128), stages).
+// (ntile rhs per N tile, threads = MMA M (64 or 128), stages); kind 5: one-rhs kernel on
+// the five-block storage of a Galerkin operator (parts, threads, stages as kind 0).
 struct CoarseTile {
   int kind = -1, rr = 0, parts = 0, threads = 0, ntile = 0, stages = 0;
 };
@@ -137,11 +140,16 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
 // (validated; an invalid tile throws).
 // lmma / scratch: the MMA copy of BF16 links (launch_links_to_mma) and a scratch of at
 // least coarse_mma4_scratch_bytes bytes, both needed by kind 4 (otherwise the fixed rule).
+// links5: the five-block copy (launch_links_to_5), needed by kind 5 (otherwise the fixed
+// rule); valid only for links with A_{-mu}(x) = sigma3 A_{+mu}(x - mu)^dag sigma3.
 template <typename R, typename L>
 void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
                          int mode, int hopdir, cudaStream_t st, int* err = nullptr,
                          const CoarseTile* tile = nullptr, const bf16c* lmma = nullptr, void* scratch = nullptr,
-                         size_t scratch_bytes = 0);
+                         size_t scratch_bytes = 0, const L* links5 = nullptr);
+// kind 5: the five-block copy (self + forward hops) of a Galerkin operator's links
+template <typename L>
+void launch_links_to_5(L* dst, const L* src, int Vc, int nb, cudaStream_t st);
 // kind 4 (tcgen05 fed by bulk copies): the links in the MMA's K-major core-matrix order,
 // [site][d][16-byte group g][row a]; its shared memory; its scratch for any rhs tile.
 void launch_links_to_mma(bf16c* dst, const bf16c* src, int Vc, int nb, cudaStream_t st);

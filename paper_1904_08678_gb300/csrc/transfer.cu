@@ -580,35 +580,31 @@ __device__ __forceinline__ dfc dfc_shfl_xor(const dfc& v, int o) {
   return {{__shfl_xor_sync(0xffffffffu, v.re.h, o), __shfl_xor_sync(0xffffffffu, v.re.l, o)},
           {__shfl_xor_sync(0xffffffffu, v.im.h, o), __shfl_xor_sync(0xffffffffu, v.im.l, o)}};
 }
-// warp_sum8_transposed in DF: on return v[0] of lane l holds the warp sum of value
-// warp_sum8_index(l)
-__device__ __forceinline__ void dfc_warp_sum8_transposed(dfc (&v)[8], int lane) {
-  {
-    const bool up = lane & 16;
+// Transposing warp sums of GS DF values (GS a power of two, at most 32): on return v[0] of lane l holds
+// the warp sum of value dfc_sum_index<GS>(l); lanes whose low 5 - log2(GS) bits are zero
+// hold each value once.
+template <int GS>
+__device__ __forceinline__ void dfc_warp_sum_transposed(dfc (&v)[GS], int lane) {
+  int off = 16;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const dfc send = up ? v[j] : v[j + 4];
-      const dfc keep = up ? v[j + 4] : v[j];
-      v[j] = dfc_add(keep, dfc_shfl_xor(send, 16));
+  for (int n = GS; n > 1; n >>= 1, off >>= 1) {
+    const bool up = lane & off;
+#pragma unroll
+    for (int j = 0; j < n / 2; ++j) {
+      const dfc send = up ? v[j] : v[j + n / 2];
+      const dfc keep = up ? v[j + n / 2] : v[j];
+      v[j] = dfc_add(keep, dfc_shfl_xor(send, off));
     }
   }
-  {
-    const bool up = lane & 8;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const dfc send = up ? v[j] : v[j + 2];
-      const dfc keep = up ? v[j + 2] : v[j];
-      v[j] = dfc_add(keep, dfc_shfl_xor(send, 8));
-    }
-  }
-  {
-    const bool up = lane & 4;
-    const dfc send = up ? v[0] : v[1];
-    const dfc keep = up ? v[1] : v[0];
-    v[0] = dfc_add(keep, dfc_shfl_xor(send, 4));
-  }
-  v[0] = dfc_add(v[0], dfc_shfl_xor(v[0], 2));
-  v[0] = dfc_add(v[0], dfc_shfl_xor(v[0], 1));
+  for (; off > 0; off >>= 1) v[0] = dfc_add(v[0], dfc_shfl_xor(v[0], off));
+}
+template <int GS>
+__device__ __forceinline__ int dfc_sum_index(int lane) {
+  int g = 0, off = 16;
+#pragma unroll
+  for (int n = GS; n > 1; n >>= 1, off >>= 1) g = 2 * g + ((lane & off) ? 1 : 0);
+  return g;
 }
 __device__ __forceinline__ dfr df_warp_sum(dfr v) {
 #pragma unroll
@@ -645,21 +641,22 @@ __device__ __forceinline__ double f2d_exact(float f) {
 }
 __device__ __forceinline__ double df_to_fast(dfr a) { return f2d_exact(a.h) + f2d_exact(a.l); }
 
-template <int MAXE>
-__global__ void __launch_bounds__(256, 3) k_block_ortho_df(double2* __restrict__ vecs, float4* __restrict__ qdf, int Vf,
-                                                        int nc, int bvol, int nvec, bool fine, int* __restrict__ err) {
+template <int MAXE, int NT, int MINB, int GS>
+__global__ void __launch_bounds__(NT, MINB) k_block_ortho_df(double2* __restrict__ vecs, float4* __restrict__ qdf,
+                                                             int Vf, int nc, int bvol, int nvec, bool fine,
+                                                             int* __restrict__ err) {
   constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
-  __shared__ dfc scratch[8][MV];
+  __shared__ dfc scratch[NT / 32][MV];
   __shared__ dfc red[MV];
   const int blk = blockIdx.x, s = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nelem = bvol * (nc >> 1);
   const long long fstride = (long long)Vf * nc;
-  long long addr[MAXE];
+  int addr[MAXE];  // offsets within one field (< 2^31: checked by the launcher)
 #pragma unroll
   for (int q = 0; q < MAXE; ++q) {
     const int e = threadIdx.x + q * blockDim.x;
-    addr[q] = e < nelem ? elem_addr(fine, blk, e, s, Vf, nc, bvol) : -1;
+    addr[q] = e < nelem ? (int)elem_addr(fine, blk, e, s, Vf, nc, bvol) : -1;
   }
   const dfc zero = {{0.f, 0.f}, {0.f, 0.f}};
   // block-wide DF sums of slots [0, n) and the norm slot
@@ -700,11 +697,11 @@ __global__ void __launch_bounds__(256, 3) k_block_ortho_df(double2* __restrict__
     }
     double before2 = 0.0, after2 = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      // projections <q_i, a> for i < k, eight at a time (one transposing warp reduction)
-      for (int i0 = 0; i0 < k; i0 += 8) {
-        dfc p[8];
+      // projections <q_i, a> for i < k, GS at a time (one transposing warp reduction)
+      for (int i0 = 0; i0 < k; i0 += GS) {
+        dfc p[GS];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
+        for (int g = 0; g < GS; ++g) {
           p[g] = zero;
           if (i0 + g < k) {
             const float4* qi = qdf + (i0 + g) * fstride;
@@ -714,9 +711,9 @@ __global__ void __launch_bounds__(256, 3) k_block_ortho_df(double2* __restrict__
           }
           p[g] = dfc_norm(p[g]);
         }
-        dfc_warp_sum8_transposed(p, lane);
-        const int g = warp_sum8_index(lane);
-        if ((lane & 3) == 0 && i0 + g < k) scratch[warp][i0 + g] = p[0];
+        dfc_warp_sum_transposed<GS>(p, lane);
+        const int g = dfc_sum_index<GS>(lane);
+        if ((lane & (32 / GS - 1)) == 0 && i0 + g < k) scratch[warp][i0 + g] = p[0];
       }
       norm2(a);
       reduce(k, true);
@@ -757,11 +754,20 @@ void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol,
   const int nelem = bvol * (nc / 2);
   if (nvec > 32) throw Error(-1, "block orthonormalisation supports nvec <= 32");
   if (nelem > 256 * 8) throw Error(-1, "aggregate too large for block orthonormalisation");
+  if ((long long)Vf * nc >= (1LL << 31)) throw Error(-1, "block orthonormalisation: field too large");
   const dim3 grid(Vf / bvol, 2);
-  if (nelem <= 256 * 2) k_block_ortho_df<2><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
-  else if (nelem <= 256 * 4) k_block_ortho_df<4><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
-  else if (nelem <= 256 * 6) k_block_ortho_df<6><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
-  else k_block_ortho_df<8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+  // Launch shapes measured on 32^3x64 (panels of 1536 x 24; threads x rows per thread,
+  // CTAs per SM, columns per warp reduction): 512 x 3, 4 CTAs (64 warps, 32 registers),
+  // groups of 4: 49.5 ms per call; the same at 3 CTAs: 53.4 ms; 3 CTAs, groups of 8:
+  // 58 ms; 256 x 6, 3 CTAs: 73 ms; 768 x 2, 2 CTAs: 63 ms; 384 x 4, 3 CTAs: 61 ms.  The
+  // kernel waits on its re-reads of earlier Q columns, so warps in flight pay more than
+  // the registers they cost (a few spills).
+  if (nelem <= 256 * 2)
+    k_block_ortho_df<2, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+  else if (nelem <= 512 * 3)
+    k_block_ortho_df<3, 512, 4, 4><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+  else
+    k_block_ortho_df<8, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
   WCMG_LAUNCH_CHECK();
 }
 

@@ -155,6 +155,12 @@ struct Level {
   bool ainv_valid = false;
   DevBuf<f16c> Lh;
   bool L32_valid = false, low_valid = false;
+  // five-block copies per link kind (FP64, FP32, BF16, FP16) of a Galerkin operator
+  // (sigma3: the links come from the setup's P^dag D P, so the hop blocks obey
+  // A_{-mu}(x) = sigma3 A_{+mu}(x - mu)^dag sigma3)
+  DevBuf<unsigned char> L5[4];
+  bool l5_valid[4] = {false, false, false, false};
+  bool sigma3 = false;
   LevelScalars sc;
   LevelScalars sc_s;  // the GMRES smoother's own Krylov state (it runs inside the outer FGMRES)
   DevBuf<unsigned char> colour;  // SAP: colour (coarse-coordinate parity) of each aggregate
@@ -409,9 +415,40 @@ static MmaOps mma_ops(wcmg_ctx* c, int l, int nrhs, int lk) {
   return m;
 }
 
+// Five-block copies (kind 5) of the links present at level l, when params.coarse_sigma3
+// is set and the level's operator is a Galerkin product.
+template <typename Lt> struct LKind;
+template <> struct LKind<double2> { static constexpr int v = 0; };
+template <> struct LKind<float2> { static constexpr int v = 1; };
+template <> struct LKind<bf16c> { static constexpr int v = 2; };
+template <> struct LKind<f16c> { static constexpr int v = 3; };
+template <typename Lt>
+static void build_links5_of(wcmg_ctx* c, int l, const Lt* src) {
+  Level& L = c->L[l];
+  const int k = LKind<Lt>::v;
+  L.L5[k].ensure((size_t)L.g.V * L.nc * links5_ld(L.nc) * sizeof(Lt));
+  launch_links_to_5<Lt>(reinterpret_cast<Lt*>(L.L5[k].p), src, L.g.V, L.nc, c->st);
+  L.l5_valid[k] = true;
+}
+static void build_links5(wcmg_ctx* c, int l) {
+  Level& L = c->L[l];
+  for (bool& v : L.l5_valid) v = false;
+  if (!c->p.coarse_sigma3 || !L.sigma3 || !L.have_op) return;
+  if (L.op64) build_links5_of<double2>(c, l, L.L64.p);
+  if (L.L32_valid) build_links5_of<float2>(c, l, L.L32.p);
+  if (L.low_valid && c->p.coarse_link_prec == WCMG_BF16) build_links5_of<bf16c>(c, l, L.Lbf.p);
+  if (L.low_valid && c->p.coarse_link_prec == WCMG_F16) build_links5_of<f16c>(c, l, L.Lh.p);
+}
+template <typename Lt>
+static const Lt* links5_of(wcmg_ctx* c, int l) {
+  Level& L = c->L[l];
+  const int k = LKind<Lt>::v;
+  return c->p.coarse_sigma3 && L.sigma3 && L.l5_valid[k] ? reinterpret_cast<const Lt*>(L.L5[k].p) : nullptr;
+}
+
 // ---------------- coarse-apply autotuner ----------------
 // Candidate launch shapes of the full nine-point coarse apply (K4 / K4m).
-static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
+static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk, bool have5) {
   std::vector<CoarseTile> v;
   auto add = [&](int kind, int rr, int parts, int threads, int ntile, int stages = 0) {
     CoarseTile t;
@@ -423,6 +460,11 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk) {
       for (int p : {1, 2, 4, 8})
         for (int rp : {1, 2}) add(0, 1, p, th, 0, rp);
     for (int p : {1, 2, 4, 8, 16}) add(1, 1, p, 0, 0);
+    // five-block storage (Galerkin operators only)
+    if (have5)
+      for (int th : {256, 512})
+        for (int p : {1, 2, 4})
+          for (int rp : {1, 2}) add(5, 1, p, th, 0, rp);
     // streaming pipeline: chunks of 8 rows up to a whole site, 2 .. 6 in flight
     for (int cr : {8, 16, 24, nb})
       for (int stg : {2, 3, 4, 6}) add(3, 0, cr, 256, 0, stg);
@@ -465,9 +507,10 @@ static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs
   WCMG_CUDA(cudaEventCreate(&e1));
   const int reps = 10;
   const MmaOps mo = mma_ops(c, l, nrhs, lk);
+  const Lt* l5 = links5_of<Lt>(c, l);
   auto launch = [&](const CoarseTile* t) {
     launch_coarse_apply<R, Lt>(out, in, links, L.g.lg(), nb, nrhs, ST_FULL, 0, c->st, c->tma_err.p, t, mo.lmma,
-                               mo.scratch, mo.bytes);
+                               mo.scratch, mo.bytes, l5);
   };
   auto time_one = [&](const CoarseTile* t) -> double {
     for (int i = 0; i < 2; ++i) launch(t);
@@ -496,7 +539,7 @@ static Level::TileInfo tune_coarse(wcmg_ctx* c, int l, const Lt* links, int nrhs
   ti.t = coarse_default_tile(nb, nrhs, ST_FULL, L.g.V, lk);
   try {
     ti.us_default = ti.us = time_one(nullptr);
-    const auto cands = coarse_candidates(nb, nrhs, lk);
+    const auto cands = coarse_candidates(nb, nrhs, lk, l5 != nullptr);
     for (const auto& cand : cands) {
       const double us = time_one(&cand);
       if (us < ti.us) {
@@ -600,7 +643,8 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
     const CoarseTile* t = mode == ST_FULL ? coarse_tile<double, double2>(c, l, L.L64.p, nrhs, 0) : nullptr;
     KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 16.0 + 2.0 * nb * 16.0 * nrhs), flops,
           (launch_coarse_apply<double, double2>((double2*)out, (const double2*)in, L.L64.p, L.g.lg(), nb, nrhs,
-                                                mode, hopdir, c->st, c->tma_err.p, t)));
+                                                mode, hopdir, c->st, c->tma_err.p, t, nullptr, nullptr, 0,
+                                                links5_of<double2>(c, l))));
     return;
   }
   const int lp = c->p.coarse_link_prec;
@@ -610,12 +654,14 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
       const MmaOps mo = mma_ops(c, l, nrhs, 2);
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
             (launch_coarse_apply<float, bf16c>((float2*)out, (const float2*)in, L.Lbf.p, L.g.lg(), nb, nrhs, mode,
-                                               hopdir, c->st, c->tma_err.p, t, mo.lmma, mo.scratch, mo.bytes)));
+                                               hopdir, c->st, c->tma_err.p, t, mo.lmma, mo.scratch, mo.bytes,
+                                               links5_of<bf16c>(c, l))));
     } else {
       const CoarseTile* t = coarse_tile<float, f16c>(c, l, L.Lh.p, nrhs, 3);
       KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 4.0 + 2.0 * nb * 8.0 * nrhs), flops,
             (launch_coarse_apply<float, f16c>((float2*)out, (const float2*)in, L.Lh.p, L.g.lg(), nb, nrhs, mode,
-                                              hopdir, c->st, c->tma_err.p, t)));
+                                              hopdir, c->st, c->tma_err.p, t, nullptr, nullptr, 0,
+                                              links5_of<f16c>(c, l))));
     }
     return;
   }
@@ -624,11 +670,13 @@ static void apply_op(wcmg_ctx* c, int l, cplx<R>* out, const cplx<R>* in, int nr
     L.L32.ensure(n);
     launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
     L.L32_valid = true;
+    if (c->p.coarse_sigma3 && L.sigma3) build_links5_of<float2>(c, l, L.L32.p);
   }
   const CoarseTile* t = mode == ST_FULL ? coarse_tile<float, float2>(c, l, L.L32.p, nrhs, 1) : nullptr;
   KPROF(c, WCMG_K_COARSE, Vc * (9.0 * nb2 * 8.0 + 2.0 * nb * 8.0 * nrhs), flops,
         (launch_coarse_apply<float, float2>((float2*)out, (const float2*)in, L.L32.p, L.g.lg(), nb, nrhs, mode,
-                                            hopdir, c->st, c->tma_err.p, t)));
+                                            hopdir, c->st, c->tma_err.p, t, nullptr, nullptr, 0,
+                                            links5_of<float2>(c, l))));
 }
 
 template <typename R>
@@ -1311,6 +1359,8 @@ static void coarsen_body(wcmg_ctx* c, int l) {
     }
     C.low_valid = true;
   }
+  C.sigma3 = true;  // a Galerkin product: the five-block copies are exact
+  build_links5(c, l + 1);
   // the even-odd coarsest solve's self-block inverses follow every new coarsest operator
   // (built here, outside any capture, so that a replayed solve never sees stale ones)
   if (c->p.coarse_eo && l + 1 == c->p.n_levels - 1) ensure_ainv(c, l + 1);
@@ -1576,6 +1626,7 @@ static void graph_prepare(wcmg_ctx* c, int nrhs) {
       L.L32.ensure(n);
       launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
       L.L32_valid = true;
+      if (c->p.coarse_sigma3 && L.sigma3) build_links5_of<float2>(c, l, L.L32.p);
     }
   }
 }
@@ -1974,6 +2025,7 @@ int wcmg_default_params(wcmg_params* p) {
   p->sap_eo = 0;
   p->ortho_df = 0;
   p->coarse_eo = 0;
+  p->coarse_sigma3 = 0;
   return WCMG_OK;
 }
 
@@ -2001,6 +2053,7 @@ int wcmg_create(const wcmg_params* p, wcmg_ctx** out) {
     if (p->sap_eo != 0 && p->sap_eo != 1) throw Error(WCMG_ERR_ARG, "sap_eo must be 0 or 1");
     if (p->ortho_df != 0 && p->ortho_df != 1) throw Error(WCMG_ERR_ARG, "ortho_df must be 0 or 1");
     if (p->coarse_eo != 0 && p->coarse_eo != 1) throw Error(WCMG_ERR_ARG, "coarse_eo must be 0 or 1");
+    if (p->coarse_sigma3 != 0 && p->coarse_sigma3 != 1) throw Error(WCMG_ERR_ARG, "coarse_sigma3 must be 0 or 1");
     if (p->sap_eo) {
       const int* fb = p->block[0];
       const int bv = fb[0] * fb[1] * fb[2] * fb[3];
@@ -2353,6 +2406,8 @@ int wcmg_set_coarse_links(wcmg_ctx* c, int level, const void* A, int where, void
   }
   L.have_op = true;
   L.ainv_valid = false;
+  L.sigma3 = false;  // caller's blocks: no symmetry assumed, nine-block kernels only
+  build_links5(c, level);
   if (c->p.coarse_eo && level == c->p.n_levels - 1) ensure_ainv(c, level);
   WCMG_CUDA(cudaStreamSynchronize(c->st));
   API_END(c)
@@ -2817,6 +2872,7 @@ int wcmg_tune_coarse(wcmg_ctx* c, int level, int nrhs, int prec, int cold, void*
       L.L32.ensure(n);
       launch_convert_links<double2, float2>(L.L32.p, L.L64.p, n, c->st);
       L.L32_valid = true;
+      if (c->p.coarse_sigma3 && L.sigma3) build_links5_of<float2>(c, level, L.L32.p);
     }
     ti = tune_coarse<float, float2>(c, level, L.L32.p, nrhs, 1, cold);
   }
@@ -2845,6 +2901,8 @@ int wcmg_set_coarse_tile(wcmg_ctx* c, int level, int nrhs, int prec, const wcmg_
     ti.t.ntile = t->ntile;
     ti.t.stages = t->stages;
     if (!coarse_tile_valid(ti.t, L.nc, nrhs, ST_FULL, lk)) throw Error(WCMG_ERR_ARG, "tile not valid for this level");
+    if (ti.t.kind == 5 && !(c->p.coarse_sigma3 && L.sigma3 && L.l5_valid[lk]))
+      throw Error(WCMG_ERR_ARG, "kind 5 needs params.coarse_sigma3 and a coarse operator built by the setup");
     ti.source = 2;
     L.tiles[{nrhs, lk}] = ti;
   }

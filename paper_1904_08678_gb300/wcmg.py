@@ -71,6 +71,7 @@ class wcmg_params(ctypes.Structure):
         ("sap_eo", ctypes.c_int),
         ("ortho_df", ctypes.c_int),
         ("coarse_eo", ctypes.c_int),
+        ("coarse_sigma3", ctypes.c_int),
     ]
 
 
