@@ -142,6 +142,115 @@ __global__ void __launch_bounds__(512) k_coarse_apply(cplx<R>* __restrict__ out,
   }
 }
 
+// Masked coarse applies of the Galerkin construction (block interior, one face hop) with
+// many fields, as one small complex GEMM per coarse site:
+//   Y(x) [nb x nf] = sum over the blocks d the mask keeps at x of A_d(x) Phi_d(x),
+// Phi_d(x) the nf input fields at the d-neighbour of x.  One CTA per (site, tile of up to
+// 16 TN fields): each kept block A_d (nb x nb, rows padded by one entry so that the rows a
+// warp reads fall in distinct banks) and Phi_d (nb x tile, transposed, padded likewise)
+// are staged in shared memory, and a 16 x 16 thread grid accumulates a TM x TN register
+// tile (rows tr + 16 i, fields tc + 16 j).  A site that keeps no block (a face hop off the
+// face) returns at once; its output is never read.  Compared with the row-per-warp
+// kernel this removes the warp-shuffle sum of every row and field.
+template <typename R, typename L, int TM, int TN>
+__global__ void __launch_bounds__(256) k_coarse_masked_gemm(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
+                                                            const L* __restrict__ links, const int* __restrict__ nbr,
+                                                            int Vc, int nb, int ld, int nrhs, int mode, int hopdir,
+                                                            BlockInfoC bi) {
+  using T = cplx<R>;
+  constexpr int NT = 16 * TN;
+  extern __shared__ unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);  // [nb][nb + 1]
+  T* Ps = As + nb * (nb + 1);                // [nb][NT + 1]
+  const int site = blockIdx.x, c0 = blockIdx.y * NT;
+  const int ncl = min(NT, nrhs - c0);
+  unsigned dmask;
+  if (mode == ST_BLOCK_INTERIOR) {
+    dmask = 1u;
+    for (int d = 1; d < 9; ++d)
+      if (!c_on_face(bi, site, d - 1)) dmask |= 1u << d;
+  } else {
+    dmask = c_on_face(bi, site, hopdir) ? 1u << (hopdir + 1) : 0u;
+  }
+  if (dmask == 0u || ncl <= 0) return;  // uniform over the CTA
+  const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = czero<R>();
+  for (int d = 0; d < 9; ++d) {
+    if (!((dmask >> d) & 1u)) continue;
+    __syncthreads();  // the previous block's reads are done
+    const L* lr = links + (long long)site * nb * ld + d * nb;
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+      const int a = idx / nb, b = idx - a * nb;
+      As[a * (nb + 1) + b] = link_load<L, R>(lr[(long long)a * ld + b]);
+    }
+    const int n = d == 0 ? site : nbr[(d - 1) * Vc + site];
+    for (int idx = threadIdx.x; idx < ncl * nb; idx += blockDim.x) {
+      const int c = idx / nb, b = idx - c * nb;
+      Ps[b * (NT + 1) + c] = in[((long long)(c0 + c) * Vc + n) * nb + b];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < nb; ++k) {
+      T p[TN];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) p[j] = Ps[k * (NT + 1) + tc + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int row = tr + 16 * i;
+        if (row < nb) {
+          const T a = As[row * (nb + 1) + k];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) cmac(acc[i][j], a, p[j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int row = tr + 16 * i, col = tc + 16 * j;
+      if (row < nb && col < ncl) out[((long long)(c0 + col) * Vc + site) * nb + row] = acc[i][j];
+    }
+}
+
+size_t coarse_masked_gemm_smem(int nb, int nrhs, int elem_bytes) {
+  const int tn = (std::min(nrhs, 64) + 15) / 16;
+  return (size_t)(nb * (nb + 1) + nb * (16 * tn + 1)) * elem_bytes;
+}
+
+template <typename R, typename L>
+static void coarse_masked_gemm(cplx<R>* out, const cplx<R>* in, const L* links, const LevelGeom& g, int nb, int nrhs,
+                               int mode, int hopdir, cudaStream_t st) {
+  BlockInfoC bi;
+  for (int k = 0; k < 4; ++k) bi.b[k] = g.b[k];
+  bi.bvol = g.bvol;
+  const int tm = (nb + 15) / 16, tn = (std::min(nrhs, 64) + 15) / 16;
+  const size_t smem = coarse_masked_gemm_smem(nb, nrhs, (int)sizeof(cplx<R>));
+  const dim3 grid((unsigned)g.V, (unsigned)((nrhs + 16 * tn - 1) / (16 * tn)));
+  const int ld = links_ld(nb);
+#define WCMG_MG(TM, TN)                                                                                      \
+  do {                                                                                                       \
+    auto kern = k_coarse_masked_gemm<R, L, TM, TN>;                                                          \
+    if (smem > 48 * 1024) WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                         (int)smem));                                        \
+    kern<<<grid, 256, smem, st>>>(out, in, links, g.nbr, g.V, nb, ld, nrhs, mode, hopdir, bi);                \
+  } while (0)
+#define WCMG_MGN(TM) \
+  if (tn == 1) WCMG_MG(TM, 1); else if (tn == 2) WCMG_MG(TM, 2); else if (tn == 3) WCMG_MG(TM, 3); else WCMG_MG(TM, 4)
+  if (tm == 1) { WCMG_MGN(1); }
+  else if (tm == 2) { WCMG_MGN(2); }
+  else if (tm == 3) { WCMG_MGN(3); }
+  else { WCMG_MGN(4); }
+#undef WCMG_MGN
+#undef WCMG_MG
+  WCMG_LAUNCH_CHECK();
+}
+
 // Single-rhs coarse apply.  One CTA per (site, block of rows): the nine
 // neighbour vectors are gathered once into shared memory; each warp owns rows
 // and loads RPW whole rows (NK 16-byte chunks per lane each) before reducing them;
@@ -219,25 +328,27 @@ __global__ void __launch_bounds__(512) k_coarse_apply1(cplx<R>* __restrict__ out
 // Only M5(x) = [A_0 | A_{+x} | A_{+y} | A_{+z} | A_{+t}] is kept (row-major nb x ld5,
 // ld5 = 5 nb rounded up to 4), 5/9 of the nine-block bytes:
 //   y(x)_a = sum_k M5(x)_{ak} Phi5(x)_k + s_a sum_mu sum_b conj(A_{+mu}(x - mu)_{ba}) s_b phi(x - mu)_b.
-// The forward part is the nine-block kernel's (one warp per row, 16-byte loads,
-// RPW rows in flight, conflict-free gathered vectors).  In the backward part thread
-// (mu, a) walks column a of the neighbour's block; at each b the lanes of a warp read
-// consecutive entries of one row.  That block was streamed from HBM by the
-// neighbour's own CTA shortly before (sites go in storage order; the -t neighbour is
-// one time slice back), so it mostly comes from L2.  `parts` CTAs split a site's rows
-// (forward) and columns (backward).
-template <typename R, typename L, int VEC, int NK, int RPW>
+// The forward part is the nine-block kernel's (one warp per row, 16-byte loads, RPW rows
+// in flight, conflict-free gathered vectors) and runs first, so the link stream starts at
+// once; each warp then joins the backward part, which reads the neighbours' forward
+// blocks row by row as well: with VB (nb a multiple of the 16-byte chunk), thread
+// t owns chunk g = t mod G of every row (G = nb / VEC chunks) and the rows t / G + k RG
+// of all four blocks, accumulating the VEC outputs of its chunk privately; the RG partial
+// vectors are then summed in a fixed order.  Otherwise thread (mu, a) walks column a of
+// block mu.  Those blocks were streamed from HBM by the neighbours' own CTAs shortly
+// before (sites go in storage order; the -t neighbour is one time slice back), so they
+// mostly come from L2 and HBM sees about 5/9 of the nine-block bytes.
+template <typename R, typename L, int VEC, int NK, int RPW, bool VB>
 __global__ void __launch_bounds__(512) k_coarse_apply5(cplx<R>* __restrict__ out, const cplx<R>* __restrict__ in,
                                                        const L* __restrict__ links5, const int* __restrict__ nbr,
-                                                       int Vc, int nb, int ld5, int parts) {
+                                                       int Vc, int nb, int ld5) {
   using T = cplx<R>;
   extern __shared__ unsigned char smem_raw[];
   T* phi = reinterpret_cast<T*>(smem_raw);  // [ld5] forward vectors (phi_slot order)
   T* phib = phi + ld5;                      // [4][nb] s_b phi(x - mu)_b
-  T* yb = phib + 4 * nb;                    // [4][nb] backward sums, sign s_a applied
-  const int site = blockIdx.x / parts, part = blockIdx.x % parts;
-  const int rpc = (nb + parts - 1) / parts;
-  const int row0 = part * rpc, row1 = min(nb, row0 + rpc), nrow = max(row1 - row0, 0);
+  T* yf = phib + 4 * nb;                    // [nb] forward part of y
+  T* part = yf + nb;                        // VB: [RG][nb] backward partial sums; else [4][nb]
+  const int site = blockIdx.x;
   const int half = nb >> 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const L* base = links5 + (long long)site * nb * ld5;
@@ -249,11 +360,11 @@ __global__ void __launch_bounds__(512) k_coarse_apply5(cplx<R>* __restrict__ out
 #pragma unroll
       for (int j = 0; j < NK; ++j) {
         const int k0 = VEC * (lane + 32 * j);
-        if (r < row1 && k0 < ld5) cur[u][j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)r * ld5 + k0);
+        if (r < nb && k0 < ld5) cur[u][j] = *reinterpret_cast<const LinkVec<L, VEC>*>(base + (long long)r * ld5 + k0);
       }
     }
   };
-  int row = row0 + warp;
+  int row = warp;
   load_rows(row);
   for (int idx = threadIdx.x; idx < ld5; idx += blockDim.x) {
     T v = czero<R>();
@@ -270,20 +381,10 @@ __global__ void __launch_bounds__(512) k_coarse_apply5(cplx<R>* __restrict__ out
     phib[idx] = b < half ? v : -v;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 4 * nrow; t += blockDim.x) {
-    const int mu = t / nrow, a = row0 + (t - mu * nrow);
-    const int n = nbr[(2 * mu + 1) * Vc + site];
-    const L* col = links5 + (long long)n * nb * ld5 + (1 + mu) * nb + a;
-    const T* pb = phib + mu * nb;
-    T acc = czero<R>();
-#pragma unroll 8
-    for (int b = 0; b < nb; ++b) cjmac(acc, link_load<L, R>(col[(long long)b * ld5]), pb[b]);
-    yb[mu * nb + a] = a < half ? acc : -acc;
-  }
-  __syncthreads();
-  const int G = ld5 / VEC;
-  for (; row < row1; row += RPW * nw) {
-    if (row != row0 + warp) load_rows(row);
+  // forward part first (HBM stream; the first rows are already in flight), kept in yf
+  const int G5 = ld5 / VEC;
+  for (; row < nb; row += RPW * nw) {
+    if (row != warp) load_rows(row);
     T acc[RPW];
 #pragma unroll
     for (int u = 0; u < RPW; ++u) acc[u] = czero<R>();
@@ -293,7 +394,7 @@ __global__ void __launch_bounds__(512) k_coarse_apply5(cplx<R>* __restrict__ out
       if (k0 < ld5) {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
-          const T p = phi[v * G + k0 / VEC];
+          const T p = phi[v * G5 + k0 / VEC];
 #pragma unroll
           for (int u = 0; u < RPW; ++u) cmac(acc[u], link_load<L, R>(cur[u][j].v[v]), p);
         }
@@ -303,7 +404,54 @@ __global__ void __launch_bounds__(512) k_coarse_apply5(cplx<R>* __restrict__ out
     for (int u = 0; u < RPW; ++u) {
       const T a = warp_sum(acc[u]);
       const int r = row + u * nw;
-      if (lane == 0 && r < row1) out[(long long)site * nb + r] = a + yb[r] + yb[nb + r] + yb[2 * nb + r] + yb[3 * nb + r];
+      if (lane == 0 && r < nb) yf[r] = a;
+    }
+  }
+  // backward part (mostly L2), overlapping the other warps' forward rows
+  if constexpr (VB) {
+    const int G = nb / VEC, RG = (int)blockDim.x / G;
+    const int g = threadIdx.x % G, rg = threadIdx.x / G;
+    if (rg < RG) {
+      T acc[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[v] = czero<R>();
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {
+        const int n = nbr[(2 * mu + 1) * Vc + site];
+        const L* blk = links5 + (long long)n * nb * ld5 + (1 + mu) * nb + VEC * g;
+        const T* pb = phib + mu * nb;
+#pragma unroll 4
+        for (int b = rg; b < nb; b += RG) {
+          const LinkVec<L, VEC> w = *reinterpret_cast<const LinkVec<L, VEC>*>(blk + (long long)b * ld5);
+          const T p = pb[b];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) cjmac(acc[v], link_load<L, R>(w.v[v]), p);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) part[rg * nb + VEC * g + v] = acc[v];
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      T sum = czero<R>();
+      for (int r = 0; r < RG; ++r) sum += part[r * nb + a];
+      out[(long long)site * nb + a] = yf[a] + (a < half ? sum : -sum);
+    }
+  } else {
+    for (int t = threadIdx.x; t < 4 * nb; t += blockDim.x) {
+      const int mu = t / nb, a = t - mu * nb;
+      const int n = nbr[(2 * mu + 1) * Vc + site];
+      const L* col = links5 + (long long)n * nb * ld5 + (1 + mu) * nb + a;
+      const T* pb = phib + mu * nb;
+      T acc = czero<R>();
+#pragma unroll 8
+      for (int b = 0; b < nb; ++b) cjmac(acc, link_load<L, R>(col[(long long)b * ld5]), pb[b]);
+      part[t] = acc;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      const T sum = part[a] + part[nb + a] + part[2 * nb + a] + part[3 * nb + a];
+      out[(long long)site * nb + a] = yf[a] + (a < half ? sum : -sum);
     }
   }
 }
@@ -983,23 +1131,29 @@ static void coarse_apply1(cplx<R>* out, const cplx<R>* in, const L* links, const
 }
 
 template <typename R, typename L>
-static void coarse_apply5(cplx<R>* out, const cplx<R>* in, const L* links5, const LevelGeom& g, int nb, int parts,
-                          int threads, int rpw, cudaStream_t st) {
+static void coarse_apply5(cplx<R>* out, const cplx<R>* in, const L* links5, const LevelGeom& g, int nb, int threads,
+                          int rpw, cudaStream_t st) {
   constexpr int VEC = VecOf<L>::v;
   const int ld5 = links5_ld(nb);
   const int nk = (ld5 + 32 * VEC - 1) / (32 * VEC);
-  const size_t smem = (size_t)(ld5 + 8 * nb) * sizeof(cplx<R>);
-  const unsigned grid = (unsigned)(g.V * parts);
-#define WCMG_C5(NKV, RP) \
-  k_coarse_apply5<R, L, VEC, NKV, RP><<<grid, threads, smem, st>>>(out, in, links5, g.nbr, g.V, nb, ld5, parts)
+  const bool vb = nb % VEC == 0 && nb / VEC <= threads;
+  const int rg = vb ? threads / (nb / VEC) : 4;
+  const size_t smem = (size_t)(ld5 + 5 * nb + (size_t)rg * nb) * sizeof(cplx<R>);
+  const unsigned grid = (unsigned)g.V;
+#define WCMG_C5(NKV, RP, VB) \
+  k_coarse_apply5<R, L, VEC, NKV, RP, VB><<<grid, threads, smem, st>>>(out, in, links5, g.nbr, g.V, nb, ld5)
+#define WCMG_C5V(NKV, RP) \
+  if (vb) WCMG_C5(NKV, RP, true); else WCMG_C5(NKV, RP, false)
 #define WCMG_C5R(NKV) \
-  if (rpw == 2) WCMG_C5(NKV, 2); else WCMG_C5(NKV, 1)
+  if (rpw == 2) { WCMG_C5V(NKV, 2); } else { WCMG_C5V(NKV, 1); }
+  if (smem > 48 * 1024) throw Error(-1, "coarse apply: five-block tile needs too much shared memory");
   if (nk <= 2) { WCMG_C5R(2); }
   else if (nk <= 4) { WCMG_C5R(4); }
-  else if (nk <= 8) { WCMG_C5(8, 1); }
-  else if (nk <= 12) { WCMG_C5(12, 1); }
+  else if (nk <= 8) { WCMG_C5V(8, 1); }
+  else if (nk <= 12) { WCMG_C5V(12, 1); }
   else throw Error(-1, "coarse apply: nbasis too large for the five-block kernel");
 #undef WCMG_C5R
+#undef WCMG_C5V
 #undef WCMG_C5
   WCMG_LAUNCH_CHECK();
 }
@@ -1169,11 +1323,16 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
              t.ntile <= 64 && t.stages >= 2 && t.stages <= MMA4_MAX_STAGES &&
              coarse_mma4_smem(nb, t.ntile, t.threads, t.stages) <= 220 * 1024;
     case 5: {
-      // stages: rows in flight per warp (0 or 1: one, 2: two while a row is <= 4 chunks per lane)
+      // one CTA per site (parts 1); stages: rows in flight per warp (0 or 1: one, 2: two while
+      // a row is <= 4 chunks per lane); shared memory within the default 48 KB
       const int vec = link_kind == 0 ? 1 : link_kind == 1 ? 2 : 4;
       const int nk = (links5_ld(nb) + 32 * vec - 1) / (32 * vec);
-      return nrhs == 1 && mode == ST_FULL && t.parts >= 1 && t.parts <= nb && t.threads >= 64 && t.threads <= 512 &&
-             t.threads % 32 == 0 && t.stages >= 0 && t.stages <= 2 && (t.stages < 2 || nk <= 4) && nk <= 12;
+      const int vb = link_kind == 0 ? 16 : 8;
+      const bool vbk = nb % vec == 0 && nb / vec <= t.threads;
+      const size_t smem = (size_t)(links5_ld(nb) + 5 * nb + (size_t)(vbk ? t.threads / (nb / vec) : 4) * nb) * vb;
+      return nrhs == 1 && mode == ST_FULL && t.parts == 1 && t.threads >= 64 && t.threads <= 512 &&
+             t.threads % 32 == 0 && t.stages >= 0 && t.stages <= 2 && (t.stages < 2 || nk <= 4) && nk <= 12 &&
+             smem <= 48 * 1024;
     }
     case 3: {
       const int lb = link_kind == 0 ? 16 : link_kind == 1 ? 8 : 4;
@@ -1217,7 +1376,7 @@ void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const 
   }
   if (t.kind == 5 && !links5) t = coarse_default_tile(nb, nrhs, mode, g.V, lk);
   if (t.kind == 5) {
-    coarse_apply5<R, L>(out, in, links5, g, nb, t.parts, t.threads, t.stages == 2 ? 2 : 1, st);
+    coarse_apply5<R, L>(out, in, links5, g, nb, t.threads, t.stages == 2 ? 2 : 1, st);
     return;
   }
   if (t.kind == 0) {
@@ -1227,6 +1386,15 @@ void launch_coarse_apply(cplx<R>* out, const cplx<R>* in, const L* links, const 
   if (t.kind == 3) {
     coarse_apply1_stream<R, L>(out, in, links, g, nb, t.threads, t.parts, t.stages, err, st);
     return;
+  }
+  // masked applies of the Galerkin construction with several fields: one GEMM per site
+  // (FP64 / FP32 link storage, nbasis <= 64, shared memory within the SM's 227 KB)
+  if constexpr (std::is_same<L, double2>::value || std::is_same<L, float2>::value) {
+    if ((mode == ST_BLOCK_INTERIOR || mode == ST_FACE_HOP) && nrhs >= 2 && nb <= 64 &&
+        coarse_masked_gemm_smem(nb, nrhs, (int)sizeof(cplx<R>)) <= 200 * 1024 && (!tile || tile->kind < 0)) {
+      coarse_masked_gemm<R, L>(out, in, links, g, nb, nrhs, mode, hopdir, st);
+      return;
+    }
   }
   if (t.rr == 1) coarse_apply_rr<R, L, 1>(out, in, links, g, nb, nrhs, mode, hopdir, t.parts, st);
   else if (t.rr == 4) coarse_apply_rr<R, L, 4>(out, in, links, g, nb, nrhs, mode, hopdir, t.parts, st);

@@ -462,9 +462,8 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk, bool 
     for (int p : {1, 2, 4, 8, 16}) add(1, 1, p, 0, 0);
     // five-block storage (Galerkin operators only)
     if (have5)
-      for (int th : {256, 512})
-        for (int p : {1, 2, 4})
-          for (int rp : {1, 2}) add(5, 1, p, th, 0, rp);
+      for (int th : {128, 256, 512})
+        for (int rp : {1, 2}) add(5, 1, 1, th, 0, rp);
     // streaming pipeline: chunks of 8 rows up to a whole site, 2 .. 6 in flight
     for (int cr : {8, 16, 24, nb})
       for (int stg : {2, 3, 4, 6}) add(3, 0, cr, 256, 0, stg);

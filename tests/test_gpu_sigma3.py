@@ -66,21 +66,23 @@ def test_five_block_apply_matches_oracle(lib, dims, block, nvec, prec, tol):
     assert apply_kind5(lib, ctx, dims, block, nvec, prec, op, 2102, threads=256, parts=1, stages=1) < tol
 
 
-@pytest.mark.parametrize("threads,parts,stages", [(512, 1, 2), (256, 2, 1), (64, 4, 2), (128, 3, 1)])
-def test_five_block_launch_shapes(lib, threads, parts, stages):
-    """Rows split over several CTAs (a ragged split for 3 parts of 48 rows), two rows in
-    flight per warp, and fewer threads than backward columns (64 < 4 x 48)."""
+@pytest.mark.parametrize("threads,stages", [(512, 2), (256, 1), (128, 2), (64, 1)])
+def test_five_block_launch_shapes(lib, threads, stages):
+    """Two rows in flight per warp, and from 42 down to 2 row groups sharing the backward
+    blocks (64 threads: 2 groups of 24 FP32 chunks per 48-entry row)."""
     dims, block, nvec = (8, 8, 8, 8), (2, 2, 2, 2), 24
     ctx, op = galerkin_ctx(lib, dims, block, nvec, 1, seed=2103)
-    assert apply_kind5(lib, ctx, dims, block, nvec, 1, op, 2104, threads=threads, parts=parts, stages=stages) < 1e-5
+    assert apply_kind5(lib, ctx, dims, block, nvec, 1, op, 2104, threads=threads, parts=1, stages=stages) < 1e-5
 
 
 @pytest.mark.parametrize("lp,tol", [(2, 5e-3), (3, 1e-3)], ids=["bf16", "fp16"])
-def test_five_block_low_precision_links(lib, lp, tol):
+@pytest.mark.parametrize("dims,block,nvec", [((8, 8, 8, 8), (2, 2, 2, 2), 24), ((6, 4, 8, 10), (3, 2, 4, 5), 5)],
+                         ids=["nbasis48", "nbasis10"])
+def test_five_block_low_precision_links(lib, lp, tol, dims, block, nvec):
     """BF16 / FP16 link storage: the five-block copy is taken from the rounded nine-block
     links, so the error is that of the rounding (unit roundoff 2^-8 / 2^-11 of the
-    entries) against the FP64 oracle."""
-    dims, block, nvec = (8, 8, 8, 8), (2, 2, 2, 2), 24
+    entries) against the FP64 oracle.  nbasis 10 is not a whole number of 16-byte link
+    chunks, so the backward blocks are read column by column there."""
     ctx, op = galerkin_ctx(lib, dims, block, nvec, 1, link_prec=lp, seed=2105)
     assert apply_kind5(lib, ctx, dims, block, nvec, 1, op, 2106, threads=256, parts=1, stages=2) < tol
 
@@ -92,6 +94,8 @@ def test_five_block_needs_a_galerkin_operator(lib):
     cd = coarse_dims(dims, block)
     Vc, nb = int(np.prod(cd)), 2 * nvec
     A = inputs.complex_gaussian(2107, 9, (9, Vc, nb, nb))
+    with pytest.raises(lib.WcmgError):  # one CTA per site only
+        ctx.set_coarse_tile(1, 1, lib.F32, kind=5, threads=256, parts=2, stages=1)
     ctx.set_coarse_links(1, dev(A))
     with pytest.raises(lib.WcmgError):
         ctx.set_coarse_tile(1, 1, lib.F32, kind=5, threads=256, parts=1, stages=1)
