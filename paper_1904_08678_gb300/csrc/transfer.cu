@@ -749,6 +749,206 @@ __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df(double2* __restrict
 }
 
 
+// Columns in pairs: the first Gram-Schmidt pass of columns k and k + 1 against the
+// finished columns Q_{<k} is one sweep over Q_{<k} (each re-read of Q serves both
+// columns), which halves the kernel's dominant traffic, the re-reads of earlier Q
+// columns.  Column k then follows the single-column kernel (selective second pass,
+// normalisation); column k + 1 is projected on the new q_k from registers, and its
+// selective second pass (against all of Q_{<=k}) is taken when the whole projection
+// cancelled more than 99 % of its norm, the same test as before.  The Q factor is the
+// same up to rounding; the second passes are rare for near-null candidates.
+template <int MAXE, int NT, int MINB, int GS>
+__global__ void __launch_bounds__(NT, MINB) k_block_ortho_df2(double2* __restrict__ vecs, float4* __restrict__ qdf,
+                                                              int Vf, int nc, int bvol, int nvec, bool fine,
+                                                              int* __restrict__ err) {
+  constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
+  __shared__ dfc scratch[2][NT / 32][MV];
+  __shared__ dfc red[2][MV];
+  const int blk = blockIdx.x, s = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nelem = bvol * (nc >> 1);
+  const long long fstride = (long long)Vf * nc;
+  int addr[MAXE];
+#pragma unroll
+  for (int q = 0; q < MAXE; ++q) {
+    const int e = threadIdx.x + q * blockDim.x;
+    addr[q] = e < nelem ? (int)elem_addr(fine, blk, e, s, Vf, nc, bvol) : -1;
+  }
+  const dfc zero = {{0.f, 0.f}, {0.f, 0.f}};
+  // block-wide DF sums of the slots [0, n) of columns [0, ncol) and of their norm slots
+  auto reduce = [&](int n, int ncol) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < ncol * MV; i += blockDim.x) {
+      const int c = i / MV, j = i - c * MV;
+      if (j < n || j == MV - 1) {
+        dfc t = scratch[c][0][j];
+        for (int w = 1; w < nw; ++w) t = dfc_add(t, scratch[c][w][j]);
+        red[c][j] = t;
+      }
+    }
+    __syncthreads();
+  };
+  auto norm2 = [&](const dfc (&a)[MAXE], int c) {
+    dfr n = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+      df_mac(n, a[q].re, a[q].re);
+      df_mac(n, a[q].im, a[q].im);
+    }
+    n = df_warp_sum(df_norm(n));
+    if (lane == 0) scratch[c][warp][MV - 1] = {n, {0.f, 0.f}};
+  };
+  // projections of columns a0 (and a1 when two) on Q_{<k} into scratch[0 / 1][.][0, k)
+  auto project = [&](const dfc (&a0)[MAXE], const dfc (&a1)[MAXE], int k, bool two) {
+    for (int i0 = 0; i0 < k; i0 += GS) {
+      dfc p0[GS], p1[GS];
+#pragma unroll
+      for (int g = 0; g < GS; ++g) {
+        p0[g] = zero;
+        p1[g] = zero;
+        if (i0 + g < k) {
+          const float4* qi = qdf + (i0 + g) * fstride;
+#pragma unroll
+          for (int q = 0; q < MAXE; ++q)
+            if (addr[q] >= 0) {
+              const dfc qv = dfc_load(qi + addr[q]);
+              dfc_cjmac(p0[g], qv, a0[q]);
+              if (two) dfc_cjmac(p1[g], qv, a1[q]);
+            }
+        }
+        p0[g] = dfc_norm(p0[g]);
+        p1[g] = dfc_norm(p1[g]);
+      }
+      dfc_warp_sum_transposed<GS>(p0, lane);
+      const int g = dfc_sum_index<GS>(lane);
+      const bool w0 = (lane & (32 / GS - 1)) == 0 && i0 + g < k;
+      if (w0) scratch[0][warp][i0 + g] = p0[0];
+      if (two) {
+        dfc_warp_sum_transposed<GS>(p1, lane);
+        if (w0) scratch[1][warp][i0 + g] = p1[0];
+      }
+    }
+  };
+  // a0 -= sum_i red[0][i] q_i (and a1 with red[1]) over i < k
+  auto subtract = [&](dfc (&a0)[MAXE], dfc (&a1)[MAXE], int k, bool two) {
+    for (int i = 0; i < k; ++i) {
+      const dfc r0 = red[0][i], r1 = red[1][i];
+      const float4* qi = qdf + i * fstride;
+#pragma unroll
+      for (int q = 0; q < MAXE; ++q)
+        if (addr[q] >= 0) {
+          const dfc qv = dfc_load(qi + addr[q]);
+          dfc_nmac(a0[q], r0, qv);
+          if (two) dfc_nmac(a1[q], r1, qv);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+      a0[q] = dfc_norm(a0[q]);
+      if (two) a1[q] = dfc_norm(a1[q]);
+    }
+  };
+  auto load_col = [&](dfc (&a)[MAXE], int k) {
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+      if (addr[q] >= 0) {
+        const double2 v = vecs[k * fstride + addr[q]];
+        a[q] = {df_split(v.x), df_split(v.y)};
+      } else {
+        a[q] = zero;
+      }
+    }
+  };
+  // normalise a by the norm whose square is n2 and store it as column k
+  auto finish = [&](dfc (&a)[MAXE], double n2, int k) {
+    const double nrm = sqrt(n2);
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+      if (threadIdx.x == 0) *err = 1;
+    }
+    const dfr inv = df_split(nrm > 0.0 ? 1.0 / nrm : 0.0);
+#pragma unroll
+    for (int q = 0; q < MAXE; ++q) {
+      const dfr re = df_mul(a[q].re, inv), im = df_mul(a[q].im, inv);
+      a[q] = {re, im};
+      if (addr[q] >= 0) {
+        vecs[k * fstride + addr[q]] = make_double2(df_to_fast(re), df_to_fast(im));
+        qdf[k * fstride + addr[q]] = make_float4(re.h, re.l, im.h, im.l);
+      }
+    }
+  };
+  dfc none[MAXE];
+#pragma unroll
+  for (int q = 0; q < MAXE; ++q) none[q] = zero;
+  for (int k = 0; k < nvec; k += 2) {
+    const bool two = k + 1 < nvec;
+    dfc a0[MAXE], a1[MAXE];
+    load_col(a0, k);
+    if (two) load_col(a1, k + 1);
+    else
+#pragma unroll
+      for (int q = 0; q < MAXE; ++q) a1[q] = zero;
+    // first pass of both columns against Q_{<k}, norms before
+    project(a0, a1, k, two);
+    norm2(a0, 0);
+    if (two) norm2(a1, 1);
+    reduce(k, two ? 2 : 1);
+    const double before0 = df_to_fast(red[0][MV - 1].re);
+    const double before1 = two ? df_to_fast(red[1][MV - 1].re) : 0.0;
+    subtract(a0, a1, k, two);
+    norm2(a0, 0);
+    reduce(0, 1);
+    double after0 = df_to_fast(red[0][MV - 1].re);
+    if (k > 0 && after0 < 1e-4 * before0) {  // second pass of column k (uniform)
+      project(a0, none, k, false);
+      norm2(a0, 0);
+      reduce(k, 1);
+      subtract(a0, none, k, false);
+      norm2(a0, 0);
+      reduce(0, 1);
+      after0 = df_to_fast(red[0][MV - 1].re);
+    }
+    finish(a0, after0, k);  // a0 now holds q_k
+    if (!two) {
+      __syncthreads();
+      continue;
+    }
+    // column k + 1: projection on q_k from registers (summed in slot 0 of column 0)
+    {
+      dfc p = zero;
+#pragma unroll
+      for (int q = 0; q < MAXE; ++q)
+        if (addr[q] >= 0) dfc_cjmac(p, a0[q], a1[q]);
+      p = dfc_norm(p);
+      p = {df_warp_sum(p.re), df_warp_sum(p.im)};
+      if (lane == 0) scratch[0][warp][0] = p;
+      reduce(1, 1);
+    }
+    {
+      const dfc r = red[0][0];
+#pragma unroll
+      for (int q = 0; q < MAXE; ++q) {
+        dfc_nmac(a1[q], r, a0[q]);
+        a1[q] = dfc_norm(a1[q]);
+      }
+    }
+    norm2(a1, 1);
+    reduce(0, 2);
+    double after1 = df_to_fast(red[1][MV - 1].re);
+    if (after1 < 1e-4 * before1) {  // second pass of column k + 1 against Q_{<=k} (uniform)
+      project(a1, none, k + 1, false);  // q_k is stored: read it back with the others
+      norm2(a1, 0);
+      reduce(k + 1, 1);
+      subtract(a1, none, k + 1, false);
+      norm2(a1, 0);
+      reduce(0, 1);
+      after1 = df_to_fast(red[0][MV - 1].re);
+    }
+    finish(a1, after1, k + 1);
+    __syncthreads();
+  }
+}
+
+
 void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
                            cudaStream_t st) {
   const int nelem = bvol * (nc / 2);
@@ -757,15 +957,15 @@ void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol,
   if ((long long)Vf * nc >= (1LL << 31)) throw Error(-1, "block orthonormalisation: field too large");
   const dim3 grid(Vf / bvol, 2);
   // Launch shapes measured on 32^3x64 (panels of 1536 x 24; threads x rows per thread,
-  // CTAs per SM, columns per warp reduction): 512 x 3, 4 CTAs (64 warps, 32 registers),
-  // groups of 4: 49.5 ms per call; the same at 3 CTAs: 53.4 ms; 3 CTAs, groups of 8:
-  // 58 ms; 256 x 6, 3 CTAs: 73 ms; 768 x 2, 2 CTAs: 63 ms; 384 x 4, 3 CTAs: 61 ms.  The
-  // kernel waits on its re-reads of earlier Q columns, so warps in flight pay more than
-  // the registers they cost (a few spills).
+  // CTAs per SM, columns per warp reduction): one column at a time, 512 x 3, 4 CTAs (64
+  // warps, 32 registers), groups of 4: 49 ms per call; the same at 3 CTAs: 53 ms; 3 CTAs,
+  // groups of 8: 58 ms; 256 x 6, 3 CTAs: 73 ms; 768 x 2, 2 CTAs: 63 ms; 384 x 4, 3 CTAs:
+  // 61 ms.  Columns in pairs, 512 x 3, 2 CTAs (64 registers), groups of 2: 47 ms (16^3x32:
+  // 3.5 against 3.8 ms).  The kernels wait on their re-reads of earlier Q columns.
   if (nelem <= 256 * 2)
     k_block_ortho_df<2, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
   else if (nelem <= 512 * 3)
-    k_block_ortho_df<3, 512, 4, 4><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+    k_block_ortho_df2<3, 512, 2, 2><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
   else
     k_block_ortho_df<8, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
   WCMG_LAUNCH_CHECK();

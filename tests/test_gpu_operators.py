@@ -80,8 +80,11 @@ def test_dslash_host_buffers_match_device_buffers(lib):
 
 
 @pytest.mark.parametrize("ortho_df", [0, 1], ids=["fp64", "double_float"])
-@pytest.mark.parametrize("dims,block,nvec", CASES)
+@pytest.mark.parametrize("dims,block,nvec", CASES + [((8, 8, 8, 8), (4, 4, 4, 4), 24), ((8, 8, 8, 8), (4, 4, 4, 4), 7)])
 def test_block_orthonormalisation_matches_oracle(lib, dims, block, nvec, ortho_df):
+    """The three lattices of CASES, and the workloads' 4^4 aggregates (panels of 1536 rows:
+    the double-float kernel takes its columns in pairs there; 7 columns leave the last one
+    alone)."""
     V = int(np.prod(dims))
     raw = inputs.complex_gaussian(11, 3, (nvec, V, 12))
     ctx = make(lib, dims, block, nvec, ortho_df=ortho_df)
@@ -258,11 +261,13 @@ def test_restrict_many_rhs_matches_oracle(lib, prec, tol, nrhs):
 
 
 @pytest.mark.parametrize("ortho_df", [0, 1], ids=["fp64", "double_float"])
-def test_block_orthonormalisation_ill_conditioned_panels(lib, ortho_df):
+@pytest.mark.parametrize("dims,block,nvec", [((8, 8, 4, 4), (4, 4, 2, 2), 16), ((8, 8, 8, 8), (4, 4, 4, 4), 16)],
+                         ids=["agg64", "agg256"])
+def test_block_orthonormalisation_ill_conditioned_panels(lib, ortho_df, dims, block, nvec):
     """Nearly parallel near-null candidates (condition number ~1e3 per aggregate) make
     the second Gram-Schmidt pass necessary; Q must stay orthonormal and equal to the
-    positive-diagonal QR factor within the conditioning (FP64 and double-float)."""
-    dims, block, nvec = (8, 8, 4, 4), (4, 4, 2, 2), 16
+    positive-diagonal QR factor within the conditioning (FP64 and double-float; on 4^4
+    aggregates the double-float kernel's paired columns take their second passes too)."""
     V = int(np.prod(dims))
     base = inputs.complex_gaussian(91, 0, (1, V, 12))
     raw = base + 1e-3 * inputs.complex_gaussian(91, 1, (nvec, V, 12))
