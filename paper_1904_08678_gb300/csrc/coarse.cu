@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
                                                               const uint4* __restrict__ bpre,
                                                               const int* __restrict__ nbr, int Vc, int nb, int nrhs,
                                                               int ntile, int ntiles, int stages,
-                                                              int* __restrict__ err) {
+                                                              int acc_cols, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[MMA4_MAX_STAGES], empty[MMA4_MAX_STAGES], tfull[2], tempty[2], fin;
   __shared__ uint32_t tmem_base;
@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
     abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(&tmem_base, 256);
+  if (warp == 1) tmem_alloc(&tmem_base, 2 * acc_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
         const int tb = (int)(i & 1);
         if (!mbar_wait_bounded(&tempty[tb], (uint32_t)(((i >> 1) & 1) ^ 1), limit)) { fail(); ok = false; break; }
         tc_fence_after();
-        const uint32_t dt = tmem + (uint32_t)tb * 128;
+        const uint32_t dt = tmem + (uint32_t)(tb * acc_cols);
         for (int d = 0; d < 9; ++d, ++c) {
           const int s = (int)(c % stages);
           if (!mbar_wait_bounded(&full[s], (uint32_t)((c / stages) & 1), limit)) { fail(); ok = false; break; }
@@ -939,7 +939,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
       }
       tc_fence_after();
       const int site = (int)(it / ntiles), t = (int)(it % ntiles);
-      const uint32_t dt = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)tb * 128;
+      const uint32_t dt = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(tb * acc_cols);
       for (int j0 = 0; j0 < ntile; j0 += 8) {
         float re[8], im[8];
         tmem_ld8(dt + j0, re);
@@ -963,7 +963,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 256);
+  if (warp == 1) tmem_dealloc(tmem, 2 * acc_cols);
 }
 
 template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
@@ -1261,12 +1261,15 @@ static void coarse_apply_mma4(float2* out, const float2* in, const bf16c* lmma, 
   const size_t smem = coarse_mma4_smem(nb, t.ntile, t.threads, t.stages);
   auto kern = t.threads == 64 ? k_coarse_apply_mma4<64> : k_coarse_apply_mma4<128>;
   WCMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // CTAs per SM as shared memory allows, at most 2: each holds 256 of the SM's 512 TMEM columns
-  const int per_sm = std::max(1, std::min(blocks_per_sm((const void*)kern, 192, smem), 2));
+  // TMEM: two accumulators of 2 N FP32 columns, each 64 columns wide when 2 N <= 64 (the
+  // allocation, a power of two, is then 128 of the SM's 512 columns) else 128.  CTAs per
+  // SM as shared memory allows and as many as the TMEM holds.
+  const int acc_cols = 2 * t.ntile <= 64 ? 64 : 128;
+  const int per_sm = std::max(1, std::min(blocks_per_sm((const void*)kern, 192, smem), 512 / (2 * acc_cols)));
   const long long items = (long long)g.V * ntiles;
   const int grid = (int)std::min<long long>(items, (long long)sm_count() * per_sm);
   kern<<<grid, 192, smem, st>>>(out, reinterpret_cast<const uint4*>(lmma), bp, g.nbr, g.V, nb, nrhs, t.ntile, ntiles,
-                                t.stages, err);
+                                t.stages, acc_cols, err);
   WCMG_LAUNCH_CHECK();
 }
 
