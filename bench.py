@@ -101,7 +101,7 @@ KCLASS = ["dslash", "coarse", "restrict", "prolong", "blas", "ortho", "coarsen",
 
 # Sources that define each kernel class (its own file and the shared headers): a
 # recorded ncu traffic figure stays valid while these files are unchanged.
-KERNEL_SOURCES = {"ortho": ["transfer.cu"], "restrict": ["transfer.cu"], "prolong": ["transfer.cu"],
+KERNEL_SOURCES = {"ortho": ["transfer.cu", "dfloat.cuh"], "restrict": ["transfer.cu"], "prolong": ["transfer.cu"],
                   "dslash": ["fine.cu"], "dslash64": ["fine.cu"], "coarse": ["coarse.cu"], "blas": ["blas.cu"],
                   "krylov": ["blas.cu"], "coarsen": ["coarse.cu", "fine.cu"], "ptc": ["ptc.cu"]}
 
@@ -1202,7 +1202,17 @@ def run_probe(args, local):
     from paper_1904_08678_gb300 import inputs
     ld = level_dims(cfg)
     out = {"probe": args.probe, "workload": cfg["workload"], "ortho": args.ortho}
-    if args.probe == "ortho":
+    if args.probe == "clover":
+        ctx = wcmg.Context(params(wcmg, cfg, "f32", profile=1 << KCLASS.index("clover"), nrhs=1))
+        U, _ = make_inputs(cfg, 1)
+        ctx.set_gauge(env.to_dev(U), stream)
+        k0 = ctx.kstats()["clover"]
+        ms = [timed_call(torch_, stream, env.flush, lambda: ctx.set_clover(cfg["csw"], stream), i)[1]
+              for i in range(3)]
+        k1 = ctx.kstats()["clover"]
+        out.update(ms_per_call=[round(t, 3) for t in ms],
+                   kernel_ms=round((k1["ms"] - k0["ms"]) / max(k1["launches"] - k0["launches"], 1), 3))
+    elif args.probe == "ortho":
         nv = cfg["nvec"][0]
         ctx = wcmg.Context(params(wcmg, cfg, "f32", profile=1 << KCLASS.index("ortho"), nrhs=1))
         V = int(np.prod(ld[0]))
@@ -1284,7 +1294,8 @@ def main(argv=None):
                     help="block orthonormalisation arithmetic of the FP32-inner runs: double-float on the FP32 "
                          "pipe (default; the same Q to 1e-14) or FP64; plain FP64 multigrid always uses FP64")
     ap.add_argument("--probe", default=None,
-                    help="kernel probe for ncu instead of the bench: 'ortho' (the fine-level block "
+                    help="kernel probe for ncu instead of the bench: 'clover' (the clover term of the "
+                         "workload's gauge field, 3 times), 'ortho' (the fine-level block "
                          "orthonormalisation of Nvec Gaussian fields, 3 times) or 'coarse:LEVEL:NRHS[:KIND:THREADS:"
                          "PARTS:STAGES:NTILE]' (5 coarse applies after one setup with the autotuned or the given "
                          "launch shape); prints one JSON line of CUDA-event times")
