@@ -563,6 +563,7 @@ def run_gpu(args, rank, world, local):
     hbm = peaks()[0]
 
     def extra_main(ctx, out, Ud, bd, xd, step):
+        out["near_null_quality"] = near_null_quality(env, ctx, cfg)
         refs = link_contexts(env, cfg)
         try:
             out["precision_per_level"] = precision_per_level(env, ctx, cfg, refs)
@@ -615,6 +616,7 @@ def run_gpu(args, rank, world, local):
             "clocks": clk.summary(), "wall_s_timed": main["wall_s_timed"], "cpu_baseline": cpu,
             "warmup_kernel_ms_per_step": main["warmup_kernel_ms_per_step"],
             "coarse_gmres_iterations": main["coarse_gmres_iterations"],
+            "near_null_quality": main.get("near_null_quality"),
             "sub_records": sub,
         }
         print(json.dumps(line), flush=True)
@@ -781,6 +783,39 @@ def precision_per_level(env, ctx, cfg, refs):
                             "prolong_f32": rel(p32, p64), "sites": Vc, "nbasis": nb}
     out["note"] = ("relative error ||y - y64|| / ||y64|| of one application on a Gaussian vector; y64 = the FP64 "
                    "apply of the same (FP32-built) coarse links and FP64 near-null vectors")
+    return out
+
+
+def near_null_quality(env, ctx, cfg):
+    """How near-null the setup's vectors are: ||D_l v_i|| / ||v_i|| for each near-null
+    vector of every level that has them (level 0 with the FP64 D, coarser levels with the
+    level's coarse operator in FP32 arithmetic), next to the same ratio for a Gaussian
+    vector.  Small ratios mean a good coarse space."""
+    torch, wcmg, stream = env.torch, env.wcmg, env.stream
+    from paper_1904_08678_gb300 import inputs
+    ld = level_dims(cfg)
+    out = {}
+    for l in range(len(cfg["blocks"])):
+        V = int(np.prod(ld[l]))
+        nc = 12 if l == 0 else 2 * cfg["nvec"][l - 1]
+        nv = cfg["nvec"][l]
+        vecs = torch.zeros((nv, V, nc), dtype=torch.complex128, device=env.dev)
+        ctx.get_nullvecs(l, vecs, stream)
+        y = torch.zeros((1, V, nc), dtype=torch.complex128, device=env.dev)
+
+        def ratio(v):
+            if l == 0:
+                ctx.apply_D(v, y, nrhs=1, prec=wcmg.F64, stream=stream)
+            else:
+                ctx.apply_coarse(l, v, y, nrhs=1, prec=wcmg.F32, stream=stream)
+            return float(torch.linalg.vector_norm(y) / torch.linalg.vector_norm(v))
+
+        r = [ratio(vecs[i:i + 1].contiguous()) for i in range(nv)]
+        g = ratio(env.to_dev(inputs.complex_gaussian(79, l, (1, V, nc))))
+        out[f"level{l}"] = {"mean": round(float(np.mean(r)), 4), "min": round(min(r), 4), "max": round(max(r), 4),
+                            "gaussian_vector": round(g, 4), "vectors": nv}
+        del vecs
+    out["note"] = "||D_l v|| / ||v|| of the near-null vectors after the setup (3 + 2 sweeps)"
     return out
 
 

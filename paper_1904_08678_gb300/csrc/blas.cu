@@ -110,7 +110,8 @@ template <typename R>
 __global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict__ partial,
                                                             const cplx<R>* __restrict__ basis, long long bstride,
                                                             int k, const cplx<R>* __restrict__ w, long long n,
-                                                            int kpad, const int* __restrict__ kdev, int kadd) {
+                                                            int kpad, const int* __restrict__ kdev, int kadd,
+                                                            int vec2) {
   __shared__ double2 scratch[(RED_T / 32) * MD_K];
   const int r = blockIdx.y, i0 = blockIdx.z * MD_K;
   if (kdev) k = *kdev + kadd;
@@ -119,12 +120,30 @@ __global__ void __launch_bounds__(RED_T) k_multidot_partial(double2* __restrict_
   cplx<R> acc[MD_K];
 #pragma unroll
   for (int q = 0; q < MD_K; ++q) acc[q] = czero<R>();
-  for (long long e = blockIdx.x * (long long)RED_T + threadIdx.x; e < n; e += (long long)gridDim.x * RED_T) {
-    const cplx<R> x = w[off + e];
+  if constexpr (sizeof(R) == 4) {
+    if (vec2) {  // two complex entries per 16-byte load (n, bstride even; 16-byte aligned fields)
+      const float4* w4 = reinterpret_cast<const float4*>(w + off);
+      const long long n2 = n >> 1;
+      for (long long e = blockIdx.x * (long long)RED_T + threadIdx.x; e < n2; e += (long long)gridDim.x * RED_T) {
+        const float4 x = w4[e];
 #pragma unroll
-    for (int q = 0; q < MD_K; ++q)
-      if (i0 + q < k) cjmac(acc[q], basis[(i0 + q) * bstride + off + e], x);
+        for (int q = 0; q < MD_K; ++q)
+          if (i0 + q < k) {
+            const float4 v = reinterpret_cast<const float4*>(basis + (i0 + q) * bstride + off)[e];
+            cjmac(acc[q], make_float2(v.x, v.y), make_float2(x.x, x.y));
+            cjmac(acc[q], make_float2(v.z, v.w), make_float2(x.z, x.w));
+          }
+      }
+      vec2 = -1;  // done
+    }
   }
+  if (vec2 >= 0)
+    for (long long e = blockIdx.x * (long long)RED_T + threadIdx.x; e < n; e += (long long)gridDim.x * RED_T) {
+      const cplx<R> x = w[off + e];
+#pragma unroll
+      for (int q = 0; q < MD_K; ++q)
+        if (i0 + q < k) cjmac(acc[q], basis[(i0 + q) * bstride + off + e], x);
+    }
   // warp sums in the working precision (one transposing butterfly for the 8 values),
   // then FP64 across the warps of the CTA and across CTAs
   static_assert(MD_K == 8, "transposing warp reduction of 8 values");
@@ -144,7 +163,10 @@ void launch_multidot(double2* out, const cplx<R>* basis, long long bstride, int 
                      long long n, int nrhs, double2* partial, cudaStream_t st, const int* kdev, int kadd) {
   const int nchunk = (k + MD_K - 1) / MD_K, kpad = nchunk * MD_K;
   const int nb = red_blocks(n, nrhs);  // independent of k: a captured graph sums in the same order
-  k_multidot_partial<R><<<dim3(nb, nrhs, nchunk), RED_T, 0, st>>>(partial, basis, bstride, k, w, n, kpad, kdev, kadd);
+  const int vec2 = sizeof(R) == 4 && n % 2 == 0 && bstride % 2 == 0 && reinterpret_cast<uintptr_t>(basis) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(w) % 16 == 0;
+  k_multidot_partial<R><<<dim3(nb, nrhs, nchunk), RED_T, 0, st>>>(partial, basis, bstride, k, w, n, kpad, kdev, kadd,
+                                                                  vec2);
   k_final<double2><<<dim3(nrhs, k), RED_T, 0, st>>>(out, partial, nb, (long long)kpad * nb, nb, ldo, kdev, kadd);
   ++launch_counter();
   WCMG_LAUNCH_CHECK();
