@@ -329,7 +329,8 @@ typedef struct wcmg_tile {
                            5 one-rhs kernel on the five-block storage, -1 none */
   int rhs_per_cta;      /* kind 1: 1, 4 or 8 rhs per CTA */
   int parts;            /* kinds 0, 1, 5: CTAs sharing one coarse site's rows (kind 1: 0 = automatic);
-                           kind 3: link rows per staged chunk */
+                           kind 3: link rows per staged chunk; kind 4: TMEM accumulators, 1 or
+                           2 (0 = 2) */
   int threads;          /* kinds 0, 3, 5: threads per CTA (kinds 0, 5: 64 .. 512, multiple of 32;
                            kind 3: 128, 256 or 512); kind 4: MMA M, 64 or 128 (>= nbasis) */
   int ntile;            /* kinds 2, 4: rhs per MMA N tile (kind 2: 16, 32, 48 or 64; kind 4: a

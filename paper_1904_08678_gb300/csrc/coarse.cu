@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
                                                               const uint4* __restrict__ bpre,
                                                               const int* __restrict__ nbr, int Vc, int nb, int nrhs,
                                                               int ntile, int ntiles, int stages,
-                                                              int acc_cols, int* __restrict__ err) {
+                                                              int acc_cols, int nacc, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[MMA4_MAX_STAGES], empty[MMA4_MAX_STAGES], tfull[2], tempty[2], fin;
   __shared__ uint32_t tmem_base;
@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
     abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(&tmem_base, 2 * acc_cols);
+  if (warp == 1) tmem_alloc(&tmem_base, nacc * acc_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -901,8 +901,8 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
       long long c = 0, i = 0;
       bool ok = true;
       for (long long it = blockIdx.x; it < items && ok; it += gridDim.x, ++i) {
-        const int tb = (int)(i & 1);
-        if (!mbar_wait_bounded(&tempty[tb], (uint32_t)(((i >> 1) & 1) ^ 1), limit)) { fail(); ok = false; break; }
+        const int tb = (int)(i % nacc);
+        if (!mbar_wait_bounded(&tempty[tb], (uint32_t)(((i / nacc) & 1) ^ 1), limit)) { fail(); ok = false; break; }
         tc_fence_after();
         const uint32_t dt = tmem + (uint32_t)(tb * acc_cols);
         for (int d = 0; d < 9; ++d, ++c) {
@@ -929,9 +929,9 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
     const int m = MM == 128 ? 32 * quad + lane : (lane < 16 ? 16 * quad + lane : nb);
     long long i = 0;
     for (long long it = blockIdx.x; it < items; it += gridDim.x, ++i) {
-      const int tb = (int)(i & 1);
+      const int tb = (int)(i % nacc);
       // one lane per warp polls the accumulator barrier, the others wait at the warp barrier
-      int good = lane != 0 || mbar_wait_bounded(&tfull[tb], (uint32_t)((i >> 1) & 1), limit) ? 1 : 0;
+      int good = lane != 0 || mbar_wait_bounded(&tfull[tb], (uint32_t)((i / nacc) & 1), limit) ? 1 : 0;
       good = __shfl_sync(0xffffffffu, good, 0);
       if (!good || *(volatile int*)&abort_flag) {
         if (!good) fail();
@@ -963,7 +963,7 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 2 * acc_cols);
+  if (warp == 1) tmem_dealloc(tmem, nacc * acc_cols);
 }
 
 template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
@@ -1264,12 +1264,14 @@ static void coarse_apply_mma4(float2* out, const float2* in, const bf16c* lmma, 
   // TMEM: two accumulators of 2 N FP32 columns, each 64 columns wide when 2 N <= 64 (the
   // allocation, a power of two, is then 128 of the SM's 512 columns) else 128.  CTAs per
   // SM as shared memory allows and as many as the TMEM holds.
-  const int acc_cols = 2 * t.ntile <= 64 ? 64 : 128;
-  const int per_sm = std::max(1, std::min(blocks_per_sm((const void*)kern, 192, smem), 512 / (2 * acc_cols)));
+  // t.parts = 1: one accumulator (the MMAs of the next item wait for the epilogue), half
+  // the TMEM, so more CTAs fit an SM
+  const int acc_cols = 2 * t.ntile <= 64 ? 64 : 128, nacc = t.parts == 1 ? 1 : 2;
+  const int per_sm = std::max(1, std::min(blocks_per_sm((const void*)kern, 192, smem), 512 / (nacc * acc_cols)));
   const long long items = (long long)g.V * ntiles;
   const int grid = (int)std::min<long long>(items, (long long)sm_count() * per_sm);
   kern<<<grid, 192, smem, st>>>(out, reinterpret_cast<const uint4*>(lmma), bp, g.nbr, g.V, nb, nrhs, t.ntile, ntiles,
-                                t.stages, acc_cols, err);
+                                t.stages, acc_cols, nacc, err);
   WCMG_LAUNCH_CHECK();
 }
 
@@ -1322,6 +1324,7 @@ bool coarse_tile_valid(const CoarseTile& t, int nb, int nrhs, int mode, int link
              (t.ntile == 16 || t.ntile == 32 || t.ntile == 48 || t.ntile == 64);
     case 4:
       return link_kind == 2 && mode == ST_FULL && nrhs >= 2 && nb % 8 == 0 && nb <= 64 &&
+             (t.parts == 0 || t.parts == 1 || t.parts == 2) &&
              (t.threads == 64 || t.threads == 128) && t.threads >= nb && t.ntile % 8 == 0 && t.ntile >= 8 &&
              t.ntile <= 64 && t.stages >= 2 && t.stages <= MMA4_MAX_STAGES &&
              coarse_mma4_smem(nb, t.ntile, t.threads, t.stages) <= 220 * 1024;

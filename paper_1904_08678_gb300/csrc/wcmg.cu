@@ -477,6 +477,10 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk, bool 
     for (int mm : {64, 128})
       for (int nt : nts)
         for (int stg : {3, 4, 6}) add(4, 0, 0, mm, nt, stg);
+    // one TMEM accumulator (parts 1): for the wide tiles, more CTAs per SM
+    for (int nt : nts)
+      if (nt > 32)
+        for (int stg : {2, 3}) add(4, 0, 1, 64, nt, stg);
   }
   for (int rr : {1, 4, 8})
     if (rr <= nrhs || rr == 4)

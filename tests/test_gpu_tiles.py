@@ -57,6 +57,9 @@ def candidate_tiles(nrhs, lk, nb):
             # ragged last one) to 64, shallow and deep pipelines
             t += [dict(kind=4, threads=mm, ntile=n, stages=st) for mm in (64, 128) for n in (8, 16, 40, 64)
                   for st in (2, 4, 6) if n <= max(8, (nrhs + 7) // 8 * 8) and mma4_fits(nb, n, mm, st)]
+            # one TMEM accumulator (the next item's MMAs wait for the epilogue)
+            t += [dict(kind=4, threads=64, ntile=n, stages=st, parts=1) for n in (8, 40) for st in (2, 3)
+                  if n <= max(8, (nrhs + 7) // 8 * 8) and mma4_fits(nb, n, 64, st)]
     return t
 
 
