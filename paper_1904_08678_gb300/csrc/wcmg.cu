@@ -477,10 +477,9 @@ static std::vector<CoarseTile> coarse_candidates(int nb, int nrhs, int lk, bool 
     for (int mm : {64, 128})
       for (int nt : nts)
         for (int stg : {3, 4, 6}) add(4, 0, 0, mm, nt, stg);
-    // one TMEM accumulator (parts 1): for the wide tiles, more CTAs per SM
-    for (int nt : nts)
-      if (nt > 32)
-        for (int stg : {2, 3}) add(4, 0, 1, 64, nt, stg);
+    // (one TMEM accumulator, parts 1, fits more CTAs per SM for the wide tiles but
+    // serialises each tile's MMAs behind the previous tile's epilogue: slower on the
+    // 48-rhs tiles measured, so it is no candidate; set_coarse_tile still takes it)
   }
   for (int rr : {1, 4, 8})
     if (rr <= nrhs || rr == 4)
