@@ -399,8 +399,7 @@ int wcmg_get_opcounts(wcmg_ctx* ctx, long long* out);
  * entries (4 MiB) that every device which loads the library keeps until the
  * process exits; nvec * V * 12 > WCMG_NOALLOC_MAX_ELEMS returns WCMG_ERR_ARG.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current: make the first call on each
- * device before any stream capture.  Every call uses the same array, which keeps
+ * (cudaGetSymbolAddress) with the device current.  Every call uses the same array, which keeps
  * the last call's contents: calls whose GPU work overlaps (several streams or
  * host threads) race and must be serialised by the caller.  No cudaMalloc,
  * cudaFree or allocating library routine is called.  Every call ends by copying
