@@ -25,15 +25,18 @@ def config1_ctx(lib, prec=0, **kw):
     return ctx, WilsonClover(U, DIMS, -0.1, 1.0)
 
 
-def test_mr_matches_oracle(lib):
+@pytest.mark.parametrize("steps", [1, 2, 4, 7])
+def test_mr_matches_oracle(lib, steps):
+    """One step (the iterate directly), two (no middle step), the configurations' four and
+    seven, for three rhs at once."""
     ctx, D = config1_ctx(lib, max_rhs=3)
     V = 256
     b = inputs.complex_gaussian(21, 0, (3, V, 12))
     x = dev(np.zeros_like(b))
-    ctx.krylov(0, 0, dev(b), x, nrhs=3, steps_or_restart=4)
+    ctx.krylov(0, 0, dev(b), x, nrhs=3, steps_or_restart=steps)
     got = host(x)
     for r, f in enumerate(fields(b, DIMS, 12)):
-        assert rel(got[r], mr(D, f, 4).reshape(V, 12)) < 1e-12
+        assert rel(got[r], mr(D, f, steps).reshape(V, 12)) < 1e-12
 
 
 @pytest.mark.parametrize("nrhs", [1, 3, 4])
