@@ -1247,6 +1247,29 @@ def run_probe(args, local):
         k1 = ctx.kstats()["clover"]
         out.update(ms_per_call=[round(t, 3) for t in ms],
                    kernel_ms=round((k1["ms"] - k0["ms"]) / max(k1["launches"] - k0["launches"], 1), 3))
+    elif args.probe.startswith("dslash"):
+        # the FP32 fine stencil alone: wcmg_apply_D with N rhs (its packing kernels are
+        # another class), 5 calls with L2 flushed before each
+        nr = int(args.probe.split(":")[1]) if ":" in args.probe else 1
+        ctx = wcmg.Context(params(wcmg, cfg, "f32", profile=1 << KCLASS.index("dslash"), nrhs=nr))
+        U, _ = make_inputs(cfg, 1)
+        ctx.set_gauge(env.to_dev(U), stream)
+        V = int(np.prod(ld[0]))
+        x = env.to_dev(inputs.complex_gaussian(33, 0, (nr, V, 12)))
+        y = torch_.zeros_like(x)
+        ctx.apply_D(x, y, nrhs=nr, prec=wcmg.F32, stream=stream)
+        k0 = ctx.kstats()["dslash"]
+        if args.ncu_region:
+            torch_.cuda.profiler.start()
+        ms = [timed_call(torch_, stream, env.flush,
+                         lambda: ctx.apply_D(x, y, nrhs=nr, prec=wcmg.F32, stream=stream), i)[1] for i in range(5)]
+        if args.ncu_region:
+            torch_.cuda.profiler.stop()
+        k1 = ctx.kstats()["dslash"]
+        kus = (k1["ms"] - k0["ms"]) / max(k1["launches"] - k0["launches"], 1) * 1e3
+        algo = V * (nr * 192 + 576)
+        out.update(nrhs=nr, ms_per_call=[round(t, 3) for t in ms], kernel_us=round(kus, 2), algorithmic_bytes=algo,
+                   frac_of_hbm=round(algo / (kus * 1e-6) / 1e9 / peaks()[0], 4))
     elif args.probe == "ortho":
         nv = cfg["nvec"][0]
         ctx = wcmg.Context(params(wcmg, cfg, "f32", profile=1 << KCLASS.index("ortho"), nrhs=1))
@@ -1331,7 +1354,8 @@ def main(argv=None):
     ap.add_argument("--probe", default=None,
                     help="kernel probe for ncu instead of the bench: 'clover' (the clover term of the "
                          "workload's gauge field, 3 times), 'ortho' (the fine-level block "
-                         "orthonormalisation of Nvec Gaussian fields, 3 times) or 'coarse:LEVEL:NRHS[:KIND:THREADS:"
+                         "orthonormalisation of Nvec Gaussian fields, 3 times), 'dslash:NRHS' (the FP32 fine stencil "
+                         "through wcmg_apply_D, 5 calls) or 'coarse:LEVEL:NRHS[:KIND:THREADS:"
                          "PARTS:STAGES:NTILE]' (5 coarse applies after one setup with the autotuned or the given "
                          "launch shape); prints one JSON line of CUDA-event times")
     ap.add_argument("--probe-fine", default=None,
