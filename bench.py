@@ -590,6 +590,9 @@ def run_gpu(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and name == DEFAULT_WORKLOAD:
         cpu = oracle_model(main["op_counts"], cfg)
+        one = oracle_model_one_core(main["op_counts"], name)
+        if one is not None:
+            cpu["one_core"] = one
 
     if rank == 0:
         line = {
@@ -1107,6 +1110,42 @@ def oracle_model(counts, cfg):
                 k: round(v, 1) for k, v in parts.items()}, "op_counts": counts, "host_cores_available": os.cpu_count()}
 
 
+ONE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                  "BLIS_NUM_THREADS": "1", "NUMEXPR_NUM_THREADS": "1", "VECLIB_MAXIMUM_THREADS": "1"}
+
+
+def oracle_model_one_core(counts, workload):
+    """The same operator model timed on one host core: a child process (started by exec,
+    never a fork of this CUDA process) whose BLAS / OpenMP thread counts are 1 in its
+    environment, pinned to one CPU where the host allows it."""
+    with tempfile.NamedTemporaryFile("w", suffix=".json", delete=False) as f:
+        json.dump({"counts": counts, "workload": workload}, f)
+        path = f.name
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-one-core", path]
+    try:
+        r = subprocess.run(cmd, env=dict(os.environ, **ONE_THREAD_ENV), capture_output=True, text=True, timeout=900)
+        out = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 and r.stdout.strip() else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        out = None
+    finally:
+        os.unlink(path)
+    return out
+
+
+def oracle_one_core_child(path):
+    with open(path) as f:
+        job = json.load(f)
+    if hasattr(os, "sched_setaffinity"):
+        try:
+            os.sched_setaffinity(0, {min(os.sched_getaffinity(0))})
+        except OSError:
+            pass
+    counts = {k: v for k, v in job["counts"].items()}
+    out = oracle_model(counts, dict(WORKLOADS[job["workload"]]))
+    print(json.dumps({"value": out["value"], "unit": "s", "cores": 1, "cores_measured": out["cores"],
+                      "seconds_per_call": out["seconds_per_call"]}), flush=True)
+
+
 def run_reference(args, rank, world):
     """The oracle arm: its modelled time-to-solution for the workload's step.  Each of the
     W + K steps times one oracle operator (round robin); value = the model from the
@@ -1325,6 +1364,7 @@ def main(argv=None):
     ap.add_argument("--links", default=None, choices=["f32", "bf16", "f16"],
                     help="coarse-link storage (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-one-core", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="headline workload only, no sub-records")
@@ -1365,6 +1405,9 @@ def main(argv=None):
                     help="bracket the timed steps of the headline workload (or a coarse probe's timed applies) "
                          "with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)
+    if args.oracle_one_core:  # the child of oracle_model_one_core (CPU only)
+        oracle_one_core_child(args.oracle_one_core)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank, world, local = dist_env()

@@ -47,3 +47,18 @@ def test_single_rank_identity():
     import bench
     assert bench.max_over_ranks(None, 4.5) == 4.5
     assert bench.sum_over_ranks(None, 4.5) == 4.5
+
+
+def test_oracle_model_one_core():
+    """cpu_baseline.one_core: the oracle's operator model timed in a child process with one
+    BLAS / OpenMP thread.  The child reports one core used, and its value is the model's
+    sum over the operators it timed (here a small count vector on the 16^3x32 workload)."""
+    import bench
+    counts = {"apply": [2, 3, 0, 0], "restrict": [1, 1, 0, 0], "prolong": [1, 1, 0, 0], "ortho": [1, 0, 0, 0],
+              "coarsen": [1, 0, 0, 0]}
+    one = bench.oracle_model_one_core(counts, "c2")
+    assert one is not None
+    assert one["cores"] == 1 and one["cores_measured"] == 1
+    total, _ = bench.model_time(one["seconds_per_call"], counts, dict(bench.WORKLOADS["c2"]))
+    assert one["value"] == pytest.approx(total, abs=0.5)
+    assert one["value"] > 0
