@@ -362,6 +362,15 @@ int wcmg_tune_coarse(wcmg_ctx* ctx, int level, int nrhs, int prec, int cold, voi
  * five-block copy of params.coarse_sigma3). */
 int wcmg_set_coarse_tile(wcmg_ctx* ctx, int level, int nrhs, int prec, const wcmg_tile* t);
 
+/* Self-test of the library's bounded device-side waits (every mbarrier wait of the
+ * bulk-copy and tensor-core kernels gives up after a fixed number of polls, sets the
+ * context's device-wait word and lets its CTA finish; the next call that checks the word
+ * returns WCMG_ERR_TIMEOUT and clears it).  Launches one kernel whose single thread waits,
+ * at most `polls` (0 .. 2^26) polls, on an mbarrier phase that nothing completes, then
+ * checks the word the same way.  Returns WCMG_ERR_TIMEOUT when the mechanism works (the
+ * context stays usable), WCMG_ERR_ARG for polls out of range. */
+int wcmg_check_bounded_wait(wcmg_ctx* ctx, long long polls, void* stream);
+
 /* Change params.profile of an existing context (no GPU work). */
 int wcmg_set_profile(wcmg_ctx* ctx, int mask);
 /* Per-kernel-class counters accumulated over the context's lifetime

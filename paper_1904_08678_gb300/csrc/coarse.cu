@@ -966,6 +966,24 @@ __global__ void __launch_bounds__(192, 1) k_coarse_apply_mma4(float2* __restrict
   if (warp == 1) tmem_dealloc(tmem, nacc * acc_cols);
 }
 
+// Self-test of the bounded waits: one thread waits, at most `polls` polls, on the first
+// phase of an mbarrier that nothing arrives on, so the wait gives up and the thread sets
+// *err = 3 the way every bounded wait of the library does.  Nothing else is in flight
+// (no copies, no TMEM), so the kernel ends normally and the context stays usable.
+__global__ void k_wait_selftest(int* __restrict__ err, long long polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, polls)) atomicExch(err, 3);
+}
+void launch_wait_selftest(int* err, long long polls, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err, polls);
+  WCMG_LAUNCH_CHECK();
+}
+
 template <typename L> struct VecOf { static constexpr int v = 16 / sizeof(L); };
 
 // ---------------- even-odd coarsest solve: self-block inverses ----------------

@@ -19,6 +19,9 @@ struct LevelGeom {
 // `hopdir`, zero on the others (the even-odd Schur complement of the coarsest solve).
 enum StencilMode { ST_FULL = 0, ST_BLOCK_INTERIOR = 1, ST_FACE_HOP = 2, ST_PARITY = 3 };
 
+// one bounded mbarrier wait that nothing completes: sets *err = 3 (coarse.cu)
+void launch_wait_selftest(int* err, long long polls, cudaStream_t st);
+
 // ---- fine level (fine.cu) ----
 template <typename R>
 void launch_pack_fine(cplx<R>* out, const double2* ext, const int* perm, int V, int nrhs, cudaStream_t st);

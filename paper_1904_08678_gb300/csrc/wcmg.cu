@@ -2912,6 +2912,17 @@ int wcmg_set_coarse_tile(wcmg_ctx* c, int level, int nrhs, int prec, const wcmg_
   API_END(c)
 }
 
+int wcmg_check_bounded_wait(wcmg_ctx* c, long long polls, void* stream) {
+  API_BEGIN(c)
+  c->st = (cudaStream_t)stream;
+  if (polls < 0 || polls > (1LL << 26)) throw Error(WCMG_ERR_ARG, "polls must be 0 .. 2^26");
+  c->tma_err.ensure(1);
+  launch_wait_selftest(c->tma_err.p, polls, c->st);
+  check_device_waits(c);
+  throw Error(WCMG_ERR_STATE, "the self-test wait did not give up");
+  API_END(c)
+}
+
 int wcmg_set_profile(wcmg_ctx* c, int mask) {
   API_BEGIN(c)
   c->prof.flush();

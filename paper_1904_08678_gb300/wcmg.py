@@ -159,6 +159,7 @@ _SIGS = {
     "wcmg_solve_batch": ([ctypes.POINTER(_PCTX), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i), _i,
                           _vp, ctypes.POINTER(wcmg_stats)], _i),
     "wcmg_set_profile": ([_PCTX, _i], _i),
+    "wcmg_check_bounded_wait": ([_PCTX, ctypes.c_longlong, _vp], _i),
     "wcmg_get_coarse_tile": ([_PCTX, _i, _i, _i, ctypes.POINTER(wcmg_tile)], _i),
     "wcmg_tune_coarse": ([_PCTX, _i, _i, _i, _i, _vp, ctypes.POINTER(wcmg_tile)], _i),
     "wcmg_set_coarse_tile": ([_PCTX, _i, _i, _i, ctypes.POINTER(wcmg_tile)], _i),
@@ -372,6 +373,10 @@ class Context:
 
     def set_profile(self, mask):
         return self._check(wcmg_set_profile(self.h, mask))
+
+    def check_bounded_wait(self, polls=1000, stream=None):
+        """Return code of wcmg_check_bounded_wait (ERR_TIMEOUT when the bounded waits work)."""
+        return self._check(wcmg_check_bounded_wait(self.h, int(polls), _stream(stream)), allow=(ERR_TIMEOUT,))
 
     def get_coarse_tile(self, level, nrhs=1, prec=F32):
         t = wcmg_tile()

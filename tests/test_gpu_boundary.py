@@ -185,3 +185,38 @@ def test_network_checkpoint_round_trip_is_bitwise(lib):
         with pytest.raises(lib.WcmgError) as e:
             b.load_net(os.path.join(d, "bad.bin"))
         assert e.value.code == lib.ERR_ARG
+
+
+@pytest.mark.parametrize("polls", [0, 1000])
+def test_bounded_device_wait_gives_up_and_the_context_stays_usable(lib, polls):
+    """Failure detection without a fault: a device-side mbarrier wait that nothing
+    completes gives up after its poll limit, sets the context's device-wait word, and the
+    call returns WCMG_ERR_TIMEOUT.  The word is cleared: a second self-test times out
+    again, and the operators that follow still match the oracle."""
+    from oracle.aggregation import Aggregation
+    from oracle.coarse import coarsen
+    from oracle.lattice import coarse_dims
+    ctx = _ctx(lib)
+    U = inputs.random_gauge(DIMS, 0.35, 2401)
+    ctx.set_gauge(dev(U))
+    assert ctx.check_bounded_wait(polls) == lib.ERR_TIMEOUT
+    assert ctx.check_bounded_wait(polls) == lib.ERR_TIMEOUT
+    with pytest.raises(lib.WcmgError) as e:
+        ctx.check_bounded_wait(-1)
+    assert e.value.code == lib.ERR_ARG
+    V = int(np.prod(DIMS))
+    D = WilsonClover(U, DIMS, -0.17, 1.13)
+    psi = inputs.complex_gaussian(2402, 0, (1, V, 4, 3))
+    out = dev(np.zeros_like(psi))
+    ctx.apply_D(dev(psi), out)
+    assert rel(host(out)[0], D(fields(psi, DIMS, 12)[0]).reshape(V, 4, 3)) < 1e-12
+    raw = inputs.complex_gaussian(2403, 0, (NVEC, V, 12))
+    ctx.set_nullvecs(0, dev(raw))
+    ctx.coarsen(0)
+    cd = coarse_dims(DIMS, BLOCK)
+    Vc, nb = int(np.prod(cd)), 2 * NVEC
+    op = coarsen(D, Aggregation(DIMS, BLOCK, fields(raw, DIMS, 12)))
+    phi = inputs.complex_gaussian(2404, 0, (1, Vc, nb))
+    y = dev(np.zeros_like(phi))
+    ctx.apply_coarse(1, dev(phi), y, nrhs=1, prec=lib.F64)
+    assert rel(host(y)[0], op(fields(phi, cd, nb)[0]).reshape(Vc, nb)) < 1e-12
