@@ -88,9 +88,11 @@ void launch_prolong(cplx<R>* out, const cplx<R>* coarse, const cplx<R>* vecs, in
 // FP64 block orthonormalisation in place; err receives 1 on a rank-deficient panel.
 void launch_block_ortho(double2* vecs, int Vf, int nc, int bvol, int nvec, bool fine, int* err, cudaStream_t st);
 // The same in double-float arithmetic on the FP32 pipe (48-bit significands, FP64
-// input and output); qdf: scratch of as many float4 as vecs has complex entries.
+// output in vecs); qdf: scratch of as many float4 as vecs has complex entries.  The
+// input is vecs itself, or the FP32 field in32 when given; out32 (nullable) receives
+// the FP32 rounding of the result as well.
 void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
-                           cudaStream_t st);
+                           cudaStream_t st, const float2* in32 = nullptr, float2* out32 = nullptr);
 // cols[b] = Pi_s v_i with (s, i) = divmod(b0 + b, nvec), for b < ncols.
 template <typename R>
 void launch_make_columns(cplx<R>* cols, const cplx<R>* vecs, int Vf, int nc, int nvec, int b0, int ncols, bool fine,

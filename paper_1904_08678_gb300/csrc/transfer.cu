@@ -518,10 +518,33 @@ __global__ void __launch_bounds__(256, 2) k_block_ortho(double2* __restrict__ ve
 // costs 12 FP32 operations.
 
 
+// Input column entry in double-float: from the FP64 field, or, when in32 is given,
+// from an FP32 field (exact: the FP32 value with a zero low part, the same as splitting
+// that value widened to FP64).
+__device__ __forceinline__ dfc ortho_df_input(const double2* vecs, const float2* in32, long long i) {
+  if (in32) {
+    const float2 v = in32[i];
+    return {{v.x, 0.f}, {v.y, 0.f}};
+  }
+  const double2 v = vecs[i];
+  return {df_split(v.x), df_split(v.y)};
+}
+// Output entry q_k: FP64 (vecs), double-float (qdf, read back by the later columns), and,
+// when out32 is given, its FP32 rounding (the FP64 value converted, as a separate
+// conversion pass would)
+__device__ __forceinline__ void ortho_df_output(double2* vecs, float4* qdf, float2* out32, long long i, dfr re,
+                                                dfr im) {
+  const double2 v = make_double2(df_to_fast(re), df_to_fast(im));
+  vecs[i] = v;
+  qdf[i] = make_float4(re.h, re.l, im.h, im.l);
+  if (out32) out32[i] = make_float2((float)v.x, (float)v.y);
+}
+
 template <int MAXE, int NT, int MINB, int GS>
 __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df(double2* __restrict__ vecs, float4* __restrict__ qdf,
                                                              int Vf, int nc, int bvol, int nvec, bool fine,
-                                                             int* __restrict__ err) {
+                                                             int* __restrict__ err, const float2* __restrict__ in32,
+                                                             float2* __restrict__ out32) {
   constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
   __shared__ dfc scratch[NT / 32][MV];
   __shared__ dfc red[MV];
@@ -566,8 +589,7 @@ __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df(double2* __restrict
 #pragma unroll
     for (int q = 0; q < MAXE; ++q) {
       if (addr[q] >= 0) {
-        const double2 v = vecs[k * fstride + addr[q]];
-        a[q] = {df_split(v.x), df_split(v.y)};
+        a[q] = ortho_df_input(vecs, in32, k * fstride + addr[q]);
       } else {
         a[q] = zero;
       }
@@ -618,8 +640,7 @@ __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df(double2* __restrict
     for (int q = 0; q < MAXE; ++q)
       if (addr[q] >= 0) {
         const dfr re = df_mul(a[q].re, inv), im = df_mul(a[q].im, inv);
-        vecs[k * fstride + addr[q]] = make_double2(df_to_fast(re), df_to_fast(im));
-        qdf[k * fstride + addr[q]] = make_float4(re.h, re.l, im.h, im.l);
+        ortho_df_output(vecs, qdf, out32, k * fstride + addr[q], re, im);
       }
     __syncthreads();
   }
@@ -637,7 +658,8 @@ __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df(double2* __restrict
 template <int MAXE, int NT, int MINB, int GS>
 __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df2(double2* __restrict__ vecs, float4* __restrict__ qdf,
                                                               int Vf, int nc, int bvol, int nvec, bool fine,
-                                                              int* __restrict__ err) {
+                                                              int* __restrict__ err, const float2* __restrict__ in32,
+                                                              float2* __restrict__ out32) {
   constexpr int MV = 33;  // nvec <= 32, slot 32: squared norm
   __shared__ dfc scratch[2][NT / 32][MV];
   __shared__ dfc red[2][MV];
@@ -729,8 +751,7 @@ __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df2(double2* __restric
 #pragma unroll
     for (int q = 0; q < MAXE; ++q) {
       if (addr[q] >= 0) {
-        const double2 v = vecs[k * fstride + addr[q]];
-        a[q] = {df_split(v.x), df_split(v.y)};
+        a[q] = ortho_df_input(vecs, in32, k * fstride + addr[q]);
       } else {
         a[q] = zero;
       }
@@ -747,10 +768,7 @@ __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df2(double2* __restric
     for (int q = 0; q < MAXE; ++q) {
       const dfr re = df_mul(a[q].re, inv), im = df_mul(a[q].im, inv);
       a[q] = {re, im};
-      if (addr[q] >= 0) {
-        vecs[k * fstride + addr[q]] = make_double2(df_to_fast(re), df_to_fast(im));
-        qdf[k * fstride + addr[q]] = make_float4(re.h, re.l, im.h, im.l);
-      }
+      if (addr[q] >= 0) ortho_df_output(vecs, qdf, out32, k * fstride + addr[q], re, im);
     }
   };
   dfc none[MAXE];
@@ -827,7 +845,7 @@ __global__ void __launch_bounds__(NT, MINB) k_block_ortho_df2(double2* __restric
 
 
 void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol, int nvec, bool fine, int* err,
-                           cudaStream_t st) {
+                           cudaStream_t st, const float2* in32, float2* out32) {
   const int nelem = bvol * (nc / 2);
   if (nvec > 32) throw Error(-1, "block orthonormalisation supports nvec <= 32");
   if (nelem > 256 * 8) throw Error(-1, "aggregate too large for block orthonormalisation");
@@ -840,11 +858,11 @@ void launch_block_ortho_df(double2* vecs, float4* qdf, int Vf, int nc, int bvol,
   // 61 ms.  Columns in pairs, 512 x 3, 2 CTAs (64 registers), groups of 2: 47 ms (16^3x32:
   // 3.5 against 3.8 ms).  The kernels wait on their re-reads of earlier Q columns.
   if (nelem <= 256 * 2)
-    k_block_ortho_df<2, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+    k_block_ortho_df<2, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err, in32, out32);
   else if (nelem <= 512 * 3)
-    k_block_ortho_df2<3, 512, 2, 2><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+    k_block_ortho_df2<3, 512, 2, 2><<<grid, 512, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err, in32, out32);
   else
-    k_block_ortho_df<8, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err);
+    k_block_ortho_df<8, 256, 3, 8><<<grid, 256, 0, st>>>(vecs, qdf, Vf, nc, bvol, nvec, fine, err, in32, out32);
   WCMG_LAUNCH_CHECK();
 }
 

@@ -1381,7 +1381,7 @@ static void coarsen(wcmg_ctx* c, int l) {
 
 // Block orthonormalisation of L.v64 in place (Sec. 2.2: Q factor per aggregate and
 // chirality), in FP64 or, with params.ortho_df, in double-float arithmetic.
-static void ortho_level(wcmg_ctx* c, int l) {
+static void ortho_level(wcmg_ctx* c, int l, const float2* in32 = nullptr, float2* out32 = nullptr) {
   Level& L = c->L[l];
   const long long n = (long long)L.nvec * L.n();
   WCMG_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->st));
@@ -1391,7 +1391,8 @@ static void ortho_level(wcmg_ctx* c, int l) {
   if (c->p.ortho_df) {
     float4* qdf = reinterpret_cast<float4*>(ws<double>(L, "ortho_qdf", L.nvec));
     KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0, 8.0 * n * (L.nvec - 1),
-          launch_block_ortho_df(L.v64.p, qdf, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
+          launch_block_ortho_df(L.v64.p, qdf, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st, in32,
+                                out32));
   } else {
     KPROF(c, WCMG_K_ORTHO, 2.0 * n * 16.0, 8.0 * n * (L.nvec - 1),
           launch_block_ortho(L.v64.p, L.g.V, L.nc, L.g.bvol, L.nvec, L.fine, c->errflag.p, c->st));
@@ -1406,6 +1407,17 @@ static void build_P(wcmg_ctx* c, int l) {
   Level& L = c->L[l];
   const long long n = (long long)L.nvec * L.n();
   L.v64.ensure(n);
+  if constexpr (sizeof(R) == 4) {
+    if (c->p.ortho_df) {
+      // the double-float kernel reads the FP32 vectors and writes the FP32 copy of P as
+      // well: no conversion passes (the same bits as converting before and after)
+      L.v32.ensure(n);
+      ortho_level(c, l, Prec<R>::raw(L).p, L.v32.p);
+      L.v32_valid = true;
+      L.have_P = true;
+      return;
+    }
+  }
   launch_convert<R, double>(L.v64.p, Prec<R>::raw(L).p, n, c->st);
   ortho_level(c, l);
   L.v32_valid = false;

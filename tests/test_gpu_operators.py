@@ -95,6 +95,35 @@ def test_block_orthonormalisation_matches_oracle(lib, dims, block, nvec, ortho_d
     assert rel(host(got), ref.reshape(nvec, V, 12)) < 1e-12
 
 
+@pytest.mark.parametrize("dims,block,nvec", [CASES[0], CASES[1], ((8, 8, 8, 8), (4, 4, 4, 4), 24)],
+                         ids=["one_column", "pairs_small", "pairs_4x4x4x4"])
+def test_fp32_setup_orthonormalises_fp32_vectors_in_double_float(lib, dims, block, nvec):
+    """FP32 inner levels with the double-float orthonormalisation: the setup's kernel reads
+    the FP32 near-null vectors and writes P in FP64 and its FP32 copy in one pass.  With no
+    setup sweeps the vectors are the given ones rounded to FP32, so P must be the oracle's
+    block orthonormalisation of those rounded vectors to 1e-12, and the FP32 restriction,
+    which reads the FP32 copy of P, the oracle's restriction to FP32 accuracy."""
+    V = int(np.prod(dims))
+    cd = coarse_dims(dims, block)
+    Vc = int(np.prod(cd))
+    iv = inputs.complex_gaussian(13, 3, (nvec, V, 12))
+    iv32 = iv.astype(np.complex64).astype(np.complex128)
+    ctx = make(lib, dims, block, nvec, prec=lib.F32, ortho_df=1, setup_init_sweeps=0, setup_refine_sweeps=0)
+    ctx.set_gauge(dev(inputs.random_gauge(dims, 0.35, 2005)))
+    ctx.setup(dev(iv))
+    got = dev(np.zeros_like(iv))
+    ctx.get_nullvecs(0, got)
+    ref = block_orthonormalise(fields(iv32, dims, 12), block)
+    assert rel(host(got), ref.reshape(nvec, V, 12)) < 1e-12
+    agg = Aggregation(dims, block, fields(iv32, dims, 12))
+    psi = inputs.complex_gaussian(13, 4, (3, V, 12))
+    out = dev(np.zeros((3, Vc, 2 * nvec), dtype=complex))
+    ctx.restrict(0, dev(psi), out, nrhs=3, prec=lib.F32)
+    o = host(out)
+    for r, f in enumerate(fields(psi, dims, 12)):
+        assert rel(o[r], agg.restrict(f).reshape(Vc, -1)) < 1e-5
+
+
 @pytest.mark.parametrize("dims,block,nvec", CASES)
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
 def test_restrict_prolong_match_oracle(lib, dims, block, nvec, prec, tol):
