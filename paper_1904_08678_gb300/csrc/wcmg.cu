@@ -140,8 +140,8 @@ struct Level {
   DevBuf<double2> v64;
   DevBuf<float2> v32;
   bool have_P = false, v32_valid = false;
-  DevBuf<double2> raw64;
-  DevBuf<float2> raw32;
+  DevBuf<double2> raw64, raw64b;  // raw near-null vectors; b: the next sweep's output
+  DevBuf<float2> raw32, raw32b;
   // coarse operator of this level (level >= 1)
   bool have_op = false;
   bool op64 = false;  // FP64 links present (else FP32)
@@ -369,6 +369,7 @@ template <> struct Prec<double> {
   static double2* clover_inv(wcmg_ctx* c) { return c->cinv64.p; }
   static double2* vecs(wcmg_ctx*, Level& L) { return L.v64.p; }
   static DevBuf<double2>& raw(Level& L) { return L.raw64; }
+  static DevBuf<double2>& raw_next(Level& L) { return L.raw64b; }
 };
 template <> struct Prec<float> {
   static float2* gauge(wcmg_ctx* c) { return c->gauge32.p; }
@@ -383,6 +384,7 @@ template <> struct Prec<float> {
     return L.v32.p;
   }
   static DevBuf<float2>& raw(Level& L) { return L.raw32; }
+  static DevBuf<float2>& raw_next(Level& L) { return L.raw32b; }
 };
 
 static double sz(int prec) { return prec == WCMG_F64 ? 16.0 : prec == WCMG_F32 ? 8.0 : 4.0; }
@@ -1424,15 +1426,21 @@ static void build_P(wcmg_ctx* c, int l) {
   L.have_P = true;
 }
 
+// One setup sweep: the smoother applied to the level's raw near-null vectors, whose
+// output becomes the new raw vectors.  They are not normalised: the next sweep's
+// smoother, the MG cycle of a refinement sweep (coarse solves to a relative tolerance)
+// and the block orthonormalisation all map a positively scaled vector to the same
+// result scaled alike or (P) unchanged, so a norm and a scaling pass over the Nvec
+// fields per sweep would change nothing but rounding.  The buffers are swapped.
 template <typename R>
 static void smooth_sweep(wcmg_ctx* c, int l) {
   Level& L = c->L[l];
   const int nv = L.nvec;
-  cplx<R>* raw = Prec<R>::raw(L).p;
-  cplx<R>* x = ws<R>(L, "sw_x", nv);
-  smooth<R>(c, l, x, raw, nv);
-  norm2_op<R>(c, L.sc.slot(7), x, L.n(), nv);
-  launch_scale_dev<R>(raw, x, L.sc.slot(7), 1, L.n(), nv, c->st);
+  auto& raw = Prec<R>::raw(L);
+  auto& next = Prec<R>::raw_next(L);
+  next.ensure((size_t)nv * L.n());
+  smooth<R>(c, l, next.p, raw.p, nv);
+  std::swap(raw, next);
 }
 
 template <typename R>
@@ -1456,11 +1464,11 @@ static void setup_all(wcmg_ctx* c, const double2* init, wcmg_stats* st) {
   for (int s = 0; s < c->p.setup_refine_sweeps; ++s) {
     Level& L = c->L[0];
     const int nv = L.nvec;
-    cplx<R>* raw = Prec<R>::raw(L).p;
-    cplx<R>* e = ws<R>(L, "ref_e", nv);
-    cycle<R>(c, 0, e, raw, nv);
-    norm2_op<R>(c, L.sc.slot(7), e, L.n(), nv);
-    launch_scale_dev<R>(raw, e, L.sc.slot(7), 1, L.n(), nv, c->st);
+    auto& raw = Prec<R>::raw(L);
+    auto& next = Prec<R>::raw_next(L);
+    next.ensure((size_t)nv * L.n());
+    cycle<R>(c, 0, next.p, raw.p, nv);  // not normalised either (see smooth_sweep)
+    std::swap(raw, next);
     build_P<R>(c, 0);
     coarsen<R>(c, 0);
     for (int l = 1; l + 1 < nl; ++l) {
