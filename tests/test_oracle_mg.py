@@ -255,3 +255,28 @@ def test_even_odd_coarsest_level_solve_reaches_the_dense_solution():
         its[eo] = info.iterations
         assert rel(x, x_ref) < 1e-8
     assert its[True] <= its[False] + 1
+
+
+def test_setup_steps_are_invariant_under_positive_scaling():
+    """The set-up normalises each vector after every sweep (inverse iteration), but every
+    step that follows it is invariant under a positive scale c of a vector: the smoother
+    (MR, and GMRES with a fixed number of steps) and the MG cycle, whose coarsest GMRES stops
+    at a tolerance relative to its right-hand side, map c v to c times the result, and the
+    block orthonormalisation (positive-diagonal QR per aggregate) of positively scaled
+    columns is unchanged.  So an implementation may skip the normalisation: P and D_c stay
+    the same up to rounding.  The scale factors span several decades."""
+    from oracle.aggregation import block_orthonormalise
+    from oracle.solvers import mr
+    dims, D, b = config1()
+    iv = [[to_grid(v, dims) for v in inputs.setup_vectors(dims, 12, 8, 0, 1001)]]
+    for smoother in ("mr", "gmres"):
+        mg = Multigrid(D, MGParams(blocks=[(2, 2, 2, 2)], nvecs=[8], smoother=smoother), iv)
+        for c in (1e-3, 7.3, 4.1e4):
+            assert rel(mg.smooth(0, c * b), c * mg.smooth(0, b)) < 1e-13
+            assert rel(mg.cycle(0, c * b), c * mg.cycle(0, b)) < 1e-12
+    vecs = mg.levels[0].vecs
+    scales = [10.0 ** (k - 3) * (1.0 + 0.1 * k) for k in range(len(vecs))]
+    q1 = block_orthonormalise(vecs, (2, 2, 2, 2))
+    q2 = block_orthonormalise([s * v for s, v in zip(scales, vecs)], (2, 2, 2, 2))
+    assert rel(q2, q1) < 1e-13
+    assert rel(mr(D, 3.0 * b, 4), 3.0 * mr(D, b, 4)) < 1e-14
